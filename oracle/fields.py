@@ -1,0 +1,94 @@
+"""Modal incident data and far fields.
+
+* Incident plane wave (eq. pw): E = e exp(i k0 d.x), H = (k0/(omega mu0)) d x e
+  exp(i k0 d.x), e the unit polarisation (the printed (d x p) x d is not a
+  unit vector unless p is orthogonal to d; it is normalised).
+* Modal data: the tangential traces n x E, n x H at each node ring, split into
+  (t, theta) components with n x v = v_theta t - v_t e_theta, and their
+  Fourier coefficients f_m = (1/2pi) int f(theta) e^{-i m theta} dtheta by the
+  trapezoid rule in theta.  Rows are scaled as in eq. mullerrep (i omega eps0
+  for the E rows, i omega mu0 for the H rows) or eq. dualmullrep.
+* Far field: letting |x| -> oo in eq. exteriorfield,
+  E_oo(xh) = (1/4pi) [ -(k0^2/(i omega eps0)) (Jh - (xh.Jh) xh) + i k0 xh x Mh ],
+  Jh = int_Gamma exp(-i k0 xh.y) J(y) da(y); the last term of the printed
+  eq. farfieldform integrates J where eq. exteriorfield has M.  The surface
+  integral uses the nodes' ds-weights along the curve and the trapezoid rule
+  in theta.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .system import node_geometry, wavenumbers, coefficients
+
+
+def _frame(theta):
+    c, s = np.cos(theta), np.sin(theta)
+    er = np.stack([c, s, np.zeros_like(c)], -1)
+    et = np.stack([-s, c, np.zeros_like(c)], -1)
+    return er, et
+
+
+def modal_rhs(curve, media, M, waves, formulation=0, n_theta=None):
+    """b[q, 4N, nrhs] for modes q = m + M and the given plane waves."""
+    geo = node_geometry(curve)
+    k0, _ = wavenumbers(media)
+    co = coefficients(media, formulation)
+    if n_theta is None:
+        n_theta = 2 * M + 2 * int(np.ceil(abs(k0) * np.max(geo.r))) + 64
+    th = 2 * np.pi * np.arange(n_theta) / n_theta
+    er, et = _frame(th)
+    ez = np.array([0.0, 0.0, 1.0])
+    N = curve.N
+    ms = np.arange(-M, M + 1)
+    E_ph = np.exp(-1j * np.outer(th, ms)) / n_theta      # [theta, modes]
+    b = np.zeros((2 * M + 1, 4 * N, len(waves)), dtype=complex)
+    for w_i, wv in enumerate(waves):
+        hvec = (k0 / (media.omega * complex(media.mu0))) * np.cross(wv.d, wv.e)
+        for i in range(N):
+            x = geo.r[i] * er + geo.z[i] * ez            # [theta, 3]
+            ph = np.exp(1j * k0 * (x @ wv.d))
+            for fvec, rows, sc in ((wv.e, (0, 1), co["sE"]), (hvec, (2, 3), co["sH"])):
+                v = ph[:, None] * fvec[None, :]
+                vr = (v * er).sum(1); vth = (v * et).sum(1); vz = v[:, 2]
+                vt = geo.rp[i] * vr + geo.zp[i] * vz
+                b[:, 4 * i + rows[0], w_i] = sc * (vth @ E_ph)
+                b[:, 4 * i + rows[1], w_i] = sc * (-vt @ E_ph)
+    return b
+
+
+def far_field(curve, media, M, x, directions, n_theta=None):
+    """E_oo at unit directions [nd, 3] for modal currents x[q, 4N, nrhs];
+    returns [nrhs, nd, 3]."""
+    geo = node_geometry(curve)
+    k0, _ = wavenumbers(media)
+    if n_theta is None:
+        n_theta = 2 * M + 2 * int(np.ceil(abs(k0) * np.max(geo.r))) + 64
+    th = 2 * np.pi * np.arange(n_theta) / n_theta
+    er, et = _frame(th)
+    ez = np.array([0.0, 0.0, 1.0])
+    ms = np.arange(-M, M + 1)
+    E_ph = np.exp(1j * np.outer(th, ms))                 # [theta, modes]
+    N = curve.N
+    nrhs = x.shape[2]
+    dirs = np.asarray(directions, float)
+    out = np.zeros((nrhs, len(dirs), 3), dtype=complex)
+    for i in range(N):
+        y = geo.r[i] * er + geo.z[i] * ez                 # [theta, 3]
+        t = geo.rp[i] * er + geo.zp[i] * ez
+        da = geo.w[i] * geo.r[i] * (2 * np.pi / n_theta)
+        ph = np.exp(-1j * k0 * (y @ dirs.T)) * da         # [theta, nd]
+        for comp in range(nrhs):
+            J1 = E_ph @ x[:, 4 * i + 0, comp]; J2 = E_ph @ x[:, 4 * i + 1, comp]
+            M1 = E_ph @ x[:, 4 * i + 2, comp]; M2 = E_ph @ x[:, 4 * i + 3, comp]
+            Jv = J1[:, None] * t + J2[:, None] * et       # [theta, 3]
+            Mv = M1[:, None] * t + M2[:, None] * et
+            Jh = ph.T @ Jv; Mh = ph.T @ Mv                 # [nd, 3]
+            out[comp] += _combine(Jh, Mh, dirs, k0, media)
+    return out
+
+
+def _combine(Jh, Mh, dirs, k0, media):
+    xJ = (dirs * Jh).sum(1, keepdims=True)
+    pre = -(k0 ** 2) / (1j * media.omega * complex(media.eps0))
+    return (pre * (Jh - xJ * dirs) + 1j * k0 * np.cross(dirs, Mh)) / (4 * np.pi)

@@ -1,0 +1,14 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This package holds only input generation: generating curves sampled at the
+16 panel Gauss-Legendre points, material parameters and plane-wave
+directions.  It contains none of the solver's arithmetic (no modal Green's
+functions, no quadrature corrections, no assembly, no factorisation), so the
+oracle and the CUDA path can both consume its output without sharing code.
+"""
+from .curves import Curve, sphere, cylinder, random_body, torus, panel_nodes
+from .configs import Media, PlaneWave, Config, config_sphere, config_cylinder, config_random, plane_wave, paper_default_wave
+
+__all__ = ["Curve", "sphere", "cylinder", "random_body", "torus", "panel_nodes",
+           "Media", "PlaneWave", "Config", "config_sphere", "config_cylinder",
+           "config_random", "plane_wave", "paper_default_wave"]
