@@ -74,15 +74,18 @@ def _series_diff(k0, k1, rho, order, nterms=28):
     return out / FOUR_PI
 
 
-def integrands(rt, zt, rs, zs, k0, k1, phi):
+def integrands(rt, zt, dr, dz, k0, k1, phi):
     """The nine integrands at azimuths phi; rows F0..F8 (see module doc).
 
-    rt, zt, rs, zs may be arrays broadcasting against phi."""
+    The pair is given by the target (rt, zt) and the displacement
+    (dr, dz) = (r_t - r_s, z_t - z_s), so that near pairs keep the relative
+    accuracy of their separation; arrays broadcast against phi."""
+    rs = rt - dr
     s2 = np.sin(0.5 * phi) ** 2
-    u = (rt - rs) ** 2 + (zt - zs) ** 2 + 4.0 * rt * rs * s2
+    u = dr ** 2 + dz ** 2 + 4.0 * rt * rs * s2
     rho = np.sqrt(u)
-    rd = (rt - rs) + 2.0 * rs * s2
-    zd = (zt - zs) + 0.0 * rho
+    rd = dr + 2.0 * rs * s2
+    zd = dz + 0.0 * rho
     out = np.empty((9,) + rho.shape, dtype=complex)
     d1, d2 = {}, {}
     for idx, k in ((0, k0), (1, k1)):
@@ -117,16 +120,23 @@ def _segments_J(J: int, M: int):
     return np.array(pts)
 
 
-def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64):
+def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64, disp=None):
     """Spectra F[pair, f, m] (f = 0..8, m = 0..M+1) for arrays of pairs.
 
+    ``disp = (dr, dz)`` optionally gives the displacements r_t - r_s, z_t - z_s
+    directly (used for support points next to the target, where they are
+    known more accurately than the difference of absolute coordinates).
     Pairs sharing the same number of graded levels are integrated together
     on the same composite rule."""
     rt, zt, rs, zs = (np.atleast_1d(np.asarray(a, float)) for a in (rt, zt, rs, zs))
     rt, zt, rs, zs = np.broadcast_arrays(rt, zt, rs, zs)
+    if disp is None:
+        dr, dz = rt - rs, zt - zs
+    else:
+        dr, dz = np.broadcast_arrays(*(np.atleast_1d(np.asarray(a, float)) for a in disp))
     n = rt.size
     out = np.empty((n, 9, M + 2), dtype=complex)
-    s = np.sqrt(((rt - rs) ** 2 + (zt - zs) ** 2) / (rt * rs))
+    s = np.sqrt((dr ** 2 + dz ** 2) / (rt * (rt - dr)))
     J = np.array([_levels(max(v, 1e-300)) for v in s])
     m = np.arange(M + 2)
     for Jv in np.unique(J):
@@ -140,7 +150,7 @@ def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64):
             sel = idx[c0:c0 + chunk]
             res = []
             for phi, Wc in rules:
-                F = integrands(rt[sel, None], zt[sel, None], rs[sel, None], zs[sel, None], k0, k1, phi[None, :])
+                F = integrands(rt[sel, None], zt[sel, None], dr[sel, None], dz[sel, None], k0, k1, phi[None, :])
                 res.append(F @ Wc)                       # [9, pairs, M+2]
             lo, hi = res
             scale = np.max(np.abs(hi), axis=2, keepdims=True) + 1e-300

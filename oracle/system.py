@@ -58,8 +58,14 @@ def wavenumbers(media):
 
 def panel_support(curve, target_panel: int, target_local: int, Q: int):
     """Support points on source panel Q for a target node, as
-    (r, z, r', z', W, L) with W the ds-weights and L[s, k] the Lagrange basis;
-    None for a far panel (plain Gauss-Legendre)."""
+    (r, z, r', z', W, L, disp) with W the ds-weights, L[s, k] the Lagrange
+    basis and disp = (r_t - r_s, z_t - z_s) for the target's own panel (None
+    otherwise); None for a far panel (plain Gauss-Legendre).
+
+    On the own panel the displacement is formed as
+    x_t - x_s = -sum_{k != a} L_k(tau_s) (x_k - x_a), which equals the
+    difference of interpolated and node positions but keeps its relative
+    accuracy when the support point is very close to the target."""
     nP = curve.n_panels
     if Q == target_panel:
         tau, wt = gauss.self_rule(target_local)
@@ -78,7 +84,13 @@ def panel_support(curve, target_panel: int, target_local: int, Q: int):
     r, z = L @ curve.r[sl], L @ curve.z[sl]
     dr, dz = L @ curve.dr[sl], L @ curve.dz[sl]
     sp = np.hypot(dr, dz)
-    return r, z, dr / sp, dz / sp, wt * sp, L
+    disp = None
+    if Q == target_panel:
+        a = target_local
+        ra, za = curve.r[sl][a], curve.z[sl][a]
+        others = [k for k in range(P) if k != a]
+        disp = (-(L[:, others] @ (curve.r[sl][others] - ra)), -(L[:, others] @ (curve.z[sl][others] - za)))
+    return r, z, dr / sp, dz / sp, wt * sp, L, disp
 
 
 def _gfam(F, fam, m):
@@ -173,13 +185,14 @@ def assemble(curve, media, M: int, formulation: int = 0, modes=None, rows=None, 
         rt, zt, rpt, zpt = geo.r[i], geo.z[i], geo.rp[i], geo.zp[i]
         for Q in range(curve.n_panels):
             sup = panel_support(curve, Pt, a, Q)
+            disp = None
             if sup is None:
                 sl = slice(Q * P, (Q + 1) * P)
                 rs, zs, rps, zps, W = geo.r[sl], geo.z[sl], geo.rp[sl], geo.zp[sl], geo.w[sl]
                 L = np.eye(P)
             else:
-                rs, zs, rps, zps, W, L = sup
-            F = modal_families_batch(rt, zt, rs, zs, k0, k1, M)
+                rs, zs, rps, zps, W, L, disp = sup
+            F = modal_families_batch(rt, zt, rs, zs, k0, k1, M, disp=disp)
             N0, N1, KD = operator_blocks(F, rs, rps, zps, rt, rpt, zpt, k0, k1, ms)
             x0, x1 = co["x"]; y0, y1 = co["y"]
             EM = -1j * om * (x0 * N0 - x1 * N1)
@@ -211,3 +224,38 @@ def l2_weights(curve):
 def weight_matrix(A, sw):
     """L2 weighting: A' = diag(sw) A diag(1/sw)."""
     return A * sw[None, :, None] / sw[None, None, :]
+
+
+def block(curve, media, M: int, i: int, j: int, formulation: int = 0, modes=None):
+    """The 4x4 blocks A_m[4i:4i+4, 4j:4j+4] (unweighted) for the given modes,
+    computed for this one (target node, column node) pair: the source panel's
+    support points if it is near the target's panel, else the single node."""
+    geo = node_geometry(curve)
+    k0, k1 = wavenumbers(media)
+    co = coefficients(media, formulation)
+    ms = np.arange(-M, M + 1) if modes is None else np.asarray(modes)
+    Pt, a = divmod(i, P)
+    Q, kloc = divmod(j, P)
+    rt, zt, rpt, zpt = geo.r[i], geo.z[i], geo.rp[i], geo.zp[i]
+    sup = panel_support(curve, Pt, a, Q)
+    disp = None
+    if sup is None:
+        rs, zs, rps, zps, W = (np.array([v[j]]) for v in (geo.r, geo.z, geo.rp, geo.zp, geo.w))
+        Lk = np.ones(1)
+    else:
+        rs, zs, rps, zps, W, L, disp = sup
+        Lk = L[:, kloc]
+    F = modal_families_batch(rt, zt, rs, zs, k0, k1, M, disp=disp)
+    N0, N1, KD = operator_blocks(F, rs, rps, zps, rt, rpt, zpt, k0, k1, ms)
+    om = media.omega
+    x0, x1 = co["x"]; y0, y1 = co["y"]
+    blk = np.zeros(N0.shape[:2] + (4, 4), dtype=complex)
+    blk[..., 0:2, 0:2] = co["aEJ"] * KD
+    blk[..., 0:2, 2:4] = -1j * om * (x0 * N0 - x1 * N1)
+    blk[..., 2:4, 0:2] = -1j * om * (y0 * N0 - y1 * N1)
+    blk[..., 2:4, 2:4] = co["aHM"] * KD
+    out = np.einsum("s,s,sqab->qab", W, Lk, blk)
+    if i == j:
+        out[:, 0, 2] += co["dEM"]; out[:, 1, 3] += co["dEM"]
+        out[:, 2, 0] += co["dHJ"]; out[:, 3, 1] += co["dHJ"]
+    return out
