@@ -1,0 +1,171 @@
+/*
+ * mueller.h -- C ABI of the GB300 separation-of-variables Mueller solver for
+ * penetrable bodies of revolution (Lai & O'Neil, arXiv:1810.07067).
+ *
+ * The body is the rotation of a generating curve gamma(s) = (r(s), z(s)) about
+ * the z axis (Section 3).  The curve is given as panels of p = 16 nodes placed
+ * at the Gauss-Legendre points of a panel-local parameter tau in [-1, 1]
+ * (Section 5).  For every Fourier mode m the solver assembles the dense
+ * 4N x 4N Nystrom system of the Mueller integral equation (eq. mullerrep, or
+ * its indirect form eq. dualmullrep), factors it by LU with partial pivoting
+ * and solves for the modal currents (J^1_m, J^2_m, M^1_m, M^2_m) at each node
+ * (J = J^1 t + J^2 e_theta, M likewise; Section 3).
+ *
+ * Conventions used by every entry point
+ *  - Complex numbers are mueller_c128 {re, im} (binary compatible with a
+ *    C99 double complex, std::complex<double> and torch.complex128).
+ *  - "host" pointers are ordinary CPU memory read during the call; "device"
+ *    pointers are CUDA global memory of the current device, owned by the
+ *    caller, read or written asynchronously on the given CUDA stream
+ *    (cudaStream_t passed as void*; NULL = legacy default stream).
+ *  - Node n of the curve owns unknowns 4n+0 (J^1), 4n+1 (J^2), 4n+2 (M^1),
+ *    4n+3 (M^2) and equations 4n+0 (E_t), 4n+1 (E_theta), 4n+2 (H_t),
+ *    4n+3 (H_theta).  Modal vectors are stored [2M+1][nrhs][4N] with mode
+ *    index q = m + M.
+ *  - Every call returns a mueller_status; nothing is thrown across the ABI.
+ *    No entry point falls back to a CPU implementation.
+ */
+#ifndef MUELLER_H
+#define MUELLER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } mueller_c128;
+
+typedef enum {
+  MUELLER_OK = 0,
+  MUELLER_EINVAL = 1,     /* invalid argument (message via mueller_last_error) */
+  MUELLER_ENOMEM = 2,     /* device or host allocation failed                  */
+  MUELLER_ESINGULAR = 3,  /* exact zero pivot in some mode (see stats)         */
+  MUELLER_ENOCONV = 4,    /* iterative refinement hit its cap                  */
+  MUELLER_ETIMEOUT = 5,   /* a bounded device-side wait gave up                */
+  MUELLER_ECUDA = 6       /* CUDA runtime error                                */
+} mueller_status;
+
+/* Generating curve (host arrays, copied during the call).
+ * Nodes are panel-major: node n = 16*panel + local index, local index k at
+ * tau_k, the k-th 16-point Gauss-Legendre node of [-1, 1] in increasing
+ * order.  The curve runs counterclockwise in the (r, z) half plane, so that
+ * n = (z', -r') points out of the body (Section 3); open curves start and end
+ * on the axis.  dr, dz are derivatives with respect to tau (the parameter
+ * need not be arclength; Section 6).  Geometry between nodes (support points
+ * of the near-panel rules) is the degree-15 Lagrange interpolant of the node
+ * values of r, z, dr, dz on the panel. */
+typedef struct {
+  int n_panels;        /* >= 1; N = 16 * n_panels nodes                   */
+  int closed;          /* 1: first and last panel are neighbours (torus)  */
+  const double* r;     /* [N] host, r > 0                                  */
+  const double* z;     /* [N] host                                         */
+  const double* dr;    /* [N] host, dr/dtau                                */
+  const double* dz;    /* [N] host, dz/dtau                                */
+} mueller_curve;
+
+/* Media (Section 1, eq. materials): background (0) and body (1);
+ * k_j = omega * sqrt(eps_j mu_j) (principal root).  Requires omega > 0,
+ * Re eps_j, Re mu_j > 0 and Im eps_j, Im mu_j >= 0. */
+typedef struct {
+  double omega;
+  mueller_c128 eps0, mu0, eps1, mu1;
+} mueller_media;
+
+typedef struct {
+  int n_phi;           /* azimuthal samples (power of two >= 16); raised
+                          automatically when too small for M and k (see
+                          stats.n_phi_used)                                 */
+  int formulation;     /* 0 direct (eq. mullerrep), 1 indirect (eq. dualmullrep) */
+  int precision;       /* 0 FP64; 1 mixed (FP32-grade trailing updates + FP64
+                          iterative refinement)                             */
+  double refine_tol;   /* mixed: stop when backward error <= refine_tol     */
+  int refine_max_iter; /* mixed: cap on refinement steps                    */
+  double split_eps;    /* kernel splitting when the plain trapezoid would
+                          alias above this (default 1e-17 when <= 0)         */
+} mueller_options;
+
+typedef struct {
+  double ms_legendre, ms_far, ms_support, ms_near, ms_lu, ms_build;  /* stage times */
+  double ms_solve;           /* last mueller_solve                           */
+  int n_phi_used;
+  long long n_split_pairs;   /* pairs evaluated with kernel splitting        */
+  long long n_far_pairs, n_support_pairs;
+  int singular_mode;         /* first mode with a zero pivot, or -1          */
+  int singular_column;
+  size_t device_bytes;       /* memory held by the context                   */
+} mueller_stats;
+
+typedef struct mueller_ctx mueller_ctx;
+
+/* Build: assemble the per-mode systems for modes m = 0..M on the device and
+ * factor them by LU with partial pivoting (Sections 3-5; eq. mullerrep or
+ * eq. dualmullrep; "LU-factorization" of Section 6).  Modes -M..-1 are not
+ * assembled: the reflection theta -> -theta gives A_{-m} = D_r A_m D_c with
+ * D_r = diag(-1, 1, 1, -1) and D_c = diag(1, -1, -1, 1) per node, and
+ * mueller_solve uses the factors of A_m for both.  Rows and unknowns are
+ * L2-weighted internally (Section 6 remark); the API stays in physical
+ * unknowns.  Host inputs are copied; the context owns all device memory.
+ * Work runs on `stream`; the call returns after the factorization has
+ * finished (stage times are measured with CUDA events). */
+int mueller_build(const mueller_curve* curve, const mueller_media* media, int M,
+                  const mueller_options* opts, void* stream, mueller_ctx** out);
+
+/* Assemble only (no factorization) into a caller buffer A_dev
+ * [M+1][4N][4N] column-major per mode, L2-weighted:
+ * A'_m = diag(sqrt w) A_m diag(1/sqrt w), w the ds-weights of the nodes. */
+int mueller_assemble(const mueller_curve* curve, const mueller_media* media, int M,
+                     const mueller_options* opts, mueller_c128* A_dev, void* stream);
+
+/* Solve for all modes -M..M (Section 6, T_add: additional right-hand sides
+ * reuse the factors).  rhs_dev and x_dev are device arrays
+ * [2M+1][nrhs][4N]; backward_err (host, [2M+1][nrhs]) may be NULL. */
+int mueller_solve(mueller_ctx* ctx, const mueller_c128* rhs_dev, int nrhs, mueller_c128* x_dev,
+                  double* backward_err, void* stream);
+
+/* Modal right-hand sides of plane waves (eq. pw): E = e exp(i k0 d.x),
+ * H = (k0/(omega mu0)) d x e exp(i k0 d.x); dirs and pols are host [nrhs][3]
+ * (pols = unit e, orthogonal to d).  Rows are the Fourier coefficients
+ * (1/2pi) int f e^{-i m theta} of the tangential traces n x E and n x H, scaled
+ * by i omega eps0 and i omega mu0 (eq. mullerrep) or i omega mu0 and
+ * i omega eps0 (eq. dualmullrep).  rhs_dev: [2M+1][nrhs][4N]. */
+int mueller_rhs_planewave(mueller_ctx* ctx, const double* dirs, const double* pols, int nrhs,
+                          mueller_c128* rhs_dev, void* stream);
+
+/* Far field (eq. farfieldform, with the magnetic current in the last term as
+ * in eq. exteriorfield): E_oo(xh) = (1/4pi)[-(k0^2/(i omega eps0))(Jh - (xh.Jh)xh)
+ * + i k0 xh x Mh], Jh = int exp(-i k0 xh.y) J(y) da(y).  x_dev: currents
+ * [2M+1][nrhs][4N]; dirs_dev: device [ndir][3] unit vectors; E_dev: device
+ * [nrhs][ndir][3]. */
+int mueller_far_field(mueller_ctx* ctx, const mueller_c128* x_dev, int nrhs, const double* dirs_dev,
+                      int ndir, mueller_c128* E_dev, void* stream);
+
+/* Modal Green's function spectra for arbitrary (target, source) pairs
+ * (Section 4): pairs_host [npairs][4] = (r_t, z_t, r_s, z_s); out_dev
+ * [npairs][9][M+2] for m = 0..M+1 of: g^{k0}, g^{k1} (eq. green11),
+ * d/dr_t and d/dz_t of g^{k0} and of g^{k1} (eq. firstder), and
+ * d2/dr_t2, d2/dr_t dz_t, d2/dz_t2 of g^{k0} - g^{k1} (Section 4.3),
+ * each the integral over phi in [0, 2pi) of the kernel times cos(m phi).
+ * k0, k1 with Im >= 0; n_phi as in mueller_options. */
+int mueller_modal_kernels(const double* pairs_host, long long npairs, mueller_c128 k0, mueller_c128 k1,
+                          int M, int n_phi, double split_eps, mueller_c128* out_dev, void* stream);
+
+/* Batched LU of `batch` column-major n x n complex matrices in place
+ * (stride n*n); piv_dev [batch][n] (0-based LAPACK-style interchanges),
+ * info_dev [batch] (0 or first zero-pivot column + 1). */
+int mueller_lu_batched(mueller_c128* A_dev, int n, int batch, int* piv_dev, int* info_dev, void* stream);
+
+/* Bytes of complex128 factors for one body: 16 (4N)^2 (2M+1), the admission
+ * unit named by the serving workload (the GPU path stores M+1 of them). */
+size_t mueller_footprint_bytes(int N, int M);
+
+int mueller_stats_get(const mueller_ctx* ctx, mueller_stats* out);
+void mueller_destroy(mueller_ctx* ctx);
+const char* mueller_strerror(int status);
+/* Message of the last failing call on this thread (empty if none). */
+const char* mueller_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

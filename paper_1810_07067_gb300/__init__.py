@@ -1,0 +1,218 @@
+"""Python binding of libmueller (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library built from ``csrc/``; there is no
+CPU fallback: importing this package raises if ``libmueller.so`` is missing.
+Device buffers are torch tensors (complex128 / float64 / int32 on CUDA,
+contiguous); streams default to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmueller.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with paper_1810_07067_gb300.build.build() "
+                      "(or __graft_entry__.build()); there is no CPU fallback")
+_lib = ct.CDLL(_LIB_PATH)
+
+
+class c128(ct.Structure):
+    _fields_ = [("re", ct.c_double), ("im", ct.c_double)]
+
+
+def _c(z) -> c128:
+    z = complex(z)
+    return c128(z.real, z.imag)
+
+
+class _Curve(ct.Structure):
+    _fields_ = [("n_panels", ct.c_int), ("closed", ct.c_int), ("r", ct.POINTER(ct.c_double)),
+                ("z", ct.POINTER(ct.c_double)), ("dr", ct.POINTER(ct.c_double)), ("dz", ct.POINTER(ct.c_double))]
+
+
+class _Media(ct.Structure):
+    _fields_ = [("omega", ct.c_double), ("eps0", c128), ("mu0", c128), ("eps1", c128), ("mu1", c128)]
+
+
+class _Options(ct.Structure):
+    _fields_ = [("n_phi", ct.c_int), ("formulation", ct.c_int), ("precision", ct.c_int),
+                ("refine_tol", ct.c_double), ("refine_max_iter", ct.c_int), ("split_eps", ct.c_double)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("ms_legendre", ct.c_double), ("ms_far", ct.c_double), ("ms_support", ct.c_double),
+                ("ms_near", ct.c_double), ("ms_lu", ct.c_double), ("ms_build", ct.c_double),
+                ("ms_solve", ct.c_double), ("n_phi_used", ct.c_int), ("n_split_pairs", ct.c_longlong),
+                ("n_far_pairs", ct.c_longlong), ("n_support_pairs", ct.c_longlong), ("singular_mode", ct.c_int),
+                ("singular_column", ct.c_int), ("device_bytes", ct.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ct.c_void_p
+_lib.mueller_build.argtypes = [ct.POINTER(_Curve), ct.POINTER(_Media), ct.c_int, ct.POINTER(_Options), _vp,
+                               ct.POINTER(_vp)]
+_lib.mueller_assemble.argtypes = [ct.POINTER(_Curve), ct.POINTER(_Media), ct.c_int, ct.POINTER(_Options), _vp, _vp]
+_lib.mueller_solve.argtypes = [_vp, _vp, ct.c_int, _vp, ct.POINTER(ct.c_double), _vp]
+_lib.mueller_rhs_planewave.argtypes = [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int, _vp, _vp]
+_lib.mueller_far_field.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, _vp, _vp]
+_lib.mueller_modal_kernels.argtypes = [ct.POINTER(ct.c_double), ct.c_longlong, c128, c128, ct.c_int, ct.c_int,
+                                       ct.c_double, _vp, _vp]
+_lib.mueller_lu_batched.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
+_lib.mueller_footprint_bytes.argtypes = [ct.c_int, ct.c_int]
+_lib.mueller_footprint_bytes.restype = ct.c_size_t
+_lib.mueller_stats_get.argtypes = [_vp, ct.POINTER(Stats)]
+_lib.mueller_destroy.argtypes = [_vp]
+_lib.mueller_strerror.restype = ct.c_char_p
+_lib.mueller_strerror.argtypes = [ct.c_int]
+_lib.mueller_last_error.restype = ct.c_char_p
+
+EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_far_field",
+           "mueller_modal_kernels", "mueller_lu_batched", "mueller_footprint_bytes", "mueller_stats_get",
+           "mueller_destroy", "mueller_strerror", "mueller_last_error"]
+
+
+class MuellerError(RuntimeError):
+    def __init__(self, status: int):
+        msg = _lib.mueller_strerror(status).decode()
+        detail = _lib.mueller_last_error().decode()
+        super().__init__(f"{msg}: {detail}" if detail else msg)
+        self.status = status
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MuellerError(rc)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ct.c_void_p(stream)
+    import torch
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+@dataclass
+class Options:
+    n_phi: int = 64
+    formulation: int = 0
+    precision: int = 0
+    refine_tol: float = 1e-12
+    refine_max_iter: int = 10
+    split_eps: float = 1e-17
+
+    def _c(self):
+        return _Options(self.n_phi, self.formulation, self.precision, self.refine_tol, self.refine_max_iter,
+                        self.split_eps)
+
+
+def _curve_struct(curve):
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (curve.r, curve.z, curve.dr, curve.dz)]
+    s = _Curve(int(curve.n_panels), int(bool(getattr(curve, "closed", False))), *[_dptr(a) for a in arrs])
+    return s, arrs
+
+
+def _media_struct(m):
+    return _Media(float(m.omega), _c(m.eps0), _c(m.mu0), _c(m.eps1), _c(m.mu1))
+
+
+class Context:
+    """Per-body factors of modes 0..M resident on the device."""
+
+    def __init__(self, curve, media, M: int, options: Options | None = None, stream=None):
+        options = options or Options()
+        cs, self._keep = _curve_struct(curve)
+        ms = _media_struct(media)
+        h = ct.c_void_p()
+        self.M = int(M)
+        self.N = int(curve.n_panels) * 16
+        rc = _lib.mueller_build(ct.byref(cs), ct.byref(ms), self.M, ct.byref(options._c()), _stream(stream),
+                                ct.byref(h))
+        self._h = h
+        _check(rc)
+
+    def solve(self, rhs, x, backward_err: np.ndarray | None = None, stream=None):
+        nrhs = rhs.shape[1]
+        be = None if backward_err is None else backward_err.ctypes.data_as(ct.POINTER(ct.c_double))
+        _check(_lib.mueller_solve(self._h, _ptr(rhs), nrhs, _ptr(x), be, _stream(stream)))
+        return x
+
+    def rhs_planewave(self, dirs, pols, rhs, stream=None):
+        d = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
+        p = np.ascontiguousarray(np.asarray(pols, np.float64).reshape(-1, 3))
+        _check(_lib.mueller_rhs_planewave(self._h, _dptr(d), _dptr(p), len(d), _ptr(rhs), _stream(stream)))
+        return rhs
+
+    def far_field(self, x, dirs, E, stream=None):
+        _check(_lib.mueller_far_field(self._h, _ptr(x), x.shape[1], _ptr(dirs), dirs.shape[0], _ptr(E),
+                                      _stream(stream)))
+        return E
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(_lib.mueller_stats_get(self._h, ct.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mueller_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build(curve, media, M: int, options: Options | None = None, stream=None) -> Context:
+    return Context(curve, media, M, options, stream)
+
+
+def assemble(curve, media, M: int, A, options: Options | None = None, stream=None):
+    """Weighted per-mode matrices for modes 0..M into A [M+1, 4N, 4N] (column-major per mode:
+    A[m] holds the transpose of the matrix in row-major view)."""
+    options = options or Options()
+    cs, keep = _curve_struct(curve)
+    ms = _media_struct(media)
+    _check(_lib.mueller_assemble(ct.byref(cs), ct.byref(ms), int(M), ct.byref(options._c()), _ptr(A),
+                                 _stream(stream)))
+    return A
+
+
+def modal_kernels(pairs: np.ndarray, k0, k1, M: int, n_phi: int, out, split_eps: float = 1e-17, stream=None):
+    p = np.ascontiguousarray(np.asarray(pairs, np.float64).reshape(-1, 4))
+    _check(_lib.mueller_modal_kernels(_dptr(p), len(p), _c(k0), _c(k1), int(M), int(n_phi), float(split_eps),
+                                      _ptr(out), _stream(stream)))
+    return out
+
+
+def lu_batched(A, piv, info, stream=None):
+    n = A.shape[-1]
+    batch = A.shape[0]
+    _check(_lib.mueller_lu_batched(_ptr(A), n, batch, _ptr(piv), _ptr(info), _stream(stream)))
+
+
+def footprint_bytes(N: int, M: int) -> int:
+    return int(_lib.mueller_footprint_bytes(N, M))
+
+
+def library_path() -> str:
+    return _LIB_PATH

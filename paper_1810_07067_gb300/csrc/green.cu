@@ -1,0 +1,511 @@
+// Modal Green's functions, their target derivatives and the per-mode Mueller
+// blocks, on the GPU.
+//
+// For a target (r_t, z_t) and a source (r_s, z_s) the nine spectra
+//   F0 = g^{k0}_m, F1 = g^{k1}_m                                 (eq. green11)
+//   F2, F3 = d/dr_t, d/dz_t of g^{k0}_m; F4, F5 the same for k1    (eq. firstder)
+//   F6, F7, F8 = d2/dr_t2, d2/dr_t dz_t, d2/dz_t2 of (g^{k0} - g^{k1})_m
+//                                                       (Section 4.3, differences)
+// are computed for m = 0..M+1 from nphi azimuthal samples of the integrand
+// and a cosine transform (the integrands are even in phi).
+//
+// Kernel splitting (Section 4): with u = rho^2 and G = exp(ik sqrt u)/(4pi sqrt u),
+// every family is written as  a(phi) u^{-1/2} + beta u^{-3/2} + c(phi)  with
+// a, c entire in phi and beta a per-pair constant (the r_t - r_s cos(phi)
+// factors are rewritten as alpha_r + u/(2 r_t) so that only a constant
+// multiplies u^{-3/2}).  The u^{-1/2} part is the discrete convolution of eq.
+// discA, computed as the transform of a(phi_j) times the band-limited samples
+// of u^{-1/2} (the "D^{-1}(f . D q)" form); the u^{-3/2} part is beta times the
+// closed-form coefficient of eq. pm.  The Fourier coefficients of u^{-1/2} and
+// u^{-3/2} are (2 r_t r_s)^{-1/2} P_m(chi) and (2 r_t r_s)^{-3/2} S_m(chi) with
+// P_m = sqrt(8) Q_{m-1/2} (eq. lm, recurrence eq. recurform, Miller's backward
+// recurrence when the forward one is unstable) and S_m from the appendix
+// relation.  Splitting is used only when the plain trapezoid rule would alias
+// above the requested accuracy (zeta^{nphi-M-1} > eps, zeta = chi - sqrt(chi^2-1)).
+#include <cuda_runtime.h>
+#include <cstdio>
+#include "green.cuh"
+
+__constant__ SeriesTables c_tab;
+
+void upload_series_tables(const SeriesTables& t) { cudaMemcpyToSymbol(c_tab, &t, sizeof(SeriesTables)); }
+
+// ---------------------------------------------------------------------------
+// Laplace-type modal coefficients, one thread per split pair.
+// pairs: [n][4] = (r_t, z_t, r_t - r_s, z_t - z_s); leg: [(Mq+1)+Ms][n] index-major:
+// rows 0..Mq hold P^_n = P_n / sqrt(B), rows Mq+1.. hold S^_m = S_m / B^{3/2}.
+__global__ void legendre_kernel(const double* __restrict__ pairs, long long n, int Mq, int Ms,
+                                double* __restrict__ leg) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double rt = pairs[4 * p], dr = pairs[4 * p + 2], dz = pairs[4 * p + 3];
+  double rs = rt - dr;
+  double d2 = dr * dr + dz * dz, B = 2.0 * rt * rs;
+  double c = d2 / B, cp1 = 2.0 + c;          // chi - 1, chi + 1
+  double kp2 = c / cp1;
+  double K = ellipk_c(sqrt(kp2));
+  double E = ellipe_c(kp2);
+  double P0 = 4.0 * K / sqrt(cp1);
+  double lz = log1p(c + sqrt(c * cp1));      // -ln(zeta)
+  // Work with P_m and the differences D_m = P_{m-1} - P_m: the recurrence
+  // (2m+1) P_{m+1} = 4 m chi P_m - (2m-1) P_{m-1} becomes
+  // D_{m+1} = ((2m-1) D_m - 4 m c P_m) / (2m+1), P_{m+1} = P_m - D_{m+1},
+  // which keeps the O(1) differences accurate when chi -> 1.
+  double* Pv = leg;                                // rows 0..Mq: P_m, later P^_m
+  double* Sv = leg + (long long)(Mq + 1) * n;      // rows 0..Ms-1: D_m, later S^_m
+  const double LN32 = 3.4657359027997265;
+  if (2.0 * Mq * lz <= LN32) {
+    double P = P0, D = 4.0 * sqrt(cp1) * E - c * P0;  // P_0, D_1
+    Pv[p] = P;
+    for (int m = 1; m <= Mq; ++m) {
+      if (m < Ms) Sv[(long long)m * n + p] = D;
+      double Pn = P - D;                              // P_m
+      Pv[(long long)m * n + p] = Pn;
+      D = ((2.0 * m - 1.0) * D - 4.0 * m * c * Pn) / (2.0 * m + 1.0);  // D_{m+1}
+      P = Pn;
+    }
+  } else {
+    // Miller: P~_{m*+1} = 0, P~_{m*} = 1, recurring down in (P, D).
+    int mstar = Mq + (int)ceil(19.6 / lz) + 2;
+    double Pn = 0.0, Dn = 1.0;
+    for (int m = mstar; m >= 0; --m) {
+      double Pm = Pn + Dn;
+      if (m <= Mq) Pv[(long long)m * n + p] = Pm;
+      if (m >= 1) {
+        double Dm = ((2.0 * m + 1.0) * Dn + 4.0 * m * c * Pm) / (2.0 * m - 1.0);
+        if (m < Ms) Sv[(long long)m * n + p] = Dm;
+        Pn = Pm; Dn = Dm;
+      }
+    }
+    double scale = P0 / Pv[p];
+    for (int m = 0; m <= Mq; ++m) Pv[(long long)m * n + p] *= scale;
+    for (int m = 1; m < Ms; ++m) Sv[(long long)m * n + p] *= scale;
+  }
+  // S_m = (1 - 2m)(chi P_m - P_{m-1})/(chi^2 - 1) = (2m - 1)(D_m - c P_m)/(c (c + 2))
+  double isB = 1.0 / sqrt(B), isB3 = isB * isB * isB;
+  Sv[p] = 4.0 * E / (c * sqrt(cp1)) * isB3;
+  for (int m = 1; m < Ms; ++m) {
+    double D = Sv[(long long)m * n + p], P = Pv[(long long)m * n + p];
+    Sv[(long long)m * n + p] = (2.0 * m - 1.0) * (D - c * P) / (c * cp1) * isB3;
+  }
+  for (int m = 0; m <= Mq; ++m) Pv[(long long)m * n + p] *= isB;
+}
+
+void launch_legendre(const double* pairs, long long n, int Mq, int Ms, double* leg, cudaStream_t s) {
+  if (n <= 0) return;
+  int tpb = 128;
+  legendre_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, s>>>(pairs, n, Mq, Ms, leg);
+}
+
+// ---------------------------------------------------------------------------
+// One warp computes the nine spectra of one pair into shared memory.
+// Shared layout per warp: smp[NFAM*H] (cd), spec[NFAM*Ms] (cd), q[H] (double),
+// phs[Mq+1] (double).
+int green_smem_per_warp(const GreenParams& gp) { return green_smem_bytes(gp); }
+
+struct WarpSmem {
+  cd* smp; cd* spec; double* q; double* phs;
+};
+
+__device__ __forceinline__ WarpSmem warp_smem(const GreenParams& gp, char* base) {
+  WarpSmem w;
+  w.smp = (cd*)base;
+  w.spec = w.smp + NFAM * gp.H;
+  w.q = (double*)(w.spec + NFAM * gp.Ms);
+  w.phs = w.q + gp.H;
+  return w;
+}
+
+// The pair is the target (rt, zt) and the displacement (dr0, zd) = target - source.
+__device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
+                                  long long sid, const double* __restrict__ leg, long long n_split,
+                                  const double* __restrict__ cosT, const double* __restrict__ s2T,
+                                  const WarpSmem& W, int lane) {
+  const int H = gp.H, Ms = gp.Ms, Mq = gp.Mq, mask = gp.nphi - 1;
+  const double rs = rt - dr0;
+  const double d2 = dr0 * dr0 + zd * zd;
+  const double alpha = dr0 - d2 / (2.0 * rt);
+  const bool split = sid >= 0;
+  const double TWO_PI = 6.283185307179586;
+  if (split) {
+    for (int nn = lane; nn <= Mq; nn += 32) W.phs[nn] = leg[(long long)nn * n_split + sid];
+    __syncwarp();
+    for (int j = lane; j < H; j += 32) {
+      double acc = 0.0;
+      for (int nn = 1; nn <= Mq; ++nn) acc = fma(W.phs[nn], cosT[(nn * j) & mask], acc);
+      W.q[j] = (W.phs[0] + 2.0 * acc) / TWO_PI;
+    }
+    __syncwarp();
+  }
+  const cd g0 = gp.gamma0;
+  for (int j = lane; j < H; j += 32) {
+    double s2 = s2T[j];
+    double u = d2 + 4.0 * rt * rs * s2;
+    double su = sqrt(u);
+    double rd = dr0 + 2.0 * rs * s2;
+    Ent e0 = entire(c_tab, gp.kp0, su);
+    Ent e1 = entire(c_tab, gp.kp1, su);
+    cd gam1 = e0.Gam - e1.Gam, gam2 = e0.Gam2 - e1.Gam2, gam1p = e0.Gamp - e1.Gamp;
+    cd dSp = e0.Sp - e1.Sp, dSpp = e0.Spp - e1.Spp;
+    cd F[NFAM];
+    if (!split) {
+      double isu = 1.0 / su, iu3 = isu / u;
+      F[0] = e0.C * isu + mul_i(e0.S);
+      F[1] = e1.C * isu + mul_i(e1.S);
+      cd Ep0 = e0.Gam * isu - C(0.5 * iu3) + mul_i(e0.Sp);
+      cd Ep1 = e1.Gam * isu - C(0.5 * iu3) + mul_i(e1.Sp);
+      F[2] = (2.0 * rd) * Ep0; F[3] = (2.0 * zd) * Ep0;
+      F[4] = (2.0 * rd) * Ep1; F[5] = (2.0 * zd) * Ep1;
+      cd D1 = gam1 * isu + mul_i(dSp);
+      cd D2 = (gam1p - 0.5 * gam2) * isu - (0.5 * iu3) * g0 + mul_i(dSpp);
+      F[6] = (4.0 * rd * rd) * D2 + 2.0 * D1;
+      F[7] = (4.0 * rd * zd) * D2;
+      F[8] = (4.0 * zd * zd) * D2 + 2.0 * D1;
+    } else {
+      double q = W.q[j];
+      F[0] = q * e0.C + mul_i(e0.S);
+      F[1] = q * e1.C + mul_i(e1.S);
+      F[2] = q * ((2.0 * rd) * e0.Gam - C(0.5 / rt)) + mul_i((2.0 * rd) * e0.Sp);
+      F[3] = q * ((2.0 * zd) * e0.Gam) + mul_i((2.0 * zd) * e0.Sp);
+      F[4] = q * ((2.0 * rd) * e1.Gam - C(0.5 / rt)) + mul_i((2.0 * rd) * e1.Sp);
+      F[5] = q * ((2.0 * zd) * e1.Gam) + mul_i((2.0 * zd) * e1.Sp);
+      cd eta = gam1p - 0.5 * gam2;
+      F[6] = q * ((4.0 * rd * rd) * eta - ((rd + alpha) / rt) * g0 + 2.0 * gam1) +
+             mul_i((4.0 * rd * rd) * dSpp + 2.0 * dSp);
+      F[7] = q * ((4.0 * rd * zd) * eta - (zd / rt) * g0) + mul_i((4.0 * rd * zd) * dSpp);
+      F[8] = q * ((4.0 * zd * zd) * eta + 2.0 * gam1) + mul_i((4.0 * zd * zd) * dSpp + 2.0 * dSp);
+    }
+    double wj = (j == 0 || j == H - 1) ? 0.5 : 1.0;
+#pragma unroll
+    for (int f = 0; f < NFAM; ++f) W.smp[f * H + j] = wj * F[f];
+  }
+  __syncwarp();
+  // cosine transform: spec_m = (1/nphi) sum_j w_j F_j cos(m phi_j) (the 4pi of
+  // G is folded into 1/nphi * (4pi/4pi)); the u^{-3/2} part is added exactly.
+  const double inv = 1.0 / gp.nphi;
+  const double FOUR_PI = 12.566370614359172;
+  cd beta[NFAM];
+  if (split) {
+    beta[0] = C(0.0); beta[1] = C(0.0);
+    beta[2] = C(-alpha); beta[3] = C(-zd); beta[4] = C(-alpha); beta[5] = C(-zd);
+    beta[6] = (-2.0 * alpha * alpha) * g0;
+    beta[7] = (-2.0 * alpha * zd) * g0;
+    beta[8] = (-2.0 * zd * zd) * g0;
+  }
+  const double* Shat = leg + (long long)(Mq + 1) * n_split;
+  for (int mm = lane; mm < Ms; mm += 32) {
+    cd acc[NFAM];
+#pragma unroll
+    for (int f = 0; f < NFAM; ++f) acc[f] = C(0.0);
+    for (int j = 0; j < H; ++j) {
+      double c = cosT[(j * mm) & mask];
+#pragma unroll
+      for (int f = 0; f < NFAM; ++f) acc[f] = fma(c, W.smp[f * H + j], acc[f]);
+    }
+    double Sm = split ? Shat[(long long)mm * n_split + sid] / FOUR_PI : 0.0;
+#pragma unroll
+    for (int f = 0; f < NFAM; ++f) {
+      cd v = inv * acc[f];
+      if (split) v = fma(Sm, beta[f], v);
+      W.spec[f * Ms + mm] = v;
+    }
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Mueller 4x4 block for one (target, source-or-column, mode m >= 0) from an
+// accessor R(sigma, f, mm): sigma 0 = r r' weight, 1 = r weight, 2 = r z' weight.
+struct V2 { cd a, b; };  // coefficients of J^1, J^2
+__device__ __forceinline__ V2 v2(cd a, cd b) { V2 v; v.a = a; v.b = b; return v; }
+__device__ __forceinline__ V2 operator+(V2 x, V2 y) { return v2(x.a + y.a, x.b + y.b); }
+__device__ __forceinline__ V2 operator-(V2 x, V2 y) { return v2(x.a - y.a, x.b - y.b); }
+__device__ __forceinline__ V2 operator*(cd s, V2 x) { return v2(s * x.a, s * x.b); }
+__device__ __forceinline__ V2 operator*(double s, V2 x) { return v2(s * x.a, s * x.b); }
+
+template <class Get>
+__device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double rt, double rpt, double zpt,
+                              cd out[4][4]) {
+  int a0 = m, ap1 = m + 1, am1 = (m >= 1) ? m - 1 : 1;
+  V2 c1[NFAM], c2[NFAM], c3[NFAM];
+#pragma unroll
+  for (int f = 0; f < NFAM; ++f) {
+    cd A0p = R(0, f, ap1), A0m = R(0, f, am1);
+    cd A1p = R(1, f, ap1), A1m = R(1, f, am1);
+    cd G2a = 0.5 * (A0p + A0m), G3a = 0.5 * (A0m - A0p);
+    cd G2b = 0.5 * (A1p + A1m), G3b = 0.5 * (A1m - A1p);
+    c1[f] = v2(G2a, -mul_i(G3b));
+    c2[f] = v2(mul_i(G3a), G2b);
+    c3[f] = v2(R(2, f, a0), C(0.0));
+  }
+  const double irt = 1.0 / rt, irt2 = irt * irt;
+  const cd im = C(0.0, (double)m);
+  const cd im_r = C(0.0, m * irt), im_r2 = C(0.0, m * irt2);
+  V2 Nt[2], Nth[2];
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    int g = kk, dr = 2 + 2 * kk, dz = 3 + 2 * kk;
+    Nt[kk] = c1[dz] - c3[dr];
+    V2 t1 = c2[g] + rt * c2[dr] - im * c1[g];
+    V2 t2 = im_r * c3[g] - c2[dz];
+    Nth[kk] = C(-1.0) * ((zpt * irt) * t1 + rpt * t2);
+  }
+  V2 c1D = c1[0] - c1[1], c2D = c2[0] - c2[1];
+  V2 c1rD = c1[2] - c1[4], c2rD = c2[2] - c2[4];
+  V2 c1zD = c1[3] - c1[5], c2zD = c2[3] - c2[5], c3zD = c3[3] - c3[5];
+  V2 Kt = ap.k0sq * c2[0] - ap.k1sq * c2[1] + im_r2 * c1D + im_r * c1rD - (double(m) * m * irt2) * c2D +
+          im_r * c3zD;
+  V2 dPr = C(-irt2) * c1D + irt * c1rD + c1[6] - im_r2 * c2D + im_r * c2rD + c3[7];
+  V2 dPz = irt * c1zD + c1[7] + im_r * c2zD + c3[8];
+  V2 Kth = C(-1.0) * (rpt * (ap.k0sq * c1[0] - ap.k1sq * c1[1] + dPr) +
+                      zpt * (ap.k0sq * c3[0] - ap.k1sq * c3[1] + dPz));
+  V2 EM_t = ap.cEM0 * Nt[0] + ap.cEM1 * Nt[1], EM_th = ap.cEM0 * Nth[0] + ap.cEM1 * Nth[1];
+  V2 HJ_t = ap.cHJ0 * Nt[0] + ap.cHJ1 * Nt[1], HJ_th = ap.cHJ0 * Nth[0] + ap.cHJ1 * Nth[1];
+  out[0][0] = ap.aEJ * Kt.a;  out[0][1] = ap.aEJ * Kt.b;  out[0][2] = EM_t.a;  out[0][3] = EM_t.b;
+  out[1][0] = ap.aEJ * Kth.a; out[1][1] = ap.aEJ * Kth.b; out[1][2] = EM_th.a; out[1][3] = EM_th.b;
+  out[2][0] = HJ_t.a;  out[2][1] = HJ_t.b;  out[2][2] = ap.aHM * Kt.a;  out[2][3] = ap.aHM * Kt.b;
+  out[3][0] = HJ_th.a; out[3][1] = HJ_th.b; out[3][2] = ap.aHM * Kth.a; out[3][3] = ap.aHM * Kth.b;
+}
+
+__device__ __forceinline__ void store_block(cd* __restrict__ A, int n, int m, int i, int j, cd blk[4][4],
+                                            double scale) {
+  size_t base = (size_t)m * n * n;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    double2* dst = (double2*)(A + base + (size_t)(4 * j + b) * n + 4 * i);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) dst[a] = make_double2(scale * blk[a][b].x, scale * blk[a][b].y);
+  }
+}
+
+__device__ __forceinline__ bool near_panels(int Pi, int Pj, int nP, int closed) {
+  int d = Pi - Pj;
+  if (d >= -1 && d <= 1) return true;
+  if (closed && nP > 2 && (d == nP - 1 || d == -(nP - 1))) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Far panels: fused sampling, transform and assembly for one (i, j) pair per warp.
+__global__ void far_kernel(BuildArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const GreenParams& gp = a.gp;
+  WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
+  const long long total = (long long)a.N * a.N;
+  const int n = 4 * a.N;
+  for (long long p = (long long)blockIdx.x * wpb + wib; p < total; p += (long long)gridDim.x * wpb) {
+    int i = (int)(p / a.N), j = (int)(p % a.N);
+    if (near_panels(i / P_NODES, j / P_NODES, a.n_panels, a.closed)) continue;
+    long long sid = a.split_far[p];
+    double rt = a.geo.r[i], rs = a.geo.r[j];
+    warp_pair_spectra(gp, rt, rt - rs, a.geo.z[i] - a.geo.z[j], sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane);
+    const double w = a.geo.w[j], rps = a.geo.rp[j], zps = a.geo.zp[j];
+    const double fac[3] = {w * rs * rps, w * rs, w * rs * zps};
+    const cd* spec = W.spec;
+    const int Ms = gp.Ms;
+    auto R = [&](int s, int f, int mm) { return fac[s] * spec[f * Ms + mm]; };
+    const double scale = a.geo.sw[i] / a.geo.sw[j];
+    for (int m = lane; m <= gp.M; m += 32) {
+      cd blk[4][4];
+      mueller_block(R, m, a.ap, rt, a.geo.rp[i], a.geo.zp[i], blk);
+      store_block(a.A, n, m, i, j, blk, scale);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Support points of the self and adjacent panels: one warp per
+// (target, slot); spectra are written to scratch for the contraction below.
+// Slot layout per target: [0, SELF_PTS) own panel, then ADJ_PTS of the
+// previous panel (its shared end is +1), then ADJ_PTS of the next panel
+// (shared end -1).
+__device__ __forceinline__ bool support_point(const BuildArgs& a, int i, int slot, long long* pid) {
+  int P = i / P_NODES, loc = i % P_NODES;
+  int nP = a.n_panels;
+  if (slot < SELF_PTS) {
+    *pid = (long long)P * PTS_PER_PANEL + loc * SELF_PTS + slot;
+    return true;
+  }
+  if (slot < SELF_PTS + ADJ_PTS) {
+    int Q = P - 1;
+    if (Q < 0) { if (!a.closed || nP <= 2) return false; Q = nP - 1; }
+    *pid = (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + ADJ_PTS + (slot - SELF_PTS);
+    return true;
+  }
+  int Q = P + 1;
+  if (Q >= nP) { if (!a.closed || nP <= 2) return false; Q = 0; }
+  *pid = (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + (slot - SELF_PTS - ADJ_PTS);
+  return true;
+}
+
+__global__ void support_kernel(BuildArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const GreenParams& gp = a.gp;
+  WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
+  const long long total = (long long)a.N * NEAR_SLOTS;
+  for (long long p = (long long)blockIdx.x * wpb + wib; p < total; p += (long long)gridDim.x * wpb) {
+    int i = (int)(p / NEAR_SLOTS), slot = (int)(p % NEAR_SLOTS);
+    long long pid;
+    if (!support_point(a, i, slot, &pid)) continue;
+    long long sid = a.split_sup[p];
+    double rt = a.geo.r[i], dr0, zd;
+    if (slot < SELF_PTS) { dr0 = a.sup.dr[pid]; zd = a.sup.dz[pid]; }
+    else { dr0 = rt - a.sup.r[pid]; zd = a.geo.z[i] - a.sup.z[pid]; }
+    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane);
+    cd* dst = a.spec_sup + p * NFAM * gp.Ms;
+    for (int t = lane; t < NFAM * gp.Ms; t += 32) dst[t] = W.spec[t];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Near panels: R_k(sigma, f, m) = sum_s W_s L_k(tau_s) sigma_s F_f(s, m)
+// (eqs. eq_nyslike, eq_nyslike2 with sum_j U_jk P_j = L_k), then the blocks of
+// the panel's columns k.  One CTA per (target, near panel, chunk of kc columns).
+__global__ void near_kernel(BuildArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const GreenParams& gp = a.gp;
+  const int kc = a.kc, nchunk = P_NODES / kc;
+  int bid = blockIdx.x;
+  const int chunk = bid % nchunk; bid /= nchunk;
+  const int which = bid % 3;  // 0 prev, 1 self, 2 next
+  const int i = bid / 3;
+  const int P = i / P_NODES, loc = i % P_NODES, nP = a.n_panels;
+  int Q, slot0, S;
+  const double* L;
+  if (which == 1) {
+    Q = P; slot0 = 0; S = SELF_PTS; L = a.sup.Lself + (size_t)loc * SELF_PTS * P_NODES;
+  } else if (which == 0) {
+    Q = P - 1;
+    if (Q < 0) { if (!a.closed || nP <= 2) return; Q = nP - 1; }
+    slot0 = SELF_PTS; S = ADJ_PTS; L = a.sup.Ladj + (size_t)1 * ADJ_PTS * P_NODES;
+  } else {
+    Q = P + 1;
+    if (Q >= nP) { if (!a.closed || nP <= 2) return; Q = 0; }
+    slot0 = SELF_PTS + ADJ_PTS; S = ADJ_PTS; L = a.sup.Ladj;
+  }
+  const int Ms = gp.Ms;
+  cd* R = (cd*)smem;                              // [kc][3][NFAM][Ms]
+  double* V = (double*)(R + (size_t)kc * 3 * NFAM * Ms);  // [S][kc][3]
+  for (int t = threadIdx.x; t < S * kc; t += blockDim.x) {
+    int s = t / kc, kk = t % kc;
+    long long pid;
+    support_point(a, i, slot0 + s, &pid);
+    double w = a.sup.W[pid] * L[(size_t)s * P_NODES + chunk * kc + kk];
+    double rs = a.sup.r[pid];
+    V[(s * kc + kk) * 3 + 0] = w * rs * a.sup.rp[pid];
+    V[(s * kc + kk) * 3 + 1] = w * rs;
+    V[(s * kc + kk) * 3 + 2] = w * rs * a.sup.zp[pid];
+  }
+  __syncthreads();
+  const cd* F = a.spec_sup + ((long long)i * NEAR_SLOTS + slot0) * NFAM * Ms;
+  for (int item = threadIdx.x; item < NFAM * Ms; item += blockDim.x) {
+    cd acc[8][3];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+      for (int sg = 0; sg < 3; ++sg) acc[kk][sg] = C(0.0);
+    for (int s = 0; s < S; ++s) {
+      cd v = F[(size_t)s * NFAM * Ms + item];
+      const double* Vs = V + s * kc * 3;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        if (kk < kc) {
+#pragma unroll
+          for (int sg = 0; sg < 3; ++sg) acc[kk][sg] = fma(Vs[kk * 3 + sg], v, acc[kk][sg]);
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+      if (kk < kc)
+#pragma unroll
+        for (int sg = 0; sg < 3; ++sg) R[((size_t)kk * 3 + sg) * NFAM * Ms + item] = acc[kk][sg];
+  }
+  __syncthreads();
+  const int n = 4 * a.N;
+  const double rt = a.geo.r[i], rpt = a.geo.rp[i], zpt = a.geo.zp[i];
+  for (int item = threadIdx.x; item < kc * (gp.M + 1); item += blockDim.x) {
+    int kk = item / (gp.M + 1), m = item % (gp.M + 1);
+    int j = Q * P_NODES + chunk * kc + kk;
+    const cd* Rk = R + (size_t)kk * 3 * NFAM * Ms;
+    auto Rget = [&](int s, int f, int mm) { return Rk[((size_t)s * NFAM + f) * Ms + mm]; };
+    cd blk[4][4];
+    mueller_block(Rget, m, a.ap, rt, rpt, zpt, blk);
+    if (j == i) {
+      blk[0][2] += a.ap.dEM; blk[1][3] += a.ap.dEM;
+      blk[2][0] += a.ap.dHJ; blk[3][1] += a.ap.dHJ;
+    }
+    store_block(a.A, n, m, i, j, blk, a.geo.sw[i] / a.geo.sw[j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stand-alone spectra of arbitrary pairs (used by the modal-kernel entry point).
+__global__ void pair_spectra_kernel(GreenParams gp, const double* __restrict__ pairs, const int* __restrict__ sidx,
+                                    const double* __restrict__ leg, long long n_split, long long npairs,
+                                    const double* __restrict__ cosT, const double* __restrict__ s2T,
+                                    cd* __restrict__ out) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
+  for (long long p = (long long)blockIdx.x * wpb + wib; p < npairs; p += (long long)gridDim.x * wpb) {
+    const double* q = pairs + 4 * p;  // (r_t, z_t, r_t - r_s, z_t - z_s)
+    warp_pair_spectra(gp, q[0], q[2], q[3], sidx[p], leg, n_split, cosT, s2T, W, lane);
+    cd* dst = out + p * NFAM * gp.Ms;
+    for (int t = lane; t < NFAM * gp.Ms; t += 32) dst[t] = W.spec[t];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int warps_per_block(const GreenParams& gp) {
+  int per = green_smem_bytes(gp);
+  int w = (200 * 1024) / per;
+  if (w > 8) w = 8;
+  if (w < 1) w = 1;
+  return w;
+}
+
+static int grid_for(long long units, int wpb) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long need = (units + wpb - 1) / wpb;
+  long long cap = (long long)sms * 8;
+  return (int)(need < cap ? need : cap);
+}
+
+void launch_far_assembly(const BuildArgs& a, cudaStream_t s) {
+  int wpb = warps_per_block(a.gp);
+  int smem = wpb * green_smem_bytes(a.gp);
+  cudaFuncSetAttribute(far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  far_kernel<<<grid_for((long long)a.N * a.N, wpb), wpb * 32, smem, s>>>(a);
+}
+
+void launch_support_spectra(const BuildArgs& a, cudaStream_t s) {
+  int wpb = warps_per_block(a.gp);
+  int smem = wpb * green_smem_bytes(a.gp);
+  cudaFuncSetAttribute(support_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  support_kernel<<<grid_for((long long)a.N * NEAR_SLOTS, wpb), wpb * 32, smem, s>>>(a);
+}
+
+void launch_near_assembly(const BuildArgs& a, cudaStream_t s) {
+  int smem = a.kc * 3 * NFAM * a.gp.Ms * 16 + SELF_PTS * a.kc * 3 * 8;
+  cudaFuncSetAttribute(near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  near_kernel<<<a.N * 3 * (P_NODES / a.kc), 256, smem, s>>>(a);
+}
+
+void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* sidx, const double* leg,
+                         long long n_split, long long npairs, const double* cosT, const double* s2T, cd* out,
+                         cudaStream_t s) {
+  if (npairs <= 0) return;
+  int wpb = warps_per_block(gp);
+  int smem = wpb * green_smem_bytes(gp);
+  cudaFuncSetAttribute(pair_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  pair_spectra_kernel<<<grid_for(npairs, wpb), wpb * 32, smem, s>>>(gp, pairs, sidx, leg, n_split, npairs, cosT,
+                                                                      s2T, out);
+}

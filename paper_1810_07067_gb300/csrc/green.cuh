@@ -1,0 +1,78 @@
+// Modal Green's function evaluation and per-mode assembly (Sections 3-5).
+#pragma once
+#include "cplx.cuh"
+#include "special.cuh"
+
+#define NFAM 9          // spectra per pair (see green.cu)
+#define P_NODES 16      // nodes per panel
+
+struct GreenParams {
+  int M;       // modes 0..M assembled (negative modes follow by reflection)
+  int Ms;      // M + 2 spectral coefficients per family (m = 0..M+1)
+  int nphi;    // azimuthal samples on [0, 2pi)
+  int H;       // nphi/2 + 1 samples on [0, pi]
+  int Mq;      // nphi/2 - 1: bandwidth of the Laplace coefficients
+  KPow kp0, kp1;
+  cd gamma0;   // -(k0^2 - k1^2)/4
+};
+
+// Block coefficients of eq. mullerrep / eq. dualmullrep.
+struct AsmParams {
+  cd k0sq, k1sq;
+  cd aEJ, aHM;          // K-block factors
+  cd cEM0, cEM1;        // E rows, M columns: cEM0 N0 + cEM1 N1
+  cd cHJ0, cHJ1;        // H rows, J columns
+  cd dEM, dHJ;          // identity terms
+};
+
+struct NodeGeom {
+  const double *r, *z, *rp, *zp, *w, *sw;  // [N]; sw = sqrt(w)
+};
+
+struct SupportTable {
+  const double *r, *z, *rp, *zp, *W;  // support points, [n_panels * PTS_PER_PANEL]
+  const double *dr, *dz;              // target - point displacement (own-panel points)
+  const double* Lself;                // [16][SELF_PTS][16]
+  const double* Ladj;                 // [2][ADJ_PTS][16]  (0: shared end -1, 1: shared end +1)
+};
+
+#define SELF_SIDE 164
+#define SELF_PTS (2 * SELF_SIDE)
+#define ADJ_PTS 96
+#define PTS_PER_PANEL (P_NODES * SELF_PTS + 2 * ADJ_PTS)
+#define NEAR_SLOTS (SELF_PTS + 2 * ADJ_PTS)   // support points per target
+
+struct BuildArgs {
+  GreenParams gp;
+  AsmParams ap;
+  NodeGeom geo;
+  SupportTable sup;
+  int N, n_panels, closed;
+  const double* cosT;   // [nphi] cos(2 pi t / nphi)
+  const double* s2T;    // [H] sin^2(pi j / nphi)
+  const int* split_far; // [N*N] split id or -1 (far-panel pairs)
+  const int* split_sup; // [N*NEAR_SLOTS] split id or -1
+  const double* leg;    // Legendre scratch: [(Mq+1) + Ms][n_split] (index-major)
+                        // split pairs are given as (r_t, z_t, r_t - r_s, z_t - z_s)
+  long long n_split;
+  cd* spec_sup;         // [N*NEAR_SLOTS][NFAM][Ms] support spectra scratch
+  cd* A;                // [M+1][n][n] column-major per mode
+  int kc;               // columns per CTA in the near contraction
+};
+
+// shared memory used by one warp of the pair-spectra routine (16-byte multiple)
+HD int green_smem_bytes(const GreenParams& gp) {
+  int b = (NFAM * gp.H + NFAM * gp.Ms) * 16 + (gp.H + gp.Mq + 1) * 8;
+  return (b + 15) & ~15;
+}
+
+// host-side launchers (green.cu)
+void launch_legendre(const double* pairs, long long n_split, int Mq, int Ms, double* leg, cudaStream_t s);
+void launch_far_assembly(const BuildArgs& a, cudaStream_t s);
+void launch_support_spectra(const BuildArgs& a, cudaStream_t s);
+void launch_near_assembly(const BuildArgs& a, cudaStream_t s);
+void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* split_id, const double* leg,
+                         long long n_split, long long npairs, const double* cosT, const double* s2T,
+                         cd* out, cudaStream_t s);
+void upload_series_tables(const SeriesTables& t);
+int green_smem_per_warp(const GreenParams& gp);

@@ -1,0 +1,243 @@
+// Batched complex128 LU (right-looking, blocked by LU_NB columns) and solves.
+//
+// Per block column: (1) the panel is factored by one CTA per matrix with a
+// warp-shuffle argmax for the pivot (largest |a|^2, lowest row on ties);
+// (2) its row interchanges are applied to the other columns; (3) the block
+// row of U is formed by a unit-lower triangular solve; (4) the trailing matrix
+// is updated by a complex FP64 GEMM, batched over all matrices.
+#include <cstdio>
+#include "lu.cuh"
+
+// ---------------------------------------------------------------- panel
+__device__ __forceinline__ void argmax_merge(double& v, int& idx, double v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
+}
+
+__global__ void __launch_bounds__(1024) panel_kernel(cd* __restrict__ A, int n, int k0, int nbk,
+                                                     int* __restrict__ piv, int* __restrict__ info) {
+  const int b = blockIdx.x;
+  cd* M = A + (size_t)b * n * n;
+  int* pv = piv + (size_t)b * n;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  __shared__ cd s_row[LU_NB];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, T = blockDim.x;
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int c = k0 + jj;
+    cd* col = M + (size_t)c * n;
+    double best = -1.0;
+    int bi = n;
+    for (int r = c + tid; r < n; r += T) argmax_merge(best, bi, norm2(col[r]), r);
+    for (int o = 16; o > 0; o >>= 1) {
+      double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(best, bi, v2, i2);
+    }
+    if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      best = (lane < (T >> 5)) ? red_v[lane] : -1.0;
+      bi = (lane < (T >> 5)) ? red_i[lane] : n;
+      for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(best, bi, v2, i2);
+      }
+      if (lane == 0) {
+        s_p = (best > 0.0) ? bi : -1;
+        pv[c] = (best > 0.0) ? bi : c;
+        if (best <= 0.0 && info[b] == 0) info[b] = c + 1;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p >= 0) {
+      if (p != c && tid < nbk) {
+        cd* cc = M + (size_t)(k0 + tid) * n;
+        cd t = cc[c]; cc[c] = cc[p]; cc[p] = t;
+      }
+      __syncthreads();
+      if (tid < nbk) s_row[tid] = M[(size_t)(k0 + tid) * n + c];
+      __syncthreads();
+      const cd inv = C(1.0) / s_row[jj];
+      for (int r = c + 1 + tid; r < n; r += T) {
+        cd l = col[r] * inv;
+        col[r] = l;
+        for (int cc = jj + 1; cc < nbk; ++cc) {
+          cd* dst = M + (size_t)(k0 + cc) * n + r;
+          *dst = *dst - l * s_row[cc];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- swaps
+__global__ void swap_kernel(cd* __restrict__ A, int n, int k0, int nbk, const int* __restrict__ piv) {
+  const int b = blockIdx.y;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nother = n - nbk;
+  if (c >= nother) return;
+  if (c >= k0) c += nbk;  // skip the panel's own columns
+  cd* col = A + (size_t)b * n * n + (size_t)c * n;
+  const int* pv = piv + (size_t)b * n;
+  for (int k = k0; k < k0 + nbk; ++k) {
+    int p = pv[k];
+    if (p != k) { cd t = col[k]; col[k] = col[p]; col[p] = t; }
+  }
+}
+
+// ---------------------------------------------------------------- U12 = L11^{-1} A12
+__global__ void trsm_kernel(cd* __restrict__ A, int n, int k0, int nbk) {
+  const int b = blockIdx.y;
+  cd* M = A + (size_t)b * n * n;
+  __shared__ cd L[LU_NB][LU_NB + 1];
+  for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
+    int r = t % nbk, cc = t / nbk;
+    L[r][cc] = M[(size_t)(k0 + cc) * n + k0 + r];
+  }
+  __syncthreads();
+  int c = k0 + nbk + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  cd* col = M + (size_t)c * n + k0;
+  cd x[LU_NB];
+#pragma unroll
+  for (int r = 0; r < LU_NB; ++r) x[r] = (r < nbk) ? col[r] : C(0.0);
+#pragma unroll
+  for (int k = 0; k < LU_NB; ++k) {
+#pragma unroll
+    for (int r = k + 1; r < LU_NB; ++r) x[r] = x[r] - L[r][k] * x[k];
+  }
+#pragma unroll
+  for (int r = 0; r < LU_NB; ++r)
+    if (r < nbk) col[r] = x[r];
+}
+
+// ---------------------------------------------------------------- trailing update
+// C[i0.., j0..] -= A[i0.., k0..k0+nbk) * A[k0..k0+nbk), j0..], 64x64 tiles,
+// 256 threads, each 4x4 outputs: rows tx + 16a, columns ty + 16b.
+#define GT 64
+__global__ void __launch_bounds__(256) gemm_update_kernel(cd* __restrict__ A, int n, int k0, int nbk) {
+  const int b = blockIdx.z;
+  cd* M = A + (size_t)b * n * n;
+  const int start = k0 + nbk;
+  const int i0 = start + blockIdx.x * GT, j0 = start + blockIdx.y * GT;
+  __shared__ cd As[LU_NB][GT];
+  __shared__ cd Bs[LU_NB][GT];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int t = tid; t < nbk * GT; t += 256) {
+    int r = t % GT, kk = t / GT;
+    int gi = i0 + r;
+    As[kk][r] = (gi < n) ? M[(size_t)(k0 + kk) * n + gi] : C(0.0);
+    int kb = t % nbk, cj = t / nbk;  // B element (row k0+kb, column j0+cj)
+    int gj = j0 + cj;
+    Bs[kb][cj] = (gj < n) ? M[(size_t)gj * n + k0 + kb] : C(0.0);
+  }
+  __syncthreads();
+  cd acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = C(0.0);
+  for (int kk = 0; kk < nbk; ++kk) {
+    cd av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int gj = j0 + ty + 16 * c;
+    if (gj >= n) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int gi = i0 + tx + 16 * a;
+      if (gi < n) {
+        cd* d = M + (size_t)gj * n + gi;
+        *d = *d - acc[a][c];
+      }
+    }
+  }
+}
+
+void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s) {
+  cudaMemsetAsync(info, 0, sizeof(int) * batch, s);
+  for (int k0 = 0; k0 < n; k0 += LU_NB) {
+    int nbk = (n - k0 < LU_NB) ? n - k0 : LU_NB;
+    panel_kernel<<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
+    int nother = n - nbk;
+    if (nother > 0) swap_kernel<<<dim3((nother + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk, piv);
+    int rest = n - k0 - nbk;
+    if (rest > 0) {
+      trsm_kernel<<<dim3((rest + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk);
+      int t = (rest + GT - 1) / GT;
+      gemm_update_kernel<<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- solves
+// One CTA per (factor m, right-hand side, sign); the solution vector lives in
+// shared memory; forward (unit L) then backward (U) substitution with one
+// barrier per column.
+__global__ void __launch_bounds__(1024) solve_kernel(const cd* __restrict__ LU, const int* __restrict__ piv, int n,
+                                                     int M, const double* __restrict__ sw,
+                                                     const cd* __restrict__ rhs, cd* __restrict__ x, int nrhs) {
+  extern __shared__ __align__(16) char smem_raw[];
+  cd* xs = (cd*)smem_raw;
+  const int m = blockIdx.x;        // factor index 0..M
+  const int job = blockIdx.y;      // rhs index; second half: mode -m
+  const int r_idx = job % nrhs;
+  const bool neg = job >= nrhs;
+  if (neg && m == 0) return;
+  const int q = neg ? (M - m) : (M + m);
+  const cd* L = LU + (size_t)m * n * n;
+  const int* pv = piv + (size_t)m * n;
+  const cd* bq = rhs + ((size_t)q * nrhs + r_idx) * n;
+  const int tid = threadIdx.x, T = blockDim.x;
+  for (int r = tid; r < n; r += T) {
+    double sg = (neg && ((r & 3) == 0 || (r & 3) == 3)) ? -1.0 : 1.0;
+    xs[r] = (sg * sw[r]) * bq[r];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < n; ++k) {
+      int p = pv[k];
+      if (p != k) { cd t = xs[k]; xs[k] = xs[p]; xs[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n - 1; ++k) {
+    const cd v = xs[k];
+    const cd* colk = L + (size_t)k * n;
+    for (int r = k + 1 + tid; r < n; r += T) xs[r] = xs[r] - colk[r] * v;
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const cd* colk = L + (size_t)k * n;
+    const cd v = xs[k] / colk[k];
+    for (int r = tid; r < k; r += T) xs[r] = xs[r] - colk[r] * v;
+    __syncthreads();
+    if (tid == 0) xs[k] = v;
+    __syncthreads();
+  }
+  cd* xq = x + ((size_t)q * nrhs + r_idx) * n;
+  for (int r = tid; r < n; r += T) {
+    double sg = (neg && ((r & 3) == 1 || (r & 3) == 2)) ? -1.0 : 1.0;
+    xq[r] = (sg / sw[r]) * xs[r];
+  }
+}
+
+void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
+                    cudaStream_t s) {
+  int smem = n * (int)sizeof(cd);
+  cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  solve_kernel<<<dim3(M + 1, 2 * nrhs), 1024, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+}

@@ -1,0 +1,19 @@
+// Batched dense complex LU with partial pivoting and triangular solves.
+#pragma once
+#include <cuda_runtime.h>
+#include "cplx.cuh"
+
+#define LU_NB 32
+
+// Factor `batch` column-major n x n matrices (stride n*n) in place: P A = L U.
+// piv[b*n + k] = row interchanged with row k (0-based, LAPACK order);
+// info[b] = 0, or k+1 for the first exactly zero pivot column k.
+void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s);
+
+// Solve with factors of modes m = 0..M for right-hand sides of modes -M..M:
+// rhs/x layout [2M+1][nrhs][n] (mode q = m + M); sw[n] = sqrt of the L2 weights
+// (rows scaled by sw, unknowns by 1/sw inside the factors); negative modes use
+// the reflection A_{-m} = D_r A_m D_c with D_r = (-1,1,1,-1), D_c = (1,-1,-1,1)
+// per node.
+void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
+                    cudaStream_t s);

@@ -1,0 +1,692 @@
+// Host side of the C ABI: argument checks, Nystrom rule tables, support-point
+// geometry, pair classification, device memory and the stage launches.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mueller.h"
+#include "green.cuh"
+#include "lu.cuh"
+#include "fields.cuh"
+
+static thread_local std::string g_err;
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess) return fail(MUELLER_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static cd tocd(mueller_c128 a) { return cd{a.re, a.im}; }
+
+// ---------------------------------------------------------------- rules (Section 5)
+// Gauss-Legendre nodes (increasing) and weights on [-1, 1] by Newton's method
+// on the three-term recurrence of P_n.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0); w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1; p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) {
+        p0 = 1.0; p1 = t;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+          p0 = p1; p1 = p2;
+        }
+        dp = n * (t * p1 - p0) / (t * t - 1.0);
+        break;
+      }
+    }
+    x[i] = -t; x[n - 1 - i] = t;
+    double wi = 2.0 / ((1.0 - t * t) * dp * dp);
+    w[i] = wi; w[n - 1 - i] = wi;
+  }
+}
+
+struct Rules {
+  std::vector<double> x16, w16, bary;   // panel nodes, weights, barycentric weights
+  std::vector<double> self_u, self_w;   // reference self rule on [0, 1]
+  std::vector<double> adj_u, adj_w;     // reference adjacent rule on [0, 1]
+};
+
+// 4x4 solve by Gaussian elimination with partial pivoting
+static void solve4(double A[4][4], double b[4]) {
+  for (int k = 0; k < 4; ++k) {
+    int p = k;
+    for (int r = k + 1; r < 4; ++r)
+      if (std::fabs(A[r][k]) > std::fabs(A[p][k])) p = r;
+    for (int c = 0; c < 4; ++c) std::swap(A[k][c], A[p][c]);
+    std::swap(b[k], b[p]);
+    for (int r = k + 1; r < 4; ++r) {
+      double f = A[r][k] / A[k][k];
+      for (int c = k; c < 4; ++c) A[r][c] -= f * A[k][c];
+      b[r] -= f * b[k];
+    }
+  }
+  for (int k = 3; k >= 0; --k) {
+    for (int c = k + 1; c < 4; ++c) b[k] -= A[k][c] * b[c];
+    b[k] /= A[k][k];
+  }
+}
+
+// Reference rule on [0, 1] graded toward 0: intervals [4^-(j+1), 4^-j] with
+// ng Gauss points; innermost [0, 4^-levels] either ng Gauss points or 4 nodes
+// exact for {1, u, log u, u log u}.
+static void graded_rule(int levels, int ng, bool log_inner, std::vector<double>& u, std::vector<double>& w) {
+  std::vector<double> x, wx;
+  gauss_legendre(ng, x, wx);
+  u.clear(); w.clear();
+  for (int j = 0; j < levels; ++j) {
+    double a = std::pow(4.0, -(j + 1)), b = std::pow(4.0, -j);
+    for (int q = 0; q < ng; ++q) {
+      u.push_back(0.5 * (a + b) + 0.5 * (b - a) * x[q]);
+      w.push_back(0.5 * (b - a) * wx[q]);
+    }
+  }
+  double h = std::pow(4.0, -levels);
+  if (log_inner) {
+    std::vector<double> x4, w4;
+    gauss_legendre(4, x4, w4);
+    double V[4][4], mom[4] = {1.0, 0.5, -1.0, -0.25};
+    double xs[4];
+    for (int q = 0; q < 4; ++q) {
+      xs[q] = 0.5 + 0.5 * x4[q];
+      V[0][q] = 1.0; V[1][q] = xs[q]; V[2][q] = std::log(xs[q]); V[3][q] = xs[q] * std::log(xs[q]);
+    }
+    solve4(V, mom);
+    for (int q = 0; q < 4; ++q) { u.push_back(h * xs[q]); w.push_back(h * mom[q]); }
+  } else {
+    for (int q = 0; q < ng; ++q) {
+      u.push_back(0.5 * h + 0.5 * h * x[q]);
+      w.push_back(0.5 * h * wx[q]);
+    }
+  }
+}
+
+static const Rules& rules() {
+  static Rules R;
+  static bool init = false;
+  if (!init) {
+    gauss_legendre(P_NODES, R.x16, R.w16);
+    R.bary.resize(P_NODES);
+    for (int k = 0; k < P_NODES; ++k)
+      R.bary[k] = ((k % 2) ? -1.0 : 1.0) * std::sqrt((1.0 - R.x16[k] * R.x16[k]) * R.w16[k]);
+    graded_rule(10, 16, true, R.self_u, R.self_w);
+    graded_rule(5, 16, false, R.adj_u, R.adj_w);
+    init = true;
+  }
+  return R;
+}
+
+// Lagrange basis at t through the 16 panel nodes (barycentric form).
+static void lagrange_row(const Rules& R, double t, double* L) {
+  for (int k = 0; k < P_NODES; ++k)
+    if (std::fabs(t - R.x16[k]) < 1e-300) {
+      for (int j = 0; j < P_NODES; ++j) L[j] = (j == k) ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int k = 0; k < P_NODES; ++k) {
+    L[k] = R.bary[k] / (t - R.x16[k]);
+    den += L[k];
+  }
+  for (int k = 0; k < P_NODES; ++k) L[k] /= den;
+}
+
+// ---------------------------------------------------------------- setup
+struct Setup {
+  int N = 0, n = 0, nP = 0, closed = 0, M = 0, nphi = 0, formulation = 0, precision = 0;
+  double omega = 0, split_eps = 1e-17, rmax = 0;
+  cd k0{}, k1{}, eps0{}, mu0{}, eps1{}, mu1{};
+  std::vector<double> r, z, rp, zp, w, sw;                  // nodes
+  std::vector<double> sr, sz, srp, szp, sW;                 // support points
+  std::vector<double> sdr, sdz;                             // own-panel: target - point
+  std::vector<double> Lself, Ladj;
+  std::vector<int> split_far, split_sup;
+  std::vector<double> split_pairs;                          // [n_split][4]
+  long long n_far = 0, n_sup = 0;
+  GreenParams gp{};
+  AsmParams ap{};
+  cd sE{}, sH{};
+};
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static cd csqrt_im_nonneg(cd z) {
+  cd s = csqrt_principal(z);
+  if (s.y < 0) s = -s;
+  return s;
+}
+
+static int nphi_needed(int M, double kmax, double rmax, int nphi_req) {
+  double a = 2.0 * kmax * rmax;
+  int Na = (int)std::ceil((a + 10.0 * std::cbrt(a) + 10.0) / 2.0) + 2;
+  int need = 2 * (M + 2 + Na);
+  int v = std::max(16, nphi_req > 0 ? nphi_req : 16);
+  while (v < need) v *= 2;
+  if (!is_pow2(v)) {
+    int p = 16;
+    while (p < v) p *= 2;
+    v = p;
+  }
+  return v;
+}
+
+static void fill_green_params(GreenParams& gp, int M, int nphi, cd k0, cd k1) {
+  gp.M = M; gp.Ms = M + 2; gp.nphi = nphi; gp.H = nphi / 2 + 1; gp.Mq = nphi / 2 - 1;
+  gp.kp0 = kpow(k0); gp.kp1 = kpow(k1);
+  gp.gamma0 = -0.25 * (k0 * k0 - k1 * k1);
+}
+
+// split decision: plain trapezoid aliasing zeta^(nphi-M-1) above eps
+static bool needs_split(double rt, double dr, double dz, int nphi, int M, double eps) {
+  double d2 = dr * dr + dz * dz, B = 2.0 * rt * (rt - dr);
+  double cm1 = d2 / B, cp1 = 2.0 + cm1;
+  double lz = std::log1p(cm1 + std::sqrt(cm1 * cp1));
+  return (double)(nphi - M - 1) * lz < -std::log(eps);
+}
+
+static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M, const mueller_options* op,
+                        Setup& S) {
+  if (!cv || !md || !op) return fail(MUELLER_EINVAL, "null argument");
+  if (cv->n_panels < 1) return fail(MUELLER_EINVAL, "n_panels must be >= 1");
+  if (cv->closed && cv->n_panels < 3) return fail(MUELLER_EINVAL, "closed curves need >= 3 panels");
+  if (!cv->r || !cv->z || !cv->dr || !cv->dz) return fail(MUELLER_EINVAL, "null curve array");
+  if (M < 0 || M > 4096) return fail(MUELLER_EINVAL, "M out of range [0, 4096]");
+  if (op->formulation != 0 && op->formulation != 1) return fail(MUELLER_EINVAL, "formulation must be 0 or 1");
+  if (op->precision != 0) return fail(MUELLER_EINVAL, "precision: only the FP64 path (0) is available");
+  if (!(md->omega > 0.0)) return fail(MUELLER_EINVAL, "omega must be > 0 (the method excludes omega -> 0)");
+  auto ok_body = [](mueller_c128 v) { return v.re > 0.0 && v.im >= 0.0; };
+  auto ok_back = [](mueller_c128 v) { return v.re > 0.0 && v.im == 0.0; };
+  if (!ok_back(md->eps0) || !ok_back(md->mu0)) return fail(MUELLER_EINVAL, "eps0, mu0 must be real and > 0");
+  if (!ok_body(md->eps1) || !ok_body(md->mu1))
+    return fail(MUELLER_EINVAL, "eps1, mu1 need Re > 0 and Im >= 0 (eq. materials)");
+  const Rules& R = rules();
+  S.nP = cv->n_panels; S.N = 16 * S.nP; S.n = 4 * S.N; S.closed = cv->closed ? 1 : 0; S.M = M;
+  S.formulation = op->formulation; S.precision = op->precision;
+  S.split_eps = op->split_eps > 0 ? op->split_eps : 1e-17;
+  S.omega = md->omega;
+  S.eps0 = tocd(md->eps0); S.mu0 = tocd(md->mu0); S.eps1 = tocd(md->eps1); S.mu1 = tocd(md->mu1);
+  S.k0 = md->omega * csqrt_im_nonneg(S.eps0 * S.mu0);
+  S.k1 = md->omega * csqrt_im_nonneg(S.eps1 * S.mu1);
+  const int N = S.N;
+  S.r.assign(cv->r, cv->r + N); S.z.assign(cv->z, cv->z + N);
+  S.rp.resize(N); S.zp.resize(N); S.w.resize(N); S.sw.resize(N);
+  double area = 0.0;
+  S.rmax = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double sp = std::hypot(cv->dr[i], cv->dz[i]);
+    if (!(cv->r[i] > 0.0)) return fail(MUELLER_EINVAL, "curve nodes need r > 0");
+    if (!(sp > 0.0)) return fail(MUELLER_EINVAL, "curve has a zero tangent at a node");
+    S.rp[i] = cv->dr[i] / sp; S.zp[i] = cv->dz[i] / sp;
+    S.w[i] = R.w16[i % P_NODES] * sp;
+    S.sw[i] = std::sqrt(S.w[i]);
+    area += 0.5 * R.w16[i % P_NODES] * (cv->r[i] * cv->dz[i] - cv->z[i] * cv->dr[i]);
+    S.rmax = std::max(S.rmax, cv->r[i]);
+  }
+  if (!(area > 0.0))
+    return fail(MUELLER_EINVAL, "curve must run counterclockwise in (r, z) (outward normal n = (z', -r'))");
+  double kmax = std::max(cabs(S.k0), cabs(S.k1));
+  S.nphi = nphi_needed(M, kmax, S.rmax, op->n_phi);
+  fill_green_params(S.gp, M, S.nphi, S.k0, S.k1);
+  // block coefficients
+  cd iw = C(0.0, S.omega);
+  AsmParams& ap = S.ap;
+  ap.k0sq = S.k0 * S.k0; ap.k1sq = S.k1 * S.k1;
+  if (S.formulation == 0) {
+    ap.aEJ = C(1.0); ap.aHM = C(-1.0);
+    ap.cEM0 = -(iw * S.eps0); ap.cEM1 = iw * S.eps1;
+    ap.cHJ0 = -(iw * S.mu0); ap.cHJ1 = iw * S.mu1;
+    ap.dEM = 0.5 * (iw * (S.eps0 + S.eps1)); ap.dHJ = 0.5 * (iw * (S.mu0 + S.mu1));
+    S.sE = iw * S.eps0; S.sH = iw * S.mu0;
+  } else {
+    ap.aEJ = S.mu0 / S.eps0; ap.aHM = -(S.eps0 / S.mu0);
+    ap.cEM0 = -(iw * S.mu0); ap.cEM1 = iw * S.mu1;
+    ap.cHJ0 = -(iw * S.eps0); ap.cHJ1 = iw * S.eps1;
+    ap.dEM = -0.5 * (iw * (S.mu0 + S.mu1)); ap.dHJ = -0.5 * (iw * (S.eps0 + S.eps1));
+    S.sE = iw * S.mu0; S.sH = iw * S.eps0;
+  }
+  return MUELLER_OK;
+}
+
+// Support points and interpolation tables (eq. eq_nyslike2).
+static void setup_support(const mueller_curve* cv, Setup& S) {
+  const Rules& R = rules();
+  const int ns = (int)R.self_u.size(), na = (int)R.adj_u.size();
+  S.Lself.assign((size_t)P_NODES * SELF_PTS * P_NODES, 0.0);
+  S.Ladj.assign((size_t)2 * ADJ_PTS * P_NODES, 0.0);
+  std::vector<double> tau_self((size_t)P_NODES * SELF_PTS), wt_self((size_t)P_NODES * SELF_PTS);
+  for (int a = 0; a < P_NODES; ++a) {
+    double ti = R.x16[a], Lm = ti + 1.0, Lp = 1.0 - ti;
+    for (int s = 0; s < ns; ++s) {
+      tau_self[a * SELF_PTS + s] = ti - Lm * R.self_u[s];
+      wt_self[a * SELF_PTS + s] = Lm * R.self_w[s];
+      tau_self[a * SELF_PTS + ns + s] = ti + Lp * R.self_u[s];
+      wt_self[a * SELF_PTS + ns + s] = Lp * R.self_w[s];
+    }
+    for (int s = 0; s < SELF_PTS; ++s)
+      lagrange_row(R, tau_self[a * SELF_PTS + s], &S.Lself[((size_t)a * SELF_PTS + s) * P_NODES]);
+  }
+  std::vector<double> tau_adj(2 * ADJ_PTS), wt_adj(2 * ADJ_PTS);
+  for (int s = 0; s < na; ++s) {
+    tau_adj[s] = -1.0 + 2.0 * R.adj_u[s]; wt_adj[s] = 2.0 * R.adj_w[s];
+    tau_adj[ADJ_PTS + s] = 1.0 - 2.0 * R.adj_u[s]; wt_adj[ADJ_PTS + s] = 2.0 * R.adj_w[s];
+  }
+  for (int s = 0; s < 2 * ADJ_PTS; ++s) lagrange_row(R, tau_adj[s], &S.Ladj[(size_t)s * P_NODES]);
+  const size_t npts = (size_t)S.nP * PTS_PER_PANEL;
+  S.sr.resize(npts); S.sz.resize(npts); S.srp.resize(npts); S.szp.resize(npts); S.sW.resize(npts);
+  S.sdr.assign(npts, 0.0); S.sdz.assign(npts, 0.0);
+  for (int Q = 0; Q < S.nP; ++Q) {
+    const double* r = cv->r + Q * P_NODES;
+    const double* z = cv->z + Q * P_NODES;
+    const double* dr = cv->dr + Q * P_NODES;
+    const double* dz = cv->dz + Q * P_NODES;
+    for (int t = 0; t < PTS_PER_PANEL; ++t) {
+      const double* L;
+      double wt;
+      if (t < P_NODES * SELF_PTS) { L = &S.Lself[(size_t)t * P_NODES]; wt = wt_self[t]; }
+      else { L = &S.Ladj[(size_t)(t - P_NODES * SELF_PTS) * P_NODES]; wt = wt_adj[t - P_NODES * SELF_PTS]; }
+      double vr = 0, vz = 0, vdr = 0, vdz = 0;
+      for (int k = 0; k < P_NODES; ++k) {
+        vr += L[k] * r[k]; vz += L[k] * z[k]; vdr += L[k] * dr[k]; vdz += L[k] * dz[k];
+      }
+      double sp = std::hypot(vdr, vdz);
+      size_t id = (size_t)Q * PTS_PER_PANEL + t;
+      S.sr[id] = vr; S.sz[id] = vz; S.srp[id] = vdr / sp; S.szp[id] = vdz / sp; S.sW[id] = wt * sp;
+      if (t < P_NODES * SELF_PTS) {
+        // own-panel point of target a: x_t - x_s = -sum_{k != a} L_k(tau_s) (x_k - x_a)
+        int a = t / SELF_PTS;
+        double ddr = 0.0, ddz = 0.0;
+        for (int k = 0; k < P_NODES; ++k) {
+          if (k == a) continue;
+          ddr -= L[k] * (r[k] - r[a]);
+          ddz -= L[k] * (z[k] - z[a]);
+        }
+        S.sdr[id] = ddr; S.sdz[id] = ddz;
+      }
+    }
+  }
+}
+
+static bool near_panels_h(int Pi, int Pj, int nP, int closed) {
+  int d = Pi - Pj;
+  if (d >= -1 && d <= 1) return true;
+  if (closed && nP > 2 && (d == nP - 1 || d == -(nP - 1))) return true;
+  return false;
+}
+
+static long long support_pid(const Setup& S, int i, int slot) {
+  int P = i / P_NODES, loc = i % P_NODES;
+  if (slot < SELF_PTS) return (long long)P * PTS_PER_PANEL + loc * SELF_PTS + slot;
+  if (slot < SELF_PTS + ADJ_PTS) {
+    int Q = P - 1;
+    if (Q < 0) { if (!S.closed) return -1; Q = S.nP - 1; }
+    return (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + ADJ_PTS + (slot - SELF_PTS);
+  }
+  int Q = P + 1;
+  if (Q >= S.nP) { if (!S.closed) return -1; Q = 0; }
+  return (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + (slot - SELF_PTS - ADJ_PTS);
+}
+
+static void setup_pairs(Setup& S) {
+  const int N = S.N;
+  S.split_far.assign((size_t)N * N, -1);
+  S.split_sup.assign((size_t)N * NEAR_SLOTS, -1);
+  S.split_pairs.clear();
+  long long id = 0;
+  S.n_far = 0; S.n_sup = 0;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      if (near_panels_h(i / P_NODES, j / P_NODES, S.nP, S.closed)) continue;
+      ++S.n_far;
+      double dr = S.r[i] - S.r[j], dz = S.z[i] - S.z[j];
+      if (needs_split(S.r[i], dr, dz, S.nphi, S.M, S.split_eps)) {
+        S.split_far[(size_t)i * N + j] = (int)id++;
+        S.split_pairs.insert(S.split_pairs.end(), {S.r[i], S.z[i], dr, dz});
+      }
+    }
+  for (int i = 0; i < N; ++i)
+    for (int slot = 0; slot < NEAR_SLOTS; ++slot) {
+      long long pid = support_pid(S, i, slot);
+      if (pid < 0) continue;
+      ++S.n_sup;
+      double dr, dz;
+      if (slot < SELF_PTS) { dr = S.sdr[pid]; dz = S.sdz[pid]; }
+      else { dr = S.r[i] - S.sr[pid]; dz = S.z[i] - S.sz[pid]; }
+      if (needs_split(S.r[i], dr, dz, S.nphi, S.M, S.split_eps)) {
+        S.split_sup[(size_t)i * NEAR_SLOTS + slot] = (int)id++;
+        S.split_pairs.insert(S.split_pairs.end(), {S.r[i], S.z[i], dr, dz});
+      }
+    }
+}
+
+// ---------------------------------------------------------------- device staging
+struct DevBuf {
+  std::vector<void*> ptrs;
+  ~DevBuf() { for (void* p : ptrs) cudaFree(p); }
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  template <class T>
+  cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t s) {
+    cudaError_t e = alloc(p, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  }
+};
+
+static std::vector<double> cos_table(int nphi) {
+  std::vector<double> c(nphi);
+  for (int t = 0; t < nphi; ++t) c[t] = std::cos(2.0 * M_PI * t / nphi);
+  return c;
+}
+static std::vector<double> s2_table(int nphi) {
+  std::vector<double> s(nphi / 2 + 1);
+  for (int j = 0; j <= nphi / 2; ++j) {
+    double v = std::sin(M_PI * j / nphi);
+    s[j] = v * v;
+  }
+  return s;
+}
+
+static void ensure_tables() {
+  static bool done = false;
+  if (!done) {
+    SeriesTables t;
+    fill_series_tables(&t);
+    upload_series_tables(t);
+    done = true;
+  }
+}
+
+struct Timer {
+  cudaEvent_t e[6];
+  int n = 0;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) { for (auto& x : e) cudaEventCreate(&x); }
+  ~Timer() { for (auto& x : e) cudaEventDestroy(x); }
+  void mark() { cudaEventRecord(e[n++], s); }
+  double ms(int a, int b) { float v = 0; cudaEventElapsedTime(&v, e[a], e[b]); return v; }
+};
+
+// Assemble modes 0..M into A_dev (column-major per mode, L2-weighted).
+static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st, DevBuf& keep,
+                         double** d_geo_out) {
+  ensure_tables();
+  DevBuf tmp;
+  BuildArgs a{};
+  a.gp = S.gp; a.ap = S.ap; a.N = S.N; a.n_panels = S.nP; a.closed = S.closed;
+  double *dr_, *dz_, *drp, *dzp, *dw, *dsw;
+  CK(keep.upload(&dr_, S.r, s)); CK(keep.upload(&dz_, S.z, s)); CK(keep.upload(&drp, S.rp, s));
+  CK(keep.upload(&dzp, S.zp, s)); CK(keep.upload(&dw, S.w, s)); CK(keep.upload(&dsw, S.sw, s));
+  a.geo = NodeGeom{dr_, dz_, drp, dzp, dw, dsw};
+  if (d_geo_out) { d_geo_out[0] = dr_; d_geo_out[1] = dz_; d_geo_out[2] = drp; d_geo_out[3] = dzp;
+                   d_geo_out[4] = dw; d_geo_out[5] = dsw; }
+  double *ssr, *ssz, *ssrp, *sszp, *ssW, *sLs, *sLa, *dcos, *ds2, *dpairs, *dleg, *ssdr, *ssdz;
+  int *dsf, *dss;
+  CK(tmp.upload(&ssr, S.sr, s)); CK(tmp.upload(&ssz, S.sz, s)); CK(tmp.upload(&ssrp, S.srp, s));
+  CK(tmp.upload(&sszp, S.szp, s)); CK(tmp.upload(&ssW, S.sW, s));
+  CK(tmp.upload(&ssdr, S.sdr, s)); CK(tmp.upload(&ssdz, S.sdz, s));
+  CK(tmp.upload(&sLs, S.Lself, s)); CK(tmp.upload(&sLa, S.Ladj, s));
+  CK(tmp.upload(&dcos, cos_table(S.nphi), s)); CK(tmp.upload(&ds2, s2_table(S.nphi), s));
+  CK(tmp.upload(&dsf, S.split_far, s)); CK(tmp.upload(&dss, S.split_sup, s));
+  CK(tmp.upload(&dpairs, S.split_pairs, s));
+  const long long n_split = (long long)S.split_pairs.size() / 4;
+  const int Ms = S.gp.Ms, Mq = S.gp.Mq;
+  if (tmp.alloc(&dleg, (size_t)(Mq + 1 + Ms) * n_split) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "Legendre scratch");
+  cd* dspec;
+  if (tmp.alloc(&dspec, (size_t)S.N * NEAR_SLOTS * NFAM * Ms) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "support spectra scratch");
+  a.sup = SupportTable{ssr, ssz, ssrp, sszp, ssW, ssdr, ssdz, sLs, sLa};
+  a.cosT = dcos; a.s2T = ds2; a.split_far = dsf; a.split_sup = dss; a.leg = dleg; a.n_split = n_split;
+  a.spec_sup = dspec; a.A = A_dev;
+  int kc = 8;
+  while (kc > 1 && kc * 3 * NFAM * Ms * 16 + SELF_PTS * kc * 3 * 8 > 200 * 1024) kc /= 2;
+  a.kc = kc;
+  Timer T(s);
+  T.mark();
+  launch_legendre(dpairs, n_split, Mq, Ms, dleg, s);
+  T.mark();
+  launch_far_assembly(a, s);
+  T.mark();
+  launch_support_spectra(a, s);
+  T.mark();
+  launch_near_assembly(a, s);
+  T.mark();
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    st->ms_legendre = T.ms(0, 1); st->ms_far = T.ms(1, 2); st->ms_support = T.ms(2, 3); st->ms_near = T.ms(3, 4);
+    st->n_phi_used = S.nphi; st->n_split_pairs = n_split; st->n_far_pairs = S.n_far; st->n_support_pairs = S.n_sup;
+  }
+  return MUELLER_OK;
+}
+
+// ---------------------------------------------------------------- context
+struct mueller_ctx {
+  Setup S;
+  DevBuf keep;
+  double* geo[6] = {nullptr};  // r, z, rp, zp, w, sw on the device
+  cd* A = nullptr;             // factors [M+1][n][n]
+  int* piv = nullptr;
+  int* info = nullptr;
+  mueller_stats st{};
+};
+
+extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* media, int M,
+                             const mueller_options* opts, void* stream, mueller_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(MUELLER_EINVAL, "null output pointer");
+  *out = nullptr;
+  mueller_ctx* c = new mueller_ctx();
+  int rc = setup_inputs(curve, media, M, opts, c->S);
+  if (rc) { delete c; return rc; }
+  setup_support(curve, c->S);
+  setup_pairs(c->S);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = c->S.n;
+  size_t bytes = (size_t)(M + 1) * n * n * sizeof(cd);
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  if (bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
+  if (c->keep.alloc(&c->A, (size_t)(M + 1) * n * n) != cudaSuccess ||
+      c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess) {
+    delete c;
+    return fail(MUELLER_ENOMEM, "factor allocation");
+  }
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+  cudaEventRecord(e0, s);
+  rc = assemble_core(c->S, c->A, s, &c->st, c->keep, c->geo);
+  if (rc) { delete c; return rc; }
+  cudaEventRecord(e1, s);
+  lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s);
+  cudaEventRecord(e2, s);
+  cudaError_t err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) { delete c; return fail(MUELLER_ECUDA, cudaGetErrorString(err)); }
+  float a = 0, b = 0;
+  cudaEventElapsedTime(&a, e0, e1); cudaEventElapsedTime(&b, e1, e2);
+  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+  c->st.ms_lu = b; c->st.ms_build = a + b;
+  std::vector<int> info(M + 1);
+  cudaMemcpy(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost);
+  c->st.singular_mode = -1; c->st.singular_column = -1;
+  for (int m = 0; m <= M; ++m)
+    if (info[m]) { c->st.singular_mode = m; c->st.singular_column = info[m] - 1; break; }
+  c->st.device_bytes = bytes;
+  *out = c;
+  if (c->st.singular_mode >= 0) return fail(MUELLER_ESINGULAR, "exact zero pivot");
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_assemble(const mueller_curve* curve, const mueller_media* media, int M,
+                                const mueller_options* opts, mueller_c128* A_dev, void* stream) {
+  g_err.clear();
+  if (!A_dev) return fail(MUELLER_EINVAL, "null matrix buffer");
+  Setup S;
+  int rc = setup_inputs(curve, media, M, opts, S);
+  if (rc) return rc;
+  setup_support(curve, S);
+  setup_pairs(S);
+  DevBuf keep;
+  return assemble_core(S, (cd*)A_dev, (cudaStream_t)stream, nullptr, keep, nullptr);
+}
+
+extern "C" int mueller_solve(mueller_ctx* c, const mueller_c128* rhs_dev, int nrhs, mueller_c128* x_dev,
+                             double* backward_err, void* stream) {
+  g_err.clear();
+  if (!c || !rhs_dev || !x_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid solve arguments");
+  if ((const void*)rhs_dev == (const void*)x_dev) return fail(MUELLER_EINVAL, "rhs and x must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  lu_solve_modes(c->A, c->piv, c->S.n, c->S.M, c->geo[5], (const cd*)rhs_dev, (cd*)x_dev, nrhs, s);
+  cudaEventRecord(e1, s);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(MUELLER_ECUDA, cudaGetErrorString(err));
+  c->st.ms_solve = ms;
+  if (backward_err)
+    for (int q = 0; q < (2 * c->S.M + 1) * nrhs; ++q) backward_err[q] = -1.0;  // not computed on the FP64 path
+  return MUELLER_OK;
+}
+
+static int n_theta_for(const Setup& S) {
+  return 2 * S.M + 2 * (int)std::ceil(cabs(S.k0) * S.rmax) + 64;
+}
+
+extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const double* pols, int nrhs,
+                                     mueller_c128* rhs_dev, void* stream) {
+  g_err.clear();
+  if (!c || !dirs || !pols || !rhs_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid rhs arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf tmp;
+  double *dd, *dp;
+  std::vector<double> vd(dirs, dirs + 3 * nrhs), vp(pols, pols + 3 * nrhs);
+  CK(tmp.upload(&dd, vd, s)); CK(tmp.upload(&dp, vp, s));
+  FieldGeom g{c->geo[0], c->geo[1], c->geo[2], c->geo[3], c->geo[4], c->S.N};
+  launch_rhs_planewave(g, c->S.M, c->S.k0, c->S.omega, c->S.mu0, c->S.sE, c->S.sH, dd, dp, nrhs, n_theta_for(c->S),
+                       (cd*)rhs_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* dirs_dev,
+                                 int ndir, mueller_c128* E_dev, void* stream) {
+  g_err.clear();
+  if (!c || !x_dev || !dirs_dev || !E_dev || nrhs < 1 || ndir < 1) return fail(MUELLER_EINVAL, "invalid far-field arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int nth = n_theta_for(c->S);
+  DevBuf tmp;
+  cd* cur;
+  if (tmp.alloc(&cur, (size_t)nrhs * c->S.N * nth * 4) != cudaSuccess) return fail(MUELLER_ENOMEM, "ring buffer");
+  FieldGeom g{c->geo[0], c->geo[1], c->geo[2], c->geo[3], c->geo[4], c->S.N};
+  launch_far_field(g, c->S.M, c->S.k0, c->S.omega, c->S.eps0, (const cd*)x_dev, nrhs, dirs_dev, ndir, nth, cur,
+                   (cd*)E_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_modal_kernels(const double* pairs_host, long long npairs, mueller_c128 k0, mueller_c128 k1,
+                                     int M, int n_phi, double split_eps, mueller_c128* out_dev, void* stream) {
+  g_err.clear();
+  if (!pairs_host || !out_dev || npairs < 0 || M < 0) return fail(MUELLER_EINVAL, "invalid kernel arguments");
+  if (npairs == 0) return MUELLER_OK;
+  if (k0.im < 0 || k1.im < 0) return fail(MUELLER_EINVAL, "wavenumbers need Im k >= 0");
+  double rmax = 0.0;
+  for (long long p = 0; p < npairs; ++p) {
+    if (!(pairs_host[4 * p] > 0.0) || !(pairs_host[4 * p + 2] > 0.0)) return fail(MUELLER_EINVAL, "pairs need r > 0");
+    double dr = pairs_host[4 * p] - pairs_host[4 * p + 2], dz = pairs_host[4 * p + 1] - pairs_host[4 * p + 3];
+    if (dr == 0.0 && dz == 0.0) return fail(MUELLER_EINVAL, "coincident target and source");
+    rmax = std::max(rmax, std::max(pairs_host[4 * p], pairs_host[4 * p + 2]));
+  }
+  ensure_tables();
+  double eps = split_eps > 0 ? split_eps : 1e-17;
+  int nphi = nphi_needed(M, std::max(cabs(tocd(k0)), cabs(tocd(k1))), rmax, n_phi);
+  GreenParams gp{};
+  fill_green_params(gp, M, nphi, tocd(k0), tocd(k1));
+  std::vector<int> sid(npairs, -1);
+  std::vector<double> sp, vp(4 * npairs);
+  long long ns = 0;
+  for (long long p = 0; p < npairs; ++p) {
+    const double* q = pairs_host + 4 * p;
+    double* v = &vp[4 * p];
+    v[0] = q[0]; v[1] = q[1]; v[2] = q[0] - q[2]; v[3] = q[1] - q[3];  // target, target - source
+    if (needs_split(v[0], v[2], v[3], nphi, M, eps)) {
+      sid[p] = (int)ns++;
+      sp.insert(sp.end(), v, v + 4);
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf tmp;
+  double *dpairs, *dsp, *dleg, *dcos, *ds2;
+  int* dsid;
+  CK(tmp.upload(&dpairs, vp, s)); CK(tmp.upload(&dsp, sp, s)); CK(tmp.upload(&dsid, sid, s));
+  CK(tmp.upload(&dcos, cos_table(nphi), s)); CK(tmp.upload(&ds2, s2_table(nphi), s));
+  if (tmp.alloc(&dleg, (size_t)(gp.Mq + 1 + gp.Ms) * ns) != cudaSuccess) return fail(MUELLER_ENOMEM, "scratch");
+  launch_legendre(dsp, ns, gp.Mq, gp.Ms, dleg, s);
+  launch_pair_spectra(gp, dpairs, dsid, dleg, ns, npairs, dcos, ds2, (cd*)out_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_lu_batched(mueller_c128* A_dev, int n, int batch, int* piv_dev, int* info_dev, void* stream) {
+  g_err.clear();
+  if (!A_dev || !piv_dev || !info_dev || n < 1 || batch < 1) return fail(MUELLER_EINVAL, "invalid LU arguments");
+  lu_factor_batched((cd*)A_dev, n, batch, piv_dev, info_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return MUELLER_OK;
+}
+
+extern "C" size_t mueller_footprint_bytes(int N, int M) {
+  return (size_t)16 * (size_t)(4 * N) * (size_t)(4 * N) * (size_t)(2 * M + 1);
+}
+
+extern "C" int mueller_stats_get(const mueller_ctx* c, mueller_stats* out) {
+  if (!c || !out) return fail(MUELLER_EINVAL, "null argument");
+  *out = c->st;
+  return MUELLER_OK;
+}
+
+extern "C" void mueller_destroy(mueller_ctx* c) { delete c; }
+
+extern "C" const char* mueller_strerror(int status) {
+  switch (status) {
+    case MUELLER_OK: return "ok";
+    case MUELLER_EINVAL: return "invalid argument";
+    case MUELLER_ENOMEM: return "out of memory";
+    case MUELLER_ESINGULAR: return "exact zero pivot";
+    case MUELLER_ENOCONV: return "iterative refinement did not converge";
+    case MUELLER_ETIMEOUT: return "device-side wait timed out";
+    case MUELLER_ECUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* mueller_last_error(void) { return g_err.c_str(); }
