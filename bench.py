@@ -1,0 +1,236 @@
+"""Benchmark: modal assemble + solve on one body of revolution per GPU.
+
+One step = mueller_build (modal Green's functions, assembly and LU of modes
+0..M) + mueller_solve for all plane waves of the workload.  Default workload:
+finite cylinder radius 1, height 2, edge-graded panels (N = 576 nodes, system
+2304 x 2304 complex128 per mode), modes -64..64, 256 azimuthal samples,
+k0 = 5, k1 = 7.5 + 0.01i, 8 incidence angles x 2 polarisations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank solves its own copy of the body (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table); DFMA loop measured 1.19
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        return subprocess.Popen(cmd, stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def _clock_summary(path, gpu_index):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            sm.append(float(f[1])); mx.append(float(f[2]))
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+    except Exception:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons)}
+
+
+def _oracle_baseline(cfg, budget_s=25.0):
+    """The oracle (as it stands) on a bounded sample of the workload, scaled to
+    one step: assembly of two target rows for all 2M+1 modes, one naive LU of
+    a full-size mode matrix (the sample's time scales by N rows and 2M+1 modes)."""
+    from oracle import system, linalg
+    N, M, n = cfg.N, cfg.M, 4 * cfg.N
+    rows = [N // 6, N // 2]
+    t0 = time.perf_counter()
+    system.assemble(cfg.curve, cfg.media, M, rows=rows)
+    t_rows = (time.perf_counter() - t0) / len(rows)
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + n * np.eye(n)
+    t0 = time.perf_counter()
+    LU, piv = linalg.lu_factor(A)
+    t_lu = time.perf_counter() - t0
+    b = rng.standard_normal((n, len(cfg.waves))) + 0j
+    t0 = time.perf_counter()
+    linalg.lu_solve(LU, piv, b)
+    t_solve = time.perf_counter() - t0
+    total = t_rows * N + (t_lu + t_solve) * (2 * M + 1)
+    sample = (f"oracle assembly of {len(rows)} of {N} target rows (all {2 * M + 1} modes) and one naive LU + "
+              f"{len(cfg.waves)}-rhs solve of a {n}x{n} mode; scaled by {N} rows and {2 * M + 1} modes")
+    return total, sample, time.perf_counter()
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    vals = []
+    sample = ""
+    for _ in range(args.warmup_ref):
+        pass
+    for _ in range(max(1, args.steps_ref)):
+        v, sample, _ = _oracle_baseline(cfg)
+        vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": len(vals), "warmup": 0, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": _config(cfg),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "modal assemble+solve time (mueller_build + mueller_solve), FP64 GPU path"
+
+
+def _config(cfg):
+    return {"workload": f"{cfg.name}: finite cylinder R=1 H=2, edge-graded panels, N={cfg.N} nodes "
+                        f"(system {4 * cfg.N}x{4 * cfg.N} c128 per mode), modes -{cfg.M}..{cfg.M}, "
+                        f"n_phi={cfg.n_phi}, k0=5, k1=7.5+0.01i, {len(cfg.waves)} plane waves",
+            "precision": "fp64", "l2_flush": "inputs larger than L2 (5.5 GB of factors per step)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.steps_ref = args.steps
+    args.warmup_ref = args.warmup
+    import workloads as W
+    cfg = W.config_cylinder(7)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import paper_1810_07067_gb300 as mb
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    M, n = cfg.M, 4 * cfg.N
+    nrhs = len(cfg.waves)
+    dirs = np.array([w.d for w in cfg.waves]); pols = np.array([w.e for w in cfg.waves])
+    opts = mb.Options(n_phi=cfg.n_phi)
+    rhs = torch.zeros((2 * M + 1, nrhs, n), dtype=torch.complex128, device=dev)
+    x = torch.zeros_like(rhs)
+    ctx0 = mb.build(cfg.curve, cfg.media, M, opts)
+    ctx0.rhs_planewave(dirs, pols, rhs)
+    ctx0.close()
+
+    def step():
+        ctx = mb.build(cfg.curve, cfg.media, M, opts)
+        ctx.solve(rhs, x)
+        st = ctx.stats()
+        ctx.close()
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f"clocks_rank{rank}.csv")
+    sampler = _clock_sampler(clk_path)
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    dev_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    # end to end through the public API from host inputs: build from host
+    # curve arrays, plane-wave data from host directions, currents back to pinned host memory
+    x_host = torch.empty((2 * M + 1, nrhs, n), dtype=torch.complex128, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx = mb.build(cfg.curve, cfg.media, M, opts)
+        ctx.rhs_planewave(dirs, pols, rhs)
+        ctx.solve(rhs, x)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        ctx.close()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clock_summary(clk_path, local)
+    t = torch.tensor([dev_s, e2e_s], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_s, e2e_s = t.tolist()
+    if rank == 0:
+        st = stats[-1]
+        gemm_tflops = st["lu_gemm_flops"] / (st["ms_lu_gemm"] * 1e-3) / 1e12
+        launches = st["launches"] + st["solve_launches"]
+        h2d = 8 * 4 * cfg.N + 8 * 6 * nrhs
+        d2h = 16 * (2 * M + 1) * nrhs * n
+        line = {"metric": METRIC, "value": dev_s, "unit": "s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_s * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)", "data": "synthetic",
+                "config": _config(cfg),
+                "bodies_per_s": ws / dev_s,
+                "stages_ms": {k: round(st[k], 3) for k in ("ms_legendre", "ms_far", "ms_support", "ms_near",
+                                                           "ms_lu", "ms_lu_gemm", "ms_solve")},
+                "roofline": {"bound": "alu", "kernel": "gemm_update_kernel (LU trailing update, complex FP64)",
+                             "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": gemm_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                             "peak_source": "nominal FP64 of the profiling recipe (no FP64 entry in "
+                                            "MEASURED_PEAKS.json); a DFMA register loop measured 1.19"},
+                "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches * args.steps,
+                "clocks": clocks}
+        if ws == 1 and not args.no_cpu_baseline:
+            v, sample, _ = _oracle_baseline(cfg)
+            line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

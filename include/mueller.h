@@ -94,6 +94,11 @@ typedef struct {
   int singular_mode;         /* first mode with a zero pivot, or -1          */
   int singular_column;
   size_t device_bytes;       /* memory held by the context                   */
+  double ms_lu_gemm;         /* device time of the LU trailing-update launches */
+  double lu_gemm_flops;      /* their algorithmic flops (8 per complex FMA)  */
+  int lu_gemm_launches;
+  int launches;              /* kernel launches of the last build            */
+  int solve_launches;        /* kernel launches of the last solve            */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;

@@ -120,14 +120,16 @@ def _segments_J(J: int, M: int):
     return np.array(pts)
 
 
-def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64, disp=None):
+def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64, disp=None, return_lo=False):
     """Spectra F[pair, f, m] (f = 0..8, m = 0..M+1) for arrays of pairs.
 
     ``disp = (dr, dz)`` optionally gives the displacements r_t - r_s, z_t - z_s
     directly (used for support points next to the target, where they are
     known more accurately than the difference of absolute coordinates).
     Pairs sharing the same number of graded levels are integrated together
-    on the same composite rule."""
+    on the same composite rule.  With ``return_lo`` the 24-point results are
+    returned too (their difference from the 32-point ones is the oracle's own
+    noise level)."""
     rt, zt, rs, zs = (np.atleast_1d(np.asarray(a, float)) for a in (rt, zt, rs, zs))
     rt, zt, rs, zs = np.broadcast_arrays(rt, zt, rs, zs)
     if disp is None:
@@ -136,6 +138,7 @@ def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64, d
         dr, dz = np.broadcast_arrays(*(np.atleast_1d(np.asarray(a, float)) for a in disp))
     n = rt.size
     out = np.empty((n, 9, M + 2), dtype=complex)
+    out_lo = np.empty((n, 9, M + 2), dtype=complex) if return_lo else None
     s = np.sqrt((dr ** 2 + dz ** 2) / (rt * (rt - dr)))
     J = np.array([_levels(max(v, 1e-300)) for v in s])
     m = np.arange(M + 2)
@@ -158,7 +161,9 @@ def modal_families_batch(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12, chunk=64, d
             if err > check_tol:
                 raise RuntimeError(f"azimuthal quadrature not converged: {err:.2e}")
             out[sel] = hi.transpose(1, 0, 2)
-    return out
+            if return_lo:
+                out_lo[sel] = lo.transpose(1, 0, 2)
+    return (out, out_lo) if return_lo else out
 
 
 def modal_families(rt, zt, rs, zs, k0, k1, M, check_tol=1e-12):

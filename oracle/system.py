@@ -226,10 +226,13 @@ def weight_matrix(A, sw):
     return A * sw[None, :, None] / sw[None, None, :]
 
 
-def block(curve, media, M: int, i: int, j: int, formulation: int = 0, modes=None):
+def block(curve, media, M: int, i: int, j: int, formulation: int = 0, modes=None, noise=False):
     """The 4x4 blocks A_m[4i:4i+4, 4j:4j+4] (unweighted) for the given modes,
     computed for this one (target node, column node) pair: the source panel's
-    support points if it is near the target's panel, else the single node."""
+    support points if it is near the target's panel, else the single node.
+
+    With ``noise`` also returns |block(32-point spectra) - block(24-point
+    spectra)|, the oracle's own noise level for each entry."""
     geo = node_geometry(curve)
     k0, k1 = wavenumbers(media)
     co = coefficients(media, formulation)
@@ -245,17 +248,27 @@ def block(curve, media, M: int, i: int, j: int, formulation: int = 0, modes=None
     else:
         rs, zs, rps, zps, W, L, disp = sup
         Lk = L[:, kloc]
-    F = modal_families_batch(rt, zt, rs, zs, k0, k1, M, disp=disp)
-    N0, N1, KD = operator_blocks(F, rs, rps, zps, rt, rpt, zpt, k0, k1, ms)
+    F, F_lo = modal_families_batch(rt, zt, rs, zs, k0, k1, M, disp=disp, return_lo=True)
     om = media.omega
     x0, x1 = co["x"]; y0, y1 = co["y"]
-    blk = np.zeros(N0.shape[:2] + (4, 4), dtype=complex)
-    blk[..., 0:2, 0:2] = co["aEJ"] * KD
-    blk[..., 0:2, 2:4] = -1j * om * (x0 * N0 - x1 * N1)
-    blk[..., 2:4, 0:2] = -1j * om * (y0 * N0 - y1 * N1)
-    blk[..., 2:4, 2:4] = co["aHM"] * KD
-    out = np.einsum("s,s,sqab->qab", W, Lk, blk)
+
+    def contract(Fv):
+        N0, N1, KD = operator_blocks(Fv, rs, rps, zps, rt, rpt, zpt, k0, k1, ms)
+        blk = np.zeros(N0.shape[:2] + (4, 4), dtype=complex)
+        blk[..., 0:2, 0:2] = co["aEJ"] * KD
+        blk[..., 0:2, 2:4] = -1j * om * (x0 * N0 - x1 * N1)
+        blk[..., 2:4, 0:2] = -1j * om * (y0 * N0 - y1 * N1)
+        blk[..., 2:4, 2:4] = co["aHM"] * KD
+        return np.einsum("s,s,sqab->qab", W, Lk, blk)
+
+    out = contract(F)
     if i == j:
         out[:, 0, 2] += co["dEM"]; out[:, 1, 3] += co["dEM"]
         out[:, 2, 0] += co["dHJ"]; out[:, 3, 1] += co["dHJ"]
+    if noise:
+        lo = contract(F_lo)
+        if i == j:
+            lo[:, 0, 2] += co["dEM"]; lo[:, 1, 3] += co["dEM"]
+            lo[:, 2, 0] += co["dHJ"]; lo[:, 3, 1] += co["dHJ"]
+        return out, np.abs(out - lo)
     return out

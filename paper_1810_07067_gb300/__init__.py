@@ -48,7 +48,9 @@ class Stats(ct.Structure):
                 ("ms_near", ct.c_double), ("ms_lu", ct.c_double), ("ms_build", ct.c_double),
                 ("ms_solve", ct.c_double), ("n_phi_used", ct.c_int), ("n_split_pairs", ct.c_longlong),
                 ("n_far_pairs", ct.c_longlong), ("n_support_pairs", ct.c_longlong), ("singular_mode", ct.c_int),
-                ("singular_column", ct.c_int), ("device_bytes", ct.c_size_t)]
+                ("singular_column", ct.c_int), ("device_bytes", ct.c_size_t), ("ms_lu_gemm", ct.c_double),
+                ("lu_gemm_flops", ct.c_double), ("lu_gemm_launches", ct.c_int), ("launches", ct.c_int),
+                ("solve_launches", ct.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

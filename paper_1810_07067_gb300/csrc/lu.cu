@@ -6,6 +6,7 @@
 // row of U is formed by a unit-lower triangular solve; (4) the trailing matrix
 // is updated by a complex FP64 GEMM, batched over all matrices.
 #include <cstdio>
+#include <vector>
 #include "lu.cuh"
 
 // ---------------------------------------------------------------- panel
@@ -167,77 +168,192 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(cd* __restrict__ A, in
   }
 }
 
-void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s) {
+void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
   cudaMemsetAsync(info, 0, sizeof(int) * batch, s);
+  std::vector<cudaEvent_t> ev;
+  int launches = 0;
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     int nbk = (n - k0 < LU_NB) ? n - k0 : LU_NB;
     panel_kernel<<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
+    ++launches;
     int nother = n - nbk;
-    if (nother > 0) swap_kernel<<<dim3((nother + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk, piv);
+    if (nother > 0) { swap_kernel<<<dim3((nother + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk, piv); ++launches; }
     int rest = n - k0 - nbk;
     if (rest > 0) {
       trsm_kernel<<<dim3((rest + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk);
       int t = (rest + GT - 1) / GT;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (tm) {
+        cudaEventCreate(&e0); cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+      }
       gemm_update_kernel<<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
+      launches += 2;
+      if (tm) {
+        cudaEventRecord(e1, s);
+        ev.push_back(e0); ev.push_back(e1);
+        tm->gemm_flops += 8.0 * (double)rest * rest * nbk * batch;
+        tm->gemm_launches += 1;
+      }
+    }
+  }
+  if (tm) {
+    tm->launches += launches;
+    if (!ev.empty()) cudaEventSynchronize(ev.back());
+    for (size_t q = 0; q + 1 < ev.size(); q += 2) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+      tm->gemm_ms += ms;
+      cudaEventDestroy(ev[q]); cudaEventDestroy(ev[q + 1]);
     }
   }
 }
 
 // ---------------------------------------------------------------- solves
-// One CTA per (factor m, right-hand side, sign); the solution vector lives in
-// shared memory; forward (unit L) then backward (U) substitution with one
-// barrier per column.
-__global__ void __launch_bounds__(1024) solve_kernel(const cd* __restrict__ LU, const int* __restrict__ piv, int n,
-                                                     int M, const double* __restrict__ sw,
-                                                     const cd* __restrict__ rhs, cd* __restrict__ x, int nrhs) {
-  extern __shared__ __align__(16) char smem_raw[];
-  cd* xs = (cd*)smem_raw;
-  const int m = blockIdx.x;        // factor index 0..M
-  const int job = blockIdx.y;      // rhs index; second half: mode -m
-  const int r_idx = job % nrhs;
-  const bool neg = job >= nrhs;
-  if (neg && m == 0) return;
-  const int q = neg ? (M - m) : (M + m);
+// Blocked forward/back substitution.  One CTA per (factor m, group of SG
+// right-hand sides); a job is (rhs index, sign) with sign - meaning mode -m.
+// The solution vectors are formed in place in x (each job owns its slot).
+// Per block of SB rows: the SB x SB diagonal triangle is solved in shared
+// memory, then the rows below (above, for U) are updated with the block column
+// of the factor, which is read once per CTA.
+#define SB 64
+#define SG 8
+__device__ __forceinline__ void job_of(int m, int M, int nrhs, int job, int* q, int* ridx, bool* neg) {
+  *ridx = job % nrhs;
+  *neg = job >= nrhs;
+  *q = *neg ? (M - m) : (M + m);
+}
+
+__global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict__ LU, const int* __restrict__ piv,
+                                                            int n, int M, const double* __restrict__ sw,
+                                                            const cd* __restrict__ rhs, cd* __restrict__ x,
+                                                            int nrhs) {
+  __shared__ cd Ls[SB][SB + 1];
+  __shared__ cd Xs[SB][SG];
+  extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation
+  const int m = blockIdx.x;
+  const int job0 = blockIdx.y * SG;
+  const int njobs_all = (m == 0) ? nrhs : 2 * nrhs;
+  if (job0 >= njobs_all) return;
+  const int G = min(SG, njobs_all - job0);
   const cd* L = LU + (size_t)m * n * n;
   const int* pv = piv + (size_t)m * n;
-  const cd* bq = rhs + ((size_t)q * nrhs + r_idx) * n;
   const int tid = threadIdx.x, T = blockDim.x;
-  for (int r = tid; r < n; r += T) {
-    double sg = (neg && ((r & 3) == 0 || (r & 3) == 3)) ? -1.0 : 1.0;
-    xs[r] = (sg * sw[r]) * bq[r];
+  cd* X[SG];
+  for (int g = 0; g < SG; ++g) {
+    int q, ri; bool neg;
+    job_of(m, M, nrhs, job0 + (g < G ? g : 0), &q, &ri, &neg);
+    X[g] = x + ((size_t)q * nrhs + ri) * n;
   }
+  // row interchanges (LAPACK order) composed into perm: (P b)[r] = b[perm[r]]
+  for (int r = tid; r < n; r += T) perm[r] = r;
   __syncthreads();
   if (tid == 0) {
     for (int k = 0; k < n; ++k) {
       int p = pv[k];
-      if (p != k) { cd t = xs[k]; xs[k] = xs[p]; xs[p] = t; }
+      if (p != k) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
     }
   }
   __syncthreads();
-  for (int k = 0; k < n - 1; ++k) {
-    const cd v = xs[k];
-    const cd* colk = L + (size_t)k * n;
-    for (int r = k + 1 + tid; r < n; r += T) xs[r] = xs[r] - colk[r] * v;
+  // permuted, scaled (sqrt weights per node) and reflected right-hand sides
+  for (int t = tid; t < G * n; t += T) {
+    int g = t / n, r = t % n;
+    int q, ri; bool neg;
+    job_of(m, M, nrhs, job0 + g, &q, &ri, &neg);
+    int src = perm[r];
+    double sg = (neg && ((src & 3) == 0 || (src & 3) == 3)) ? -1.0 : 1.0;
+    X[g][r] = (sg * sw[src >> 2]) * rhs[((size_t)q * nrhs + ri) * n + src];
+  }
+  __syncthreads();
+  // forward: L unit lower
+  for (int kb = 0; kb < n; kb += SB) {
+    const int bs = min(SB, n - kb);
+    for (int t = tid; t < bs * bs; t += T) {
+      int r = t % bs, c = t / bs;
+      Ls[r][c] = L[(size_t)(kb + c) * n + kb + r];
+    }
+    for (int t = tid; t < bs * G; t += T) {
+      int r = t % bs, g = t / bs;
+      Xs[r][g] = X[g][kb + r];
+    }
+    __syncthreads();
+    for (int c = 0; c < bs - 1; ++c) {
+      for (int t = tid; t < (bs - 1 - c) * G; t += T) {
+        int r = c + 1 + t % (bs - 1 - c), g = t / (bs - 1 - c);
+        Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < bs * G; t += T) {
+      int r = t % bs, g = t / bs;
+      X[g][kb + r] = Xs[r][g];
+    }
+    for (int r = kb + bs + tid; r < n; r += T) {
+      cd acc[SG];
+#pragma unroll
+      for (int g = 0; g < SG; ++g) acc[g] = C(0.0);
+      for (int c = 0; c < bs; ++c) {
+        cd l = L[(size_t)(kb + c) * n + r];
+#pragma unroll
+        for (int g = 0; g < SG; ++g) acc[g] = fma(l, Xs[c][g], acc[g]);
+      }
+      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - acc[g];
+    }
     __syncthreads();
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const cd* colk = L + (size_t)k * n;
-    const cd v = xs[k] / colk[k];
-    for (int r = tid; r < k; r += T) xs[r] = xs[r] - colk[r] * v;
+  // backward: U upper, non-unit diagonal
+  const int nblk = (n + SB - 1) / SB;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int kb = bi * SB, bs = min(SB, n - kb);
+    for (int t = tid; t < bs * bs; t += T) {
+      int r = t % bs, c = t / bs;
+      Ls[r][c] = L[(size_t)(kb + c) * n + kb + r];
+    }
+    for (int t = tid; t < bs * G; t += T) {
+      int r = t % bs, g = t / bs;
+      Xs[r][g] = X[g][kb + r];
+    }
     __syncthreads();
-    if (tid == 0) xs[k] = v;
+    for (int c = bs - 1; c >= 0; --c) {
+      if (tid < G) Xs[c][tid] = Xs[c][tid] / Ls[c][c];
+      __syncthreads();
+      for (int t = tid; t < c * G; t += T) {
+        int r = t % c, g = t / c;
+        Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < bs * G; t += T) {
+      int r = t % bs, g = t / bs;
+      X[g][kb + r] = Xs[r][g];
+    }
+    for (int r = tid; r < kb; r += T) {
+      cd acc[SG];
+#pragma unroll
+      for (int g = 0; g < SG; ++g) acc[g] = C(0.0);
+      for (int c = 0; c < bs; ++c) {
+        cd u = L[(size_t)(kb + c) * n + r];
+#pragma unroll
+        for (int g = 0; g < SG; ++g) acc[g] = fma(u, Xs[c][g], acc[g]);
+      }
+      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - acc[g];
+    }
     __syncthreads();
   }
-  cd* xq = x + ((size_t)q * nrhs + r_idx) * n;
-  for (int r = tid; r < n; r += T) {
+  // back to physical unknowns (and reflection for -m)
+  for (int t = tid; t < G * n; t += T) {
+    int g = t / n, r = t % n;
+    int q, ri; bool neg;
+    job_of(m, M, nrhs, job0 + g, &q, &ri, &neg);
     double sg = (neg && ((r & 3) == 1 || (r & 3) == 2)) ? -1.0 : 1.0;
-    xq[r] = (sg / sw[r]) * xs[r];
+    X[g][r] = (sg / sw[r >> 2]) * X[g][r];
   }
 }
 
 void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
                     cudaStream_t s) {
-  int smem = n * (int)sizeof(cd);
-  cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  solve_kernel<<<dim3(M + 1, 2 * nrhs), 1024, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+  int groups = (2 * nrhs + SG - 1) / SG;
+  int smem = n * (int)sizeof(int);
+  cudaFuncSetAttribute(solve_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  solve_blocked_kernel<<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
 }

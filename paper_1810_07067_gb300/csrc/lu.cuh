@@ -8,10 +8,16 @@
 // Factor `batch` column-major n x n matrices (stride n*n) in place: P A = L U.
 // piv[b*n + k] = row interchanged with row k (0-based, LAPACK order);
 // info[b] = 0, or k+1 for the first exactly zero pivot column k.
-void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s);
+struct LuTiming {
+  double gemm_ms = 0.0;      // summed device time of the trailing-update launches
+  double gemm_flops = 0.0;   // their algorithmic flops (8 per complex multiply-add)
+  int gemm_launches = 0;
+  int launches = 0;          // all kernel launches of the factorization
+};
+void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* t = nullptr);
 
 // Solve with factors of modes m = 0..M for right-hand sides of modes -M..M:
-// rhs/x layout [2M+1][nrhs][n] (mode q = m + M); sw[n] = sqrt of the L2 weights
+// rhs/x layout [2M+1][nrhs][n] (mode q = m + M); sw[n/4] = sqrt of the L2 weights of the nodes
 // (rows scaled by sw, unknowns by 1/sw inside the factors); negative modes use
 // the reflection A_{-m} = D_r A_m D_c with D_r = (-1,1,1,-1), D_c = (1,-1,-1,1)
 // per node.

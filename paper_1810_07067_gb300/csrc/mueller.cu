@@ -519,7 +519,8 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   rc = assemble_core(c->S, c->A, s, &c->st, c->keep, c->geo);
   if (rc) { delete c; return rc; }
   cudaEventRecord(e1, s);
-  lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s);
+  LuTiming lt;
+  lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s, &lt);
   cudaEventRecord(e2, s);
   cudaError_t err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) { delete c; return fail(MUELLER_ECUDA, cudaGetErrorString(err)); }
@@ -527,6 +528,8 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   cudaEventElapsedTime(&a, e0, e1); cudaEventElapsedTime(&b, e1, e2);
   cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
   c->st.ms_lu = b; c->st.ms_build = a + b;
+  c->st.ms_lu_gemm = lt.gemm_ms; c->st.lu_gemm_flops = lt.gemm_flops; c->st.lu_gemm_launches = lt.gemm_launches;
+  c->st.launches = 4 + lt.launches;
   std::vector<int> info(M + 1);
   cudaMemcpy(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost);
   c->st.singular_mode = -1; c->st.singular_column = -1;
@@ -568,6 +571,7 @@ extern "C" int mueller_solve(mueller_ctx* c, const mueller_c128* rhs_dev, int nr
   cudaEventDestroy(e0); cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail(MUELLER_ECUDA, cudaGetErrorString(err));
   c->st.ms_solve = ms;
+  c->st.solve_launches = 1;
   if (backward_err)
     for (int q = 0; q < (2 * c->S.M + 1) * nrhs; ++q) backward_err[q] = -1.0;  // not computed on the FP64 path
   return MUELLER_OK;
