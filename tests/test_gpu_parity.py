@@ -112,7 +112,7 @@ def test_sphere_matrices_vs_oracle(mb, sphere_oracle):
         ref, noise = system.block(cfg.curve, cfg.media, M, i, j, modes=modes, noise=True)
         s = sw[4 * i] / sw[4 * j]
         got = G[:, 4 * i:4 * i + 4, 4 * j:4 * j + 4]
-        floor = 20 * noise.max(axis=(1, 2), keepdims=True) * s   # per mode, whole block
+        floor = 20 * noise.max() * s   # noise level of this (target, column) pair, all modes
         assert (np.abs(got - ref * s) <= 1e-12 * np.abs(Aw).max() + floor).all(), (i, j)
 
 
@@ -193,7 +193,7 @@ def test_cylinder_full_size_sampled_blocks(mb, cylinder_full):
         ref, noise = system.block(cfg.curve, cfg.media, M, i, j, modes=modes, noise=True)
         s = sw[4 * i] / sw[4 * j]
         got = np.stack([A[q, 4 * j:4 * j + 4, 4 * i:4 * i + 4].cpu().numpy().T for q in modes])
-        ok = np.abs(got - ref * s) <= 1e-12 * scale + 20 * noise.max(axis=(1, 2), keepdims=True) * s
+        ok = np.abs(got - ref * s) <= 1e-12 * scale + 20 * noise.max() * s
         assert ok.all(), (i, j, (np.abs(got - ref * s) / scale).max())
 
 
