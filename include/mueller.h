@@ -155,6 +155,35 @@ int mueller_far_field(mueller_ctx* ctx, const mueller_c128* x_dev, int nrhs, con
 int mueller_modal_kernels(const double* pairs_host, long long npairs, mueller_c128 k0, mueller_c128 k1,
                           int M, int n_phi, double split_eps, mueller_c128* out_dev, void* stream);
 
+/* Allocation-free variant of mueller_modal_kernels.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory,
+ * for example a host application whose device memory is owned by another
+ * allocator (a framework's memory pool, or a budget enforced by a serving
+ * runtime), or a latency-critical loop in which a cudaMalloc could block or
+ * fail.  It computes the same spectra as mueller_modal_kernels, but
+ *  - pairs_dev is a DEVICE array [npairs][4] = (r_t, z_t, r_s, z_s), with
+ *    r_t, r_s > 0 and distinct points (not checked on the host; a bad pair
+ *    yields non-finite values in its own output rows);
+ *  - n_phi is used as given (power of two in [16, 8192], >= 2M + 4); unlike
+ *    mueller_modal_kernels it is not raised automatically, so the caller
+ *    picks it large enough for the wavenumbers (see stats.n_phi_used of a
+ *    build for a safe value);
+ *  - all scratch (transform tables, split flags, pair displacements and
+ *    Laplace-type coefficients) lives in one fixed 16 MiB device array that
+ *    every GPU loading the library holds until the process exits; a call is
+ *    rejected with MUELLER_EINVAL when
+ *    n_phi + npairs * (n_phi/2 + M + 7) (rounded up) exceeds 2^21 doubles;
+ *  - it calls no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device performs a one-time set-up on that device (it
+ * looks up the scratch array's device address and uploads series tables);
+ * make that first call before any stream capture.  All calls share the one
+ * array and every call rewrites the parts it reads, so no state carries over,
+ * but calls that overlap on the GPU (several streams, threads or processes
+ * using the same device) race on the scratch and must be serialised by the
+ * caller.  The work is enqueued on `stream`; the call does not synchronise. */
+int mueller_modal_kernels_noalloc(const double* pairs_dev, long long npairs, mueller_c128 k0, mueller_c128 k1,
+                                  int M, int n_phi, double split_eps, mueller_c128* out_dev, void* stream);
+
 /* Batched LU of `batch` column-major n x n complex matrices in place
  * (stride n*n); piv_dev [batch][n] (0-based LAPACK-style interchanges),
  * info_dev [batch] (0 or first zero-pivot column + 1). */

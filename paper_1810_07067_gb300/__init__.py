@@ -66,6 +66,8 @@ _lib.mueller_far_field.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, _vp, _vp]
 _lib.mueller_modal_kernels.argtypes = [ct.POINTER(ct.c_double), ct.c_longlong, c128, c128, ct.c_int, ct.c_int,
                                        ct.c_double, _vp, _vp]
 _lib.mueller_lu_batched.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
+_lib.mueller_modal_kernels_noalloc.argtypes = [_vp, ct.c_longlong, c128, c128, ct.c_int, ct.c_int, ct.c_double,
+                                               _vp, _vp]
 _lib.mueller_footprint_bytes.argtypes = [ct.c_int, ct.c_int]
 _lib.mueller_footprint_bytes.restype = ct.c_size_t
 _lib.mueller_stats_get.argtypes = [_vp, ct.POINTER(Stats)]
@@ -75,7 +77,7 @@ _lib.mueller_strerror.argtypes = [ct.c_int]
 _lib.mueller_last_error.restype = ct.c_char_p
 
 EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_far_field",
-           "mueller_modal_kernels", "mueller_lu_batched", "mueller_footprint_bytes", "mueller_stats_get",
+           "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_footprint_bytes", "mueller_stats_get",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
@@ -203,6 +205,14 @@ def modal_kernels(pairs: np.ndarray, k0, k1, M: int, n_phi: int, out, split_eps:
     p = np.ascontiguousarray(np.asarray(pairs, np.float64).reshape(-1, 4))
     _check(_lib.mueller_modal_kernels(_dptr(p), len(p), _c(k0), _c(k1), int(M), int(n_phi), float(split_eps),
                                       _ptr(out), _stream(stream)))
+    return out
+
+
+def modal_kernels_noalloc(pairs_dev, k0, k1, M: int, n_phi: int, out, split_eps: float = 1e-17, stream=None):
+    """Same spectra as ``modal_kernels`` for pairs already on the device, using
+    the library's fixed scratch array instead of allocating (see mueller.h)."""
+    _check(_lib.mueller_modal_kernels_noalloc(_ptr(pairs_dev), pairs_dev.shape[0], _c(k0), _c(k1), int(M),
+                                              int(n_phi), float(split_eps), _ptr(out), _stream(stream)))
     return out
 
 

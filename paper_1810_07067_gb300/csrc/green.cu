@@ -34,11 +34,8 @@ void upload_series_tables(const SeriesTables& t) { cudaMemcpyToSymbol(c_tab, &t,
 // Laplace-type modal coefficients, one thread per split pair.
 // pairs: [n][4] = (r_t, z_t, r_t - r_s, z_t - z_s); leg: [(Mq+1)+Ms][n] index-major:
 // rows 0..Mq hold P^_n = P_n / sqrt(B), rows Mq+1.. hold S^_m = S_m / B^{3/2}.
-__global__ void legendre_kernel(const double* __restrict__ pairs, long long n, int Mq, int Ms,
-                                double* __restrict__ leg) {
-  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  double rt = pairs[4 * p], dr = pairs[4 * p + 2], dz = pairs[4 * p + 3];
+__device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms,
+                             double* __restrict__ leg) {
   double rs = rt - dr;
   double d2 = dr * dr + dz * dz, B = 2.0 * rt * rs;
   double c = d2 / B, cp1 = 2.0 + c;          // chi - 1, chi + 1
@@ -89,6 +86,13 @@ __global__ void legendre_kernel(const double* __restrict__ pairs, long long n, i
     Sv[(long long)m * n + p] = (2.0 * m - 1.0) * (D - c * P) / (c * cp1) * isB3;
   }
   for (int m = 0; m <= Mq; ++m) Pv[(long long)m * n + p] *= isB;
+}
+
+__global__ void legendre_kernel(const double* __restrict__ pairs, long long n, int Mq, int Ms,
+                                double* __restrict__ leg) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  legendre_one(pairs[4 * p], pairs[4 * p + 2], pairs[4 * p + 3], p, n, Mq, Ms, leg);
 }
 
 void launch_legendre(const double* pairs, long long n, int Mq, int Ms, double* leg, cudaStream_t s) {
@@ -508,4 +512,114 @@ void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* 
   cudaFuncSetAttribute(pair_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   pair_spectra_kernel<<<grid_for(npairs, wpb), wpb * 32, smem, s>>>(gp, pairs, sidx, leg, n_split, npairs, cosT,
                                                                       s2T, out);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of mueller_modal_kernels (declared in mueller.h).
+// Its scratch (transform tables, split flags, pair displacements, Laplace-type
+// coefficients) lives in one fixed file-scope device array instead of memory
+// from cudaMalloc.  Host code must not use the array's name as a device
+// address: its address is fetched once per device with cudaGetSymbolAddress.
+#include "mueller.h"
+
+#define NOALLOC_SCRATCH_DOUBLES ((size_t)2 * 1024 * 1024)  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+#define NOALLOC_MAX_DEVICES 64
+static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+static bool g_noalloc_tables[NOALLOC_MAX_DEVICES] = {false};
+// message reported by mueller_last_error (defined with the other ABI functions)
+void mueller_internal_set_error(const char* msg);
+
+__global__ void noalloc_tables_kernel(int nphi, double* __restrict__ cosT, double* __restrict__ s2T) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nphi) cosT[t] = cospi(2.0 * t / nphi);
+  if (t <= nphi / 2) {
+    double v = sinpi((double)t / nphi);
+    s2T[t] = v * v;
+  }
+}
+
+// (r_t, z_t, r_s, z_s) -> (r_t, z_t, r_t - r_s, z_t - z_s); split flag per pair
+__global__ void noalloc_prep_kernel(const double* __restrict__ pairs, long long n, int nphi, int M, double lneps,
+                                    double* __restrict__ disp, int* __restrict__ sid) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double rt = pairs[4 * p], zt = pairs[4 * p + 1];
+  double dr = rt - pairs[4 * p + 2], dz = zt - pairs[4 * p + 3];
+  disp[4 * p] = rt; disp[4 * p + 1] = zt; disp[4 * p + 2] = dr; disp[4 * p + 3] = dz;
+  double d2 = dr * dr + dz * dz, B = 2.0 * rt * (rt - dr);
+  double c = d2 / B, cp1 = 2.0 + c;
+  double lz = log1p(c + sqrt(c * cp1));
+  sid[p] = ((double)(nphi - M - 1) * lz < lneps) ? (int)p : -1;
+}
+
+__global__ void noalloc_legendre_kernel(const double* __restrict__ disp, const int* __restrict__ sid, long long n,
+                                        int Mq, int Ms, double* __restrict__ leg) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= n || sid[p] < 0) return;
+  legendre_one(disp[4 * p], disp[4 * p + 2], disp[4 * p + 3], p, n, Mq, Ms, leg);
+}
+
+static int noalloc_fail(const char* msg, int code = MUELLER_EINVAL) {
+  mueller_internal_set_error(msg);
+  return code;
+}
+
+extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long npairs, mueller_c128 k0,
+                                             mueller_c128 k1, int M, int n_phi, double split_eps,
+                                             mueller_c128* out_dev, void* stream) {
+  mueller_internal_set_error("");
+  if (!pairs_dev || !out_dev || npairs < 0 || M < 0) return noalloc_fail("invalid arguments");
+  if (n_phi < 16 || n_phi > 8192 || (n_phi & (n_phi - 1)) != 0) return noalloc_fail("n_phi must be a power of two in [16, 8192]");
+  if (M + 2 > n_phi / 2) return noalloc_fail("n_phi must be at least 2M + 4");
+  if (k0.im < 0 || k1.im < 0) return noalloc_fail("wavenumbers need Im k >= 0");
+  if (npairs == 0) return MUELLER_OK;
+  const int Mq = n_phi / 2 - 1, Ms = M + 2, H = n_phi / 2 + 1;
+  auto up32 = [](size_t v) { return (v + 31) & ~(size_t)31; };
+  const size_t o_cos = 0, o_s2 = o_cos + up32(n_phi), o_disp = o_s2 + up32(H);
+  const size_t o_sid = o_disp + up32(4 * (size_t)npairs);
+  const size_t o_leg = o_sid + up32(((size_t)npairs + 1) / 2);
+  const size_t need = o_leg + (size_t)(Mq + 1 + Ms) * (size_t)npairs;
+  if (need > NOALLOC_SCRATCH_DOUBLES) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "npairs * (n_phi/2 + M + 7) exceeds the fixed scratch of %zu doubles (16 MiB): need %zu",
+             (size_t)NOALLOC_SCRATCH_DOUBLES, need);
+    return noalloc_fail(msg);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail("no current CUDA device");
+  if (!g_noalloc_ptr[dev]) {  // one-time set-up on this device
+    double* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return noalloc_fail(cudaGetErrorString(e), MUELLER_ECUDA);
+    g_noalloc_ptr[dev] = p;
+  }
+  if (!g_noalloc_tables[dev]) {
+    SeriesTables t;
+    fill_series_tables(&t);
+    if (cudaMemcpyToSymbol(c_tab, &t, sizeof(SeriesTables)) != cudaSuccess) return noalloc_fail("series tables");
+    g_noalloc_tables[dev] = true;
+  }
+  double* base = g_noalloc_ptr[dev];
+  double* cosT = base + o_cos;
+  double* s2T = base + o_s2;
+  double* disp = base + o_disp;
+  int* sid = (int*)(base + o_sid);
+  double* leg = base + o_leg;
+  cudaStream_t s = (cudaStream_t)stream;
+  GreenParams gp{};
+  cd K0{k0.re, k0.im}, K1{k1.re, k1.im};
+  gp.M = M; gp.Ms = Ms; gp.nphi = n_phi; gp.H = H; gp.Mq = Mq;
+  gp.kp0 = kpow(K0); gp.kp1 = kpow(K1);
+  gp.gamma0 = -0.25 * (K0 * K0 - K1 * K1);
+  double eps = split_eps > 0 ? split_eps : 1e-17;
+  noalloc_tables_kernel<<<(n_phi + 255) / 256, 256, 0, s>>>(n_phi, cosT, s2T);
+  unsigned blocks = (unsigned)((npairs + 127) / 128);
+  noalloc_prep_kernel<<<blocks, 128, 0, s>>>(pairs_dev, npairs, n_phi, M, -log(eps), disp, sid);
+  noalloc_legendre_kernel<<<blocks, 128, 0, s>>>(disp, sid, npairs, Mq, Ms, leg);
+  launch_pair_spectra(gp, disp, sid, leg, npairs, npairs, cosT, s2T, (cd*)out_dev, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(cudaGetErrorString(e), MUELLER_ECUDA);
+  return MUELLER_OK;
 }

@@ -66,6 +66,10 @@ HD int green_smem_bytes(const GreenParams& gp) {
   return (b + 15) & ~15;
 }
 
+// Laplace-type coefficients of one split pair p (target r_t, displacement dr, dz)
+// into leg (stride n, rows 0..Mq P^_m, rows Mq+1.. S^_m).
+__device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms, double* leg);
+
 // host-side launchers (green.cu)
 void launch_legendre(const double* pairs, long long n_split, int Mq, int Ms, double* leg, cudaStream_t s);
 void launch_far_assembly(const BuildArgs& a, cudaStream_t s);

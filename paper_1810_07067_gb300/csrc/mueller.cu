@@ -694,3 +694,5 @@ extern "C" const char* mueller_strerror(int status) {
 }
 
 extern "C" const char* mueller_last_error(void) { return g_err.c_str(); }
+
+void mueller_internal_set_error(const char* msg) { g_err = msg; }
