@@ -115,10 +115,17 @@ METRIC = "modal assemble+solve time (mueller_build + mueller_solve), FP64 GPU pa
 
 
 def _config(cfg):
-    return {"workload": f"{cfg.name}: finite cylinder R=1 H=2, edge-graded panels, N={cfg.N} nodes "
-                        f"(system {4 * cfg.N}x{4 * cfg.N} c128 per mode), modes -{cfg.M}..{cfg.M}, "
-                        f"n_phi={cfg.n_phi}, k0=5, k1=7.5+0.01i, {len(cfg.waves)} plane waves",
-            "precision": "fp64", "l2_flush": "inputs larger than L2 (5.5 GB of factors per step)"}
+    if cfg.name.startswith("cylinder"):
+        body = "finite cylinder R=1 H=2, edge-graded panels"
+    else:
+        body = "smooth random body r = sin t (1 + sum a_j cos jt)"
+    k0 = cfg.media.omega
+    k1 = k0 * complex(cfg.media.eps1) ** 0.5
+    fb = 16 * (4 * cfg.N) ** 2 * (cfg.M + 1) / 1e9
+    return {"workload": f"{cfg.name}: {body}, N={cfg.N} nodes (system {4 * cfg.N}x{4 * cfg.N} c128 per mode), "
+                        f"modes -{cfg.M}..{cfg.M}, n_phi={cfg.n_phi}, k0={k0:g}, k1={k1:.4g}, "
+                        f"{len(cfg.waves)} plane waves",
+            "precision": "fp64", "l2_flush": f"inputs larger than L2 ({fb:.2g} GB of factors per step)"}
 
 
 def main():
@@ -128,11 +135,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "small"],
+                    help="small: random smooth body N=256, M=32 (profiling captures)")
     args = ap.parse_args()
     args.steps_ref = args.steps
     args.warmup_ref = args.warmup
     import workloads as W
-    cfg = W.config_cylinder(7)
+    cfg = W.config_cylinder(7) if args.workload == "cylinder" else W.config_random(16, 1810, 32, 128)
     if args.impl == "reference":
         run_reference(args, cfg)
         return
