@@ -99,6 +99,8 @@ typedef struct {
   int lu_gemm_launches;
   int launches;              /* kernel launches of the last build            */
   int solve_launches;        /* kernel launches of the last solve            */
+  int refine_iters;          /* mixed path: refinement steps of the last solve */
+  double backward_err_max;   /* mixed path: largest final backward error       */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;
@@ -124,7 +126,14 @@ int mueller_assemble(const mueller_curve* curve, const mueller_media* media, int
 
 /* Solve for all modes -M..M (Section 6, T_add: additional right-hand sides
  * reuse the factors).  rhs_dev and x_dev are device arrays
- * [2M+1][nrhs][4N]; backward_err (host, [2M+1][nrhs]) may be NULL. */
+ * [2M+1][nrhs][4N]; backward_err (host, [2M+1][nrhs]) may be NULL.
+ * FP64 path: one solve with the complex128 factors (backward_err = -1, not
+ * computed).  Mixed path: y0 from the complex64 factors, then
+ * y <- y + LU32^{-1}(b' - A' y) with complex128 residuals of the L2-weighted
+ * matrices until ||b' - A'y||_inf <= refine_tol (||A'||_inf ||y||_inf + ||b'||_inf)
+ * for every mode and right-hand side (the normwise backward errors are
+ * returned); MUELLER_ENOCONV with the last iterate if refine_max_iter steps
+ * do not reach it. */
 int mueller_solve(mueller_ctx* ctx, const mueller_c128* rhs_dev, int nrhs, mueller_c128* x_dev,
                   double* backward_err, void* stream);
 

@@ -50,7 +50,7 @@ class Stats(ct.Structure):
                 ("n_far_pairs", ct.c_longlong), ("n_support_pairs", ct.c_longlong), ("singular_mode", ct.c_int),
                 ("singular_column", ct.c_int), ("device_bytes", ct.c_size_t), ("ms_lu_gemm", ct.c_double),
                 ("lu_gemm_flops", ct.c_double), ("lu_gemm_launches", ct.c_int), ("launches", ct.c_int),
-                ("solve_launches", ct.c_int)]
+                ("solve_launches", ct.c_int), ("refine_iters", ct.c_int), ("backward_err_max", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -118,7 +118,7 @@ class Options:
     n_phi: int = 64
     formulation: int = 0
     precision: int = 0
-    refine_tol: float = 1e-12
+    refine_tol: float = 1e-14
     refine_max_iter: int = 10
     split_eps: float = 1e-17
 

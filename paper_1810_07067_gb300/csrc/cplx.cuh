@@ -72,3 +72,31 @@ HD cd csqrt_principal(cd z) {
   if (z.y < 0) im = -im;
   return cd{re, im};
 }
+
+// complex64 for the mixed-precision factors
+struct cf {
+  float x, y;
+};
+HD cf CF(float a, float b = 0.f) { return cf{a, b}; }
+HD cf operator+(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+HD cf operator-(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
+HD cf operator-(cf a) { return cf{-a.x, -a.y}; }
+HD cf operator*(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+HD cf operator*(float s, cf a) { return cf{s * a.x, s * a.y}; }
+HD cf& operator+=(cf& a, cf b) { a.x += b.x; a.y += b.y; return a; }
+HD double norm2(cf a) { return (double)a.x * a.x + (double)a.y * a.y; }
+HD cf operator/(cf a, cf b) {
+  cd q = cd{a.x, a.y} / cd{b.x, b.y};
+  return cf{(float)q.x, (float)q.y};
+}
+HD cf fma(cf a, cf b, cf c) {
+  return cf{fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y))};
+}
+template <class T> HD T czero();
+template <> HD cd czero<cd>() { return cd{0.0, 0.0}; }
+template <> HD cf czero<cf>() { return cf{0.f, 0.f}; }
+template <class T> HD T cone();
+template <> HD cd cone<cd>() { return cd{1.0, 0.0}; }
+template <> HD cf cone<cf>() { return cf{1.f, 0.f}; }
+HD cf to_cf(cd a) { return cf{(float)a.x, (float)a.y}; }
+HD cd to_cd(cf a) { return cd{a.x, a.y}; }

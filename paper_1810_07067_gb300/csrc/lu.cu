@@ -14,22 +14,23 @@ __device__ __forceinline__ void argmax_merge(double& v, int& idx, double v2, int
   if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
 }
 
-__global__ void __launch_bounds__(1024) panel_kernel(cd* __restrict__ A, int n, int k0, int nbk,
+template <class T>
+__global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, int k0, int nbk,
                                                      int* __restrict__ piv, int* __restrict__ info) {
   const int b = blockIdx.x;
-  cd* M = A + (size_t)b * n * n;
+  T* M = A + (size_t)b * n * n;
   int* pv = piv + (size_t)b * n;
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_p;
-  __shared__ cd s_row[LU_NB];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, T = blockDim.x;
+  __shared__ T s_row[LU_NB];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, NT = blockDim.x;
   for (int jj = 0; jj < nbk; ++jj) {
     const int c = k0 + jj;
-    cd* col = M + (size_t)c * n;
+    T* col = M + (size_t)c * n;
     double best = -1.0;
     int bi = n;
-    for (int r = c + tid; r < n; r += T) argmax_merge(best, bi, norm2(col[r]), r);
+    for (int r = c + tid; r < n; r += NT) argmax_merge(best, bi, norm2(col[r]), r);
     for (int o = 16; o > 0; o >>= 1) {
       double v2 = __shfl_xor_sync(0xffffffffu, best, o);
       int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -38,8 +39,8 @@ __global__ void __launch_bounds__(1024) panel_kernel(cd* __restrict__ A, int n, 
     if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
     __syncthreads();
     if (wid == 0) {
-      best = (lane < (T >> 5)) ? red_v[lane] : -1.0;
-      bi = (lane < (T >> 5)) ? red_i[lane] : n;
+      best = (lane < (NT >> 5)) ? red_v[lane] : -1.0;
+      bi = (lane < (NT >> 5)) ? red_i[lane] : n;
       for (int o = 16; o > 0; o >>= 1) {
         double v2 = __shfl_xor_sync(0xffffffffu, best, o);
         int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -55,18 +56,18 @@ __global__ void __launch_bounds__(1024) panel_kernel(cd* __restrict__ A, int n, 
     const int p = s_p;
     if (p >= 0) {
       if (p != c && tid < nbk) {
-        cd* cc = M + (size_t)(k0 + tid) * n;
-        cd t = cc[c]; cc[c] = cc[p]; cc[p] = t;
+        T* cc = M + (size_t)(k0 + tid) * n;
+        T t = cc[c]; cc[c] = cc[p]; cc[p] = t;
       }
       __syncthreads();
       if (tid < nbk) s_row[tid] = M[(size_t)(k0 + tid) * n + c];
       __syncthreads();
-      const cd inv = C(1.0) / s_row[jj];
-      for (int r = c + 1 + tid; r < n; r += T) {
-        cd l = col[r] * inv;
+      const T inv = cone<T>() / s_row[jj];
+      for (int r = c + 1 + tid; r < n; r += NT) {
+        T l = col[r] * inv;
         col[r] = l;
         for (int cc = jj + 1; cc < nbk; ++cc) {
-          cd* dst = M + (size_t)(k0 + cc) * n + r;
+          T* dst = M + (size_t)(k0 + cc) * n + r;
           *dst = *dst - l * s_row[cc];
         }
       }
@@ -76,25 +77,27 @@ __global__ void __launch_bounds__(1024) panel_kernel(cd* __restrict__ A, int n, 
 }
 
 // ---------------------------------------------------------------- swaps
-__global__ void swap_kernel(cd* __restrict__ A, int n, int k0, int nbk, const int* __restrict__ piv) {
+template <class T>
+__global__ void swap_kernel(T* __restrict__ A, int n, int k0, int nbk, const int* __restrict__ piv) {
   const int b = blockIdx.y;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int nother = n - nbk;
   if (c >= nother) return;
   if (c >= k0) c += nbk;  // skip the panel's own columns
-  cd* col = A + (size_t)b * n * n + (size_t)c * n;
+  T* col = A + (size_t)b * n * n + (size_t)c * n;
   const int* pv = piv + (size_t)b * n;
   for (int k = k0; k < k0 + nbk; ++k) {
     int p = pv[k];
-    if (p != k) { cd t = col[k]; col[k] = col[p]; col[p] = t; }
+    if (p != k) { T t = col[k]; col[k] = col[p]; col[p] = t; }
   }
 }
 
 // ---------------------------------------------------------------- U12 = L11^{-1} A12
-__global__ void trsm_kernel(cd* __restrict__ A, int n, int k0, int nbk) {
+template <class T>
+__global__ void trsm_kernel(T* __restrict__ A, int n, int k0, int nbk) {
   const int b = blockIdx.y;
-  cd* M = A + (size_t)b * n * n;
-  __shared__ cd L[LU_NB][LU_NB + 1];
+  T* M = A + (size_t)b * n * n;
+  __shared__ T L[LU_NB][LU_NB + 1];
   for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
     int r = t % nbk, cc = t / nbk;
     L[r][cc] = M[(size_t)(k0 + cc) * n + k0 + r];
@@ -102,10 +105,10 @@ __global__ void trsm_kernel(cd* __restrict__ A, int n, int k0, int nbk) {
   __syncthreads();
   int c = k0 + nbk + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  cd* col = M + (size_t)c * n + k0;
-  cd x[LU_NB];
+  T* col = M + (size_t)c * n + k0;
+  T x[LU_NB];
 #pragma unroll
-  for (int r = 0; r < LU_NB; ++r) x[r] = (r < nbk) ? col[r] : C(0.0);
+  for (int r = 0; r < LU_NB; ++r) x[r] = (r < nbk) ? col[r] : czero<T>();
 #pragma unroll
   for (int k = 0; k < LU_NB; ++k) {
 #pragma unroll
@@ -120,30 +123,31 @@ __global__ void trsm_kernel(cd* __restrict__ A, int n, int k0, int nbk) {
 // C[i0.., j0..] -= A[i0.., k0..k0+nbk) * A[k0..k0+nbk), j0..], 64x64 tiles,
 // 256 threads, each 4x4 outputs: rows tx + 16a, columns ty + 16b.
 #define GT 64
-__global__ void __launch_bounds__(256) gemm_update_kernel(cd* __restrict__ A, int n, int k0, int nbk) {
+template <class T>
+__global__ void __launch_bounds__(256) gemm_update_kernel(T* __restrict__ A, int n, int k0, int nbk) {
   const int b = blockIdx.z;
-  cd* M = A + (size_t)b * n * n;
+  T* M = A + (size_t)b * n * n;
   const int start = k0 + nbk;
   const int i0 = start + blockIdx.x * GT, j0 = start + blockIdx.y * GT;
-  __shared__ cd As[LU_NB][GT];
-  __shared__ cd Bs[LU_NB][GT];
+  __shared__ T As[LU_NB][GT];
+  __shared__ T Bs[LU_NB][GT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int t = tid; t < nbk * GT; t += 256) {
     int r = t % GT, kk = t / GT;
     int gi = i0 + r;
-    As[kk][r] = (gi < n) ? M[(size_t)(k0 + kk) * n + gi] : C(0.0);
+    As[kk][r] = (gi < n) ? M[(size_t)(k0 + kk) * n + gi] : czero<T>();
     int kb = t % nbk, cj = t / nbk;  // B element (row k0+kb, column j0+cj)
     int gj = j0 + cj;
-    Bs[kb][cj] = (gj < n) ? M[(size_t)gj * n + k0 + kb] : C(0.0);
+    Bs[kb][cj] = (gj < n) ? M[(size_t)gj * n + k0 + kb] : czero<T>();
   }
   __syncthreads();
-  cd acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = C(0.0);
+    for (int c = 0; c < 4; ++c) acc[a][c] = czero<T>();
   for (int kk = 0; kk < nbk; ++kk) {
-    cd av[4], bv[4];
+    T av[4], bv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
 #pragma unroll
@@ -161,33 +165,34 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(cd* __restrict__ A, in
     for (int a = 0; a < 4; ++a) {
       int gi = i0 + tx + 16 * a;
       if (gi < n) {
-        cd* d = M + (size_t)gj * n + gi;
+        T* d = M + (size_t)gj * n + gi;
         *d = *d - acc[a][c];
       }
     }
   }
 }
 
-void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
+template <class T>
+static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
   cudaMemsetAsync(info, 0, sizeof(int) * batch, s);
   std::vector<cudaEvent_t> ev;
   int launches = 0;
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     int nbk = (n - k0 < LU_NB) ? n - k0 : LU_NB;
-    panel_kernel<<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
+    panel_kernel<T><<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
     ++launches;
     int nother = n - nbk;
-    if (nother > 0) { swap_kernel<<<dim3((nother + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk, piv); ++launches; }
+    if (nother > 0) { swap_kernel<T><<<dim3((nother + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk, piv); ++launches; }
     int rest = n - k0 - nbk;
     if (rest > 0) {
-      trsm_kernel<<<dim3((rest + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk);
+      trsm_kernel<T><<<dim3((rest + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk);
       int t = (rest + GT - 1) / GT;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (tm) {
         cudaEventCreate(&e0); cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
       }
-      gemm_update_kernel<<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
+      gemm_update_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
       launches += 2;
       if (tm) {
         cudaEventRecord(e1, s);
@@ -209,6 +214,14 @@ void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_
   }
 }
 
+void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
+  lu_factor_impl<cd>(A, n, batch, piv, info, s, tm);
+}
+
+void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
+  lu_factor_impl<cf>(A, n, batch, piv, info, s, tm);
+}
+
 // ---------------------------------------------------------------- solves
 // Blocked forward/back substitution.  One CTA per (factor m, group of SG
 // right-hand sides); a job is (rhs index, sign) with sign - meaning mode -m.
@@ -224,19 +237,29 @@ __device__ __forceinline__ void job_of(int m, int M, int nrhs, int job, int* q, 
   *q = *neg ? (M - m) : (M + m);
 }
 
-__global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict__ LU, const int* __restrict__ piv,
+template <class T> __device__ __forceinline__ T conv(cd a);
+template <> __device__ __forceinline__ cd conv<cd>(cd a) { return a; }
+template <> __device__ __forceinline__ cf conv<cf>(cd a) { return to_cf(a); }
+__device__ __forceinline__ cd to_cd(cd a) { return a; }
+
+// TF: factor type (cd, or cf for the mixed path's correction solves, which
+// then run in FP32 arithmetic on FP64 storage).  PHYS: right-hand sides and
+// solutions in physical unknowns (scaled by the sqrt weights here); otherwise
+// both are already in the weighted space.
+template <class TF, bool PHYS>
+__global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict__ LU, const int* __restrict__ piv,
                                                             int n, int M, const double* __restrict__ sw,
                                                             const cd* __restrict__ rhs, cd* __restrict__ x,
                                                             int nrhs) {
-  __shared__ cd Ls[SB][SB + 1];
-  __shared__ cd Xs[SB][SG];
+  __shared__ TF Ls[SB][SB + 1];
+  __shared__ TF Xs[SB][SG];
   extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation
   const int m = blockIdx.x;
   const int job0 = blockIdx.y * SG;
   const int njobs_all = (m == 0) ? nrhs : 2 * nrhs;
   if (job0 >= njobs_all) return;
   const int G = min(SG, njobs_all - job0);
-  const cd* L = LU + (size_t)m * n * n;
+  const TF* L = LU + (size_t)m * n * n;
   const int* pv = piv + (size_t)m * n;
   const int tid = threadIdx.x, T = blockDim.x;
   cd* X[SG];
@@ -262,7 +285,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict
     job_of(m, M, nrhs, job0 + g, &q, &ri, &neg);
     int src = perm[r];
     double sg = (neg && ((src & 3) == 0 || (src & 3) == 3)) ? -1.0 : 1.0;
-    X[g][r] = (sg * sw[src >> 2]) * rhs[((size_t)q * nrhs + ri) * n + src];
+    X[g][r] = ((PHYS ? sw[src >> 2] : 1.0) * sg) * rhs[((size_t)q * nrhs + ri) * n + src];
   }
   __syncthreads();
   // forward: L unit lower
@@ -274,7 +297,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict
     }
     for (int t = tid; t < bs * G; t += T) {
       int r = t % bs, g = t / bs;
-      Xs[r][g] = X[g][kb + r];
+      Xs[r][g] = conv<TF>(X[g][kb + r]);
     }
     __syncthreads();
     for (int c = 0; c < bs - 1; ++c) {
@@ -286,18 +309,18 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict
     }
     for (int t = tid; t < bs * G; t += T) {
       int r = t % bs, g = t / bs;
-      X[g][kb + r] = Xs[r][g];
+      X[g][kb + r] = to_cd(Xs[r][g]);
     }
     for (int r = kb + bs + tid; r < n; r += T) {
-      cd acc[SG];
+      TF acc[SG];
 #pragma unroll
-      for (int g = 0; g < SG; ++g) acc[g] = C(0.0);
+      for (int g = 0; g < SG; ++g) acc[g] = czero<TF>();
       for (int c = 0; c < bs; ++c) {
-        cd l = L[(size_t)(kb + c) * n + r];
+        TF l = L[(size_t)(kb + c) * n + r];
 #pragma unroll
         for (int g = 0; g < SG; ++g) acc[g] = fma(l, Xs[c][g], acc[g]);
       }
-      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - acc[g];
+      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - to_cd(acc[g]);
     }
     __syncthreads();
   }
@@ -311,7 +334,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict
     }
     for (int t = tid; t < bs * G; t += T) {
       int r = t % bs, g = t / bs;
-      Xs[r][g] = X[g][kb + r];
+      Xs[r][g] = conv<TF>(X[g][kb + r]);
     }
     __syncthreads();
     for (int c = bs - 1; c >= 0; --c) {
@@ -325,18 +348,18 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict
     }
     for (int t = tid; t < bs * G; t += T) {
       int r = t % bs, g = t / bs;
-      X[g][kb + r] = Xs[r][g];
+      X[g][kb + r] = to_cd(Xs[r][g]);
     }
     for (int r = tid; r < kb; r += T) {
-      cd acc[SG];
+      TF acc[SG];
 #pragma unroll
-      for (int g = 0; g < SG; ++g) acc[g] = C(0.0);
+      for (int g = 0; g < SG; ++g) acc[g] = czero<TF>();
       for (int c = 0; c < bs; ++c) {
-        cd u = L[(size_t)(kb + c) * n + r];
+        TF u = L[(size_t)(kb + c) * n + r];
 #pragma unroll
         for (int g = 0; g < SG; ++g) acc[g] = fma(u, Xs[c][g], acc[g]);
       }
-      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - acc[g];
+      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - to_cd(acc[g]);
     }
     __syncthreads();
   }
@@ -346,7 +369,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const cd* __restrict
     int q, ri; bool neg;
     job_of(m, M, nrhs, job0 + g, &q, &ri, &neg);
     double sg = (neg && ((r & 3) == 1 || (r & 3) == 2)) ? -1.0 : 1.0;
-    X[g][r] = (sg / sw[r >> 2]) * X[g][r];
+    X[g][r] = (sg / (PHYS ? sw[r >> 2] : 1.0)) * X[g][r];
   }
 }
 
@@ -354,6 +377,14 @@ void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw
                     cudaStream_t s) {
   int groups = (2 * nrhs + SG - 1) / SG;
   int smem = n * (int)sizeof(int);
-  cudaFuncSetAttribute(solve_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  solve_blocked_kernel<<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+  cudaFuncSetAttribute(solve_blocked_kernel<cd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  solve_blocked_kernel<cd, true><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+}
+
+void lu_correction_solve_c64(const cf* LU, const int* piv, int n, int M, const cd* r, cd* d, int nrhs,
+                             cudaStream_t s) {
+  int groups = (2 * nrhs + SG - 1) / SG;
+  int smem = n * (int)sizeof(int);
+  cudaFuncSetAttribute(solve_blocked_kernel<cf, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  solve_blocked_kernel<cf, false><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, nullptr, r, d, nrhs);
 }

@@ -15,6 +15,8 @@ struct LuTiming {
   int launches = 0;          // all kernel launches of the factorization
 };
 void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* t = nullptr);
+// The same factorization in complex64 (mixed-precision path).
+void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* t = nullptr);
 
 // Solve with factors of modes m = 0..M for right-hand sides of modes -M..M:
 // rhs/x layout [2M+1][nrhs][n] (mode q = m + M); sw[n/4] = sqrt of the L2 weights of the nodes
@@ -23,3 +25,9 @@ void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_
 // per node.
 void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
                     cudaStream_t s);
+
+// Mixed path: d = A'^{-1} r with the complex64 factors of modes 0..M in FP32
+// arithmetic, in the L2-weighted space (no sqrt-weight scaling), for all modes
+// -M..M (layout [2M+1][nrhs][n], -m by reflection).
+void lu_correction_solve_c64(const cf* LU, const int* piv, int n, int M, const cd* r, cd* d, int nrhs,
+                             cudaStream_t s);

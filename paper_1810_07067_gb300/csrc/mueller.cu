@@ -11,6 +11,7 @@
 #include "green.cuh"
 #include "lu.cuh"
 #include "fields.cuh"
+#include "mixed.cuh"
 
 static thread_local std::string g_err;
 static int fail(int code, const std::string& msg) {
@@ -151,7 +152,8 @@ static void lagrange_row(const Rules& R, double t, double* L) {
 // ---------------------------------------------------------------- setup
 struct Setup {
   int N = 0, n = 0, nP = 0, closed = 0, M = 0, nphi = 0, formulation = 0, precision = 0;
-  double omega = 0, split_eps = 1e-17, rmax = 0;
+  double omega = 0, split_eps = 1e-17, rmax = 0, refine_tol = 1e-14;
+  int refine_max_iter = 10;
   cd k0{}, k1{}, eps0{}, mu0{}, eps1{}, mu1{};
   std::vector<double> r, z, rp, zp, w, sw;                  // nodes
   std::vector<double> sr, sz, srp, szp, sW;                 // support points
@@ -209,7 +211,9 @@ static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M,
   if (!cv->r || !cv->z || !cv->dr || !cv->dz) return fail(MUELLER_EINVAL, "null curve array");
   if (M < 0 || M > 4096) return fail(MUELLER_EINVAL, "M out of range [0, 4096]");
   if (op->formulation != 0 && op->formulation != 1) return fail(MUELLER_EINVAL, "formulation must be 0 or 1");
-  if (op->precision != 0) return fail(MUELLER_EINVAL, "precision: only the FP64 path (0) is available");
+  if (op->precision != 0 && op->precision != 1) return fail(MUELLER_EINVAL, "precision must be 0 (FP64) or 1 (mixed)");
+  if (op->precision == 1 && !(op->refine_tol > 0.0 && op->refine_tol < 1.0))
+    return fail(MUELLER_EINVAL, "mixed precision needs 0 < refine_tol < 1");
   if (!(md->omega > 0.0)) return fail(MUELLER_EINVAL, "omega must be > 0 (the method excludes omega -> 0)");
   auto ok_body = [](mueller_c128 v) { return v.re > 0.0 && v.im >= 0.0; };
   auto ok_back = [](mueller_c128 v) { return v.re > 0.0 && v.im == 0.0; };
@@ -219,6 +223,7 @@ static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M,
   const Rules& R = rules();
   S.nP = cv->n_panels; S.N = 16 * S.nP; S.n = 4 * S.N; S.closed = cv->closed ? 1 : 0; S.M = M;
   S.formulation = op->formulation; S.precision = op->precision;
+  S.refine_tol = op->refine_tol; S.refine_max_iter = op->refine_max_iter > 0 ? op->refine_max_iter : 10;
   S.split_eps = op->split_eps > 0 ? op->split_eps : 1e-17;
   S.omega = md->omega;
   S.eps0 = tocd(md->eps0); S.mu0 = tocd(md->mu0); S.eps1 = tocd(md->eps1); S.mu1 = tocd(md->mu1);
@@ -486,7 +491,9 @@ struct mueller_ctx {
   Setup S;
   DevBuf keep;
   double* geo[6] = {nullptr};  // r, z, rp, zp, w, sw on the device
-  cd* A = nullptr;             // factors [M+1][n][n]
+  cd* A = nullptr;             // FP64 path: factors; mixed path: the weighted matrices [M+1][n][n]
+  cf* A32 = nullptr;           // mixed path: complex64 factors
+  double* normA = nullptr;     // mixed path: ||A'_m||_inf
   int* piv = nullptr;
   int* info = nullptr;
   mueller_stats st{};
@@ -504,12 +511,15 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   setup_pairs(c->S);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = c->S.n;
-  size_t bytes = (size_t)(M + 1) * n * n * sizeof(cd);
+  const bool mixed = c->S.precision == 1;
+  size_t bytes = (size_t)(M + 1) * n * n * (sizeof(cd) + (mixed ? sizeof(cf) : 0));
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   if (bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
   if (c->keep.alloc(&c->A, (size_t)(M + 1) * n * n) != cudaSuccess ||
-      c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess) {
+      c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess ||
+      (mixed && (c->keep.alloc(&c->A32, (size_t)(M + 1) * n * n) != cudaSuccess ||
+                 c->keep.alloc(&c->normA, M + 1) != cudaSuccess))) {
     delete c;
     return fail(MUELLER_ENOMEM, "factor allocation");
   }
@@ -520,7 +530,14 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   if (rc) { delete c; return rc; }
   cudaEventRecord(e1, s);
   LuTiming lt;
-  lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s, &lt);
+  if (mixed) {
+    mixed_norm_inf(c->A, (int)n, M + 1, c->normA, s);
+    mixed_convert(c->A, c->A32, (size_t)(M + 1) * n * n, s);
+    lu_factor_batched_c64(c->A32, (int)n, M + 1, c->piv, c->info, s, &lt);
+    lt.launches += 2;
+  } else {
+    lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s, &lt);
+  }
   cudaEventRecord(e2, s);
   cudaError_t err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) { delete c; return fail(MUELLER_ECUDA, cudaGetErrorString(err)); }
@@ -554,12 +571,68 @@ extern "C" int mueller_assemble(const mueller_curve* curve, const mueller_media*
   return assemble_core(S, (cd*)A_dev, (cudaStream_t)stream, nullptr, keep, nullptr);
 }
 
+// Iterative refinement with complex64 factors and FP64 residuals (see mixed.cu).
+static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* backward_err, cudaStream_t s) {
+  const int n = c->S.n, M = c->S.M;
+  const long long nvec = (long long)(2 * M + 1) * nrhs;
+  DevBuf tmp;
+  cd *bw, *y, *r, *d;
+  double* norms;  // [3][nvec]: b', y, r
+  if (tmp.alloc(&bw, (size_t)nvec * n) || tmp.alloc(&y, (size_t)nvec * n) || tmp.alloc(&r, (size_t)nvec * n) ||
+      tmp.alloc(&d, (size_t)nvec * n) || tmp.alloc(&norms, (size_t)3 * nvec))
+    return fail(MUELLER_ENOMEM, "refinement work vectors");
+  double *bn = norms, *yn = norms + nvec, *rn = norms + 2 * nvec;
+  std::vector<double> hA(M + 1), hn((size_t)3 * nvec), be((size_t)nvec, 0.0);
+  CK(cudaMemcpyAsync(hA.data(), c->normA, sizeof(double) * (M + 1), cudaMemcpyDeviceToHost, s));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  mixed_scale(rhs, bw, c->geo[5], n, nvec, bn, s);
+  lu_correction_solve_c64(c->A32, c->piv, n, M, bw, d, nrhs, s);
+  mixed_update(y, d, n, nvec, true, yn, s);
+  int it = 0, launches = 3;
+  bool done = false;
+  double worst = 0.0;
+  for (; it < c->S.refine_max_iter; ++it) {
+    mixed_residual(c->A, n, M, bw, y, r, nrhs, rn, s);
+    launches += 1;
+    CK(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * 3 * nvec, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    worst = 0.0;
+    for (long long v = 0; v < nvec; ++v) {
+      int q = (int)(v / nrhs), m = std::abs(q - M);
+      double den = hA[m] * hn[nvec + v] + hn[v];
+      be[v] = den > 0 ? hn[2 * nvec + v] / den : 0.0;
+      worst = std::max(worst, be[v]);
+    }
+    if (worst <= c->S.refine_tol) { done = true; break; }
+    lu_correction_solve_c64(c->A32, c->piv, n, M, r, d, nrhs, s);
+    mixed_update(y, d, n, nvec, false, yn, s);
+    launches += 2;
+  }
+  mixed_unscale(y, x, c->geo[5], n, nvec, s);
+  cudaEventRecord(e1, s);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(MUELLER_ECUDA, cudaGetErrorString(err));
+  c->st.ms_solve = ms;
+  c->st.solve_launches = launches + 1;
+  c->st.refine_iters = it;
+  c->st.backward_err_max = worst;
+  if (backward_err) std::copy(be.begin(), be.end(), backward_err);
+  if (!done) return fail(MUELLER_ENOCONV, "refinement stopped at refine_max_iter");
+  return MUELLER_OK;
+}
+
 extern "C" int mueller_solve(mueller_ctx* c, const mueller_c128* rhs_dev, int nrhs, mueller_c128* x_dev,
                              double* backward_err, void* stream) {
   g_err.clear();
   if (!c || !rhs_dev || !x_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid solve arguments");
   if ((const void*)rhs_dev == (const void*)x_dev) return fail(MUELLER_EINVAL, "rhs and x must not alias");
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->S.precision == 1) return solve_mixed(c, (const cd*)rhs_dev, nrhs, (cd*)x_dev, backward_err, s);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0); cudaEventCreate(&e1);
   cudaEventRecord(e0, s);

@@ -1,0 +1,74 @@
+"""Mixed-precision path: complex64 factors + FP64 iterative refinement."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_07067_gb300 as m
+    return m
+
+
+def _rel(xa, xb, M):
+    num = max(np.linalg.norm(xa[q] - xb[q]) for q in range(2 * M + 1))
+    den = max(np.linalg.norm(xb[q]) for q in range(2 * M + 1))
+    return num / den
+
+
+def test_mixed_sphere_vs_oracle(mb, sphere_oracle):
+    cfg = sphere_oracle["cfg"]
+    M = cfg.M
+    ctx = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi, precision=1, refine_tol=1e-14))
+    b = torch.tensor(np.ascontiguousarray(sphere_oracle["b"].transpose(0, 2, 1)), device=DEV)
+    x = torch.zeros_like(b)
+    be = np.zeros((2 * M + 1) * b.shape[1])
+    ctx.solve(b, x, backward_err=be)
+    st = ctx.stats()
+    assert st["refine_iters"] >= 1 and be.max() <= 1e-14
+    xg = x.cpu().numpy().transpose(0, 2, 1)
+    assert _rel(xg, sphere_oracle["x"], M) < 1e-10
+
+
+def test_mixed_cylinder_full_size_vs_fp64(mb):
+    """Cylinder workload at full size: mixed-path currents against the FP64
+    path's (the FP64 path is itself checked against the oracle block by block)."""
+    cfg = W.config_cylinder(7)
+    M, n = cfg.M, 4 * cfg.N
+    nrhs = len(cfg.waves)
+    dirs = [w.d for w in cfg.waves]; pols = [w.e for w in cfg.waves]
+    c64 = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi))
+    b = torch.zeros((2 * M + 1, nrhs, n), dtype=torch.complex128, device=DEV)
+    c64.rhs_planewave(dirs, pols, b)
+    x64 = torch.zeros_like(b)
+    c64.solve(b, x64)
+    c64.close()
+    cmx = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi, precision=1, refine_tol=1e-14))
+    xmx = torch.zeros_like(b)
+    be = np.zeros((2 * M + 1) * nrhs)
+    cmx.solve(b, xmx, backward_err=be)
+    assert be.max() <= 1e-14
+    a, r = xmx.cpu().numpy(), x64.cpu().numpy()
+    assert _rel(a, r, M) < 1e-11
+
+
+def test_mixed_reports_no_convergence(mb):
+    cur = W.sphere(2)
+    med = W.Media.from_k(1.0, 1.5)
+    M = 2
+    ctx = mb.build(cur, med, M, mb.Options(n_phi=64, precision=1, refine_tol=1e-300, refine_max_iter=1))
+    n = 4 * cur.N
+    b = torch.ones((2 * M + 1, 1, n), dtype=torch.complex128, device=DEV)
+    x = torch.zeros_like(b)
+    with pytest.raises(mb.MuellerError) as e:
+        ctx.solve(b, x)
+    assert e.value.status == 4
+    assert torch.isfinite(x.abs()).all()
