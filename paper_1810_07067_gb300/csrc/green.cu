@@ -121,37 +121,93 @@ __device__ __forceinline__ WarpSmem warp_smem(const GreenParams& gp, char* base)
 }
 
 // The pair is the target (rt, zt) and the displacement (dr0, zd) = target - source.
+// Non-split pairs are sampled on every dec-th point of the n_phi grid
+// (dec = 1, 2, 4: a coarser grid for well-separated pairs, chosen so that the
+// trapezoid aliasing stays below the splitting threshold); split pairs use
+// the full grid.  The cosine transform folds samples j and n/2 - j (cos of
+// the mirrored angle is (-1)^m times the original), halving its work.
+__device__ int decimation(const GreenParams& gp, double rt, double dr0, double zd, bool split, double lneps) {
+  if (split) return 1;
+  const double d2 = dr0 * dr0 + zd * zd, B = 2.0 * rt * (rt - dr0);
+  const double c = d2 / B;
+  const double lz = log1p(c + sqrt(c * (2.0 + c)));
+  int dec = 1;
+  while (dec < 4) {
+    int nl = gp.nphi / (2 * dec);
+    if (nl < 16 || nl < 2 * gp.M + 4 || (double)(nl - gp.M - 1) * lz < lneps) break;
+    dec *= 2;
+  }
+  return dec;
+}
+
 __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
                                   long long sid, const double* __restrict__ leg, long long n_split,
                                   const double* __restrict__ cosT, const double* __restrict__ s2T,
-                                  const WarpSmem& W, int lane) {
-  const int H = gp.H, Ms = gp.Ms, Mq = gp.Mq, mask = gp.nphi - 1;
+                                  const WarpSmem& W, int lane, int dec = 1) {
+  const int Ms = gp.Ms, Mq = gp.Mq, mask = gp.nphi - 1;
+  const int nl = gp.nphi / dec;          // local grid size
+  const int H = nl / 2 + 1, Q = nl / 4;  // samples on [0, pi]; fold point
   const double rs = rt - dr0;
   const double d2 = dr0 * dr0 + zd * zd;
   const double alpha = dr0 - d2 / (2.0 * rt);
   const bool split = sid >= 0;
   const double TWO_PI = 6.283185307179586;
-  if (split) {
+  if (split) {  // dec == 1
     for (int nn = lane; nn <= Mq; nn += 32) W.phs[nn] = leg[(long long)nn * n_split + sid];
     __syncwarp();
-    for (int j = lane; j < H; j += 32) {
-      double acc = 0.0;
-      for (int nn = 1; nn <= Mq; ++nn) acc = fma(W.phs[nn], cosT[(nn * j) & mask], acc);
-      W.q[j] = (W.phs[0] + 2.0 * acc) / TWO_PI;
+    // q_j = (P^_0 + 2 sum_n P^_n cos(n phi_j)) / 2pi, folded: even n give E, odd n give O,
+    // q_j = E + O and q_{n/2 - j} = E - O
+    for (int j = lane; j <= Q; j += 32) {
+      double e = 0.0, o = 0.0;
+      for (int nn = 1; nn <= Mq; nn += 2) o = fma(W.phs[nn], cosT[(nn * j) & mask], o);
+      for (int nn = 2; nn <= Mq; nn += 2) e = fma(W.phs[nn], cosT[(nn * j) & mask], e);
+      e = W.phs[0] + 2.0 * e;
+      o = 2.0 * o;
+      W.q[j] = (e + o) / TWO_PI;
+      W.q[H - 1 - j] = (e - o) / TWO_PI;
     }
     __syncwarp();
   }
   const cd g0 = gp.gamma0;
+  const double kmin = fmin(cabs(gp.kp0.k), cabs(gp.kp1.k));
   for (int j = lane; j < H; j += 32) {
-    double s2 = s2T[j];
+    double s2 = s2T[j * dec];
     double u = d2 + 4.0 * rt * rs * s2;
     double su = sqrt(u);
     double rd = dr0 + 2.0 * rs * s2;
+    cd F[NFAM];
+    if (!split && kmin * su >= 2.0) {
+      // both |k rho| >= 2: the kernels and their u-derivatives directly from
+      // exp(i k rho), 4 pi E = e/rho, 4 pi E' = e (ik rho - 1)/(2 rho^3),
+      // 4 pi E'' = e ((ik rho)^2 - 3 ik rho + 3)/(4 rho^5); the k0 - k1
+      // difference does not cancel at these arguments.
+      double isu = 1.0 / su, iu = isu * isu;
+      cd E0[3], E1[3];
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        cd ikr = mul_i(((w == 0) ? gp.kp0.k : gp.kp1.k) * su);
+        cd e = cexpi(((w == 0) ? gp.kp0.k : gp.kp1.k) * su);
+        cd* E = (w == 0) ? E0 : E1;
+        E[0] = e * isu;
+        E[1] = (0.5 * iu * isu) * (e * (ikr - C(1.0)));
+        E[2] = (0.25 * iu * iu * isu) * (e * (ikr * ikr - 3.0 * ikr + C(3.0)));
+      }
+      F[0] = E0[0]; F[1] = E1[0];
+      F[2] = (2.0 * rd) * E0[1]; F[3] = (2.0 * zd) * E0[1];
+      F[4] = (2.0 * rd) * E1[1]; F[5] = (2.0 * zd) * E1[1];
+      cd D1 = E0[1] - E1[1], D2 = E0[2] - E1[2];
+      F[6] = (4.0 * rd * rd) * D2 + 2.0 * D1;
+      F[7] = (4.0 * rd * zd) * D2;
+      F[8] = (4.0 * zd * zd) * D2 + 2.0 * D1;
+      double wj = (j == 0 || j == H - 1) ? 0.5 : 1.0;
+#pragma unroll
+      for (int f = 0; f < NFAM; ++f) W.smp[f * H + j] = wj * F[f];
+      continue;
+    }
     Ent e0 = entire(c_tab, gp.kp0, su);
     Ent e1 = entire(c_tab, gp.kp1, su);
     cd gam1 = e0.Gam - e1.Gam, gam2 = e0.Gam2 - e1.Gam2, gam1p = e0.Gamp - e1.Gamp;
     cd dSp = e0.Sp - e1.Sp, dSpp = e0.Spp - e1.Spp;
-    cd F[NFAM];
     if (!split) {
       double isu = 1.0 / su, iu3 = isu / u;
       F[0] = e0.C * isu + mul_i(e0.S);
@@ -184,9 +240,17 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
     for (int f = 0; f < NFAM; ++f) W.smp[f * H + j] = wj * F[f];
   }
   __syncwarp();
-  // cosine transform: spec_m = (1/nphi) sum_j w_j F_j cos(m phi_j) (the 4pi of
-  // G is folded into 1/nphi * (4pi/4pi)); the u^{-3/2} part is added exactly.
-  const double inv = 1.0 / gp.nphi;
+  // fold: smp[j] <- w_j F_j + w_{n/2-j} F_{n/2-j} (even m), smp[n/2-j] <- difference (odd m)
+  for (int t = lane; t < NFAM * Q; t += 32) {
+    int f = t / Q, j = t % Q;
+    cd a = W.smp[f * H + j], b = W.smp[f * H + H - 1 - j];
+    W.smp[f * H + j] = a + b;
+    W.smp[f * H + H - 1 - j] = a - b;
+  }
+  __syncwarp();
+  // cosine transform: spec_m = (1/n) sum_j w_j F_j cos(m phi_j) (the 4pi of G
+  // is folded into the normalisation); the u^{-3/2} part is added exactly.
+  const double inv = 1.0 / nl;
   const double FOUR_PI = 12.566370614359172;
   cd beta[NFAM];
   if (split) {
@@ -201,10 +265,17 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
     cd acc[NFAM];
 #pragma unroll
     for (int f = 0; f < NFAM; ++f) acc[f] = C(0.0);
-    for (int j = 0; j < H; ++j) {
-      double c = cosT[(j * mm) & mask];
+    const bool odd = mm & 1;
+    for (int j = 0; j < Q; ++j) {
+      double c = cosT[(j * mm * dec) & mask];
+      int jj = odd ? (H - 1 - j) : j;
 #pragma unroll
-      for (int f = 0; f < NFAM; ++f) acc[f] = fma(c, W.smp[f * H + j], acc[f]);
+      for (int f = 0; f < NFAM; ++f) acc[f] = fma(c, W.smp[f * H + jj], acc[f]);
+    }
+    if (!odd) {  // centre sample j = n/4 pairs with itself (odd m: cos = 0)
+      double c = cosT[(Q * mm * dec) & mask];
+#pragma unroll
+      for (int f = 0; f < NFAM; ++f) acc[f] = fma(c, W.smp[f * H + Q], acc[f]);
     }
     double Sm = split ? Shat[(long long)mm * n_split + sid] / FOUR_PI : 0.0;
 #pragma unroll
@@ -303,7 +374,9 @@ __global__ void far_kernel(BuildArgs a) {
     if (near_panels(i / P_NODES, j / P_NODES, a.n_panels, a.closed)) continue;
     long long sid = a.split_far[p];
     double rt = a.geo.r[i], rs = a.geo.r[j];
-    warp_pair_spectra(gp, rt, rt - rs, a.geo.z[i] - a.geo.z[j], sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane);
+    const double dr0 = rt - rs, zd0 = a.geo.z[i] - a.geo.z[j];
+    int dec = decimation(gp, rt, dr0, zd0, sid >= 0, a.lneps);
+    warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec);
     const double w = a.geo.w[j], rps = a.geo.rp[j], zps = a.geo.zp[j];
     const double fac[3] = {w * rs * rps, w * rs, w * rs * zps};
     const cd* spec = W.spec;
@@ -358,7 +431,8 @@ __global__ void support_kernel(BuildArgs a) {
     double rt = a.geo.r[i], dr0, zd;
     if (slot < SELF_PTS) { dr0 = a.sup.dr[pid]; zd = a.sup.dz[pid]; }
     else { dr0 = rt - a.sup.r[pid]; zd = a.geo.z[i] - a.sup.z[pid]; }
-    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane);
+    int dec = decimation(gp, rt, dr0, zd, sid >= 0, a.lneps);
+    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec);
     cd* dst = a.spec_sup + p * NFAM * gp.Ms;
     for (int t = lane; t < NFAM * gp.Ms; t += 32) dst[t] = W.spec[t];
     __syncwarp();

@@ -58,6 +58,7 @@ struct BuildArgs {
   cd* spec_sup;         // [N*NEAR_SLOTS][NFAM][Ms] support spectra scratch
   cd* A;                // [M+1][n][n] column-major per mode
   int kc;               // columns per CTA in the near contraction
+  double lneps;         // -ln(split threshold): grid decimation criterion
 };
 
 // shared memory used by one warp of the pair-spectra routine (16-byte multiple)

@@ -464,6 +464,7 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   a.sup = SupportTable{ssr, ssz, ssrp, sszp, ssW, ssdr, ssdz, sLs, sLa};
   a.cosT = dcos; a.s2T = ds2; a.split_far = dsf; a.split_sup = dss; a.leg = dleg; a.n_split = n_split;
   a.spec_sup = dspec; a.A = A_dev;
+  a.lneps = -std::log(S.split_eps);
   int kc = 8;
   while (kc > 1 && kc * 3 * NFAM * Ms * 16 + SELF_PTS * kc * 3 * 8 > 200 * 1024) kc /= 2;
   a.kc = kc;

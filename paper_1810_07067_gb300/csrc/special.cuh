@@ -46,9 +46,15 @@ inline void fill_series_tables(SeriesTables* t) {
   }
 }
 
-HD cd horner(const double* c, cd x2) {
-  cd acc = C(c[SPECIAL_NTERM - 1]);
-  for (int p = SPECIAL_NTERM - 2; p >= 0; --p) acc = fma(acc, x2, C(c[p]));
+// terms needed for |x^2| <= a2 so that the truncated tail is below 1e-17
+// relative (the coefficients decay at least like 4^n / (2n)!)
+HD int series_terms(double a2) {
+  return a2 < 0.0625 ? 7 : (a2 < 0.25 ? 8 : (a2 < 1.0 ? 10 : (a2 < 2.25 ? 12 : (a2 < 4.0 ? 14 : SPECIAL_NTERM))));
+}
+
+HD cd horner(const double* c, cd x2, int nt = SPECIAL_NTERM) {
+  cd acc = C(c[nt - 1]);
+  for (int p = nt - 2; p >= 0; --p) acc = fma(acc, x2, C(c[p]));
   return acc;
 }
 
@@ -67,11 +73,12 @@ HD SphFun sph_closed(cd x, cd s, cd c) {
   return f;
 }
 
-HD SphFun sph_series(const SeriesTables& T, cd x2) {
+HD SphFun sph_series(const SeriesTables& T, cd x2, bool need_sig2 = true) {
+  int nt = series_terms(norm2(x2) > 0 ? sqrt(norm2(x2)) : 0.0);
   SphFun f;
-  f.sinc = horner(T.sinc, x2);
-  f.sig1 = horner(T.sig1, x2);
-  f.sig2 = horner(T.sig2, x2);
+  f.sinc = horner(T.sinc, x2, nt);
+  f.sig1 = horner(T.sig1, x2, nt);
+  f.sig2 = need_sig2 ? horner(T.sig2, x2, nt) : C(0.0);
   return f;
 }
 
@@ -105,22 +112,23 @@ HD Ent entire(const SeriesTables& T, const KPow& kp, double su) {
   cd cosx;
   if (ax < 2.0) {
     fx = sph_series(T, x2);
-    fh = sph_series(T, 0.25 * x2);
+    fh = sph_series(T, 0.25 * x2, false);
   } else {
     cd sh, chh;
     csincos(h, &sh, &chh);
     cd sx = 2.0 * (sh * chh);
     cd cx = C(1.0) - 2.0 * (sh * sh);
     fx = sph_closed(x, sx, cx);
-    if (ax < 4.0) fh = sph_series(T, 0.25 * x2);
+    if (ax < 4.0) fh = sph_series(T, 0.25 * x2, false);
     else fh = sph_closed(h, sh, chh);
   }
   // cos x = 1 - 2 sin^2(x/2) = 1 - (x^2/2) sinc(x/2)^2  (stable for all x)
   cosx = C(1.0) - 0.5 * (x2 * (fh.sinc * fh.sinc));
   cd phi2, phi3;
   if (ax < 2.0) {
-    phi2 = horner(T.phi2, x2);
-    phi3 = horner(T.phi3, x2);
+    int nt = series_terms(ax * ax);
+    phi2 = horner(T.phi2, x2, nt);
+    phi3 = horner(T.phi3, x2, nt);
   } else {
     phi2 = (C(1.0) + fh.sinc * fh.sinc - 2.0 * fx.sinc) / (4.0 * x2);
     phi3 = (0.5 * (fh.sinc * fh.sig1) - 2.0 * fx.sig1) * 0.125;
