@@ -77,8 +77,10 @@ typedef struct {
                           automatically when too small for M and k (see
                           stats.n_phi_used)                                 */
   int formulation;     /* 0 direct (eq. mullerrep), 1 indirect (eq. dualmullrep) */
-  int precision;       /* 0 FP64; 1 mixed (FP32-grade trailing updates + FP64
-                          iterative refinement)                             */
+  int precision;       /* 0 FP64; 1 mixed: complex64 LU + iterative refinement
+                          whose complex128-accurate residuals run on BF16
+                          tensor cores (exact 8-digit slicing of A' and y);
+                          2 mixed with residuals on the FP64 pipe           */
   double refine_tol;   /* mixed: stop when backward error <= refine_tol     */
   int refine_max_iter; /* mixed: cap on refinement steps                    */
   double split_eps;    /* kernel splitting when the plain trapezoid would

@@ -12,6 +12,7 @@
 #include "lu.cuh"
 #include "fields.cuh"
 #include "mixed.cuh"
+#include "ozaki.cuh"
 
 static thread_local std::string g_err;
 static int fail(int code, const std::string& msg) {
@@ -211,8 +212,9 @@ static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M,
   if (!cv->r || !cv->z || !cv->dr || !cv->dz) return fail(MUELLER_EINVAL, "null curve array");
   if (M < 0 || M > 4096) return fail(MUELLER_EINVAL, "M out of range [0, 4096]");
   if (op->formulation != 0 && op->formulation != 1) return fail(MUELLER_EINVAL, "formulation must be 0 or 1");
-  if (op->precision != 0 && op->precision != 1) return fail(MUELLER_EINVAL, "precision must be 0 (FP64) or 1 (mixed)");
-  if (op->precision == 1 && !(op->refine_tol > 0.0 && op->refine_tol < 1.0))
+  if (op->precision < 0 || op->precision > 2)
+    return fail(MUELLER_EINVAL, "precision must be 0 (FP64), 1 (mixed, tensor-core residuals) or 2 (mixed, FP64 residuals)");
+  if (op->precision != 0 && !(op->refine_tol > 0.0 && op->refine_tol < 1.0))
     return fail(MUELLER_EINVAL, "mixed precision needs 0 < refine_tol < 1");
   if (!(md->omega > 0.0)) return fail(MUELLER_EINVAL, "omega must be > 0 (the method excludes omega -> 0)");
   auto ok_body = [](mueller_c128 v) { return v.re > 0.0 && v.im >= 0.0; };
@@ -495,6 +497,9 @@ struct mueller_ctx {
   cd* A = nullptr;             // FP64 path: factors; mixed path: the weighted matrices [M+1][n][n]
   cf* A32 = nullptr;           // mixed path: complex64 factors
   double* normA = nullptr;     // mixed path: ||A'_m||_inf
+  __nv_bfloat16* Asl = nullptr;  // precision 1: digit slices of A' for tensor-core residuals
+  double* rowscale = nullptr;
+  int npad = 0;
   int* piv = nullptr;
   int* info = nullptr;
   mueller_stats st{};
@@ -512,15 +517,20 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   setup_pairs(c->S);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = c->S.n;
-  const bool mixed = c->S.precision == 1;
-  size_t bytes = (size_t)(M + 1) * n * n * (sizeof(cd) + (mixed ? sizeof(cf) : 0));
+  const bool mixed = c->S.precision != 0;
+  const bool slices = c->S.precision == 1;
+  c->npad = (int)((n + OZ_RT - 1) / OZ_RT * OZ_RT);
+  const size_t slice_bytes = slices ? ozaki_matrix_slices_elems(c->npad, M + 1) * 2 : 0;
+  size_t bytes = (size_t)(M + 1) * n * n * (sizeof(cd) + (mixed ? sizeof(cf) : 0)) + slice_bytes;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   if (bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
   if (c->keep.alloc(&c->A, (size_t)(M + 1) * n * n) != cudaSuccess ||
       c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess ||
       (mixed && (c->keep.alloc(&c->A32, (size_t)(M + 1) * n * n) != cudaSuccess ||
-                 c->keep.alloc(&c->normA, M + 1) != cudaSuccess))) {
+                 c->keep.alloc(&c->normA, M + 1) != cudaSuccess)) ||
+      (slices && (c->keep.alloc(&c->Asl, ozaki_matrix_slices_elems(c->npad, M + 1)) != cudaSuccess ||
+                  c->keep.alloc(&c->rowscale, (size_t)(M + 1) * c->npad) != cudaSuccess))) {
     delete c;
     return fail(MUELLER_ENOMEM, "factor allocation");
   }
@@ -534,6 +544,10 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   if (mixed) {
     mixed_norm_inf(c->A, (int)n, M + 1, c->normA, s);
     mixed_convert(c->A, c->A32, (size_t)(M + 1) * n * n, s);
+    if (slices) {
+      ozaki_slice_matrix(c->A, (int)n, c->npad, M + 1, c->Asl, c->rowscale, s);
+      lt.launches += 2;
+    }
     lu_factor_batched_c64(c->A32, (int)n, M + 1, c->piv, c->info, s, &lt);
     lt.launches += 2;
   } else {
@@ -553,6 +567,12 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   c->st.singular_mode = -1; c->st.singular_column = -1;
   for (int m = 0; m <= M; ++m)
     if (info[m]) { c->st.singular_mode = m; c->st.singular_column = info[m] - 1; break; }
+  if (slices) {  // the residuals use the slices; the complex128 matrices are no longer needed
+    cudaFree(c->A);
+    c->keep.ptrs.erase(std::find(c->keep.ptrs.begin(), c->keep.ptrs.end(), (void*)c->A));
+    c->A = nullptr;
+    bytes -= (size_t)(M + 1) * n * n * sizeof(cd);
+  }
   c->st.device_bytes = bytes;
   *out = c;
   if (c->st.singular_mode >= 0) return fail(MUELLER_ESINGULAR, "exact zero pivot");
@@ -576,12 +596,20 @@ extern "C" int mueller_assemble(const mueller_curve* curve, const mueller_media*
 static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* backward_err, cudaStream_t s) {
   const int n = c->S.n, M = c->S.M;
   const long long nvec = (long long)(2 * M + 1) * nrhs;
+  const bool tcres = c->Asl != nullptr;
+  const int njt = (2 * nrhs + OZ_JT - 1) / OZ_JT;
   DevBuf tmp;
   cd *bw, *y, *r, *d;
   double* norms;  // [3][nvec]: b', y, r
+  __nv_bfloat16* Ysl = nullptr;
+  double* colscale = nullptr;
+  int* derr = nullptr;
   if (tmp.alloc(&bw, (size_t)nvec * n) || tmp.alloc(&y, (size_t)nvec * n) || tmp.alloc(&r, (size_t)nvec * n) ||
-      tmp.alloc(&d, (size_t)nvec * n) || tmp.alloc(&norms, (size_t)3 * nvec))
+      tmp.alloc(&d, (size_t)nvec * n) || tmp.alloc(&norms, (size_t)3 * nvec) ||
+      (tcres && (tmp.alloc(&Ysl, ozaki_vector_slices_elems(c->npad, M + 1, njt)) ||
+                 tmp.alloc(&colscale, (size_t)(M + 1) * njt * OZ_JT) || tmp.alloc(&derr, 1))))
     return fail(MUELLER_ENOMEM, "refinement work vectors");
+  if (derr) CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
   double *bn = norms, *yn = norms + nvec, *rn = norms + 2 * nvec;
   std::vector<double> hA(M + 1), hn((size_t)3 * nvec), be((size_t)nvec, 0.0);
   CK(cudaMemcpyAsync(hA.data(), c->normA, sizeof(double) * (M + 1), cudaMemcpyDeviceToHost, s));
@@ -595,8 +623,13 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   bool done = false;
   double worst = 0.0;
   for (; it < c->S.refine_max_iter; ++it) {
-    mixed_residual(c->A, n, M, bw, y, r, nrhs, rn, s);
-    launches += 1;
+    if (tcres) {
+      ozaki_residual(c->Asl, c->rowscale, n, c->npad, M, bw, y, r, nrhs, rn, Ysl, colscale, derr, s);
+      launches += 2;
+    } else {
+      mixed_residual(c->A, n, M, bw, y, r, nrhs, rn, s);
+      launches += 1;
+    }
     CK(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * 3 * nvec, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     worst = 0.0;
@@ -623,6 +656,11 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   c->st.refine_iters = it;
   c->st.backward_err_max = worst;
   if (backward_err) std::copy(be.begin(), be.end(), backward_err);
+  if (derr) {
+    int h = 0;
+    cudaMemcpy(&h, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (h) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core residual timed out");
+  }
   if (!done) return fail(MUELLER_ENOCONV, "refinement stopped at refine_max_iter");
   return MUELLER_OK;
 }
@@ -633,7 +671,7 @@ extern "C" int mueller_solve(mueller_ctx* c, const mueller_c128* rhs_dev, int nr
   if (!c || !rhs_dev || !x_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid solve arguments");
   if ((const void*)rhs_dev == (const void*)x_dev) return fail(MUELLER_EINVAL, "rhs and x must not alias");
   cudaStream_t s = (cudaStream_t)stream;
-  if (c->S.precision == 1) return solve_mixed(c, (const cd*)rhs_dev, nrhs, (cd*)x_dev, backward_err, s);
+  if (c->S.precision != 0) return solve_mixed(c, (const cd*)rhs_dev, nrhs, (cd*)x_dev, backward_err, s);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0); cudaEventCreate(&e1);
   cudaEventRecord(e0, s);

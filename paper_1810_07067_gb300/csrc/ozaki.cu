@@ -1,0 +1,313 @@
+// FP64-accurate products on BF16 tensor cores.
+//
+// Every row of A (and every column of Y) is scaled by a power of two sigma so
+// that |a/sigma| < 1/2, then written exactly as a/sigma = sum_{s=1..8} d_s 2^{-7s}
+// with integer digits |d_s| <= 64 (8 signed 7-bit digits, 56 bits; bf16 holds
+// them exactly).  Then
+//   sum_k a_ik y_kj = sigma_i tau_j sum_{s,t} 2^{-7(s+t)} sum_k d_s(ik) e_t(kj),
+// where the digit products are exact in FP32 and, for a fixed level s + t,
+// their sums over 256 values of k stay below 2^24 and hence exact as well.
+// Levels s + t <= 9 are kept (36 digit products per real product; the dropped
+// part is below 2^-68 of |a||y| per term).  Tensor memory holds one FP32
+// accumulator per level and per real/imaginary part (8 x 2 x 32 columns =
+// all 512); every 256 values of k they are drained into FP64 registers.
+// Operand tiles are stored in global memory in the shared-memory layout of the
+// MMA (no-swizzle K-major core matrices), so each 16-wide k-tile is a single
+// bulk asynchronous copy (TMA), double-buffered behind mbarriers.
+#include <cstdio>
+#include "ozaki.cuh"
+#include "tc.cuh"
+
+#define OZ_ATILE (OZ_RT * OZ_KT)          // bf16 elements per slice tile of A
+#define OZ_YTILE (OZ_JT * OZ_KT)          // bf16 elements per slice tile of Y
+#define OZ_ABLOCK (2 * OZ_S * OZ_ATILE)   // per (row tile, k-tile): re/im x 8 slices
+#define OZ_YBLOCK (2 * OZ_S * OZ_YTILE)
+
+size_t ozaki_matrix_slices_elems(int npad, int batch) {
+  return (size_t)batch * (npad / OZ_RT) * (npad / OZ_KT) * OZ_ABLOCK;
+}
+size_t ozaki_vector_slices_elems(int npad, int batch, int njt) {
+  return (size_t)batch * njt * (npad / OZ_KT) * OZ_YBLOCK;
+}
+
+// offset of element (row r, k) inside a slice tile with R rows and 16 columns
+// (core matrices of 8 x 8, row-group major; two core matrices along k)
+__device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ void digits(double v, float* d) {
+  // v in (-1/2, 1/2): d_s = rint(v * 2^7), v <- v * 2^7 - d_s (exact)
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    double x = v * 128.0;
+    double t = rint(x);
+    d[s] = (float)t;
+    v = x - t;
+  }
+}
+
+__device__ __forceinline__ double pow2_scale(double mx) {
+  if (!(mx > 0.0)) return 1.0;
+  int e;
+  frexp(mx, &e);               // mx = f 2^e, f in [1/2, 1)
+  return ldexp(1.0, e + 1);    // |a| / scale < 1/2
+}
+
+// row maxima: thread per row, columns streamed
+__global__ void oz_rowscale_kernel(const cd* __restrict__ A, int n, int npad, double* __restrict__ rowscale) {
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  double mx = 0.0;
+  if (i < n) {
+    const cd* M = A + (size_t)b * n * n;
+    for (int j = 0; j < n; ++j) {
+      cd v = M[(size_t)j * n + i];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  }
+  rowscale[(size_t)b * npad + i] = pow2_scale(mx);
+}
+
+// thread per (row i, group of 8 consecutive k): 16 digit rows of 16 bytes
+__global__ void oz_slice_matrix_kernel(const cd* __restrict__ A, int n, int npad, const double* __restrict__ rowscale,
+                                       __nv_bfloat16* __restrict__ Asl) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // row
+  const int kg = blockIdx.y;                              // group of 8 columns
+  if (i >= npad) return;
+  const int nrt = npad / OZ_RT, nkt = npad / OZ_KT;
+  const double inv = 1.0 / rowscale[(size_t)b * npad + i];
+  float dre[8][OZ_S], dim_[8][OZ_S];
+  const cd* M = A + (size_t)b * n * n;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    int k = kg * 8 + c;
+    cd v = (i < n && k < n) ? M[(size_t)k * n + i] : C(0.0);
+    digits(v.x * inv, dre[c]);
+    digits(v.y * inv, dim_[c]);
+  }
+  const int rt = i / OZ_RT, r = i % OZ_RT, kt = (kg * 8) / OZ_KT, kk = (kg * 8) % OZ_KT;
+  __nv_bfloat16* blk = Asl + (((size_t)b * nrt + rt) * nkt + kt) * OZ_ABLOCK;
+  const int off = core_off(r, kk);
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    __align__(16) __nv_bfloat16 re[8], im[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) { re[c] = __float2bfloat16(dre[c][s]); im[c] = __float2bfloat16(dim_[c][s]); }
+    *(uint4*)(blk + (0 * OZ_S + s) * OZ_ATILE + off) = *(uint4*)re;
+    *(uint4*)(blk + (1 * OZ_S + s) * OZ_ATILE + off) = *(uint4*)im;
+  }
+}
+
+void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* Asl, double* rowscale,
+                        cudaStream_t s) {
+  oz_rowscale_kernel<<<dim3((npad + 127) / 128, batch), 128, 0, s>>>(A, n, npad, rowscale);
+  oz_slice_matrix_kernel<<<dim3((npad + 127) / 128, npad / 8, batch), 128, 0, s>>>(A, n, npad, rowscale, Asl);
+}
+
+// Y for mode m, job g: column j of [y_{+m} (nrhs jobs), D_c y_{-m} (nrhs jobs)]
+__device__ __forceinline__ bool job_vec(int m, int M, int nrhs, int g, int* q, int* ridx, bool* neg) {
+  if (g >= 2 * nrhs || (m == 0 && g >= nrhs)) return false;
+  *neg = g >= nrhs;
+  *ridx = *neg ? g - nrhs : g;
+  *q = *neg ? M - m : M + m;
+  return true;
+}
+
+// one block per (mode, job): column scale, then digits
+__global__ void oz_slice_vectors_kernel(const cd* __restrict__ y, int n, int npad, int M, int nrhs, int njt,
+                                        double* __restrict__ colscale, __nv_bfloat16* __restrict__ Ysl) {
+  const int m = blockIdx.y, g = blockIdx.x;
+  const int jt = g / OZ_JT, jj = g % OZ_JT, nkt = npad / OZ_KT;
+  int q = 0, ridx = 0;
+  bool neg = false;
+  const bool valid = job_vec(m, M, nrhs, g, &q, &ridx, &neg);
+  const cd* v = valid ? y + ((size_t)q * nrhs + ridx) * n : nullptr;
+  __shared__ double red[32];
+  double mx = 0.0;
+  if (valid)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, fmax(fabs(v[k].x), fabs(v[k].y)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) red[0] = pow2_scale(mx);
+  }
+  __syncthreads();
+  const double sc = red[0];
+  if (threadIdx.x == 0) colscale[(size_t)m * njt * OZ_JT + g] = sc;
+  const double inv = 1.0 / sc;
+  for (int k = threadIdx.x; k < npad; k += blockDim.x) {
+    cd val = C(0.0);
+    if (valid && k < n) {
+      val = v[k];
+      if (neg && ((k & 3) == 1 || (k & 3) == 2)) val = -val;   // D_c
+    }
+    float dre[OZ_S], dim_[OZ_S];
+    digits(val.x * inv, dre);
+    digits(val.y * inv, dim_);
+    const int kt = k / OZ_KT, kk = k % OZ_KT;
+    __nv_bfloat16* blk = Ysl + (((size_t)m * njt + jt) * nkt + kt) * OZ_YBLOCK;
+    const int off = core_off(jj, kk);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      blk[(0 * OZ_S + s) * OZ_YTILE + off] = __float2bfloat16(dre[s]);
+      blk[(1 * OZ_S + s) * OZ_YTILE + off] = __float2bfloat16(dim_[s]);
+    }
+  }
+}
+
+__device__ __forceinline__ void atomic_max_pos_oz(double* addr, double v) {
+  atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// CTA per (row tile, mode, job tile); 128 threads; thread 0 issues copies and MMAs.
+__global__ void __launch_bounds__(128, 1)
+    oz_residual_kernel(const __nv_bfloat16* __restrict__ Asl, const double* __restrict__ rowscale,
+                       const __nv_bfloat16* __restrict__ Ysl, const double* __restrict__ colscale, int n, int npad,
+                       int M, int nrhs, int njt, const cd* __restrict__ bw, cd* __restrict__ r,
+                       double* __restrict__ rnorm, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __nv_bfloat16* bufA = (__nv_bfloat16*)smem;                         // [2][OZ_ABLOCK]
+  __nv_bfloat16* bufY = bufA + 2 * OZ_ABLOCK;                         // [2][OZ_YBLOCK]
+  __shared__ __align__(8) uint64_t full[2], empty[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int rt = blockIdx.x, m = blockIdx.y, jt = blockIdx.z;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nrt = npad / OZ_RT, nkt = npad / OZ_KT;
+  const __nv_bfloat16* Ab = Asl + ((size_t)m * nrt + rt) * nkt * OZ_ABLOCK;
+  const __nv_bfloat16* Yb = Ysl + ((size_t)m * njt + jt) * nkt * OZ_YBLOCK;
+  const uint32_t abytes = OZ_ABLOCK * 2, ybytes = OZ_YBLOCK * 2;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    s_fail = 0;
+    tc::mbar_init(&full[0], 1); tc::mbar_init(&full[1], 1);
+    tc::mbar_init(&empty[0], 1); tc::mbar_init(&empty[1], 1);
+    tc::mbar_init(&drain, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  auto load = [&](int kt) {
+    int b = kt & 1;
+    tc::mbar_expect_tx(&full[b], abytes + ybytes);
+    tc::bulk_g2s(bufA + b * OZ_ABLOCK, Ab + (size_t)kt * OZ_ABLOCK, abytes, &full[b]);
+    tc::bulk_g2s(bufY + b * OZ_YBLOCK, Yb + (size_t)kt * OZ_YBLOCK, ybytes, &full[b]);
+  };
+  if (tid == 0) {
+    load(0);
+    if (nkt > 1) load(1);
+  }
+  const uint32_t id_pos = tc::idesc_bf16_f32(OZ_RT, OZ_JT, false);
+  const uint32_t id_neg = tc::idesc_bf16_f32(OZ_RT, OZ_JT, true);
+  double zre[OZ_JT], zim[OZ_JT];
+#pragma unroll
+  for (int j = 0; j < OZ_JT; ++j) { zre[j] = 0.0; zim[j] = 0.0; }
+  const int nchunk = (nkt + OZ_CHUNK - 1) / OZ_CHUNK;
+  for (int c = 0; c < nchunk; ++c) {
+    const int kt0 = c * OZ_CHUNK, kt1 = min(nkt, kt0 + OZ_CHUNK);
+    if (tid == 0 && !s_fail) {
+      for (int kt = kt0; kt < kt1; ++kt) {
+        const int b = kt & 1;
+        if (!tc::mbar_wait(&full[b], (kt >> 1) & 1)) { s_fail = 1; break; }
+        tc::fence_after();
+        const uint32_t a0 = tc::smem_u32(bufA + b * OZ_ABLOCK), y0 = tc::smem_u32(bufY + b * OZ_YBLOCK);
+        const bool first = kt == kt0;
+#pragma unroll 1
+        for (int s = 0; s < OZ_S; ++s) {
+          for (int t = 0; s + t < OZ_S; ++t) {
+            const int l = s + t;
+            const uint32_t acc_re = tmem + (uint32_t)((l * 2 + 0) * OZ_JT);
+            const uint32_t acc_im = tmem + (uint32_t)((l * 2 + 1) * OZ_JT);
+            const uint64_t are = tc::desc_noswizzle(a0 + (0 * OZ_S + s) * OZ_ATILE * 2, 128, 256);
+            const uint64_t aim = tc::desc_noswizzle(a0 + (1 * OZ_S + s) * OZ_ATILE * 2, 128, 256);
+            const uint64_t yre = tc::desc_noswizzle(y0 + (0 * OZ_S + t) * OZ_YTILE * 2, 128, 256);
+            const uint64_t yim = tc::desc_noswizzle(y0 + (1 * OZ_S + t) * OZ_YTILE * 2, 128, 256);
+            const uint32_t fresh = (first && s == 0) ? 0u : 1u;  // first product of this level in the chunk
+            tc::mma_bf16(acc_re, are, yre, id_pos, fresh);
+            tc::mma_bf16(acc_re, aim, yim, id_neg, 1u);
+            tc::mma_bf16(acc_im, are, yim, id_pos, fresh);
+            tc::mma_bf16(acc_im, aim, yre, id_pos, 1u);
+          }
+        }
+        tc::commit(&empty[b]);
+        // refill the buffer of the previous k-tile with k-tile kt + 1
+        if (kt >= 1 && kt + 1 < nkt) {
+          const int pb = (kt - 1) & 1;
+          if (!tc::mbar_wait(&empty[pb], ((kt - 1) >> 1) & 1)) { s_fail = 1; break; }
+          load(kt + 1);
+        }
+      }
+      tc::commit(&drain);
+    }
+    __syncthreads();
+    if (s_fail) break;
+    if (!tc::mbar_wait(&drain, c & 1)) { atomicExch(&s_fail, 1); }
+    __syncthreads();
+    if (s_fail) break;
+    tc::fence_after();
+    // drain: this warp's 32 rows, all levels
+    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int l = 0; l < OZ_S; ++l) {
+      const double sc = ldexp(1.0, -7 * (l + 2));
+      float v[OZ_JT];
+      tc::tmem_ld32(tw + (uint32_t)((l * 2 + 0) * OZ_JT), v);
+#pragma unroll
+      for (int j = 0; j < OZ_JT; ++j) zre[j] = fma(sc, (double)v[j], zre[j]);
+      tc::tmem_ld32(tw + (uint32_t)((l * 2 + 1) * OZ_JT), v);
+#pragma unroll
+      for (int j = 0; j < OZ_JT; ++j) zim[j] = fma(sc, (double)v[j], zim[j]);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+  if (s_fail) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // let copies still in flight land before the CTA exits (bounded)
+      tc::mbar_wait(&full[0], 0, 1 << 20);
+      tc::mbar_wait(&full[1], 0, 1 << 20);
+    }
+  } else {
+    const int i = rt * OZ_RT + warp * 32 + lane;
+    if (i < n) {
+      const double si = rowscale[(size_t)m * npad + i];
+#pragma unroll 1
+      for (int j = 0; j < OZ_JT; ++j) {
+        const int g = jt * OZ_JT + j;
+        int q, ridx;
+        bool neg;
+        if (!job_vec(m, M, nrhs, g, &q, &ridx, &neg)) continue;
+        const double sc = si * colscale[(size_t)m * njt * OZ_JT + g];
+        cd z = C(sc * zre[j], sc * zim[j]);
+        if (neg && ((i & 3) == 0 || (i & 3) == 3)) z = -z;   // D_r
+        const size_t idx = ((size_t)q * nrhs + ridx) * n + i;
+        cd val = bw[idx] - z;
+        r[idx] = val;
+        atomic_max_pos_oz(rnorm + (size_t)q * nrhs + ridx, cabs(val));
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int npad, int M, const cd* bw,
+                    const cd* y, cd* r, int nrhs, double* rnorm, __nv_bfloat16* Ysl, double* colscale, int* err,
+                    cudaStream_t s) {
+  const int njt = (2 * nrhs + OZ_JT - 1) / OZ_JT;
+  oz_slice_vectors_kernel<<<dim3(njt * OZ_JT, M + 1), 256, 0, s>>>(y, n, npad, M, nrhs, njt, colscale, Ysl);
+  cudaMemsetAsync(rnorm, 0, sizeof(double) * (2 * M + 1) * nrhs, s);
+  const int smem = 2 * (OZ_ABLOCK + OZ_YBLOCK) * 2;
+  cudaFuncSetAttribute(oz_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  oz_residual_kernel<<<dim3(npad / OZ_RT, M + 1, njt), 128, smem, s>>>(Asl, rowscale, Ysl, colscale, n, npad, M,
+                                                                      nrhs, njt, bw, r, rnorm, err);
+}

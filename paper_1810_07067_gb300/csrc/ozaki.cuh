@@ -1,0 +1,26 @@
+// FP64-accurate complex GEMM on BF16 tensor cores (exact digit slicing), used
+// for the refinement residuals of the mixed-precision path.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include "cplx.cuh"
+
+#define OZ_S 8        // digits per value (7 bits each)
+#define OZ_RT 128     // output rows per CTA
+#define OZ_JT 32      // right-hand sides per CTA
+#define OZ_KT 16      // k per tile
+#define OZ_CHUNK 16   // k-tiles per exact FP32 accumulation (256 values of k)
+
+size_t ozaki_matrix_slices_elems(int npad, int batch);  // bf16 elements
+size_t ozaki_vector_slices_elems(int npad, int batch, int njt);
+
+// Slices of the complex matrices A[batch][n][n] (column-major) for rows padded
+// to npad (multiple of 128); rowscale[batch][npad] = power-of-two row scales.
+void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* Asl, double* rowscale,
+                        cudaStream_t s);
+
+// r = b' - A'_{+-m} y for modes -M..M with the sliced matrices (see mixed.cu);
+// Ysl / colscale are workspaces; err is set on a timed-out device wait.
+void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int npad, int M, const cd* bw,
+                    const cd* y, cd* r, int nrhs, double* rnorm, __nv_bfloat16* Ysl, double* colscale, int* err,
+                    cudaStream_t s);

@@ -24,10 +24,13 @@ def _rel(xa, xb, M):
     return num / den
 
 
-def test_mixed_sphere_vs_oracle(mb, sphere_oracle):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_sphere_vs_oracle(mb, sphere_oracle, precision):
+    """precision 1: residuals on BF16 tensor cores (exact digit slicing);
+    precision 2: residuals on the FP64 pipe."""
     cfg = sphere_oracle["cfg"]
     M = cfg.M
-    ctx = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi, precision=1, refine_tol=1e-14))
+    ctx = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi, precision=precision, refine_tol=1e-14))
     b = torch.tensor(np.ascontiguousarray(sphere_oracle["b"].transpose(0, 2, 1)), device=DEV)
     x = torch.zeros_like(b)
     be = np.zeros((2 * M + 1) * b.shape[1])
