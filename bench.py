@@ -256,6 +256,12 @@ def main():
                                        "ms": st["ms_lu_gemm"],
                                        "arith": "complex64 FFMA" if prec else "complex128 DFMA"},
                 "refine_iters": st["refine_iters"], "backward_err_max": st["backward_err_max"],
+                "tensor_core_residual": ({"ms": st["ms_residual"], "launches": st["residual_launches"],
+                                          "bf16_tflops": st["residual_tc_flops"] / (st["ms_residual"] * 1e-3) / 1e12,
+                                          "peak_bf16_tflops": 1915.0,
+                                          "peak_source": "bf16 burst of the profiling recipe (fallback; "
+                                                         "MEASURED_PEAKS.json absent)"}
+                                         if st["ms_residual"] > 0 else None),
                 "other_path": {"precision": "fp64" if prec else "mixed", "s": other_s,
                                "stages_ms": {k: round(st_other[k], 3) for k in
                                              ("ms_far", "ms_support", "ms_near", "ms_lu", "ms_solve")}},

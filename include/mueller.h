@@ -103,6 +103,9 @@ typedef struct {
   int solve_launches;        /* kernel launches of the last solve            */
   int refine_iters;          /* mixed path: refinement steps of the last solve */
   double backward_err_max;   /* mixed path: largest final backward error       */
+  double ms_residual;        /* precision 1: device time of the tensor-core residuals (incl. slicing) */
+  int residual_launches;     /* precision 1: residual evaluations of the last solve */
+  double residual_tc_flops;  /* precision 1: their BF16 tensor work (2 flops per MAC) */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;

@@ -50,7 +50,8 @@ class Stats(ct.Structure):
                 ("n_far_pairs", ct.c_longlong), ("n_support_pairs", ct.c_longlong), ("singular_mode", ct.c_int),
                 ("singular_column", ct.c_int), ("device_bytes", ct.c_size_t), ("ms_lu_gemm", ct.c_double),
                 ("lu_gemm_flops", ct.c_double), ("lu_gemm_launches", ct.c_int), ("launches", ct.c_int),
-                ("solve_launches", ct.c_int), ("refine_iters", ct.c_int), ("backward_err_max", ct.c_double)]
+                ("solve_launches", ct.c_int), ("refine_iters", ct.c_int), ("backward_err_max", ct.c_double),
+                ("ms_residual", ct.c_double), ("residual_launches", ct.c_int), ("residual_tc_flops", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -19,22 +19,30 @@ void mixed_convert(const cd* A, cf* A32, size_t count, cudaStream_t s) {
   convert_kernel<<<152 * 16, 256, 0, s>>>(A, A32, count);
 }
 
-// one thread per row: sum_j |a_ij| (columns are contiguous, so a warp reads
-// consecutive rows of one column)
+// 32 rows x 8 column slices per block: each thread sums |a_ij| over its
+// slice of columns (a warp reads 32 consecutive rows of one column)
 __global__ void norm_inf_kernel(const cd* __restrict__ A, int n, double* __restrict__ out) {
   const int b = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int slice = threadIdx.x >> 5;  // 0..7
   const cd* M = A + (size_t)b * n * n;
   double s = 0.0;
   if (i < n)
-    for (int j = 0; j < n; ++j) s += cabs(M[(size_t)j * n + i]);
-  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_pos(out + b, s);
+    for (int j = slice; j < n; j += 8) s += cabs(M[(size_t)j * n + i]);
+  __shared__ double part[8][32];
+  part[slice][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (slice == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += part[q][threadIdx.x & 31];
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(out + b, t);
+  }
 }
 
 void mixed_norm_inf(const cd* A, int n, int batch, double* out, cudaStream_t s) {
   cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
-  norm_inf_kernel<<<dim3((n + 127) / 128, batch), 128, 0, s>>>(A, n, out);
+  norm_inf_kernel<<<dim3((n + 31) / 32, batch), 256, 0, s>>>(A, n, out);
 }
 
 __global__ void scale_kernel(const cd* __restrict__ b, cd* __restrict__ bw, const double* __restrict__ sw, int n,

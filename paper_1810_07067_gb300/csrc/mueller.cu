@@ -622,9 +622,15 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   int it = 0, launches = 3;
   bool done = false;
   double worst = 0.0;
+  std::vector<cudaEvent_t> rev;
   for (; it < c->S.refine_max_iter; ++it) {
     if (tcres) {
+      cudaEvent_t a0, a1;
+      cudaEventCreate(&a0); cudaEventCreate(&a1);
+      cudaEventRecord(a0, s);
       ozaki_residual(c->Asl, c->rowscale, n, c->npad, M, bw, y, r, nrhs, rn, Ysl, colscale, derr, s);
+      cudaEventRecord(a1, s);
+      rev.push_back(a0); rev.push_back(a1);
       launches += 2;
     } else {
       mixed_residual(c->A, n, M, bw, y, r, nrhs, rn, s);
@@ -654,6 +660,18 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   c->st.ms_solve = ms;
   c->st.solve_launches = launches + 1;
   c->st.refine_iters = it;
+  c->st.ms_residual = 0.0;
+  c->st.residual_launches = (int)rev.size() / 2;
+  for (size_t q = 0; q + 1 < rev.size(); q += 2) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, rev[q], rev[q + 1]);
+    c->st.ms_residual += t;
+    cudaEventDestroy(rev[q]); cudaEventDestroy(rev[q + 1]);
+  }
+  // tensor work per residual: 36 digit products x 4 real products of
+  // (npad x npad) x (npad x 32 jobs per job tile) per mode, 2 flops per MAC
+  c->st.residual_tc_flops = (double)c->st.residual_launches * 144.0 * 2.0 * (double)c->npad * c->npad *
+                            OZ_JT * ((2 * nrhs + OZ_JT - 1) / OZ_JT) * (M + 1);
   c->st.backward_err_max = worst;
   if (backward_err) std::copy(be.begin(), be.end(), backward_err);
   if (derr) {

@@ -35,14 +35,18 @@ size_t ozaki_vector_slices_elems(int npad, int batch, int njt) {
 __device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
 __device__ __forceinline__ void digits(double v, float* d) {
-  // v in (-1/2, 1/2): d_s = rint(v * 2^7), v <- v * 2^7 - d_s (exact)
+  // v in (-1/2, 1/2): the fixed-point integer F = round(v 2^56) (|F| < 2^55),
+  // written in balanced base 128 from the least significant digit up:
+  // d = ((F + 64) mod 128) - 64, F <- (F - d) / 128; the leading digit ends in
+  // [-64, 64].  v = sum_s d_s 2^{-7s} + (rounding < 2^{-57}).
+  long long F = __double2ll_rn(v * 72057594037927936.0);  // 2^56
 #pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    double x = v * 128.0;
-    double t = rint(x);
-    d[s] = (float)t;
-    v = x - t;
+  for (int s = OZ_S - 1; s >= 1; --s) {
+    long long dd = ((F + 64) & 127) - 64;
+    d[s] = (float)dd;
+    F = (F - dd) >> 7;
   }
+  d[0] = (float)F;
 }
 
 __device__ __forceinline__ double pow2_scale(double mx) {
@@ -114,11 +118,10 @@ __device__ __forceinline__ bool job_vec(int m, int M, int nrhs, int g, int* q, i
   return true;
 }
 
-// one block per (mode, job): column scale, then digits
-__global__ void oz_slice_vectors_kernel(const cd* __restrict__ y, int n, int npad, int M, int nrhs, int njt,
-                                        double* __restrict__ colscale, __nv_bfloat16* __restrict__ Ysl) {
+// column scales: one block per (mode, job)
+__global__ void oz_colscale_kernel(const cd* __restrict__ y, int n, int M, int nrhs, int njt,
+                                   double* __restrict__ colscale) {
   const int m = blockIdx.y, g = blockIdx.x;
-  const int jt = g / OZ_JT, jj = g % OZ_JT, nkt = npad / OZ_KT;
   int q = 0, ridx = 0;
   bool neg = false;
   const bool valid = job_vec(m, M, nrhs, g, &q, &ridx, &neg);
@@ -133,29 +136,45 @@ __global__ void oz_slice_vectors_kernel(const cd* __restrict__ y, int n, int npa
   if (threadIdx.x < 32) {
     mx = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) red[0] = pow2_scale(mx);
+    if (threadIdx.x == 0) colscale[(size_t)m * njt * OZ_JT + g] = pow2_scale(mx);
   }
-  __syncthreads();
-  const double sc = red[0];
-  if (threadIdx.x == 0) colscale[(size_t)m * njt * OZ_JT + g] = sc;
-  const double inv = 1.0 / sc;
-  for (int k = threadIdx.x; k < npad; k += blockDim.x) {
+}
+
+// digits: thread per (mode, job, group of 8 consecutive k); 16-byte stores
+__global__ void oz_slice_vectors_kernel(const cd* __restrict__ y, int n, int npad, int M, int nrhs, int njt,
+                                        const double* __restrict__ colscale, __nv_bfloat16* __restrict__ Ysl) {
+  const int m = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ngroups = npad / 8;
+  const int g = t / ngroups, kg = t % ngroups;  // consecutive threads: consecutive k groups of one job
+  if (g >= njt * OZ_JT) return;
+  int q = 0, ridx = 0;
+  bool neg = false;
+  const bool valid = job_vec(m, M, nrhs, g, &q, &ridx, &neg);
+  const double inv = 1.0 / colscale[(size_t)m * njt * OZ_JT + g];
+  float dre[8][OZ_S], dim_[8][OZ_S];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int k = kg * 8 + c;
     cd val = C(0.0);
     if (valid && k < n) {
-      val = v[k];
+      val = y[((size_t)q * nrhs + ridx) * n + k];
       if (neg && ((k & 3) == 1 || (k & 3) == 2)) val = -val;   // D_c
     }
-    float dre[OZ_S], dim_[OZ_S];
-    digits(val.x * inv, dre);
-    digits(val.y * inv, dim_);
-    const int kt = k / OZ_KT, kk = k % OZ_KT;
-    __nv_bfloat16* blk = Ysl + (((size_t)m * njt + jt) * nkt + kt) * OZ_YBLOCK;
-    const int off = core_off(jj, kk);
+    digits(val.x * inv, dre[c]);
+    digits(val.y * inv, dim_[c]);
+  }
+  const int jt = g / OZ_JT, jj = g % OZ_JT, nkt = npad / OZ_KT;
+  const int kt = (kg * 8) / OZ_KT, kk = (kg * 8) % OZ_KT;
+  __nv_bfloat16* blk = Ysl + (((size_t)m * njt + jt) * nkt + kt) * OZ_YBLOCK;
+  const int off = core_off(jj, kk);
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      blk[(0 * OZ_S + s) * OZ_YTILE + off] = __float2bfloat16(dre[s]);
-      blk[(1 * OZ_S + s) * OZ_YTILE + off] = __float2bfloat16(dim_[s]);
-    }
+  for (int s = 0; s < OZ_S; ++s) {
+    __align__(16) __nv_bfloat16 re[8], im[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) { re[c] = __float2bfloat16(dre[c][s]); im[c] = __float2bfloat16(dim_[c][s]); }
+    *(uint4*)(blk + (0 * OZ_S + s) * OZ_YTILE + off) = *(uint4*)re;
+    *(uint4*)(blk + (1 * OZ_S + s) * OZ_YTILE + off) = *(uint4*)im;
   }
 }
 
@@ -216,19 +235,26 @@ __global__ void __launch_bounds__(128, 1)
         const int b = kt & 1;
         if (!tc::mbar_wait(&full[b], (kt >> 1) & 1)) { s_fail = 1; break; }
         tc::fence_after();
-        const uint32_t a0 = tc::smem_u32(bufA + b * OZ_ABLOCK), y0 = tc::smem_u32(bufY + b * OZ_YBLOCK);
-        const bool first = kt == kt0;
-#pragma unroll 1
+        // descriptors of slice 0 of this buffer; slice tiles follow at fixed
+        // offsets (4 KiB for A, 1 KiB for y: 256 and 64 in the 16-byte units
+        // of the descriptor's start-address field, which cannot carry)
+        const uint64_t a_re0 = tc::desc_noswizzle(tc::smem_u32(bufA + b * OZ_ABLOCK), 128, 256);
+        const uint64_t y_re0 = tc::desc_noswizzle(tc::smem_u32(bufY + b * OZ_YBLOCK), 128, 256);
+        const uint64_t a_im0 = a_re0 + (uint64_t)(OZ_S * OZ_ATILE * 2 / 16);
+        const uint64_t y_im0 = y_re0 + (uint64_t)(OZ_S * OZ_YTILE * 2 / 16);
+        const uint32_t first = (kt == kt0) ? 1u : 0u;
+#pragma unroll
         for (int s = 0; s < OZ_S; ++s) {
-          for (int t = 0; s + t < OZ_S; ++t) {
+#pragma unroll
+          for (int t = 0; t < OZ_S - s; ++t) {
             const int l = s + t;
             const uint32_t acc_re = tmem + (uint32_t)((l * 2 + 0) * OZ_JT);
             const uint32_t acc_im = tmem + (uint32_t)((l * 2 + 1) * OZ_JT);
-            const uint64_t are = tc::desc_noswizzle(a0 + (0 * OZ_S + s) * OZ_ATILE * 2, 128, 256);
-            const uint64_t aim = tc::desc_noswizzle(a0 + (1 * OZ_S + s) * OZ_ATILE * 2, 128, 256);
-            const uint64_t yre = tc::desc_noswizzle(y0 + (0 * OZ_S + t) * OZ_YTILE * 2, 128, 256);
-            const uint64_t yim = tc::desc_noswizzle(y0 + (1 * OZ_S + t) * OZ_YTILE * 2, 128, 256);
-            const uint32_t fresh = (first && s == 0) ? 0u : 1u;  // first product of this level in the chunk
+            const uint64_t are = a_re0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
+            const uint64_t aim = a_im0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
+            const uint64_t yre = y_re0 + (uint64_t)(t * (OZ_YTILE * 2 / 16));
+            const uint64_t yim = y_im0 + (uint64_t)(t * (OZ_YTILE * 2 / 16));
+            const uint32_t fresh = (s == 0) ? (first ^ 1u) : 1u;  // first product of this level in the chunk
             tc::mma_bf16(acc_re, are, yre, id_pos, fresh);
             tc::mma_bf16(acc_re, aim, yim, id_neg, 1u);
             tc::mma_bf16(acc_im, are, yim, id_pos, fresh);
@@ -304,7 +330,9 @@ void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int
                     const cd* y, cd* r, int nrhs, double* rnorm, __nv_bfloat16* Ysl, double* colscale, int* err,
                     cudaStream_t s) {
   const int njt = (2 * nrhs + OZ_JT - 1) / OZ_JT;
-  oz_slice_vectors_kernel<<<dim3(njt * OZ_JT, M + 1), 256, 0, s>>>(y, n, npad, M, nrhs, njt, colscale, Ysl);
+  oz_colscale_kernel<<<dim3(njt * OZ_JT, M + 1), 256, 0, s>>>(y, n, M, nrhs, njt, colscale);
+  const int threads = njt * OZ_JT * (npad / 8);
+  oz_slice_vectors_kernel<<<dim3((threads + 127) / 128, M + 1), 128, 0, s>>>(y, n, npad, M, nrhs, njt, colscale, Ysl);
   cudaMemsetAsync(rnorm, 0, sizeof(double) * (2 * M + 1) * nrhs, s);
   const int smem = 2 * (OZ_ABLOCK + OZ_YBLOCK) * 2;
   cudaFuncSetAttribute(oz_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -226,3 +226,48 @@ def test_cylinder_full_size_backward_error(mb, cylinder_full):
         ref = torch.linalg.solve(Am, bs)
         assert ((xs - ref).abs().max() / ref.abs().max()).item() < 1e-11
     assert worst < 1e-14, worst
+
+
+def test_random_body_full_size(mb):
+    """Smooth random body at full size (N = 1024, system 4096, modes 0..128,
+    512 azimuthal samples, k0 = 10, k1 = 15): sampled blocks against the
+    oracle, FP64 and mixed paths against each other and against the assembled
+    matrices (normwise backward error)."""
+    cfg = W.config_random()
+    M, n = cfg.M, 4 * cfg.N
+    sw = system.l2_weights(cfg.curve)
+    A = torch.zeros((M + 1, n, n), dtype=torch.complex128, device=DEV)
+    mb.assemble(cfg.curve, cfg.media, M, A, mb.Options(n_phi=cfg.n_phi))
+    modes = np.array([0, 3, 64, 128])
+    scale = max(float(A[q].abs().max()) for q in modes)
+    for (i, j) in [(0, 700), (400, 400), (401, 391), (512, 530), (1023, 1000), (700, 100)]:
+        ref, noise = system.block(cfg.curve, cfg.media, M, i, j, modes=modes, noise=True)
+        s = sw[4 * i] / sw[4 * j]
+        got = np.stack([A[q, 4 * j:4 * j + 4, 4 * i:4 * i + 4].cpu().numpy().T for q in modes])
+        ok = np.abs(got - ref * s) <= 1e-12 * scale + 20 * noise.max() * s
+        assert ok.all(), (i, j, (np.abs(got - ref * s) / scale).max())
+    dirs = [w.d for w in cfg.waves]; pols = [w.e for w in cfg.waves]
+    nrhs = len(cfg.waves)
+    b = torch.zeros((2 * M + 1, nrhs, n), dtype=torch.complex128, device=DEV)
+    xs = {}
+    for prec in (0, 1):
+        ctx = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi, precision=prec, refine_tol=1e-14))
+        if prec == 0:
+            ctx.rhs_planewave(dirs, pols, b)
+        x = torch.zeros_like(b)
+        ctx.solve(b, x)
+        xs[prec] = x
+        ctx.close()
+    swt = torch.tensor(sw, device=DEV, dtype=torch.float64)
+    for prec in (0, 1):
+        for m in (0, 1, 128):
+            Am = A[m].transpose(0, 1)
+            ys = (xs[prec][M + m] * swt[None, :]).transpose(0, 1)
+            bs = (b[M + m] * swt[None, :]).transpose(0, 1)
+            r = Am @ ys - bs
+            be = (r.abs().max(0).values / (Am.abs().sum(1).max() * ys.abs().max(0).values +
+                                          bs.abs().max(0).values)).max().item()
+            assert be < 1e-14, (prec, m, be)
+    num = max(float((xs[1][q] - xs[0][q]).norm()) for q in range(2 * M + 1))
+    den = max(float(xs[0][q].norm()) for q in range(2 * M + 1))
+    assert num / den < 1e-10
