@@ -204,8 +204,8 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
       for (int f = 0; f < NFAM; ++f) W.smp[f * H + j] = wj * F[f];
       continue;
     }
-    Ent e0 = entire(c_tab, gp.kp0, su);
-    Ent e1 = entire(c_tab, gp.kp1, su);
+    Ent e0 = gp.k0_real ? entire_real(c_tab, gp.kp0.k.x, su) : entire(c_tab, gp.kp0, su);
+    Ent e1 = gp.k1_real ? entire_real(c_tab, gp.kp1.k.x, su) : entire(c_tab, gp.kp1, su);
     cd gam1 = e0.Gam - e1.Gam, gam2 = e0.Gam2 - e1.Gam2, gam1p = e0.Gamp - e1.Gamp;
     cd dSp = e0.Sp - e1.Sp, dSpp = e0.Spp - e1.Spp;
     if (!split) {
@@ -687,6 +687,7 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   gp.M = M; gp.Ms = Ms; gp.nphi = n_phi; gp.H = H; gp.Mq = Mq;
   gp.kp0 = kpow(K0); gp.kp1 = kpow(K1);
   gp.gamma0 = -0.25 * (K0 * K0 - K1 * K1);
+  gp.k0_real = K0.y == 0.0; gp.k1_real = K1.y == 0.0;
   double eps = split_eps > 0 ? split_eps : 1e-17;
   noalloc_tables_kernel<<<(n_phi + 255) / 256, 256, 0, s>>>(n_phi, cosT, s2T);
   unsigned blocks = (unsigned)((npairs + 127) / 128);

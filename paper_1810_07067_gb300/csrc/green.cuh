@@ -14,6 +14,7 @@ struct GreenParams {
   int Mq;      // nphi/2 - 1: bandwidth of the Laplace coefficients
   KPow kp0, kp1;
   cd gamma0;   // -(k0^2 - k1^2)/4
+  int k0_real, k1_real;  // real wavenumbers take the real-arithmetic path
 };
 
 // Block coefficients of eq. mullerrep / eq. dualmullrep.

@@ -66,9 +66,15 @@ __global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, i
       for (int r = c + 1 + tid; r < n; r += NT) {
         T l = col[r] * inv;
         col[r] = l;
-        for (int cc = jj + 1; cc < nbk; ++cc) {
-          T* dst = M + (size_t)(k0 + cc) * n + r;
-          *dst = *dst - l * s_row[cc];
+        // the row's remaining panel entries in chunks of 8: loads batched, then updates
+        for (int c0 = jj + 1; c0 < nbk; c0 += 8) {
+          T v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + u < nbk) v[u] = M[(size_t)(k0 + c0 + u) * n + r];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + u < nbk) M[(size_t)(k0 + c0 + u) * n + r] = v[u] - l * s_row[c0 + u];
         }
       }
     }

@@ -194,6 +194,7 @@ static void fill_green_params(GreenParams& gp, int M, int nphi, cd k0, cd k1) {
   gp.M = M; gp.Ms = M + 2; gp.nphi = nphi; gp.H = nphi / 2 + 1; gp.Mq = nphi / 2 - 1;
   gp.kp0 = kpow(k0); gp.kp1 = kpow(k1);
   gp.gamma0 = -0.25 * (k0 * k0 - k1 * k1);
+  gp.k0_real = k0.y == 0.0; gp.k1_real = k1.y == 0.0;
 }
 
 // split decision: plain trapezoid aliasing zeta^(nphi-M-1) above eps

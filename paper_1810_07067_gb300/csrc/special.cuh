@@ -144,6 +144,63 @@ HD Ent entire(const SeriesTables& T, const KPow& kp, double su) {
   return e;
 }
 
+// Real-argument versions (real wavenumber): same functions, real arithmetic.
+HD double horner_r(const double* c, double x2, int nt) {
+  double acc = c[nt - 1];
+  for (int p = nt - 2; p >= 0; --p) acc = fma(acc, x2, c[p]);
+  return acc;
+}
+
+HD Ent entire_real(const SeriesTables& T, double k, double su) {
+  const double x = k * su, h = 0.5 * x, x2 = x * x, ax = fabs(x);
+  double sx_c, s1x, s2x, sh_c, s1h, cosx, phi2, phi3;
+  if (ax < 2.0) {
+    int nt = series_terms(x2);
+    sx_c = horner_r(T.sinc, x2, nt);
+    s1x = horner_r(T.sig1, x2, nt);
+    s2x = horner_r(T.sig2, x2, nt);
+    int nh = series_terms(0.25 * x2);
+    sh_c = horner_r(T.sinc, 0.25 * x2, nh);
+    s1h = horner_r(T.sig1, 0.25 * x2, nh);
+    phi2 = horner_r(T.phi2, x2, nt);
+    phi3 = horner_r(T.phi3, x2, nt);
+  } else {
+    double sh, chh;
+#ifdef __CUDA_ARCH__
+    sincos(h, &sh, &chh);
+#else
+    sh = std::sin(h); chh = std::cos(h);
+#endif
+    const double sx = 2.0 * sh * chh, cx = 1.0 - 2.0 * sh * sh;
+    const double xi = 1.0 / x, xi2 = xi * xi;
+    sx_c = sx * xi;
+    s1x = (x * cx - sx) * xi2 * xi;
+    s2x = ((3.0 - x2) * sx - 3.0 * x * cx) * xi2 * xi2 * xi;
+    if (ax < 4.0) {
+      int nh = series_terms(0.25 * x2);
+      sh_c = horner_r(T.sinc, 0.25 * x2, nh);
+      s1h = horner_r(T.sig1, 0.25 * x2, nh);
+    } else {
+      const double hi = 1.0 / h;
+      sh_c = sh * hi;
+      s1h = (h * chh - sh) * hi * hi * hi;
+    }
+    phi2 = (1.0 + sh_c * sh_c - 2.0 * sx_c) / (4.0 * x2);
+    phi3 = (0.5 * sh_c * s1h - 2.0 * s1x) * 0.125;
+  }
+  cosx = 1.0 - 0.5 * x2 * sh_c * sh_c;
+  const double k2 = k * k, k3 = k2 * k, k4 = k2 * k2, k5 = k4 * k;
+  Ent e;
+  e.C = C(cosx);
+  e.S = C(k * sx_c);
+  e.Gam = C(-0.5 * k2 * sx_c + 0.25 * k2 * sh_c * sh_c);
+  e.Gam2 = C(k4 * phi2);
+  e.Gamp = C(k4 * phi3);
+  e.Sp = C(0.5 * k3 * s1x);
+  e.Spp = C(0.25 * k5 * s2x);
+  return e;
+}
+
 // Complete elliptic integral of the first kind from the complementary modulus
 // kp = sqrt(1 - kappa^2): K = pi / (2 AGM(1, kp)).
 HD double ellipk_c(double kp) {
