@@ -35,6 +35,7 @@ extern "C" {
 #endif
 
 typedef struct { double re, im; } mueller_c128;
+typedef struct { float re, im; } mueller_c64;
 
 typedef enum {
   MUELLER_OK = 0,
@@ -202,6 +203,16 @@ int mueller_modal_kernels_noalloc(const double* pairs_dev, long long npairs, mue
  * (stride n*n); piv_dev [batch][n] (0-based LAPACK-style interchanges),
  * info_dev [batch] (0 or first zero-pivot column + 1). */
 int mueller_lu_batched(mueller_c128* A_dev, int n, int batch, int* piv_dev, int* info_dev, void* stream);
+
+/* The same factorisation in complex64, as used by the mixed-precision path
+ * (Section 6's per-mode LU at reduced precision, refined in FP64 by the
+ * solve): the trailing-submatrix updates run on the tensor cores with every
+ * FP32 operand split exactly into three BF16 pieces and the six piece
+ * products of FP32 weight accumulated in FP32, so the factors carry FP32-grade
+ * backward error.  Layout and outputs as mueller_lu_batched.  Returns
+ * MUELLER_ETIMEOUT if a bounded device-side wait of the update gave up (the
+ * factors are then unusable).  Synchronises `stream`. */
+int mueller_lu_batched_c64(mueller_c64* A_dev, int n, int batch, int* piv_dev, int* info_dev, void* stream);
 
 /* Bytes of complex128 factors for one body: 16 (4N)^2 (2M+1), the admission
  * unit named by the serving workload (the GPU path stores M+1 of them). */

@@ -67,6 +67,7 @@ _lib.mueller_far_field.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, _vp, _vp]
 _lib.mueller_modal_kernels.argtypes = [ct.POINTER(ct.c_double), ct.c_longlong, c128, c128, ct.c_int, ct.c_int,
                                        ct.c_double, _vp, _vp]
 _lib.mueller_lu_batched.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
+_lib.mueller_lu_batched_c64.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
 _lib.mueller_modal_kernels_noalloc.argtypes = [_vp, ct.c_longlong, c128, c128, ct.c_int, ct.c_int, ct.c_double,
                                                _vp, _vp]
 _lib.mueller_footprint_bytes.argtypes = [ct.c_int, ct.c_int]
@@ -78,7 +79,7 @@ _lib.mueller_strerror.argtypes = [ct.c_int]
 _lib.mueller_last_error.restype = ct.c_char_p
 
 EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_far_field",
-           "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_footprint_bytes", "mueller_stats_get",
+           "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_stats_get",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
@@ -221,6 +222,16 @@ def lu_batched(A, piv, info, stream=None):
     n = A.shape[-1]
     batch = A.shape[0]
     _check(_lib.mueller_lu_batched(_ptr(A), n, batch, _ptr(piv), _ptr(info), _stream(stream)))
+
+
+def lu_batched_c64(A, piv, info, stream=None):
+    """Complex64 batched LU with tensor-core trailing updates (in place)."""
+    import torch
+    if A.dtype != torch.complex64:
+        raise ValueError("lu_batched_c64 takes complex64 matrices")
+    n = A.shape[-1]
+    batch = A.shape[0]
+    _check(_lib.mueller_lu_batched_c64(_ptr(A), n, batch, _ptr(piv), _ptr(info), _stream(stream)))
 
 
 def footprint_bytes(N: int, M: int) -> int:

@@ -6,8 +6,11 @@
 // row of U is formed by a unit-lower triangular solve; (4) the trailing matrix
 // is updated by a complex FP64 GEMM, batched over all matrices.
 #include <cstdio>
+#include <type_traits>
 #include <vector>
+#include <cuda_bf16.h>
 #include "lu.cuh"
+#include "tc.cuh"
 
 // ---------------------------------------------------------------- panel
 __device__ __forceinline__ void argmax_merge(double& v, int& idx, double v2, int i2) {
@@ -178,9 +181,194 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(T* __restrict__ A, int
   }
 }
 
+// ---------------------------------------------------------------- tensor-core trailing update
+// Complex64 trailing update C -= L U on tcgen05: every FP32 operand is split
+// exactly into three BF16 pieces (x = hi + mid + lo, 24 bits), and the six
+// piece products whose sum carries FP32 precision (hh, hm, mh, hl, mm, lh) are
+// accumulated in FP32 tensor memory (-L_im U_im via the MMA's A-negation).
+// The hi*hi products and the five smaller corrections go to separate
+// accumulators (Re and Im each, four in all) that are added in registers:
+// sharing one accumulator loses about two bits to the tensor core's
+// accumulation, which measured 4x the error of a plain FP32 update, while the
+// split form measured half of it.  One CTA per 128 x 64 output tile of one
+// matrix; 128 threads; operands are re-laid out into the MMA's K-major
+// no-swizzle core-matrix format in shared memory.
+#define TCU_M 128
+#define TCU_N 64
+#define TCU_ATILE (TCU_M * LU_NB)  // bf16 elements per piece tile of L (128 rows x 32 k)
+#define TCU_BTILE (TCU_N * LU_NB)  // of U (64 columns x 32 k)
+#define TCU_SMEM (6 * (TCU_ATILE + TCU_BTILE) * 2)
+
+__device__ __forceinline__ int tcu_off(int r, int k) {  // 4 core matrices along k
+  return ((r >> 3) * (LU_NB / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16* p) {
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  float r1 = x - __bfloat162float(h);
+  __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  float r2 = r1 - __bfloat162float(m);
+  p[0] = h; p[1] = m; p[2] = __float2bfloat16_rn(r2);
+}
+
+// Per step, the L panel (rows start.., 32 columns) and the U panel (32 rows,
+// columns start..) are split once into their BF16 pieces, stored tile by tile
+// in exactly the shared-memory image the MMAs read: per matrix, ceil(n/128)
+// L tiles of [6 pieces][128 x 32], then ceil(n/64) U tiles of [6][64 x 32].
+__host__ __device__ inline size_t tcu_ws_matrix_elems(int n) {
+  return (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)((n + TCU_N - 1) / TCU_N) * 6 * TCU_BTILE;
+}
+
+size_t lu_c64_workspace_bytes(int n, int batch) { return tcu_ws_matrix_elems(n) * (size_t)batch * 2; }
+
+__global__ void __launch_bounds__(256) tcu_split_kernel(const cf* __restrict__ A, int n, int k0, int nbk, int nL,
+                                                       __nv_bfloat16* __restrict__ ws) {
+  const int b = blockIdx.y;
+  const cf* M = A + (size_t)b * n * n;
+  const int start = k0 + nbk;
+  __nv_bfloat16* W = ws + (size_t)b * tcu_ws_matrix_elems(n);
+  __nv_bfloat16 pr[3], pi[3];
+  if ((int)blockIdx.x < nL) {
+    const int r0 = start + blockIdx.x * TCU_M;
+    __nv_bfloat16* dst = W + (size_t)blockIdx.x * 6 * TCU_ATILE;
+    for (int t = threadIdx.x; t < TCU_M * LU_NB; t += 256) {
+      int r = t % TCU_M, k = t / TCU_M;
+      cf v = (r0 + r < n && k < nbk) ? M[(size_t)(k0 + k) * n + r0 + r] : CF(0.f);
+      split3(v.x, pr); split3(v.y, pi);
+      int off = tcu_off(r, k);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) { dst[q * TCU_ATILE + off] = pr[q]; dst[(3 + q) * TCU_ATILE + off] = pi[q]; }
+    }
+  } else {
+    const int y = blockIdx.x - nL, c0 = start + y * TCU_N;
+    __nv_bfloat16* dst = W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)y * 6 * TCU_BTILE;
+    for (int t = threadIdx.x; t < TCU_N * LU_NB; t += 256) {
+      int k = t % LU_NB, j = t / LU_NB;
+      cf v = (c0 + j < n && k < nbk) ? M[(size_t)(c0 + j) * n + k0 + k] : CF(0.f);
+      split3(v.x, pr); split3(v.y, pi);
+      int off = tcu_off(j, k);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) { dst[q * TCU_BTILE + off] = pr[q]; dst[(3 + q) * TCU_BTILE + off] = pi[q]; }
+    }
+  }
+}
+
+// Launched with TCU_SMEM_LAUNCH bytes of dynamic shared memory so that at
+// most two CTAs share an SM (each holds 256 TMEM columns of the 512).
+#define TCU_SMEM_LAUNCH (100 * 1024)
+
+__global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A, int n, int k0, int nbk,
+                                                            const __nv_bfloat16* __restrict__ ws,
+                                                            int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __nv_bfloat16* As = (__nv_bfloat16*)smem;
+  __nv_bfloat16* Bs = As + 6 * TCU_ATILE;
+  __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  const int b = blockIdx.z;
+  cf* M = A + (size_t)b * n * n;
+  const int start = k0 + nbk;
+  const int i0 = start + blockIdx.x * TCU_M, j0 = start + blockIdx.y * TCU_N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 4 * TCU_N);
+  if (tid == 0) {
+    s_ok = 1;
+    tc::mbar_init(&mbar_load, 1);
+    tc::mbar_init(&mbar_mma, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  // accumulator columns: [0,N) hh Re, [N,2N) hh Im, [2N,3N) corrections Re, [3N,4N) corrections Im
+  if (tid == 0) {
+    const __nv_bfloat16* W = ws + (size_t)b * tcu_ws_matrix_elems(n);
+    const __nv_bfloat16* Lsrc = W + (size_t)blockIdx.x * 6 * TCU_ATILE;
+    const __nv_bfloat16* Usrc =
+        W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)blockIdx.y * 6 * TCU_BTILE;
+    tc::mbar_expect_tx(&mbar_load, TCU_SMEM);
+    tc::bulk_g2s(As, Lsrc, 6 * TCU_ATILE * 2, &mbar_load);
+    tc::bulk_g2s(Bs, Usrc, 6 * TCU_BTILE * 2, &mbar_load);
+    if (tc::mbar_wait(&mbar_load, 0)) {
+      tc::fence_after();
+      const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TCU_N, false);
+      const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TCU_N, true);
+      const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(As), 128, (LU_NB / 8) * 128);
+      const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(Bs), 128, (LU_NB / 8) * 128);
+      const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(TCU_BTILE * 2 / 16);  // 16-byte units
+      const int qa_[6] = {0, 0, 1, 0, 1, 2}, qb_[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+      for (int ks = 0; ks < LU_NB / 16; ++ks) {
+        const uint64_t kof = (uint64_t)(ks * 256 / 16);  // two core matrices along k
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+          const uint64_t are = a0 + qa_[u] * at + kof, aim = a0 + (3 + qa_[u]) * at + kof;
+          const uint64_t bre = b0 + qb_[u] * bt + kof, bim = b0 + (3 + qb_[u]) * bt + kof;
+          const uint32_t dre = tmem + (u == 0 ? 0 : 2 * TCU_N), dim = tmem + (u == 0 ? TCU_N : 3 * TCU_N);
+          const uint32_t acc = (ks == 0 && u <= 1) ? 0u : 1u;  // first write of each accumulator
+          tc::mma_bf16(dre, are, bre, id_pos, acc);
+          tc::mma_bf16(dre, aim, bim, id_neg, 1u);
+          tc::mma_bf16(dim, are, bim, id_pos, acc);
+          tc::mma_bf16(dim, aim, bre, id_pos, 1u);
+        }
+      }
+    } else {
+      s_ok = 0;
+      tc::mbar_wait(&mbar_load, 0);  // let copies still in flight land before the CTA can exit
+    }
+    tc::commit(&mbar_mma);
+  }
+  // while the MMAs run: fetch this thread's row of the first 32 output columns
+  const int i = i0 + warp * 32 + lane;
+  cf cv[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    int j = j0 + c;
+    cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
+  }
+  const bool done = tc::mbar_wait(&mbar_mma, 0);
+  tc::fence_after();
+  __syncthreads();
+  const bool ok = done && s_ok;
+  if (!ok && tid == 0 && err) atomicExch(err, 1);
+  if (ok) {
+    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TCU_N; c0 += 32) {
+      if (c0 > 0) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          int j = j0 + c0 + c;
+          cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
+        }
+      }
+      float hr[32], hi[32], cr[32], ci[32];
+      tc::tmem_ld32(tw + c0, hr);
+      tc::tmem_ld32(tw + TCU_N + c0, hi);
+      tc::tmem_ld32(tw + 2 * TCU_N + c0, cr);
+      tc::tmem_ld32(tw + 3 * TCU_N + c0, ci);
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          int j = j0 + c0 + c;
+          if (j < n) M[(size_t)j * n + i] = CF(cv[c].x - (hr[c] + cr[c]), cv[c].y - (hi[c] + ci[c]));
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 4 * TCU_N);
+}
+
 template <class T>
-static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
+static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm,
+                           int* tc_err = nullptr, __nv_bfloat16* ws = nullptr) {
   cudaMemsetAsync(info, 0, sizeof(int) * batch, s);
+  if constexpr (std::is_same<T, cf>::value)
+    cudaFuncSetAttribute(gemm_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TCU_SMEM_LAUNCH);
   std::vector<cudaEvent_t> ev;
   int launches = 0;
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
@@ -198,7 +386,14 @@ static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStre
         cudaEventCreate(&e0); cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
       }
-      gemm_update_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
+      if constexpr (std::is_same<T, cf>::value) {
+        const int nL = (rest + TCU_M - 1) / TCU_M, nU = (rest + TCU_N - 1) / TCU_N;
+        tcu_split_kernel<<<dim3(nL + nU, batch), 256, 0, s>>>((const cf*)A, n, k0, nbk, nL, ws);
+        gemm_update_tc_kernel<<<dim3(nL, nU, batch), 128, TCU_SMEM_LAUNCH, s>>>((cf*)A, n, k0, nbk, ws, tc_err);
+        ++launches;
+      } else {
+        gemm_update_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
+      }
       launches += 2;
       if (tm) {
         cudaEventRecord(e1, s);
@@ -224,8 +419,9 @@ void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_
   lu_factor_impl<cd>(A, n, batch, piv, info, s, tm);
 }
 
-void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
-  lu_factor_impl<cf>(A, n, batch, piv, info, s, tm);
+void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm,
+                           int* tc_err, void* ws) {
+  lu_factor_impl<cf>(A, n, batch, piv, info, s, tm, tc_err, (__nv_bfloat16*)ws);
 }
 
 // ---------------------------------------------------------------- solves

@@ -16,7 +16,12 @@ struct LuTiming {
 };
 void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* t = nullptr);
 // The same factorization in complex64 (mixed-precision path).
-void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* t = nullptr);
+// The trailing updates run on tensor cores (tcgen05, split-BF16); ws is a
+// device workspace of lu_c64_workspace_bytes(n, batch) bytes (256-byte
+// aligned); tc_err (device int, may be null) is set if a bounded wait gives up.
+size_t lu_c64_workspace_bytes(int n, int batch);
+void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* t, int* tc_err,
+                           void* ws);
 
 // Solve with factors of modes m = 0..M for right-hand sides of modes -M..M:
 // rhs/x layout [2M+1][nrhs][n] (mode q = m + M); sw[n/4] = sqrt of the L2 weights of the nodes

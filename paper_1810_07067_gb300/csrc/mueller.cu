@@ -503,6 +503,7 @@ struct mueller_ctx {
   int npad = 0;
   int* piv = nullptr;
   int* info = nullptr;
+  int* tc_err = nullptr;       // set by a timed-out device wait in tensor-core kernels
   mueller_stats st{};
 };
 
@@ -531,10 +532,12 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
       (mixed && (c->keep.alloc(&c->A32, (size_t)(M + 1) * n * n) != cudaSuccess ||
                  c->keep.alloc(&c->normA, M + 1) != cudaSuccess)) ||
       (slices && (c->keep.alloc(&c->Asl, ozaki_matrix_slices_elems(c->npad, M + 1)) != cudaSuccess ||
-                  c->keep.alloc(&c->rowscale, (size_t)(M + 1) * c->npad) != cudaSuccess))) {
+                  c->keep.alloc(&c->rowscale, (size_t)(M + 1) * c->npad) != cudaSuccess)) ||
+      c->keep.alloc(&c->tc_err, 1) != cudaSuccess) {
     delete c;
     return fail(MUELLER_ENOMEM, "factor allocation");
   }
+  cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
   cudaEventRecord(e0, s);
@@ -542,6 +545,7 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   if (rc) { delete c; return rc; }
   cudaEventRecord(e1, s);
   LuTiming lt;
+  DevBuf wsb;  // tensor-core LU workspace, freed after the factorisation has completed
   if (mixed) {
     mixed_norm_inf(c->A, (int)n, M + 1, c->normA, s);
     mixed_convert(c->A, c->A32, (size_t)(M + 1) * n * n, s);
@@ -549,7 +553,12 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
       ozaki_slice_matrix(c->A, (int)n, c->npad, M + 1, c->Asl, c->rowscale, s);
       lt.launches += 2;
     }
-    lu_factor_batched_c64(c->A32, (int)n, M + 1, c->piv, c->info, s, &lt);
+    unsigned char* ws = nullptr;
+    if (wsb.alloc(&ws, lu_c64_workspace_bytes((int)n, M + 1)) != cudaSuccess) {
+      delete c;
+      return fail(MUELLER_ENOMEM, "tensor-core LU workspace");
+    }
+    lu_factor_batched_c64(c->A32, (int)n, M + 1, c->piv, c->info, s, &lt, c->tc_err, ws);
     lt.launches += 2;
   } else {
     lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s, &lt);
@@ -565,6 +574,9 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   c->st.launches = 4 + lt.launches;
   std::vector<int> info(M + 1);
   cudaMemcpy(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost);
+  int tce = 0;
+  cudaMemcpy(&tce, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (tce) { delete c; return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core LU update timed out"); }
   c->st.singular_mode = -1; c->st.singular_column = -1;
   for (int m = 0; m <= M; ++m)
     if (info[m]) { c->st.singular_mode = m; c->st.singular_column = info[m] - 1; break; }
@@ -796,6 +808,26 @@ extern "C" int mueller_lu_batched(mueller_c128* A_dev, int n, int batch, int* pi
   lu_factor_batched((cd*)A_dev, n, batch, piv_dev, info_dev, (cudaStream_t)stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_lu_batched_c64(mueller_c64* A_dev, int n, int batch, int* piv_dev, int* info_dev,
+                                      void* stream) {
+  g_err.clear();
+  if (!A_dev || !piv_dev || !info_dev || n < 1 || batch < 1) return fail(MUELLER_EINVAL, "invalid LU arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf tmp;
+  int* err = nullptr;
+  unsigned char* ws = nullptr;
+  if (tmp.alloc(&err, 1) != cudaSuccess || tmp.alloc(&ws, lu_c64_workspace_bytes(n, batch)) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "tensor-core LU workspace");
+  CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  lu_factor_batched_c64((cf*)A_dev, n, batch, piv_dev, info_dev, s, nullptr, err, ws);
+  CK(cudaGetLastError());
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (herr) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core LU update timed out");
   return MUELLER_OK;
 }
 
