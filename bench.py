@@ -1,7 +1,8 @@
 """Benchmark: modal assemble + solve on one body of revolution per GPU.
 
 One step = mueller_build (modal Green's functions, assembly and LU of modes
-0..M) + mueller_solve for all plane waves of the workload.  Default workload:
+0..M) + mueller_rhs_planewave (modal incident data) + mueller_solve for all
+plane waves of the workload.  Default workload:
 finite cylinder radius 1, height 2, edge-graded panels (N = 576 nodes, system
 2304 x 2304 complex128 per mode), modes -64..64, 256 azimuthal samples,
 k0 = 5, k1 = 7.5 + 0.01i, 8 incidence angles x 2 polarisations.
@@ -173,6 +174,7 @@ def main():
 
     def step(o=opts, out=x):
         ctx = mb.build(cfg.curve, cfg.media, M, o)
+        ctx.rhs_planewave(dirs, pols, rhs)
         ctx.solve(rhs, out)
         st = ctx.stats()
         ctx.close()
@@ -229,7 +231,7 @@ def main():
     dev_s, e2e_s = t.tolist()
     if rank == 0:
         st = stats[-1]
-        launches = st["launches"] + st["solve_launches"]
+        launches = st["launches"] + st["solve_launches"] + 1  # + rhs_kernel
         # dominant kernel: far_kernel (FP64 pipe).  Algorithmic flops per far
         # pair: 9 FFT-based cosine transforms 9 * 2.5 n_phi log2 n_phi, sampling
         # (n_phi/2 + 1) * 140 (both wavenumbers), assembly 256 per mode.

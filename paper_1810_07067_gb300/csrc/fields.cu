@@ -7,7 +7,8 @@ __global__ void rhs_kernel(FieldGeom g, int M, cd k0, double omega, cd mu0, cd s
                            const double* __restrict__ dirs, const double* __restrict__ pols, int nrhs, int n_theta,
                            cd* __restrict__ rhs) {
   extern __shared__ __align__(16) char smem[];
-  cd* smp = (cd*)smem;  // [n_theta][4]
+  cd* smp = (cd*)smem;         // [n_theta][4]
+  cd* tw = smp + 4 * n_theta;  // [n_theta]: e^{-2 pi i t / n_theta}
   const int i = blockIdx.x, w = blockIdx.y;
   const double* d = dirs + 3 * w;
   const double* e = pols + 3 * w;
@@ -15,11 +16,10 @@ __global__ void rhs_kernel(FieldGeom g, int M, cd k0, double omega, cd mu0, cd s
   cd hf = k0 / (omega * mu0);
   double hx = d[1] * e[2] - d[2] * e[1], hy = d[2] * e[0] - d[0] * e[2], hz = d[0] * e[1] - d[1] * e[0];
   const double r = g.r[i], z = g.z[i], rp = g.rp[i], zp = g.zp[i];
-  const double TWO_PI = 6.283185307179586;
   for (int t = threadIdx.x; t < n_theta; t += blockDim.x) {
-    double th = TWO_PI * t / n_theta;
     double ct, st;
-    sincos(th, &st, &ct);
+    sincospi(2.0 * t / n_theta, &st, &ct);
+    tw[t] = C(ct, -st);
     double phase = r * (d[0] * ct + d[1] * st) + z * d[2];
     cd ph = cexpi(k0 * phase);
     // E components in (e_r, e_theta, e_z)
@@ -33,31 +33,27 @@ __global__ void rhs_kernel(FieldGeom g, int M, cd k0, double omega, cd mu0, cd s
   }
   __syncthreads();
   const int n = 4 * g.N;
-  for (int mq = threadIdx.x; mq < 2 * M + 1; mq += blockDim.x) {
-    int m = mq - M;
-    cd acc[4] = {C(0.0), C(0.0), C(0.0), C(0.0)};
-    int mm = ((m % n_theta) + n_theta) % n_theta;
+  const double inv = 1.0 / n_theta;
+  // one (mode, component) per item: the DFT sum over the ring samples
+  for (int item = threadIdx.x; item < 4 * (2 * M + 1); item += blockDim.x) {
+    const int mq = item >> 2, a = item & 3;
+    const int m = mq - M;
+    const int mm = ((m % n_theta) + n_theta) % n_theta;
+    cd acc = C(0.0);
+    int idx = 0;
     for (int t = 0; t < n_theta; ++t) {
-      int idx = (int)(((long long)mm * t) % n_theta);
-      double s, c;
-      sincospi(2.0 * idx / n_theta, &s, &c);
-      cd ex = C(c, -s);  // e^{-i m theta_t}
-#pragma unroll
-      for (int a = 0; a < 4; ++a) acc[a] = fma(smp[4 * t + a], ex, acc[a]);
+      acc = fma(smp[4 * t + a], tw[idx], acc);
+      idx += mm;
+      if (idx >= n_theta) idx -= n_theta;
     }
-    double inv = 1.0 / n_theta;
-    cd* dst = rhs + ((size_t)mq * nrhs + w) * n + 4 * i;
-    dst[0] = sE * (inv * acc[0]);
-    dst[1] = sE * (inv * acc[1]);
-    dst[2] = sH * (inv * acc[2]);
-    dst[3] = sH * (inv * acc[3]);
+    rhs[((size_t)mq * nrhs + w) * n + 4 * i + a] = (a < 2 ? sE : sH) * (inv * acc);
   }
 }
 
 void launch_rhs_planewave(const FieldGeom& g, int M, cd k0, double omega, cd mu0, cd sE, cd sH,
                           const double* dirs_dev, const double* pols_dev, int nrhs, int n_theta, cd* rhs,
                           cudaStream_t s) {
-  int smem = n_theta * 4 * (int)sizeof(cd);
+  int smem = n_theta * 5 * (int)sizeof(cd);
   cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   rhs_kernel<<<dim3(g.N, nrhs), 256, smem, s>>>(g, M, k0, omega, mu0, sE, sH, dirs_dev, pols_dev, nrhs, n_theta,
                                                  rhs);

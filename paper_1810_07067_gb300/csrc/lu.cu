@@ -8,9 +8,12 @@
 #include <cstdio>
 #include <type_traits>
 #include <vector>
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include "lu.cuh"
 #include "tc.cuh"
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------- panel
 __device__ __forceinline__ void argmax_merge(double& v, int& idx, double v2, int i2) {
@@ -85,19 +88,197 @@ __global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, i
   }
 }
 
-// ---------------------------------------------------------------- swaps
+// ---------------------------------------------------------------- cluster panel
+// The panel (rows k0..n-1, nbk columns) held in the shared memory of a
+// cluster of C CTAs: CTA q owns rows k0 + q R .. k0 + (q+1) R - 1 as a
+// column-major slice [nbk][R].  Per column: local argmax, candidates written
+// into every CTA's shared memory through the cluster's distributed shared
+// memory, cluster barrier; the pivot row's owner broadcasts it (and the
+// displaced row is sent to the pivot's owner), cluster barrier; then the
+// interchange and the rank-1 update of the owned rows.  Same pivot rule as
+// panel_kernel (largest |a|^2, lowest row on ties).
+#define PANEL_SMEM_MAX (200 * 1024)
+#define PANEL_THREADS 512
+
 template <class T>
-__global__ void swap_kernel(T* __restrict__ A, int n, int k0, int nbk, const int* __restrict__ piv) {
+__global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restrict__ A, int n, int k0, int nbk,
+                                                                      int R, int* __restrict__ piv,
+                                                                      int* __restrict__ info) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
   const int b = blockIdx.y;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nother = n - nbk;
-  if (c >= nother) return;
-  if (c >= k0) c += nbk;  // skip the panel's own columns
-  T* col = A + (size_t)b * n * n + (size_t)c * n;
-  const int* pv = piv + (size_t)b * n;
-  for (int k = k0; k < k0 + nbk; ++k) {
-    int p = pv[k];
-    if (p != k) { T t = col[k]; col[k] = col[p]; col[p] = t; }
+  T* M = A + (size_t)b * n * n;
+  int* pv = piv + (size_t)b * n;
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  T* a = (T*)panel_smem;  // [nbk][R]
+  __shared__ double cand_v[8];
+  __shared__ int cand_i[8];
+  __shared__ T s_row[LU_NB], s_rowc[LU_NB];
+  __shared__ double red_v[PANEL_THREADS / 32];
+  __shared__ int red_i[PANEL_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int row0 = k0 + q * R;
+  const int nr = max(0, min(R, n - row0));  // rows owned by this CTA
+  for (int t = tid; t < nbk * nr; t += PANEL_THREADS) {
+    int r = t % nr, j = t / nr;
+    a[j * R + r] = M[(size_t)(k0 + j) * n + row0 + r];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int c = k0 + jj;
+    const T* aj = a + jj * R;
+    double best = -1.0;
+    int bi = n;
+    for (int r = max(0, c - row0) + tid; r < nr; r += PANEL_THREADS) argmax_merge(best, bi, norm2(aj[r]), row0 + r);
+    for (int o = 16; o > 0; o >>= 1) {
+      double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(best, bi, v2, i2);
+    }
+    if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      best = (lane < PANEL_THREADS / 32) ? red_v[lane] : -1.0;
+      bi = (lane < PANEL_THREADS / 32) ? red_i[lane] : n;
+      for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(best, bi, v2, i2);
+      }
+      if (lane < C) {  // this CTA's candidate into slot q of every CTA
+        cl.map_shared_rank(cand_v, lane)[q] = best;
+        cl.map_shared_rank(cand_i, lane)[q] = bi;
+      }
+    }
+    cl.sync();
+    best = -1.0;
+    bi = n;
+    for (int u = 0; u < C; ++u) argmax_merge(best, bi, cand_v[u], cand_i[u]);
+    const int p = (best > 0.0) ? bi : -1;
+    if (q == 0 && tid == 0) {
+      pv[c] = (p >= 0) ? p : c;
+      if (p < 0 && info[b] == 0) info[b] = c + 1;
+    }
+    const int qp = (p >= 0) ? (p - k0) / R : -1, qc = (c - k0) / R;
+    if (p >= 0) {
+      if (q == qp && tid < nbk * C) {
+        int j = tid % nbk, u = tid / nbk;
+        cl.map_shared_rank(s_row, u)[j] = a[j * R + p - row0];
+      }
+      if (q == qc && p != c && tid < nbk) cl.map_shared_rank(s_rowc, qp)[tid] = a[tid * R + c - row0];
+    }
+    cl.sync();
+    if (p >= 0) {
+      if (q == qc && tid < nbk) a[tid * R + c - row0] = s_row[tid];
+      if (q == qp && p != c && tid < nbk) a[tid * R + p - row0] = s_rowc[tid];
+      __syncthreads();
+      const T inv = cone<T>() / s_row[jj];
+      for (int r = max(0, c + 1 - row0) + tid; r < nr; r += PANEL_THREADS) {
+        T l = a[jj * R + r] * inv;
+        a[jj * R + r] = l;
+        for (int j = jj + 1; j < nbk; ++j) a[j * R + r] = a[j * R + r] - l * s_row[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < nbk * nr; t += PANEL_THREADS) {
+    int r = t % nr, j = t / nr;
+    M[(size_t)(k0 + j) * n + row0 + r] = a[j * R + r];
+  }
+  cl.sync();  // no CTA leaves while a peer could still address its shared memory
+}
+
+// Cluster size: the smallest of 1, 2, 4, 8 whose row slices fit PANEL_SMEM_MAX.
+// Returns false (nothing launched) when none fits or no such cluster can be
+// resident; the caller then uses panel_kernel.
+template <class T>
+static bool launch_panel_cluster(T* A, int n, int k0, int nbk, int batch, int* piv, int* info, cudaStream_t s) {
+  const int rows = n - k0;
+  int C = 1;
+  while (C < 8 && (size_t)LU_NB * ((rows + C - 1) / C) * sizeof(T) > PANEL_SMEM_MAX) C *= 2;
+  const int R = (rows + C - 1) / C;
+  const size_t smem = (size_t)LU_NB * R * sizeof(T);
+  if (smem > PANEL_SMEM_MAX) return false;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, batch);
+  cfg.blockDim = dim3(PANEL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, panel_cluster_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, A, n, k0, nbk, R, piv, info) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- swaps
+// The nbk interchanges of a block column compose to a permutation of at most
+// 2 nbk rows: the block's own rows (slots 0..nbk-1) and the distinct targets
+// below it (slot nbk + lane of the first interchange naming it).  One warp
+// forms it per CTA; each warp then moves the affected entries of its columns
+// (all loads before all stores).
+#define SWAP_COLS 64
+template <class T>
+__global__ void __launch_bounds__(256) swap_kernel(T* __restrict__ A, int n, int k0, int nbk,
+                                                   const int* __restrict__ piv) {
+  const int b = blockIdx.y;
+  __shared__ int pos[2 * LU_NB], src[2 * LU_NB], slot[LU_NB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kend = k0 + nbk;
+  if (warp == 0) {
+    const int p = (lane < nbk) ? piv[(size_t)b * n + k0 + lane] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, p);
+    const bool below = p >= kend;
+    const bool first = below && (__ffs(same) - 1 == lane);
+    const int sp = (lane >= nbk) ? 0 : (below ? LU_NB + __ffs(same) - 1 : p - k0);
+    pos[lane] = (lane < nbk) ? k0 + lane : -1;
+    src[lane] = pos[lane];
+    pos[LU_NB + lane] = first ? p : -1;
+    src[LU_NB + lane] = first ? p : -1;
+    slot[lane] = sp;
+    __syncwarp();
+    if (lane == 0)
+      for (int k = 0; k < nbk; ++k) {
+        const int s2 = slot[k];
+        if (s2 != k) { int t = src[k]; src[k] = src[s2]; src[s2] = t; }
+      }
+  }
+  __syncthreads();
+  const int d0 = pos[lane], d1 = pos[lane + 32], s0 = src[lane], s1 = src[lane + 32];
+  for (int cc = warp; cc < SWAP_COLS; cc += 8) {
+    int c = blockIdx.x * SWAP_COLS + cc;
+    if (c >= n - nbk) break;  // whole warp
+    if (c >= k0) c += nbk;     // skip the panel's own columns
+    T* col = A + (size_t)b * n * n + (size_t)c * n;
+    T v0 = czero<T>(), v1 = czero<T>();
+    if (d0 >= 0 && d0 != s0) v0 = col[s0];
+    if (d1 >= 0 && d1 != s1) v1 = col[s1];
+    __syncwarp();
+    if (d0 >= 0 && d0 != s0) col[d0] = v0;
+    if (d1 >= 0 && d1 != s1) col[d1] = v1;
+    __syncwarp();
   }
 }
 
@@ -373,10 +554,11 @@ static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStre
   int launches = 0;
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     int nbk = (n - k0 < LU_NB) ? n - k0 : LU_NB;
-    panel_kernel<T><<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
+    if (!launch_panel_cluster<T>(A, n, k0, nbk, batch, piv, info, s))
+      panel_kernel<T><<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
     ++launches;
     int nother = n - nbk;
-    if (nother > 0) { swap_kernel<T><<<dim3((nother + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk, piv); ++launches; }
+    if (nother > 0) { swap_kernel<T><<<dim3((nother + SWAP_COLS - 1) / SWAP_COLS, batch), 256, 0, s>>>(A, n, k0, nbk, piv); ++launches; }
     int rest = n - k0 - nbk;
     if (rest > 0) {
       trsm_kernel<T><<<dim3((rest + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk);

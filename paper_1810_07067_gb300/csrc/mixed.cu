@@ -26,9 +26,18 @@ __global__ void norm_inf_kernel(const cd* __restrict__ A, int n, double* __restr
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   const int slice = threadIdx.x >> 5;  // 0..7
   const cd* M = A + (size_t)b * n * n;
+  // |a| in FP32 (a norm for the stopping test needs no more), summed in FP64
   double s = 0.0;
-  if (i < n)
-    for (int j = slice; j < n; j += 8) s += cabs(M[(size_t)j * n + i]);
+  if (i < n) {
+#pragma unroll 4
+    for (int j = slice; j < n; j += 8) {
+      const cd v = M[(size_t)j * n + i];
+      const float fx = fabsf((float)v.x), fy = fabsf((float)v.y);
+      const float hi = fmaxf(fx, fy), lo = fminf(fx, fy);
+      const float q = (hi > 0.f) ? lo / hi : 0.f;
+      s += (double)(hi * sqrtf(1.f + q * q));
+    }
+  }
   __shared__ double part[8][32];
   part[slice][threadIdx.x & 31] = s;
   __syncthreads();

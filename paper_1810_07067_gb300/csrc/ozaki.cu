@@ -72,32 +72,49 @@ __global__ void oz_rowscale_kernel(const cd* __restrict__ A, int n, int npad, do
   rowscale[(size_t)b * npad + i] = pow2_scale(mx);
 }
 
-// thread per (row i, group of 8 consecutive k): 16 digit rows of 16 bytes
-__global__ void oz_slice_matrix_kernel(const cd* __restrict__ A, int n, int npad, const double* __restrict__ rowscale,
-                                       __nv_bfloat16* __restrict__ Asl) {
+// thread per (row i, group of 8 consecutive k): 16 digit rows of 16 bytes.
+// The 16 values are held as fixed-point integers F = round(v 2^56) and their
+// balanced base-128 digits are taken from the top, one level at a time:
+// d = round-half-up(F / 2^(7 l)), F -= d 2^(7 l), for l = 7..1, then the last
+// digit is the remainder; every digit lies in [-64, 64] and
+// v = sum_s d_s 2^{-7(s+1)} up to the rounding of F.
+__global__ void __launch_bounds__(128) oz_slice_matrix_kernel(const cd* __restrict__ A, int n, int npad,
+                                                              const double* __restrict__ rowscale,
+                                                              __nv_bfloat16* __restrict__ Asl) {
   const int b = blockIdx.z;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;   // row
   const int kg = blockIdx.y;                              // group of 8 columns
   if (i >= npad) return;
   const int nrt = npad / OZ_RT, nkt = npad / OZ_KT;
-  const double inv = 1.0 / rowscale[(size_t)b * npad + i];
-  float dre[8][OZ_S], dim_[8][OZ_S];
+  const double inv = 72057594037927936.0 / rowscale[(size_t)b * npad + i];  // 2^56 / scale
+  long long Fr[8], Fi[8];
   const cd* M = A + (size_t)b * n * n;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     int k = kg * 8 + c;
     cd v = (i < n && k < n) ? M[(size_t)k * n + i] : C(0.0);
-    digits(v.x * inv, dre[c]);
-    digits(v.y * inv, dim_[c]);
+    Fr[c] = __double2ll_rn(v.x * inv);
+    Fi[c] = __double2ll_rn(v.y * inv);
   }
   const int rt = i / OZ_RT, r = i % OZ_RT, kt = (kg * 8) / OZ_KT, kk = (kg * 8) % OZ_KT;
   __nv_bfloat16* blk = Asl + (((size_t)b * nrt + rt) * nkt + kt) * OZ_ABLOCK;
   const int off = core_off(r, kk);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
+    const int sh = 7 * (OZ_S - 1 - s);
     __align__(16) __nv_bfloat16 re[8], im[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) { re[c] = __float2bfloat16(dre[c][s]); im[c] = __float2bfloat16(dim_[c][s]); }
+    for (int c = 0; c < 8; ++c) {
+      long long dr = Fr[c], di = Fi[c];
+      if (sh > 0) {
+        dr = (Fr[c] + (1ll << (sh - 1))) >> sh;
+        di = (Fi[c] + (1ll << (sh - 1))) >> sh;
+        Fr[c] -= dr << sh;
+        Fi[c] -= di << sh;
+      }
+      re[c] = __float2bfloat16((float)dr);
+      im[c] = __float2bfloat16((float)di);
+    }
     *(uint4*)(blk + (0 * OZ_S + s) * OZ_ATILE + off) = *(uint4*)re;
     *(uint4*)(blk + (1 * OZ_S + s) * OZ_ATILE + off) = *(uint4*)im;
   }

@@ -93,10 +93,11 @@ def test_lu_c64_tensor_core_vs_lapack(mb):
     as accurate as LAPACK's complex64 LU on the same matrices (same pivoting
     rule): a split that dropped a piece product would be two or more orders
     of magnitude worse.  Sizes span one partial tile, several 128-row tiles
-    with a ragged tail, and a batch."""
+    with a ragged tail, a batch, and panels spread over clusters of two
+    (1000 rows) and four (1700) CTAs."""
     sl = pytest.importorskip("scipy.linalg")
     rng = np.random.default_rng(11)
-    for n, batch in ((77, 2), (300, 3), (517, 1)):
+    for n, batch in ((77, 2), (300, 3), (517, 1), (1000, 1), (1700, 1)):
         A = (rng.standard_normal((batch, n, n)) + 1j * rng.standard_normal((batch, n, n))).astype(np.complex64)
         At = torch.tensor(np.ascontiguousarray(A.transpose(0, 2, 1)), device=DEV)
         piv = torch.zeros((batch, n), dtype=torch.int32, device=DEV)
@@ -120,3 +121,15 @@ def test_lu_c64_detects_zero_pivot(mb):
     info = torch.zeros(1, dtype=torch.int32, device=DEV)
     mb.lu_batched_c64(At, piv, info)
     assert info.item() == 151
+
+
+def test_lu_c64_zero_pivot_in_cluster_panel(mb):
+    """A zero pivot in the second CTA's row slice of a two-CTA panel."""
+    n = 1000
+    A = np.eye(n, dtype=np.complex64)[None].copy()
+    A[0, 700, 700] = 0.0
+    At = torch.tensor(A, device=DEV)
+    piv = torch.zeros((1, n), dtype=torch.int32, device=DEV)
+    info = torch.zeros(1, dtype=torch.int32, device=DEV)
+    mb.lu_batched_c64(At, piv, info)
+    assert info.item() == 701

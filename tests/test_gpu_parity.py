@@ -55,8 +55,11 @@ def test_modal_kernels_vs_oracle(mb, k0, k1, M, nphi):
 
 
 def test_lu_batched_vs_reconstruction(mb):
+    """Sizes up to 400 rows factor each panel in one CTA; 900 spreads the
+    panel over a cluster of four CTAs (row slices in distributed shared
+    memory, pivots crossing slice boundaries) with a ragged last panel."""
     rng = np.random.default_rng(7)
-    for n, batch in ((5, 2), (77, 3), (200, 2)):
+    for n, batch in ((5, 2), (77, 3), (200, 2), (900, 2)):
         A = rng.standard_normal((batch, n, n)) + 1j * rng.standard_normal((batch, n, n))
         At = torch.tensor(np.ascontiguousarray(A.transpose(0, 2, 1)), device=DEV)  # column-major per matrix
         piv = torch.zeros((batch, n), dtype=torch.int32, device=DEV)
