@@ -14,6 +14,16 @@
   eq. farfieldform integrates J where eq. exteriorfield has M.  The surface
   integral uses the nodes' ds-weights along the curve and the trapezoid rule
   in theta.
+* Fields at points off the surface: eq. exteriorfield (exterior, k0) and
+  eq. interiorfield (direct form) or eq. interior_dual (indirect form) in the
+  body (k1), with
+    curl S J (x)      = int grad_x G x J da = int G (ik - 1/R) Rh x J da,
+    curl curl S J (x) = int G [(k^2 + ik/R - 1/R^2) J + (-k^2 - 3ik/R + 3/R^2)(Rh.J) Rh] da,
+  R = x - y, Rh = R/|R| (the second from curl curl = grad div + k^2 off the
+  surface).  Same surface rule as the far field, so the points must lie a
+  few node spacings away from the surface.
+* Modal data from sampled fields: the same traces and scaling as for the
+  plane wave, from E and H given at the ring points.
 """
 from __future__ import annotations
 
@@ -92,3 +102,83 @@ def _combine(Jh, Mh, dirs, k0, media):
     xJ = (dirs * Jh).sum(1, keepdims=True)
     pre = -(k0 ** 2) / (1j * media.omega * complex(media.eps0))
     return (pre * (Jh - xJ * dirs) + 1j * k0 * np.cross(dirs, Mh)) / (4 * np.pi)
+
+
+def modal_rhs_samples(curve, media, M, EH, formulation=0):
+    """b[q, 4N, nrhs] from incident fields sampled at the ring points:
+    EH[nrhs, N, n_theta, 6] holds (E, H) in Cartesian components at
+    (r_i cos th_t, r_i sin th_t, z_i), th_t = 2 pi t / n_theta."""
+    geo = node_geometry(curve)
+    co = coefficients(media, formulation)
+    EH = np.asarray(EH, complex)
+    nrhs, N, n_theta, _ = EH.shape
+    th = 2 * np.pi * np.arange(n_theta) / n_theta
+    er, et = _frame(th)
+    ms = np.arange(-M, M + 1)
+    E_ph = np.exp(-1j * np.outer(th, ms)) / n_theta
+    b = np.zeros((2 * M + 1, 4 * N, nrhs), dtype=complex)
+    for w_i in range(nrhs):
+        for i in range(N):
+            for sl, rows, sc in ((slice(0, 3), (0, 1), co["sE"]), (slice(3, 6), (2, 3), co["sH"])):
+                v = EH[w_i, i, :, sl]
+                vr = (v * er).sum(1); vth = (v * et).sum(1); vz = v[:, 2]
+                vt = geo.rp[i] * vr + geo.zp[i] * vz
+                b[:, 4 * i + rows[0], w_i] = sc * (vth @ E_ph)
+                b[:, 4 * i + rows[1], w_i] = sc * (-vt @ E_ph)
+    return b
+
+
+def field_coefficients(media, region, formulation=0):
+    """(k, cJ, cM, dM, dJ) with E = cJ curl curl S J + cM curl S M and
+    H = dM curl curl S M + dJ curl S J in the region (0 exterior, 1 body)."""
+    k0, k1 = wavenumbers(media)
+    om = media.omega
+    e0, e1, u0, u1 = (complex(media.eps0), complex(media.eps1), complex(media.mu0), complex(media.mu1))
+    if region == 0:                      # eq. exteriorfield
+        return k0, -1 / (1j * om * e0), 1.0, 1 / (1j * om * u0), 1.0
+    if formulation == 0:                 # eq. interiorfield
+        return k1, 1 / (1j * om * e1), -1.0, -1 / (1j * om * u1), -1.0
+    return k1, -1 / (1j * om * e0), u1 / u0, 1 / (1j * om * u0), e1 / e0   # eq. interior_dual
+
+
+def near_field(curve, media, M, x, targets, region, formulation=0, n_theta=None):
+    """E, H [nrhs, nt, 3] at points targets [nt, 3] off the surface, from modal
+    currents x[q, 4N, nrhs]; region 0 = exterior, 1 = inside the body."""
+    geo = node_geometry(curve)
+    k, cJ, cM, dM, dJ = field_coefficients(media, region, formulation)
+    if n_theta is None:
+        n_theta = 2 * M + 2 * int(np.ceil(abs(k) * np.max(geo.r))) + 64
+    th = 2 * np.pi * np.arange(n_theta) / n_theta
+    er, et = _frame(th)
+    ez = np.array([0.0, 0.0, 1.0])
+    ms = np.arange(-M, M + 1)
+    E_ph = np.exp(1j * np.outer(th, ms))                  # [theta, modes]
+    X = np.atleast_2d(np.asarray(targets, float))
+    nrhs = x.shape[2]
+    E = np.zeros((nrhs, len(X), 3), dtype=complex)
+    H = np.zeros_like(E)
+    for i in range(curve.N):
+        y = geo.r[i] * er + geo.z[i] * ez                  # [T, 3]
+        t = geo.rp[i] * er + geo.zp[i] * ez
+        da = geo.w[i] * geo.r[i] * (2 * np.pi / n_theta)
+        cur = [E_ph @ x[:, 4 * i + a, :] for a in range(4)]           # 4 x [T, nrhs]
+        Jv = cur[0][..., None] * t[:, None, :] + cur[1][..., None] * et[:, None, :]   # [T, nrhs, 3]
+        Mv = cur[2][..., None] * t[:, None, :] + cur[3][..., None] * et[:, None, :]
+        Rv = X[None, :, :] - y[:, None, :]                 # [T, nt, 3]
+        R = np.linalg.norm(Rv, axis=-1)
+        Rh = Rv / R[..., None]
+        g = da * np.exp(1j * k * R) / (4 * np.pi * R)
+        c1 = g * (1j * k - 1 / R)
+        a = g * (k * k + 1j * k / R - 1 / R ** 2)
+        b = g * (-k * k - 3j * k / R + 3 / R ** 2)
+
+        def curl(V):      # [nrhs, nt, 3]
+            return np.einsum("tp,twpk->wpk", c1, np.cross(Rh[:, None, :, :], V[:, :, None, :]))
+
+        def curlcurl(V):
+            proj = np.einsum("tpk,twk->twp", Rh, V)
+            return (np.einsum("tp,twk->wpk", a, V) + np.einsum("tp,twp,tpk->wpk", b, proj, Rh))
+
+        E += cJ * curlcurl(Jv) + cM * curl(Mv)
+        H += dM * curlcurl(Mv) + dJ * curl(Jv)
+    return E, H

@@ -223,3 +223,46 @@ def test_mie_against_rayleigh_limit():
     ray = -1j * x ** 3 * (m * m - 1) / (m * m + 2)
     assert abs(S1[0] - ray) < 1e-5 * abs(ray)
     assert abs(S2[0] - ray * 0.3) < 1e-5 * abs(ray)
+
+
+def test_extinction_current_loop_indirect(loop_oracle):
+    """Section 6's accuracy test: with the current loop's k1 field as the
+    interior field and zero outside, the indirect formulation's currents must
+    reproduce both through eqs. interior_dual and exteriorfield (uniqueness of
+    the transmission problem).  Measured 4e-15 inside and 1e-16 outside."""
+    from oracle import fields
+    from workloads.sources import current_loop_field
+    L = loop_oracle
+    cfg = L["cfg"]
+    Er, Hr = current_loop_field(L["inner"], L["k1"], cfg.media.omega, complex(cfg.media.mu1))
+    Ei, Hi = fields.near_field(cfg.curve, cfg.media, L["M"], L["x"], L["inner"], 1, formulation=1)
+    Eo, Ho = fields.near_field(cfg.curve, cfg.media, L["M"], L["x"], L["outer"], 0, formulation=1)
+    se, sh = np.abs(Er).max(), np.abs(Hr).max()
+    assert np.abs(Ei[0] - Er).max() <= 1e-12 * se
+    assert np.abs(Hi[0] - Hr).max() <= 1e-12 * sh
+    assert np.abs(Eo[0]).max() <= 1e-13 * se and np.abs(Ho[0]).max() <= 1e-13 * sh
+
+
+def test_extinction_direct_plane_wave(sphere_oracle):
+    """Direct form (eq. mullerrep) with a plane wave: the exterior
+    representation (eq. exteriorfield) evaluated inside the body cancels the
+    incident field, and the interior one (eq. interiorfield) vanishes outside
+    (the extinction theorem of Section 3).  Measured 1e-14 and 2e-16."""
+    from oracle import fields, system
+    cfg = sphere_oracle["cfg"]
+    M, x = cfg.M, sphere_oracle["x"]
+    k0, _ = system.wavenumbers(cfg.media)
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal((6, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    inner = d * rng.uniform(0.1, 0.6, (6, 1))
+    outer = d * rng.uniform(1.8, 2.6, (6, 1))
+    Eo, Ho = fields.near_field(cfg.curve, cfg.media, M, x, inner, 0, formulation=0)
+    Ei, Hi = fields.near_field(cfg.curve, cfg.media, M, x, outer, 1, formulation=0)
+    for w, wv in enumerate(cfg.waves):
+        ph = np.exp(1j * k0 * inner @ wv.d)[:, None]
+        Einc = wv.e[None, :] * ph
+        Hinc = (k0 / (cfg.media.omega * complex(cfg.media.mu0))) * np.cross(wv.d, wv.e)[None, :] * ph
+        assert np.abs(Eo[w] + Einc).max() <= 1e-12
+        assert np.abs(Ho[w] + Hinc).max() <= 1e-12
+        assert np.abs(Ei[w]).max() <= 1e-13 and np.abs(Hi[w]).max() <= 1e-13
