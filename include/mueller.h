@@ -152,6 +152,27 @@ int mueller_solve(mueller_ctx* ctx, const mueller_c128* rhs_dev, int nrhs, muell
 int mueller_rhs_planewave(mueller_ctx* ctx, const double* dirs, const double* pols, int nrhs,
                           mueller_c128* rhs_dev, void* stream);
 
+/* Modal right-hand sides from incident fields sampled by the caller (for
+ * fields other than plane waves, e.g. the current loop of Section 6,
+ * eq. loop).  EH_dev: device [nrhs][N][n_theta][6] complex, (E, H) in
+ * Cartesian components at the ring points (r_i cos th, r_i sin th, z_i),
+ * th = 2 pi t / n_theta, nodes in curve order; 2M+2 <= n_theta <= 2048.
+ * Traces, Fourier coefficients and row scaling as mueller_rhs_planewave;
+ * rhs_dev: [2M+1][nrhs][4N]. */
+int mueller_rhs_fields(mueller_ctx* ctx, const mueller_c128* EH_dev, int nrhs, int n_theta,
+                       mueller_c128* rhs_dev, void* stream);
+
+/* Fields at points off the surface from modal currents (Section 3):
+ * region 0 (the exterior medium) by eq. exteriorfield with k0; region 1 (the
+ * body) by eq. interiorfield for the direct formulation or eq. interior_dual
+ * for the indirect one, with k1.  The surface integrals use the nodes'
+ * ds-weights along the curve and 2M + 2 ceil(|k| r_max) + 64 azimuths, so
+ * points should lie a few node spacings away from the surface.  x_dev:
+ * currents [2M+1][nrhs][4N]; targets: host [ntargets][3]; out_dev: device
+ * [nrhs][ntargets][6] complex, (E, H) in Cartesian components. */
+int mueller_eval(mueller_ctx* ctx, const mueller_c128* x_dev, int nrhs, const double* targets, int ntargets,
+                 int region, mueller_c128* out_dev, void* stream);
+
 /* Far field (eq. farfieldform, with the magnetic current in the last term as
  * in eq. exteriorfield): E_oo(xh) = (1/4pi)[-(k0^2/(i omega eps0))(Jh - (xh.Jh)xh)
  * + i k0 xh x Mh], Jh = int exp(-i k0 xh.y) J(y) da(y).  x_dev: currents

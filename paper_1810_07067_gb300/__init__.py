@@ -67,6 +67,8 @@ _lib.mueller_far_field.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, _vp, _vp]
 _lib.mueller_modal_kernels.argtypes = [ct.POINTER(ct.c_double), ct.c_longlong, c128, c128, ct.c_int, ct.c_int,
                                        ct.c_double, _vp, _vp]
 _lib.mueller_lu_batched.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
+_lib.mueller_rhs_fields.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
+_lib.mueller_eval.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, ct.c_int, _vp, _vp]
 _lib.mueller_lu_batched_c64.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
 _lib.mueller_modal_kernels_noalloc.argtypes = [_vp, ct.c_longlong, c128, c128, ct.c_int, ct.c_int, ct.c_double,
                                                _vp, _vp]
@@ -78,7 +80,8 @@ _lib.mueller_strerror.restype = ct.c_char_p
 _lib.mueller_strerror.argtypes = [ct.c_int]
 _lib.mueller_last_error.restype = ct.c_char_p
 
-EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_far_field",
+EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_rhs_fields",
+           "mueller_far_field", "mueller_eval",
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_stats_get",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
@@ -165,6 +168,18 @@ class Context:
         p = np.ascontiguousarray(np.asarray(pols, np.float64).reshape(-1, 3))
         _check(_lib.mueller_rhs_planewave(self._h, _dptr(d), _dptr(p), len(d), _ptr(rhs), _stream(stream)))
         return rhs
+
+    def rhs_fields(self, EH, rhs, stream=None):
+        """Modal data from sampled fields EH [nrhs, N, n_theta, 6] (device, complex128)."""
+        _check(_lib.mueller_rhs_fields(self._h, _ptr(EH), EH.shape[0], EH.shape[2], _ptr(rhs), _stream(stream)))
+        return rhs
+
+    def eval(self, x, targets, region, out, stream=None):
+        """E, H at host points targets [nt, 3] into out [nrhs, nt, 6] (device); region 0 exterior, 1 body."""
+        t = np.ascontiguousarray(np.asarray(targets, np.float64).reshape(-1, 3))
+        _check(_lib.mueller_eval(self._h, _ptr(x), x.shape[1], _dptr(t), len(t), int(region), _ptr(out),
+                                 _stream(stream)))
+        return out
 
     def far_field(self, x, dirs, E, stream=None):
         _check(_lib.mueller_far_field(self._h, _ptr(x), x.shape[1], _ptr(dirs), dirs.shape[0], _ptr(E),

@@ -3,6 +3,34 @@
 
 // One CTA per (node, wave): samples of the tangential traces on the node's
 // ring at n_theta azimuths, then their Fourier coefficients for m = -M..M.
+// Fourier coefficients (1/n_theta) sum_t s_t e^{-i m theta_t} of the four ring
+// traces smp[n_theta][4] (twiddles tw[t] = e^{-2 pi i t/n_theta}), scaled by
+// sE (rows 0, 1) and sH (rows 2, 3): one (mode, row) per thread.
+__device__ void modal_dft(const cd* smp, const cd* tw, int n_theta, int M, int nrhs, int w, int i, int n, cd sE,
+                          cd sH, cd* __restrict__ rhs) {
+  const double inv = 1.0 / n_theta;
+  for (int item = threadIdx.x; item < 4 * (2 * M + 1); item += blockDim.x) {
+    const int mq = item >> 2, a = item & 3;
+    const int m = mq - M;
+    const int mm = ((m % n_theta) + n_theta) % n_theta;
+    cd acc = C(0.0);
+    int idx = 0;
+    for (int t = 0; t < n_theta; ++t) {
+      acc = fma(smp[4 * t + a], tw[idx], acc);
+      idx += mm;
+      if (idx >= n_theta) idx -= n_theta;
+    }
+    rhs[((size_t)mq * nrhs + w) * n + 4 * i + a] = (a < 2 ? sE : sH) * (inv * acc);
+  }
+}
+
+// n x v = v_theta t - v_t e_theta at one ring point: (v_theta, -v_t)
+__device__ __forceinline__ void traces(const cd v[3], double ct, double st, double rp, double zp, cd* out2) {
+  cd vr = ct * v[0] + st * v[1], vth = ct * v[1] - st * v[0];
+  out2[0] = vth;
+  out2[1] = -(rp * vr + zp * v[2]);
+}
+
 __global__ void rhs_kernel(FieldGeom g, int M, cd k0, double omega, cd mu0, cd sE, cd sH,
                            const double* __restrict__ dirs, const double* __restrict__ pols, int nrhs, int n_theta,
                            cd* __restrict__ rhs) {
@@ -22,32 +50,42 @@ __global__ void rhs_kernel(FieldGeom g, int M, cd k0, double omega, cd mu0, cd s
     tw[t] = C(ct, -st);
     double phase = r * (d[0] * ct + d[1] * st) + z * d[2];
     cd ph = cexpi(k0 * phase);
-    // E components in (e_r, e_theta, e_z)
-    double Er = e[0] * ct + e[1] * st, Et = -e[0] * st + e[1] * ct, Ez = e[2];
-    double Hr = hx * ct + hy * st, Ht = -hx * st + hy * ct, Hz = hz;
-    // n x v = v_theta t - v_t e_theta
-    smp[4 * t + 0] = Et * ph;
-    smp[4 * t + 1] = -(rp * Er + zp * Ez) * ph;
-    smp[4 * t + 2] = Ht * (hf * ph);
-    smp[4 * t + 3] = -(rp * Hr + zp * Hz) * (hf * ph);
+    cd hph = hf * ph;
+    const cd E[3] = {e[0] * ph, e[1] * ph, e[2] * ph};
+    const cd H[3] = {hx * hph, hy * hph, hz * hph};
+    traces(E, ct, st, rp, zp, smp + 4 * t);
+    traces(H, ct, st, rp, zp, smp + 4 * t + 2);
   }
   __syncthreads();
-  const int n = 4 * g.N;
-  const double inv = 1.0 / n_theta;
-  // one (mode, component) per item: the DFT sum over the ring samples
-  for (int item = threadIdx.x; item < 4 * (2 * M + 1); item += blockDim.x) {
-    const int mq = item >> 2, a = item & 3;
-    const int m = mq - M;
-    const int mm = ((m % n_theta) + n_theta) % n_theta;
-    cd acc = C(0.0);
-    int idx = 0;
-    for (int t = 0; t < n_theta; ++t) {
-      acc = fma(smp[4 * t + a], tw[idx], acc);
-      idx += mm;
-      if (idx >= n_theta) idx -= n_theta;
-    }
-    rhs[((size_t)mq * nrhs + w) * n + 4 * i + a] = (a < 2 ? sE : sH) * (inv * acc);
+  modal_dft(smp, tw, n_theta, M, nrhs, w, i, 4 * g.N, sE, sH, rhs);
+}
+
+// Sampled incident fields EH[w][i][t][6] (E then H, Cartesian) at the ring
+// points of node i -> modal data, as rhs_kernel.
+__global__ void rhs_samples_kernel(FieldGeom g, int M, cd sE, cd sH, const cd* __restrict__ EH, int nrhs,
+                                   int n_theta, cd* __restrict__ rhs) {
+  extern __shared__ __align__(16) char smem[];
+  cd* smp = (cd*)smem;
+  cd* tw = smp + 4 * n_theta;
+  const int i = blockIdx.x, w = blockIdx.y;
+  const double rp = g.rp[i], zp = g.zp[i];
+  const cd* src = EH + ((size_t)w * g.N + i) * n_theta * 6;
+  for (int t = threadIdx.x; t < n_theta; t += blockDim.x) {
+    double ct, st;
+    sincospi(2.0 * t / n_theta, &st, &ct);
+    tw[t] = C(ct, -st);
+    traces(src + 6 * t, ct, st, rp, zp, smp + 4 * t);
+    traces(src + 6 * t + 3, ct, st, rp, zp, smp + 4 * t + 2);
   }
+  __syncthreads();
+  modal_dft(smp, tw, n_theta, M, nrhs, w, i, 4 * g.N, sE, sH, rhs);
+}
+
+void launch_rhs_samples(const FieldGeom& g, int M, cd sE, cd sH, const cd* EH, int nrhs, int n_theta, cd* rhs,
+                        cudaStream_t s) {
+  int smem = n_theta * 5 * (int)sizeof(cd);
+  cudaFuncSetAttribute(rhs_samples_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  rhs_samples_kernel<<<dim3(g.N, nrhs), 256, smem, s>>>(g, M, sE, sH, EH, nrhs, n_theta, rhs);
 }
 
 void launch_rhs_planewave(const FieldGeom& g, int M, cd k0, double omega, cd mu0, cd sE, cd sH,
@@ -141,4 +179,85 @@ void launch_far_field(const FieldGeom& g, int M, cd k0, double omega, cd eps0, c
                       const double* dirs_dev, int ndir, int n_theta, cd* cur, cd* E, cudaStream_t s) {
   ring_kernel<<<dim3(g.N, nrhs), 128, 0, s>>>(g.N, M, x, nrhs, n_theta, cur);
   farfield_kernel<<<dim3(ndir, nrhs), 256, 0, s>>>(g, k0, omega, eps0, cur, nrhs, dirs_dev, ndir, n_theta, E);
+}
+
+// ---------------------------------------------------------------------------
+// Fields at points off the surface: E = cJ curl curl S J + cM curl S M,
+// H = dM curl curl S M + dJ curl S J (eqs. exteriorfield, interiorfield,
+// interior_dual with the region's constants), with
+//   curl S V      = sum G (ik - 1/R) Rh x V da,
+//   curl curl S V = sum G [(k^2 + ik/R - 1/R^2) V + (-k^2 - 3ik/R + 3/R^2)(Rh.V) Rh] da
+// over the node rings (ds-weights x trapezoid in theta).  One CTA per
+// (point, right-hand side); ring currents cur[w][i][t][4] from ring_kernel.
+__global__ void __launch_bounds__(256) nearfield_kernel(FieldGeom g, int n_theta, const cd* __restrict__ cur,
+                                                        const double* __restrict__ X, int nt, int nrhs, cd k,
+                                                        cd cJ, cd cM, cd dM, cd dJ, cd* __restrict__ out) {
+  const int p = blockIdx.x, w = blockIdx.y;
+  const double x0 = X[3 * p], x1 = X[3 * p + 1], x2 = X[3 * p + 2];
+  cd acc[12];  // curl curl S J, curl S M, curl curl S M, curl S J (3 components each)
+#pragma unroll
+  for (int a = 0; a < 12; ++a) acc[a] = C(0.0);
+  const cd ik = mul_i(k), k2 = k * k;
+  const double FOUR_PI = 12.566370614359172, TWO_PI = 6.283185307179586;
+  const long long total = (long long)g.N * n_theta;
+  for (long long it = threadIdx.x; it < total; it += blockDim.x) {
+    const int i = (int)(it / n_theta), t = (int)(it % n_theta);
+    double s, c;
+    sincospi(2.0 * t / n_theta, &s, &c);
+    const double r = g.r[i], z = g.z[i];
+    const double tx = g.rp[i] * c, ty = g.rp[i] * s, tz = g.zp[i];  // unit tangent; e_theta = (-s, c, 0)
+    const cd* cv = cur + (((size_t)w * g.N + i) * n_theta + t) * 4;
+    const cd J[3] = {tx * cv[0] - s * cv[1], ty * cv[0] + c * cv[1], tz * cv[0]};
+    const cd Mv[3] = {tx * cv[2] - s * cv[3], ty * cv[2] + c * cv[3], tz * cv[2]};
+    const double R0 = x0 - r * c, R1 = x1 - r * s, R2 = x2 - z;
+    const double R = sqrt(R0 * R0 + R1 * R1 + R2 * R2), iR = 1.0 / R;
+    const double h0 = R0 * iR, h1 = R1 * iR, h2 = R2 * iR;
+    const double da = g.w[i] * r * (TWO_PI / n_theta);
+    const cd G = (da * iR / FOUR_PI) * cexpi(k * R);
+    const cd c1 = G * (ik - C(iR));
+    const cd aa = G * (k2 + iR * ik - C(iR * iR));
+    const cd bb = G * (C(3.0 * iR * iR) - k2 - (3.0 * iR) * ik);
+    const cd pJ = h0 * J[0] + h1 * J[1] + h2 * J[2];
+    const cd pM = h0 * Mv[0] + h1 * Mv[1] + h2 * Mv[2];
+    const double hv[3] = {h0, h1, h2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      acc[d] += aa * J[d] + (bb * pJ) * hv[d];
+      acc[6 + d] += aa * Mv[d] + (bb * pM) * hv[d];
+    }
+    acc[3] += c1 * (h1 * Mv[2] - h2 * Mv[1]);
+    acc[4] += c1 * (h2 * Mv[0] - h0 * Mv[2]);
+    acc[5] += c1 * (h0 * Mv[1] - h1 * Mv[0]);
+    acc[9] += c1 * (h1 * J[2] - h2 * J[1]);
+    acc[10] += c1 * (h2 * J[0] - h0 * J[2]);
+    acc[11] += c1 * (h0 * J[1] - h1 * J[0]);
+  }
+  __shared__ cd red[12][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[a].x += __shfl_xor_sync(0xffffffffu, acc[a].x, o);
+      acc[a].y += __shfl_xor_sync(0xffffffffu, acc[a].y, o);
+    }
+    if (lane == 0) red[a][wid] = acc[a];
+  }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    cd tot = C(0.0);
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += red[threadIdx.x][q];
+    red[threadIdx.x][0] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int d = threadIdx.x % 3;
+    cd v = (threadIdx.x < 3) ? cJ * red[d][0] + cM * red[3 + d][0] : dM * red[6 + d][0] + dJ * red[9 + d][0];
+    out[((size_t)w * nt + p) * 6 + threadIdx.x] = v;
+  }
+}
+
+void launch_near_field(const FieldGeom& g, int M, const cd* x, int nrhs, const double* X_dev, int nt, int n_theta,
+                       cd k, cd cJ, cd cM, cd dM, cd dJ, cd* cur, cd* out, cudaStream_t s) {
+  ring_kernel<<<dim3(g.N, nrhs), 128, 0, s>>>(g.N, M, x, nrhs, n_theta, cur);
+  nearfield_kernel<<<dim3(nt, nrhs), 256, 0, s>>>(g, n_theta, cur, X_dev, nt, nrhs, k, cJ, cM, dM, dJ, out);
 }

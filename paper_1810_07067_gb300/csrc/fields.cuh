@@ -16,3 +16,12 @@ void launch_rhs_planewave(const FieldGeom& g, int M, cd k0, double omega, cd mu0
 // cur[rhs][N][n_theta][4].
 void launch_far_field(const FieldGeom& g, int M, cd k0, double omega, cd eps0, const cd* x, int nrhs,
                       const double* dirs_dev, int ndir, int n_theta, cd* cur, cd* E, cudaStream_t s);
+
+// Modal data from sampled incident fields EH[rhs][N][n_theta][6] (device).
+void launch_rhs_samples(const FieldGeom& g, int M, cd sE, cd sH, const cd* EH, int nrhs, int n_theta, cd* rhs,
+                        cudaStream_t s);
+
+// E, H at points X[nt][3] (device) into out[rhs][nt][6]; cur is a ring work
+// buffer [rhs][N][n_theta][4]; k and the four constants are the region's.
+void launch_near_field(const FieldGeom& g, int M, const cd* x, int nrhs, const double* X_dev, int nt, int n_theta,
+                       cd k, cd cJ, cd cM, cd dM, cd dJ, cd* cur, cd* out, cudaStream_t s);

@@ -741,6 +741,52 @@ extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const d
   return MUELLER_OK;
 }
 
+extern "C" int mueller_rhs_fields(mueller_ctx* c, const mueller_c128* EH_dev, int nrhs, int n_theta,
+                                  mueller_c128* rhs_dev, void* stream) {
+  g_err.clear();
+  if (!c || !EH_dev || !rhs_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid field-sample arguments");
+  if (n_theta < 2 * c->S.M + 2 || n_theta > 2048)
+    return fail(MUELLER_EINVAL, "n_theta must lie in [2M+2, 2048]");
+  cudaStream_t s = (cudaStream_t)stream;
+  FieldGeom g{c->geo[0], c->geo[1], c->geo[2], c->geo[3], c->geo[4], c->S.N};
+  launch_rhs_samples(g, c->S.M, c->S.sE, c->S.sH, (const cd*)EH_dev, nrhs, n_theta, (cd*)rhs_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_eval(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* targets, int ntargets,
+                            int region, mueller_c128* out_dev, void* stream) {
+  g_err.clear();
+  if (!c || !x_dev || !targets || !out_dev || nrhs < 1 || ntargets < 1 || (region != 0 && region != 1))
+    return fail(MUELLER_EINVAL, "invalid evaluation arguments");
+  for (int p = 0; p < 3 * ntargets; ++p)
+    if (!std::isfinite(targets[p])) return fail(MUELLER_EINVAL, "non-finite target coordinate");
+  const Setup& S = c->S;
+  const cd iw = C(0.0, S.omega);
+  cd k, cJ, cM, dM, dJ;
+  if (region == 0) {  // eq. exteriorfield
+    k = S.k0; cJ = -(C(1.0) / (iw * S.eps0)); cM = C(1.0); dM = C(1.0) / (iw * S.mu0); dJ = C(1.0);
+  } else if (S.formulation == 0) {  // eq. interiorfield
+    k = S.k1; cJ = C(1.0) / (iw * S.eps1); cM = C(-1.0); dM = -(C(1.0) / (iw * S.mu1)); dJ = C(-1.0);
+  } else {  // eq. interior_dual
+    k = S.k1; cJ = -(C(1.0) / (iw * S.eps0)); cM = S.mu1 / S.mu0; dM = C(1.0) / (iw * S.mu0); dJ = S.eps1 / S.eps0;
+  }
+  const int nth = 2 * S.M + 2 * (int)std::ceil(cabs(k) * S.rmax) + 64;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf tmp;
+  cd* cur;
+  double* X;
+  std::vector<double> vx(targets, targets + 3 * ntargets);
+  if (tmp.alloc(&cur, (size_t)nrhs * S.N * nth * 4) != cudaSuccess) return fail(MUELLER_ENOMEM, "ring buffer");
+  CK(tmp.upload(&X, vx, s));
+  FieldGeom g{c->geo[0], c->geo[1], c->geo[2], c->geo[3], c->geo[4], S.N};
+  launch_near_field(g, S.M, (const cd*)x_dev, nrhs, X, ntargets, nth, k, cJ, cM, dM, dJ, cur, (cd*)out_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MUELLER_OK;
+}
+
 extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* dirs_dev,
                                  int ndir, mueller_c128* E_dev, void* stream) {
   g_err.clear();

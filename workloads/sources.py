@@ -19,9 +19,13 @@ LOOP_CENTER = (0.4, 0.5, 5.0)
 LOOP_RADIUS = 0.42
 
 
-def current_loop_field(points, k, omega, mu, center=LOOP_CENTER, radius=LOOP_RADIUS, n_seg=256):
+def current_loop_field(points, k, omega, mu, center=LOOP_CENTER, radius=LOOP_RADIUS, n_seg=256, chunk=2048):
     """E and H [npts, 3] of the loop at the given points [npts, 3]."""
     x = np.atleast_2d(np.asarray(points, float))
+    if len(x) > chunk:
+        parts = [current_loop_field(x[i:i + chunk], k, omega, mu, center, radius, n_seg, chunk)
+                 for i in range(0, len(x), chunk)]
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
     c = np.asarray(center, float)
     s = 2 * np.pi * np.arange(n_seg) / n_seg
     y = c[None, :] + radius * np.stack([np.cos(s), np.sin(s), np.zeros_like(s)], -1)      # [S, 3]
