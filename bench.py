@@ -36,6 +36,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(values, dist=None, device="cpu"):
+    """Per-rank timings -> their maximum over all ranks (the job's time);
+    identity on a single rank."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(n_ranks, step_s):
+    """Bodies per second of the whole job: every rank solves its own body per
+    step (weak scaling), the step lasting the slowest rank's time."""
+    return n_ranks / step_s
+
+
 def _clock_sampler(path):
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -225,10 +241,7 @@ def main():
         sampler.terminate()
         sampler.wait()
     clocks = _clock_summary(clk_path, local)
-    t = torch.tensor([dev_s, e2e_s], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_s, e2e_s = t.tolist()
+    dev_s, e2e_s = reduce_max([dev_s, e2e_s], dist, dev)
     if rank == 0:
         st = stats[-1]
         launches = st["launches"] + st["solve_launches"] + 1  # + rhs_kernel
@@ -244,7 +257,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": dev_s * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)", "data": "synthetic",
                 "config": dict(_config(cfg), precision=args.precision),
-                "bodies_per_s": ws / dev_s,
+                "bodies_per_s": job_throughput(ws, dev_s),
                 "stages_ms": {k: round(st[k], 3) for k in ("ms_legendre", "ms_far", "ms_support", "ms_near",
                                                            "ms_lu", "ms_lu_gemm", "ms_solve")},
                 "roofline": {"bound": "alu", "kernel": "far_kernel (far pairs: sampling, cosine transform, "
