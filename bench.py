@@ -146,6 +146,65 @@ def _config(cfg):
             "precision": "fp64", "l2_flush": f"inputs larger than L2 ({fb:.2g} GB of factors per step)"}
 
 
+def run_batched(args):
+    """The batched workload: every body of workloads.config_batch() built and
+    solved (mixed path, both plane waves) once, under a device-memory budget,
+    on args.streams concurrent streams.  Warm-up: the args.warmup smallest
+    bodies, untimed.  value = wall time of the whole batch (host clock around
+    the pass, device synchronised on both sides)."""
+    import torch
+    import workloads as W
+    import paper_1810_07067_gb300 as mb
+    from paper_1810_07067_gb300 import batch
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle timing "
+                          "(the oracle is timed on the cylinder workload)"}))
+        return
+    bodies = W.config_batch()
+    if args.bodies:
+        bodies = bodies[:args.bodies]
+    free, total = torch.cuda.mem_get_info()
+    budget = int(args.budget_gb * 1e9) if args.budget_gb > 0 else int(0.9 * free)
+    small = sorted(bodies, key=lambda c: mb.build_bytes(c.N, c.M, 1)[0])[:max(args.warmup, 0)]
+    batch.run_batch(small, budget, n_streams=args.streams)
+    torch.cuda.synchronize()
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            "clocks_batched.csv")
+    sampler = _clock_sampler(clk_path)
+    time.sleep(0.3)
+    walls = []
+    for _ in range(max(args.steps, 1)):
+        torch.cuda.synchronize()
+        res, wall, adm = batch.run_batch(bodies, budget, n_streams=args.streams)
+        torch.cuda.synchronize()
+        walls.append(wall)
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    wall = statistics.median(walls)
+    nrhs = sum(len(c.waves) * (2 * c.M + 1) for c in bodies)
+    line = {"metric": "batched: wall time to build (mixed) and solve every body of the batch under a memory budget",
+            "value": wall, "unit": "s", "n_gpus": 1, "steps": len(walls), "warmup": len(small),
+            "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 factors + c128 refinement", "data": "synthetic",
+            "config": {"workload": f"{len(bodies)} bodies of workloads.config_batch (random smooth bodies, "
+                                   f"cylinders, cones; N {min(c.N for c in bodies)}..{max(c.N for c in bodies)}, "
+                                   f"M {min(c.M for c in bodies)}..{max(c.M for c in bodies)}, k1 = 1.5 k0)",
+                       "streams": args.streams, "budget_gb": budget / 1e9,
+                       "l2_flush": "inputs larger than L2 (every body's matrices)"},
+            "bodies_per_s": len(bodies) / wall,
+            "modal_solves_per_s": nrhs / wall,
+            "resident_tb_total": sum(r.resident_bytes for r in res) / 1e12,
+            "budget_high_water_gb": adm.high_water / 1e9,
+            "sum_build_s": sum(r.build_ms for r in res) / 1e3, "sum_solve_s": sum(r.solve_ms for r in res) / 1e3,
+            "backward_err_max": max(r.backward_err for r in res),
+            "refine_iters_max": max(r.refine_iters for r in res),
+            "largest_body": max(((r.N, r.M) for r in res)),
+            "gpu_launches": sum(r.launches for r in res) * len(walls),
+            "clocks": _clock_summary(clk_path, 0)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -153,14 +212,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "small"],
-                    help="small: random smooth body N=256, M=32 (profiling captures)")
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "small", "batched", "serving"],
+                    help="small: random smooth body N=256, M=32 (profiling captures); batched: the 72-body "
+                         "batch under a memory budget; serving: Poisson request stream with a factor cache")
+    ap.add_argument("--bodies", type=int, default=0, help="batched: only the first K bodies (0 = all)")
+    ap.add_argument("--streams", type=int, default=2, help="batched: concurrent bodies (CUDA streams)")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="batched/serving: device-memory budget (0 = 90%% of the free memory)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="path timed for the headline value (the other path is timed once beside it)")
     args = ap.parse_args()
     args.steps_ref = args.steps
     args.warmup_ref = args.warmup
     import workloads as W
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "serving":
+        from paper_1810_07067_gb300 import serving  # noqa: F401
+        run_serving(args)
+        return
     cfg = W.config_cylinder(7) if args.workload == "cylinder" else W.config_random(16, 1810, 32, 128)
     if args.impl == "reference":
         run_reference(args, cfg)

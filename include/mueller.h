@@ -235,6 +235,13 @@ int mueller_lu_batched(mueller_c128* A_dev, int n, int batch, int* piv_dev, int*
  * factors are then unusable).  Synchronises `stream`. */
 int mueller_lu_batched_c64(mueller_c64* A_dev, int n, int batch, int* piv_dev, int* info_dev, void* stream);
 
+/* Device bytes of mueller_build for a body of N nodes and modes 0..M at the
+ * given precision option: the return value is the peak during the build
+ * (matrices, complex64 factors, residual slices and the near-panel spectra
+ * scratch), *resident (if not null) what the context holds afterwards.  Used
+ * to admit bodies under a memory budget; 0 for invalid sizes. */
+size_t mueller_build_bytes(int N, int M, int precision, size_t* resident);
+
 /* Bytes of complex128 factors for one body: 16 (4N)^2 (2M+1), the admission
  * unit named by the serving workload (the GPU path stores M+1 of them). */
 size_t mueller_footprint_bytes(int N, int M);

@@ -73,6 +73,8 @@ _lib.mueller_lu_batched_c64.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
 _lib.mueller_modal_kernels_noalloc.argtypes = [_vp, ct.c_longlong, c128, c128, ct.c_int, ct.c_int, ct.c_double,
                                                _vp, _vp]
 _lib.mueller_footprint_bytes.argtypes = [ct.c_int, ct.c_int]
+_lib.mueller_build_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
+_lib.mueller_build_bytes.restype = ct.c_size_t
 _lib.mueller_footprint_bytes.restype = ct.c_size_t
 _lib.mueller_stats_get.argtypes = [_vp, ct.POINTER(Stats)]
 _lib.mueller_destroy.argtypes = [_vp]
@@ -82,7 +84,7 @@ _lib.mueller_last_error.restype = ct.c_char_p
 
 EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_rhs_fields",
            "mueller_far_field", "mueller_eval",
-           "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_stats_get",
+           "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
@@ -109,7 +111,7 @@ def _ptr(t):
 
 def _stream(stream):
     if stream is not None:
-        return ct.c_void_p(stream)
+        return ct.c_void_p(getattr(stream, "cuda_stream", stream))
     import torch
     return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -247,6 +249,13 @@ def lu_batched_c64(A, piv, info, stream=None):
     n = A.shape[-1]
     batch = A.shape[0]
     _check(_lib.mueller_lu_batched_c64(_ptr(A), n, batch, _ptr(piv), _ptr(info), _stream(stream)))
+
+
+def build_bytes(N: int, M: int, precision: int) -> tuple[int, int]:
+    """(peak bytes during mueller_build, bytes resident afterwards)."""
+    res = ct.c_size_t(0)
+    peak = int(_lib.mueller_build_bytes(int(N), int(M), int(precision), ct.byref(res)))
+    return peak, int(res.value)
 
 
 def footprint_bytes(N: int, M: int) -> int:

@@ -877,6 +877,19 @@ extern "C" int mueller_lu_batched_c64(mueller_c64* A_dev, int n, int batch, int*
   return MUELLER_OK;
 }
 
+extern "C" size_t mueller_build_bytes(int N, int M, int precision, size_t* resident) {
+  if (N < 1 || M < 0) return 0;
+  const size_t n = 4 * (size_t)N, modes = (size_t)M + 1;
+  const size_t npad = (n + OZ_RT - 1) / OZ_RT * OZ_RT;
+  const size_t A = modes * n * n * sizeof(cd);
+  const size_t A32 = precision != 0 ? modes * n * n * sizeof(cf) : 0;
+  const size_t sl = precision == 1 ? ozaki_matrix_slices_elems((int)npad, (int)modes) * 2 + modes * npad * 8 : 0;
+  const size_t small = modes * n * 4 + modes * 16 + (size_t)N * 64;
+  const size_t scratch = (size_t)N * NEAR_SLOTS * NFAM * (size_t)(M + 2) * sizeof(cd);
+  if (resident) *resident = (precision == 1 ? 0 : A) + A32 + sl + small;
+  return A + A32 + sl + small + scratch;
+}
+
 extern "C" size_t mueller_footprint_bytes(int N, int M) {
   return (size_t)16 * (size_t)(4 * N) * (size_t)(4 * N) * (size_t)(2 * M + 1);
 }

@@ -5,7 +5,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .curves import Curve, sphere, cylinder, random_body
+from .curves import Curve, sphere, cylinder, cone, random_body
 
 
 @dataclass
@@ -91,3 +91,33 @@ def config_random(n_panels: int = 64, seed: int = 1810, M: int = 128, n_phi: int
     from .configs import paper_default_wave  # noqa
     return Config(f"random{seed}_N{16 * n_panels}_M{M}", random_body(n_panels, seed),
                   Media.from_k(10.0, 15.0), M, n_phi, [paper_default_wave(), _polar_wave(np.pi / 4, 0)])
+
+
+def config_batch(n_random: int = 64, n_edged: int = 8) -> list:
+    """The batched workload: n_random smooth random bodies (seeds 0..n_random-1,
+    the random-body generator) and n_edged edged bodies (seeds n_random..:
+    cylinders, then cones, radius and half-height ~ U(0.5, 1.5)).  Per body,
+    from default_rng(10000 + seed): N ~ U[200, 1200] rounded to whole panels
+    (edged bodies: the nearest refinement level), M ~ U{32..128},
+    k0 ~ U[1, 12], k1 = 1.5 k0; the paper's default plane wave and the
+    45-degree wave.  n_phi is left to the solver (16 = smallest)."""
+    waves = [paper_default_wave(), _polar_wave(np.pi / 4, 0)]
+    out = []
+    for s in range(n_random + n_edged):
+        rng = np.random.default_rng(10000 + s)
+        N = int(rng.uniform(200, 1200))
+        M = int(rng.integers(32, 129))
+        k0 = float(rng.uniform(1.0, 12.0))
+        if s < n_random:
+            curve = random_body(max(1, round(N / 16)), seed=s)
+        else:
+            R, h = float(rng.uniform(0.5, 1.5)), float(rng.uniform(0.5, 1.5))
+            if s < n_random + (n_edged + 1) // 2:
+                levels = max(1, round((N / 16 - 8) / 4))
+                curve = cylinder(levels, R, h)
+            else:
+                levels = max(1, round((N / 16 - 6) / 3))
+                curve = cone(levels, R, h)
+        out.append(Config(f"batch{s}_{curve.name}_N{curve.N}_M{M}", curve, Media.from_k(k0, 1.5 * k0), M, 16,
+                          list(waves)))
+    return out

@@ -122,6 +122,40 @@ def cylinder(levels: int = 7, radius: float = 1.0, half_height: float = 1.0,
                  {"min_panel": float(min(widths))})
 
 
+def cone(levels: int = 5, radius: float = 1.0, half_height: float = 1.0, base=(2, 4)) -> Curve:
+    """Cone with its apex on the axis: bottom disk (0,-h) -> (R,-h), then the
+    slant side (R,-h) -> (0,h).  The panels next to the rim edge (on both
+    sides) and next to the apex are refined dyadically `levels` times toward
+    them, so N = 16 * (base[0] + base[1] + 3 * levels)."""
+    R, h = radius, half_height
+    segs = [((0.0, -h), (R, -h), base[0]), ((R, -h), (0.0, h), base[1])]
+    all_panels = []
+    for si, (_, _, nb) in enumerate(segs):
+        edges = np.linspace(0.0, 1.0, nb + 1)
+        for pi, (s0, s1) in enumerate(zip(edges[:-1], edges[1:])):
+            if si == 0 and pi == nb - 1:
+                parts = _dyadic(s0, s1, levels, toward_b=True)            # toward the rim
+            elif si == 1 and pi == 0:
+                parts = _dyadic(s0, s1, levels, toward_b=False)           # from the rim
+            elif si == 1 and pi == nb - 1:
+                parts = _dyadic(s0, s1, levels, toward_b=True)            # toward the apex
+            else:
+                parts = [(s0, s1)]
+            all_panels += [(si, a, b) for (a, b) in parts]
+    x = panel_nodes()
+    rs, zs, drs, dzs, widths = [], [], [], [], []
+    for (si, s0, s1) in all_panels:
+        (ra, za), (rb, zb), _ = segs[si]
+        s = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * x
+        rs.append(ra + (rb - ra) * s); zs.append(za + (zb - za) * s)
+        jac = 0.5 * (s1 - s0)
+        drs.append(np.full(P, (rb - ra) * jac)); dzs.append(np.full(P, (zb - za) * jac))
+        widths.append(np.hypot(rb - ra, zb - za) * (s1 - s0))
+    return Curve(len(all_panels), np.concatenate(rs), np.concatenate(zs),
+                 np.concatenate(drs), np.concatenate(dzs), False, f"cone_L{levels}",
+                 {"min_panel": float(min(widths))})
+
+
 def random_body(n_panels: int = 64, seed: int = 1810, n_coef: int = 6, amp: float = 0.08) -> Curve:
     """Smooth random body r(t) = sin t (1 + sum_j a_j cos jt), z = -cos t,
     a_j ~ U(-amp, amp) drawn from numpy's default_rng(seed)."""
