@@ -205,6 +205,54 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """The serving workload: Poisson arrivals (default_rng(5)) at args.rate
+    per second for args.duration seconds over the 32-body pool
+    (workloads.config_pool), body choice Zipf(args.zipf), nrhs ~ U{1..max_rhs},
+    far field on the 180 x 360 (polar x azimuth) grid per request, factors
+    cached on the device under the memory budget.  Warm-up: args.warmup
+    requests on the smallest body, untimed.  value = p99 latency."""
+    import torch
+    import workloads as W
+    from paper_1810_07067_gb300 import serving
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no oracle timing "
+                          "(the oracle is timed on the cylinder workload)"}))
+        return
+    pool = W.config_pool(32)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(args.budget_gb * 1e9) if args.budget_gb > 0 else int(0.9 * free)
+    srv = serving.Server(pool, budget, precision=1, max_rhs=args.max_rhs, grid=(180, 360))
+    smallest = min(range(len(pool)), key=lambda k: srv.peaks[k])
+    warm = [serving.Request(i, smallest, 0.0, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+            for i in range(max(args.warmup, 1))]
+    srv.run(warm)
+    srv.close()
+    reqs = serving.poisson_requests(len(pool), args.rate, args.duration, seed=5, zipf=args.zipf,
+                                    max_rhs=args.max_rhs)
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            "clocks_serving.csv")
+    sampler = _clock_sampler(clk_path)
+    torch.cuda.synchronize()
+    st = srv.run(reqs, drain_limit=args.drain)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    summ = serving.summarize(st, len(reqs), args.duration)
+    line = {"metric": "serving: p99 latency (arrival to far field on the host) of a Poisson request stream",
+            "value": summ["p99_latency_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": len(warm),
+            "ms_per_step": st.wall * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 factors + c128 refinement", "data": "synthetic",
+            "config": {"workload": f"serving: 32-body pool (workloads.config_pool), Poisson {args.rate:g}/s for "
+                                   f"{args.duration:g} s, Zipf({args.zipf:g}) bodies, nrhs U{{1..{args.max_rhs}}}, "
+                                   f"far field 180x360 per request", "budget_gb": budget / 1e9,
+                       "l2_flush": "inputs larger than L2 (factors of every key)"},
+            "serving": summ, "clocks": _clock_summary(clk_path, 0)}
+    srv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +265,11 @@ def main():
                          "batch under a memory budget; serving: Poisson request stream with a factor cache")
     ap.add_argument("--bodies", type=int, default=0, help="batched: only the first K bodies (0 = all)")
     ap.add_argument("--streams", type=int, default=2, help="batched: concurrent bodies (CUDA streams)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window in seconds")
+    ap.add_argument("--zipf", type=float, default=1.1, help="serving: body choice Zipf exponent (0 = uniform)")
+    ap.add_argument("--max-rhs", type=int, default=256, help="serving: right-hand sides per request at most")
+    ap.add_argument("--drain", type=float, default=120.0, help="serving: seconds after the last arrival to finish")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="batched/serving: device-memory budget (0 = 90%% of the free memory)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
@@ -229,7 +282,6 @@ def main():
         run_batched(args)
         return
     if args.workload == "serving":
-        from paper_1810_07067_gb300 import serving  # noqa: F401
         run_serving(args)
         return
     cfg = W.config_cylinder(7) if args.workload == "cylinder" else W.config_random(16, 1810, 32, 128)
@@ -278,9 +330,11 @@ def main():
     time.sleep(0.3)
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_step")            # lets a profiler select the timed launches
     e0.record(stream)
     stats = [step() for _ in range(args.steps)]
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()

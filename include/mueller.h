@@ -162,6 +162,16 @@ int mueller_rhs_planewave(mueller_ctx* ctx, const double* dirs, const double* po
 int mueller_rhs_fields(mueller_ctx* ctx, const mueller_c128* EH_dev, int nrhs, int n_theta,
                        mueller_c128* rhs_dev, void* stream);
 
+/* Far field of mueller_far_field on the grid theta_p = (p + 1/2) pi / n_polar
+ * (p < n_polar), phi_s = 2 pi s / n_azim (s < n_azim <= 8192), computed by
+ * modes: for each theta, the ring integrals become per-mode coefficients and
+ * the far field is a sum over m of e^{i m phi} times a per-mode vector
+ * (Section 4's separation of variables applied to eq. farfieldform), then
+ * rotated to Cartesian components.  x_dev: currents [2M+1][nrhs][4N];
+ * E_dev: device [nrhs][n_polar][n_azim][3]. */
+int mueller_far_field_grid(mueller_ctx* ctx, const mueller_c128* x_dev, int nrhs, int n_polar, int n_azim,
+                           mueller_c128* E_dev, void* stream);
+
 /* Fields at points off the surface from modal currents (Section 3):
  * region 0 (the exterior medium) by eq. exteriorfield with k0; region 1 (the
  * body) by eq. interiorfield for the direct formulation or eq. interior_dual

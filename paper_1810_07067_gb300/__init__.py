@@ -69,6 +69,7 @@ _lib.mueller_modal_kernels.argtypes = [ct.POINTER(ct.c_double), ct.c_longlong, c
 _lib.mueller_lu_batched.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
 _lib.mueller_rhs_fields.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
 _lib.mueller_eval.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, ct.c_int, _vp, _vp]
+_lib.mueller_far_field_grid.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, _vp]
 _lib.mueller_lu_batched_c64.argtypes = [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp]
 _lib.mueller_modal_kernels_noalloc.argtypes = [_vp, ct.c_longlong, c128, c128, ct.c_int, ct.c_int, ct.c_double,
                                                _vp, _vp]
@@ -83,7 +84,7 @@ _lib.mueller_strerror.argtypes = [ct.c_int]
 _lib.mueller_last_error.restype = ct.c_char_p
 
 EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_rhs_fields",
-           "mueller_far_field", "mueller_eval",
+           "mueller_far_field", "mueller_far_field_grid", "mueller_eval",
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
@@ -182,6 +183,12 @@ class Context:
         _check(_lib.mueller_eval(self._h, _ptr(x), x.shape[1], _dptr(t), len(t), int(region), _ptr(out),
                                  _stream(stream)))
         return out
+
+    def far_field_grid(self, x, E, stream=None):
+        """E [nrhs, n_polar, n_azim, 3] (device) on the grid theta_p = (p + 1/2) pi / n_polar, phi_s = 2 pi s / n_azim."""
+        _check(_lib.mueller_far_field_grid(self._h, _ptr(x), x.shape[1], E.shape[1], E.shape[2], _ptr(E),
+                                           _stream(stream)))
+        return E
 
     def far_field(self, x, dirs, E, stream=None):
         _check(_lib.mueller_far_field(self._h, _ptr(x), x.shape[1], _ptr(dirs), dirs.shape[0], _ptr(E),

@@ -261,3 +261,149 @@ void launch_near_field(const FieldGeom& g, int M, const cd* x, int nrhs, const d
   ring_kernel<<<dim3(g.N, nrhs), 128, 0, s>>>(g.N, M, x, nrhs, n_theta, cur);
   nearfield_kernel<<<dim3(nt, nrhs), 256, 0, s>>>(g, n_theta, cur, X_dev, nt, nrhs, k, cJ, cM, dM, dJ, out);
 }
+
+// ---------------------------------------------------------------------------
+// Far field on a (polar x azimuth) grid, mode by mode.  For x_hat at polar
+// angle theta and azimuth phi, substituting theta' = phi + alpha on each ring
+// turns eq. farfieldform into E(theta, phi) = R_z(phi) sum_m e^{i m phi} F_m(theta),
+// with F_m the far-field vector of mode m in the frame (e_rho, e_phi, e_z) of
+// azimuth phi, where x_hat = (sin theta, 0, cos theta).  The ring integrals
+// need c_m = (1/n) sum_t e^{-i a cos alpha_t} e^{i m alpha_t}, a = k0 r sin theta
+// (same trapezoid rule in alpha as mueller_far_field):
+//   (1/2pi) int e^{-i a cos} e^{i m alpha} {1, cos, sin} = {c_m, (c_{m+1}+c_{m-1})/2, (c_{m+1}-c_{m-1})/(2i)}.
+
+// coef[p][j][m + M + 1], |m| <= M + 1: one CTA per (polar angle, node)
+__global__ void ffgrid_coef_kernel(FieldGeom g, int M, cd k0, int n_polar, int n_alpha, cd* __restrict__ coef) {
+  extern __shared__ __align__(16) char smem[];
+  cd* f = (cd*)smem;           // [n_alpha]
+  cd* tw = f + n_alpha;        // [n_alpha] e^{+2 pi i t / n_alpha}
+  const int p = blockIdx.x, j = blockIdx.y;
+  double sth, cth;
+  sincospi((p + 0.5) / n_polar, &sth, &cth);
+  const cd a = (g.r[j] * sth) * k0;
+  for (int t = threadIdx.x; t < n_alpha; t += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * t / n_alpha, &s, &c);
+    tw[t] = C(c, s);
+    f[t] = cexpi(-(c * a));
+  }
+  __syncthreads();
+  const int nm = 2 * M + 3;
+  const double inv = 1.0 / n_alpha;
+  // f is even in alpha, so c_{-m} = c_m: m = 0..M+1 computed, mirrored
+  for (int m = threadIdx.x; m <= M + 1; m += blockDim.x) {
+    const int mm = m % n_alpha;
+    cd acc = C(0.0);
+    int idx = 0;
+    for (int t = 0; t < n_alpha; ++t) {
+      acc = fma(f[t], tw[idx], acc);
+      idx += mm;
+      if (idx >= n_alpha) idx -= n_alpha;
+    }
+    cd* dst = coef + ((size_t)p * g.N + j) * nm + (M + 1);
+    dst[m] = inv * acc;
+    dst[-m] = inv * acc;
+  }
+}
+
+// F[w][p][q][3] for mode m = q - M: one CTA per (polar angle, mode, rhs)
+__global__ void __launch_bounds__(128) ffgrid_mode_kernel(FieldGeom g, int M, cd k0, double omega, cd eps0,
+                                                          int n_polar, const cd* __restrict__ coef,
+                                                          const cd* __restrict__ x, int nrhs, cd* __restrict__ F) {
+  const int p = blockIdx.x, q = blockIdx.y, w = blockIdx.z;
+  const int nm = 2 * M + 3, n = 4 * g.N;
+  double sth, cth;
+  sincospi((p + 0.5) / n_polar, &sth, &cth);
+  cd Jh[3] = {C(0.0), C(0.0), C(0.0)}, Mh[3] = {C(0.0), C(0.0), C(0.0)};
+  const cd* xv = x + ((size_t)q * nrhs + w) * n;
+  for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+    const cd* cc = coef + ((size_t)p * g.N + j) * nm + q + 1;  // c_m at cc[0], c_{m-1} at cc[-1]
+    const cd c0 = cc[0], cm = cc[-1], cp = cc[1];
+    const cd Ic = 0.5 * (cp + cm);
+    const cd Is = mul_i(0.5 * (cm - cp));                      // (c_{m+1} - c_{m-1})/(2i)
+    const double wr = 6.283185307179586 * g.w[j] * g.r[j];
+    const cd ph = wr * cexpi(-(k0 * (g.z[j] * cth)));
+    const double rp = g.rp[j], zp = g.zp[j];
+    const cd J1 = ph * xv[4 * j], J2 = ph * xv[4 * j + 1], M1 = ph * xv[4 * j + 2], M2 = ph * xv[4 * j + 3];
+    Jh[0] += J1 * (rp * Ic) - J2 * Is;
+    Jh[1] += J1 * (rp * Is) + J2 * Ic;
+    Jh[2] += J1 * (zp * c0);
+    Mh[0] += M1 * (rp * Ic) - M2 * Is;
+    Mh[1] += M1 * (rp * Is) + M2 * Ic;
+    Mh[2] += M1 * (zp * c0);
+  }
+  __shared__ cd red[6][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  cd v[6] = {Jh[0], Jh[1], Jh[2], Mh[0], Mh[1], Mh[2]};
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      v[a].x += __shfl_xor_sync(0xffffffffu, v[a].x, o);
+      v[a].y += __shfl_xor_sync(0xffffffffu, v[a].y, o);
+    }
+    if (lane == 0) red[a][wid] = v[a];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cd t[6];
+    for (int a = 0; a < 6; ++a) t[a] = red[a][0] + red[a][1] + red[a][2] + red[a][3];
+    const double xh[3] = {sth, 0.0, cth};
+    const cd xJ = xh[0] * t[0] + xh[2] * t[2];
+    const cd pre = -(k0 * k0) / (C(0.0, omega) * eps0);
+    const cd ik = mul_i(k0);
+    cd cr[3];
+    cr[0] = xh[1] * t[5] - xh[2] * t[4];
+    cr[1] = xh[2] * t[3] - xh[0] * t[5];
+    cr[2] = xh[0] * t[4] - xh[1] * t[3];
+    const double inv4pi = 1.0 / (4.0 * 3.141592653589793);
+    cd* dst = F + (((size_t)w * n_polar + p) * (2 * M + 1) + q) * 3;
+    for (int a = 0; a < 3; ++a) dst[a] = inv4pi * (pre * (t[a] - xh[a] * xJ) + ik * cr[a]);
+  }
+}
+
+// E[w][p][s][3] (Cartesian) = R_z(phi_s) sum_m e^{i m phi_s} F_m: one CTA per (polar angle, rhs)
+__global__ void ffgrid_synth_kernel(int M, int n_polar, int n_azim, const cd* __restrict__ F, int nrhs,
+                                    cd* __restrict__ E) {
+  extern __shared__ __align__(16) char smem[];
+  const int nq = 2 * M + 1;
+  cd* Fs = (cd*)smem;          // [nq][3]
+  cd* tw = Fs + 3 * nq;        // [n_azim] e^{2 pi i s / n_azim}
+  const int p = blockIdx.x, w = blockIdx.y;
+  const cd* src = F + ((size_t)w * n_polar + p) * nq * 3;
+  for (int t = threadIdx.x; t < 3 * nq; t += blockDim.x) Fs[t] = src[t];
+  for (int s = threadIdx.x; s < n_azim; s += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * s / n_azim, &sn, &cs);
+    tw[s] = C(cs, sn);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < n_azim; s += blockDim.x) {
+    cd a[3] = {C(0.0), C(0.0), C(0.0)};
+    int idx = (int)(((long long)(n_azim - (M % n_azim)) * s) % n_azim);  // (-M s) mod n_azim
+    for (int q = 0; q < nq; ++q) {
+      const cd e = tw[idx];
+      a[0] = fma(Fs[3 * q], e, a[0]);
+      a[1] = fma(Fs[3 * q + 1], e, a[1]);
+      a[2] = fma(Fs[3 * q + 2], e, a[2]);
+      idx += s;
+      if (idx >= n_azim) idx -= n_azim;
+    }
+    const cd cphi = tw[s];  // (cos phi, sin phi)
+    cd* dst = E + (((size_t)w * n_polar + p) * n_azim + s) * 3;
+    dst[0] = cphi.x * a[0] - cphi.y * a[1];
+    dst[1] = cphi.y * a[0] + cphi.x * a[1];
+    dst[2] = a[2];
+  }
+}
+
+void launch_far_field_grid(const FieldGeom& g, int M, cd k0, double omega, cd eps0, const cd* x, int nrhs,
+                           int n_polar, int n_azim, int n_alpha, cd* coef, cd* F, cd* E, cudaStream_t s) {
+  const int smem1 = 2 * n_alpha * (int)sizeof(cd);
+  cudaFuncSetAttribute(ffgrid_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
+  ffgrid_coef_kernel<<<dim3(n_polar, g.N), 256, smem1, s>>>(g, M, k0, n_polar, n_alpha, coef);
+  ffgrid_mode_kernel<<<dim3(n_polar, 2 * M + 1, nrhs), 128, 0, s>>>(g, M, k0, omega, eps0, n_polar, coef, x, nrhs,
+                                                                    F);
+  const int smem3 = (3 * (2 * M + 1) + n_azim) * (int)sizeof(cd);
+  cudaFuncSetAttribute(ffgrid_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
+  ffgrid_synth_kernel<<<dim3(n_polar, nrhs), 256, smem3, s>>>(M, n_polar, n_azim, F, nrhs, E);
+}

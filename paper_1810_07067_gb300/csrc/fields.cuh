@@ -25,3 +25,8 @@ void launch_rhs_samples(const FieldGeom& g, int M, cd sE, cd sH, const cd* EH, i
 // buffer [rhs][N][n_theta][4]; k and the four constants are the region's.
 void launch_near_field(const FieldGeom& g, int M, const cd* x, int nrhs, const double* X_dev, int nt, int n_theta,
                        cd k, cd cJ, cd cM, cd dM, cd dJ, cd* cur, cd* out, cudaStream_t s);
+
+// Far field on the grid theta_p = (p + 1/2) pi / n_polar, phi_s = 2 pi s / n_azim:
+// E[rhs][p][s][3]; work buffers coef [n_polar][N][2M+3], F [rhs][n_polar][2M+1][3].
+void launch_far_field_grid(const FieldGeom& g, int M, cd k0, double omega, cd eps0, const cd* x, int nrhs,
+                           int n_polar, int n_azim, int n_alpha, cd* coef, cd* F, cd* E, cudaStream_t s);

@@ -804,6 +804,26 @@ extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int 
   return MUELLER_OK;
 }
 
+extern "C" int mueller_far_field_grid(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, int n_polar,
+                                      int n_azim, mueller_c128* E_dev, void* stream) {
+  g_err.clear();
+  if (!c || !x_dev || !E_dev || nrhs < 1 || n_polar < 1 || n_azim < 1 || n_azim > 8192)
+    return fail(MUELLER_EINVAL, "invalid far-field grid arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int M = c->S.M, nth = n_theta_for(c->S);
+  DevBuf tmp;
+  cd *coef, *F;
+  if (tmp.alloc(&coef, (size_t)n_polar * c->S.N * (2 * M + 3)) != cudaSuccess ||
+      tmp.alloc(&F, (size_t)nrhs * n_polar * (2 * M + 1) * 3) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "far-field grid buffers");
+  FieldGeom g{c->geo[0], c->geo[1], c->geo[2], c->geo[3], c->geo[4], c->S.N};
+  launch_far_field_grid(g, M, c->S.k0, c->S.omega, c->S.eps0, (const cd*)x_dev, nrhs, n_polar, n_azim, nth, coef, F,
+                        (cd*)E_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MUELLER_OK;
+}
+
 extern "C" int mueller_modal_kernels(const double* pairs_host, long long npairs, mueller_c128 k0, mueller_c128 k1,
                                      int M, int n_phi, double split_eps, mueller_c128* out_dev, void* stream) {
   g_err.clear();

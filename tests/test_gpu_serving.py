@@ -1,0 +1,80 @@
+"""Serving loop on the GPU: every request's far field must equal that of the
+same request solved alone (fresh factors, its own right-hand sides only),
+whether it was batched with other requests of its body or not, with the
+factor cache holding all keys or evicting between them."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+
+DEV = "cuda:0"
+GRID = (8, 16)
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_07067_gb300 as m
+    return m
+
+
+def _pool():
+    out = []
+    for s, (npan, M, k0) in enumerate([(10, 14, 2.0), (12, 18, 2.5), (14, 12, 3.0)]):
+        out.append(W.Config(f"p{s}", W.random_body(npan, seed=200 + s), W.Media.from_k(k0, 1.5 * k0), M, 16, []))
+    return out
+
+
+def _requests(serving):
+    rng = np.random.default_rng(9)
+    reqs = []
+    for i, key in enumerate([0, 0, 1, 0, 2, 1, 1, 0, 2, 2, 0]):
+        k = int(rng.integers(1, 7))
+        d = rng.standard_normal((k, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+        p = np.cross(d, rng.standard_normal((k, 3))); p /= np.linalg.norm(p, axis=1, keepdims=True)
+        reqs.append(serving.Request(i, key, 0.005 * i, d, p))
+    return reqs
+
+
+def _alone(mb, body, r):
+    ctx = mb.build(body.curve, body.media, body.M, mb.Options(n_phi=body.n_phi, precision=1))
+    n = 4 * body.curve.N
+    rhs = torch.zeros((2 * body.M + 1, r.nrhs, n), dtype=torch.complex128, device=DEV)
+    ctx.rhs_planewave(r.dirs, r.pols, rhs)
+    x = torch.zeros_like(rhs)
+    ctx.solve(rhs, x)
+    E = torch.zeros((r.nrhs, GRID[0], GRID[1], 3), dtype=torch.complex128, device=DEV)
+    ctx.far_field_grid(x, E)
+    out = E.cpu().numpy()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("tight", [False, True])
+def test_served_equals_alone(mb, tight):
+    from paper_1810_07067_gb300 import serving
+    pool = _pool()
+    reqs = _requests(serving)
+    peaks = [mb.build_bytes(b.curve.N, b.M, 1)[0] for b in pool]
+    probe = serving.Server(pool, 10 ** 13, max_rhs=16, grid=GRID)
+    head = probe.headroom
+    probe.close()
+    # tight: room for one key's build at a time, so keys are evicted and rebuilt
+    budget = head + (max(peaks) + 1 if tight else 4 * sum(peaks))
+    srv = serving.Server(pool, budget, max_rhs=16, grid=GRID)
+    st, res = srv.run(reqs, keep_results=True)
+    srv.close()
+    assert len(st.done) == len(reqs) and st.unfinished == 0
+    if tight:
+        assert st.evictions >= 2 and st.builds >= 4
+    else:
+        assert st.builds == 3 and st.evictions == 0
+    assert st.batches < len(reqs)                      # some requests shared a batch
+    for r in reqs:
+        ref = _alone(mb, pool[r.key], r)
+        got = res[r.id].numpy()
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), r.id

@@ -8,8 +8,9 @@ oracle and the CUDA path can both consume its output without sharing code.
 """
 from .curves import Curve, sphere, cylinder, cone, random_body, torus, panel_nodes
 from .configs import (Media, PlaneWave, Config, config_sphere, config_cylinder, config_random, config_batch,
+                      config_pool,
                       plane_wave, paper_default_wave)
 
 __all__ = ["Curve", "sphere", "cylinder", "cone", "random_body", "torus", "panel_nodes",
            "Media", "PlaneWave", "Config", "config_sphere", "config_cylinder",
-           "config_random", "config_batch", "plane_wave", "paper_default_wave"]
+           "config_random", "config_batch", "config_pool", "plane_wave", "paper_default_wave"]
