@@ -36,6 +36,12 @@ def _dist():
     return ws, rank, local
 
 
+# DRAM bytes per (far pair, mode) of far_kernel, from one ncu capture
+# (profiles/far_kernel_random_N256_M32.md); the launch writes the pairs' 4x4
+# blocks of every mode.
+FAR_TRAFFIC_PER_PAIR_MODE = 402.8e6 / (53760 * 33)
+
+
 def reduce_max(values, dist=None, device="cpu"):
     """Per-rank timings -> their maximum over all ranks (the job's time);
     identity on a single rank."""
@@ -253,6 +259,75 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tables(args):
+    """The paper's four numerical examples (Section 6, Tables 1-4): for every
+    row, the body with the row's N_pts nodes and modes -N_f..N_f, the
+    extinction test of eq. loop on the indirect formulation (mixed path),
+    E_error = relative l2 error of E and H at random interior points, the
+    build and solve times, and one more solve with a single right-hand side
+    (the paper's T_add).  The paper's printed times (its CPU) and errors are
+    context.  value = summed build + solve time over all rows."""
+    import torch
+    import workloads as W  # noqa: F401
+    import paper_1810_07067_gb300 as mb
+    from workloads import paper_tables as T
+    from workloads.sources import current_loop_field, ring_points
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the paper-table workload has no oracle timing"}))
+        return
+    dev = torch.device("cuda", 0)
+    rows_out = []
+    for ex, rows in T.EXAMPLES.items():
+        for row in rows:
+            cfg = T.config(ex, row)
+            media, M, N = cfg.media, cfg.M, cfg.N
+            k1 = media.omega * np.sqrt(complex(media.eps1) * complex(media.mu1))
+            rmax = float(np.max(cfg.curve.r))
+            nth = 2 * M + 2 * int(np.ceil(abs(k1) * rmax)) + 64
+            pts = ring_points(cfg.curve.r, cfg.curve.z, nth)
+            E, H = current_loop_field(pts.reshape(-1, 3), k1, media.omega, complex(media.mu1))
+            EH = torch.tensor(np.concatenate([E, H], -1).reshape(1, N, nth, 6), device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = mb.build(cfg.curve, media, M, mb.Options(n_phi=16, formulation=1, precision=1))
+            rhs = torch.zeros((2 * M + 1, 1, 4 * N), dtype=torch.complex128, device=dev)
+            ctx.rhs_fields(EH, rhs)
+            x = torch.zeros_like(rhs)
+            ctx.solve(rhs, x)
+            torch.cuda.synchronize()
+            t_total = time.perf_counter() - t0
+            st = ctx.stats()
+            t1 = time.perf_counter()
+            x2 = torch.zeros_like(rhs)
+            ctx.solve(rhs, x2)
+            torch.cuda.synchronize()
+            t_add = time.perf_counter() - t1
+            P = T.interior_points(ex)
+            out = torch.zeros((1, len(P), 6), dtype=torch.complex128, device=dev)
+            ctx.eval(x, P, 1, out)
+            Er, Hr = current_loop_field(P, k1, media.omega, complex(media.mu1))
+            ref = np.concatenate([Er, Hr], -1)
+            got = out.cpu().numpy()[0]
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            ctx.close()
+            rows_out.append({"example": ex, "k0": row[0], "k1": row[1], "N_f": row[2], "N_pts": row[3],
+                             "n_phi": int(st["n_phi_used"]), "build_s": st["ms_build"] / 1e3,
+                             "total_s": t_total, "add_s": t_add, "E_error": err,
+                             "paper": {"T_kernel+T_matgen+T_solve": row[4] + row[5] + row[6], "T_add": row[7],
+                                       "E_error": row[8]}})
+            print(json.dumps(rows_out[-1]), file=sys.stderr, flush=True)
+    tot = sum(r["total_s"] for r in rows_out)
+    line = {"metric": "paper's four examples (Tables 1-4): extinction-test error and build+solve time per row",
+            "value": tot, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": tot * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 factors + c128 refinement", "data": "synthetic",
+            "config": {"workload": "torus, rotated starfish, droplet, cylinder at the rows of Tables 1-4; "
+                                   "current loop (0.4, 0.5, 5.0), radius 0.42; indirect formulation"},
+            "rows_E_error_le_paper": sum(r["E_error"] <= r["paper"]["E_error"] for r in rows_out),
+            "rows": rows_out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -260,7 +335,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "small", "batched", "serving"],
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "small", "batched", "serving", "tables"],
                     help="small: random smooth body N=256, M=32 (profiling captures); batched: the 72-body "
                          "batch under a memory budget; serving: Poisson request stream with a factor cache")
     ap.add_argument("--bodies", type=int, default=0, help="batched: only the first K bodies (0 = all)")
@@ -283,6 +358,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "tables":
+        run_tables(args)
         return
     cfg = W.config_cylinder(7) if args.workload == "cylinder" else W.config_random(16, 1810, 32, 128)
     if args.impl == "reference":
@@ -388,7 +466,11 @@ def main():
                 "roofline": {"bound": "alu", "kernel": "far_kernel (far pairs: sampling, cosine transform, "
                                                        "assembly; FP64)",
                              "achieved": far_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": far_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                             "frac": far_tflops / FP64_PEAK_TFLOPS,
+                             "traffic": st["n_far_pairs"] * (M + 1) * FAR_TRAFFIC_PER_PAIR_MODE,
+                             "traffic_source": "ncu dram__bytes_read+write of one far_kernel launch on the "
+                                               "N=256, M=32 body (402.8 MB / (53760 far pairs x 33 modes)), "
+                                               "scaled by far pairs x modes",
                              "algorithmic_flops_per_far_pair": per_pair,
                              "peak_source": "nominal FP64 of the profiling recipe (no FP64 entry in "
                                             "MEASURED_PEAKS.json); a DFMA register loop measured 1.19"},

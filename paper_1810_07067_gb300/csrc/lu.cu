@@ -16,7 +16,21 @@
 namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------- panel
-__device__ __forceinline__ void argmax_merge(double& v, int& idx, double v2, int i2) {
+// Pivot measure: |a|^2 in FP64 for complex128; |Re a| + |Im a| in FP32 for
+// complex64 (LAPACK's complex pivot measure; GB300's FP64 pipe is too slow to
+// sit on the panel's critical path).  Largest measure, lowest row on ties.
+template <class T> struct Pivot;
+template <> struct Pivot<cd> {
+  using V = double;
+  __device__ static V measure(cd a) { return norm2(a); }
+};
+template <> struct Pivot<cf> {
+  using V = float;
+  __device__ static V measure(cf a) { return fabsf(a.x) + fabsf(a.y); }
+};
+
+template <class V>
+__device__ __forceinline__ void argmax_merge(V& v, int& idx, V v2, int i2) {
   if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
 }
 
@@ -26,7 +40,8 @@ __global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, i
   const int b = blockIdx.x;
   T* M = A + (size_t)b * n * n;
   int* pv = piv + (size_t)b * n;
-  __shared__ double red_v[32];
+  using V = typename Pivot<T>::V;
+  __shared__ V red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_p;
   __shared__ T s_row[LU_NB];
@@ -34,28 +49,28 @@ __global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, i
   for (int jj = 0; jj < nbk; ++jj) {
     const int c = k0 + jj;
     T* col = M + (size_t)c * n;
-    double best = -1.0;
+    V best = V(-1);
     int bi = n;
-    for (int r = c + tid; r < n; r += NT) argmax_merge(best, bi, norm2(col[r]), r);
+    for (int r = c + tid; r < n; r += NT) argmax_merge(best, bi, Pivot<T>::measure(col[r]), r);
     for (int o = 16; o > 0; o >>= 1) {
-      double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      V v2 = __shfl_xor_sync(0xffffffffu, best, o);
       int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
       argmax_merge(best, bi, v2, i2);
     }
     if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
     __syncthreads();
     if (wid == 0) {
-      best = (lane < (NT >> 5)) ? red_v[lane] : -1.0;
+      best = (lane < (NT >> 5)) ? red_v[lane] : V(-1);
       bi = (lane < (NT >> 5)) ? red_i[lane] : n;
       for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        V v2 = __shfl_xor_sync(0xffffffffu, best, o);
         int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
         argmax_merge(best, bi, v2, i2);
       }
       if (lane == 0) {
-        s_p = (best > 0.0) ? bi : -1;
-        pv[c] = (best > 0.0) ? bi : c;
-        if (best <= 0.0 && info[b] == 0) info[b] = c + 1;
+        s_p = (best > V(0)) ? bi : -1;
+        pv[c] = (best > V(0)) ? bi : c;
+        if (best <= V(0) && info[b] == 0) info[b] = c + 1;
       }
     }
     __syncthreads();
@@ -112,10 +127,11 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restr
   int* pv = piv + (size_t)b * n;
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T* a = (T*)panel_smem;  // [nbk][R]
-  __shared__ double cand_v[8];
+  using V = typename Pivot<T>::V;
+  __shared__ V cand_v[8];
   __shared__ int cand_i[8];
   __shared__ T s_row[LU_NB], s_rowc[LU_NB];
-  __shared__ double red_v[PANEL_THREADS / 32];
+  __shared__ V red_v[PANEL_THREADS / 32];
   __shared__ int red_i[PANEL_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int row0 = k0 + q * R;
@@ -128,21 +144,22 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restr
   for (int jj = 0; jj < nbk; ++jj) {
     const int c = k0 + jj;
     const T* aj = a + jj * R;
-    double best = -1.0;
+    V best = V(-1);
     int bi = n;
-    for (int r = max(0, c - row0) + tid; r < nr; r += PANEL_THREADS) argmax_merge(best, bi, norm2(aj[r]), row0 + r);
+    for (int r = max(0, c - row0) + tid; r < nr; r += PANEL_THREADS)
+      argmax_merge(best, bi, Pivot<T>::measure(aj[r]), row0 + r);
     for (int o = 16; o > 0; o >>= 1) {
-      double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      V v2 = __shfl_xor_sync(0xffffffffu, best, o);
       int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
       argmax_merge(best, bi, v2, i2);
     }
     if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
     __syncthreads();
     if (wid == 0) {
-      best = (lane < PANEL_THREADS / 32) ? red_v[lane] : -1.0;
+      best = (lane < PANEL_THREADS / 32) ? red_v[lane] : V(-1);
       bi = (lane < PANEL_THREADS / 32) ? red_i[lane] : n;
       for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        V v2 = __shfl_xor_sync(0xffffffffu, best, o);
         int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
         argmax_merge(best, bi, v2, i2);
       }
@@ -152,10 +169,10 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restr
       }
     }
     cl.sync();
-    best = -1.0;
+    best = V(-1);
     bi = n;
     for (int u = 0; u < C; ++u) argmax_merge(best, bi, cand_v[u], cand_i[u]);
-    const int p = (best > 0.0) ? bi : -1;
+    const int p = (best > V(0)) ? bi : -1;
     if (q == 0 && tid == 0) {
       pv[c] = (p >= 0) ? p : c;
       if (p < 0 && info[b] == 0) info[b] = c + 1;

@@ -6,11 +6,11 @@ directions.  It contains none of the solver's arithmetic (no modal Green's
 functions, no quadrature corrections, no assembly, no factorisation), so the
 oracle and the CUDA path can both consume its output without sharing code.
 """
-from .curves import Curve, sphere, cylinder, cone, random_body, torus, panel_nodes
+from .curves import Curve, sphere, cylinder, cone, random_body, torus, starfish, droplet, panel_nodes
 from .configs import (Media, PlaneWave, Config, config_sphere, config_cylinder, config_random, config_batch,
                       config_pool,
                       plane_wave, paper_default_wave)
 
-__all__ = ["Curve", "sphere", "cylinder", "cone", "random_body", "torus", "panel_nodes",
+__all__ = ["Curve", "sphere", "cylinder", "cone", "random_body", "torus", "starfish", "droplet", "panel_nodes",
            "Media", "PlaneWave", "Config", "config_sphere", "config_cylinder",
            "config_random", "config_batch", "config_pool", "plane_wave", "paper_default_wave"]

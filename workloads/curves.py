@@ -175,6 +175,42 @@ def random_body(n_panels: int = 64, seed: int = 1810, n_coef: int = 6, amp: floa
                    meta={"a": a.tolist()})
 
 
+def starfish(n_panels: int = 19) -> Curve:
+    """Rotated starfish of Section 6 (Example 2): with R(t) = 2 + 0.5 cos(5 pi (t - 1))
+    and psi = pi (t - 1/2), r = R cos psi, z = R sin psi, t in [0, 1], uniform
+    panels in t."""
+    edges = np.linspace(0.0, 1.0, n_panels + 1)
+
+    def fun(t):
+        t = np.asarray(t)
+        R = 2.0 + 0.5 * np.cos(5 * np.pi * (t - 1.0))
+        dR = -2.5 * np.pi * np.sin(5 * np.pi * (t - 1.0))
+        ps = np.pi * (t - 0.5)
+        return (R * np.cos(ps), R * np.sin(ps),
+                dR * np.cos(ps) - np.pi * R * np.sin(ps), dR * np.sin(ps) + np.pi * R * np.cos(ps))
+    return _sample(list(zip(edges[:-1], edges[1:])), fun, name=f"starfish{n_panels}")
+
+
+def droplet(n_base: int = 15, levels: int = 5) -> Curve:
+    """Droplet of Section 6 (Example 3): r = sin(pi t) cos(pi (t - 1.5)/2),
+    z = sin(pi t) sin(pi (t - 1.5)/2) + 1/2, t in [1/2, 1] (a tip on the axis
+    at t = 1); n_base uniform panels in t, the last one refined dyadically
+    `levels` times toward the tip."""
+    edges = np.linspace(0.5, 1.0, n_base + 1)
+    panels = list(zip(edges[:-1], edges[1:]))
+    panels = panels[:-1] + _dyadic(panels[-1][0], panels[-1][1], levels, toward_b=True)
+
+    def fun(t):
+        t = np.asarray(t)
+        s, ds = np.sin(np.pi * t), np.pi * np.cos(np.pi * t)
+        th = 0.5 * np.pi * (t - 1.5)
+        return (s * np.cos(th), s * np.sin(th) + 0.5,
+                ds * np.cos(th) - 0.5 * np.pi * s * np.sin(th), ds * np.sin(th) + 0.5 * np.pi * s * np.cos(th))
+    out = _sample(panels, fun, name=f"droplet{n_base}_L{levels}")
+    out.meta["min_panel_t"] = float(panels[-1][1] - panels[-1][0])
+    return out
+
+
 def torus(n_panels: int = 20, R: float = 2.0, a: float = 1.0, b: float = 0.5) -> Curve:
     """Torus meridian r = R + a cos t, z = b sin t (closed curve, Section 6.1)."""
     edges = np.linspace(0.0, 2 * np.pi, n_panels + 1)
