@@ -252,37 +252,41 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
   // is folded into the normalisation); the u^{-3/2} part is added exactly.
   const double inv = 1.0 / nl;
   const double FOUR_PI = 12.566370614359172;
-  cd beta[NFAM];
-  if (split) {
-    beta[0] = C(0.0); beta[1] = C(0.0);
-    beta[2] = C(-alpha); beta[3] = C(-zd); beta[4] = C(-alpha); beta[5] = C(-zd);
-    beta[6] = (-2.0 * alpha * alpha) * g0;
-    beta[7] = (-2.0 * alpha * zd) * g0;
-    beta[8] = (-2.0 * zd * zd) * g0;
-  }
+  // coefficient of the exact u^{-3/2} part of family f (split pairs)
+  auto beta = [&](int f) -> cd {
+    switch (f) {
+      case 2: case 4: return C(-alpha);
+      case 3: case 5: return C(-zd);
+      case 6: return (-2.0 * alpha * alpha) * g0;
+      case 7: return (-2.0 * alpha * zd) * g0;
+      case 8: return (-2.0 * zd * zd) * g0;
+      default: return C(0.0);
+    }
+  };
   const double* Shat = leg + (long long)(Mq + 1) * n_split;
-  for (int mm = lane; mm < Ms; mm += 32) {
-    cd acc[NFAM];
-#pragma unroll
-    for (int f = 0; f < NFAM; ++f) acc[f] = C(0.0);
+  // one (mode, family triple) per lane and round: 3 (M+2) items keep the
+  // lanes busy where one mode per lane would leave most of the last round idle
+  for (int it = lane; it < 3 * Ms; it += 32) {
+    const int mm = it / 3, f0 = 3 * (it % 3);
+    cd acc[3] = {C(0.0), C(0.0), C(0.0)};
     const bool odd = mm & 1;
     for (int j = 0; j < Q; ++j) {
       double c = cosT[(j * mm * dec) & mask];
       int jj = odd ? (H - 1 - j) : j;
 #pragma unroll
-      for (int f = 0; f < NFAM; ++f) acc[f] = fma(c, W.smp[f * H + jj], acc[f]);
+      for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + jj], acc[f]);
     }
     if (!odd) {  // centre sample j = n/4 pairs with itself (odd m: cos = 0)
       double c = cosT[(Q * mm * dec) & mask];
 #pragma unroll
-      for (int f = 0; f < NFAM; ++f) acc[f] = fma(c, W.smp[f * H + Q], acc[f]);
+      for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + Q], acc[f]);
     }
     double Sm = split ? Shat[(long long)mm * n_split + sid] / FOUR_PI : 0.0;
 #pragma unroll
-    for (int f = 0; f < NFAM; ++f) {
+    for (int f = 0; f < 3; ++f) {
       cd v = inv * acc[f];
-      if (split) v = fma(Sm, beta[f], v);
-      W.spec[f * Ms + mm] = v;
+      if (split) v = fma(Sm, beta(f0 + f), v);
+      W.spec[(f0 + f) * Ms + mm] = v;
     }
   }
   __syncwarp();
