@@ -54,50 +54,57 @@ void mixed_norm_inf(const cd* A, int n, int batch, double* out, cudaStream_t s) 
   norm_inf_kernel<<<dim3((n + 31) / 32, batch), 256, 0, s>>>(A, n, out);
 }
 
+// Vector kernels: grid.y strides over the (mode, right-hand side) vectors, so
+// any count fits the 65535 limit of gridDim.y.
+static inline unsigned vec_grid(long long nvec) { return (unsigned)(nvec < 65535 ? nvec : 65535); }
+
 __global__ void scale_kernel(const cd* __restrict__ b, cd* __restrict__ bw, const double* __restrict__ sw, int n,
-                             double* __restrict__ bnorm) {
-  const long long v = blockIdx.y;
-  double mx = 0.0;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    cd val = sw[r >> 2] * b[v * n + r];
-    bw[v * n + r] = val;
-    mx = fmax(mx, cabs(val));
+                             long long nvec, double* __restrict__ bnorm) {
+  for (long long v = blockIdx.y; v < nvec; v += gridDim.y) {
+    double mx = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+      cd val = sw[r >> 2] * b[v * n + r];
+      bw[v * n + r] = val;
+      mx = fmax(mx, cabs(val));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(bnorm + v, mx);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_pos(bnorm + v, mx);
 }
 
 void mixed_scale(const cd* b, cd* bw, const double* sw, int n, long long nvec, double* bnorm, cudaStream_t s) {
   cudaMemsetAsync(bnorm, 0, sizeof(double) * nvec, s);
-  scale_kernel<<<dim3((n + 255) / 256, (unsigned)nvec), 256, 0, s>>>(b, bw, sw, n, bnorm);
+  scale_kernel<<<dim3((n + 255) / 256, vec_grid(nvec)), 256, 0, s>>>(b, bw, sw, n, nvec, bnorm);
 }
 
-__global__ void update_kernel(cd* __restrict__ y, const cd* __restrict__ d, int n, bool first,
+__global__ void update_kernel(cd* __restrict__ y, const cd* __restrict__ d, int n, long long nvec, bool first,
                               double* __restrict__ ynorm) {
-  const long long v = blockIdx.y;
-  double mx = 0.0;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    cd val = first ? d[v * n + r] : y[v * n + r] + d[v * n + r];
-    y[v * n + r] = val;
-    mx = fmax(mx, cabs(val));
+  for (long long v = blockIdx.y; v < nvec; v += gridDim.y) {
+    double mx = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+      cd val = first ? d[v * n + r] : y[v * n + r] + d[v * n + r];
+      y[v * n + r] = val;
+      mx = fmax(mx, cabs(val));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(ynorm + v, mx);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_pos(ynorm + v, mx);
 }
 
 void mixed_update(cd* y, const cd* d, int n, long long nvec, bool first, double* ynorm, cudaStream_t s) {
   cudaMemsetAsync(ynorm, 0, sizeof(double) * nvec, s);
-  update_kernel<<<dim3((n + 255) / 256, (unsigned)nvec), 256, 0, s>>>(y, d, n, first, ynorm);
+  update_kernel<<<dim3((n + 255) / 256, vec_grid(nvec)), 256, 0, s>>>(y, d, n, nvec, first, ynorm);
 }
 
-__global__ void unscale_kernel(const cd* __restrict__ y, cd* __restrict__ x, const double* __restrict__ sw, int n) {
-  const long long v = blockIdx.y;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-    x[v * n + r] = (1.0 / sw[r >> 2]) * y[v * n + r];
+__global__ void unscale_kernel(const cd* __restrict__ y, cd* __restrict__ x, const double* __restrict__ sw, int n,
+                               long long nvec) {
+  for (long long v = blockIdx.y; v < nvec; v += gridDim.y)
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+      x[v * n + r] = (1.0 / sw[r >> 2]) * y[v * n + r];
 }
 
 void mixed_unscale(const cd* y, cd* x, const double* sw, int n, long long nvec, cudaStream_t s) {
-  unscale_kernel<<<dim3((n + 255) / 256, (unsigned)nvec), 256, 0, s>>>(y, x, sw, n);
+  unscale_kernel<<<dim3((n + 255) / 256, vec_grid(nvec)), 256, 0, s>>>(y, x, sw, n, nvec);
 }
 
 // Residual GEMM: Z = A'_m [y_{+m}, D_c y_{-m}] for a 64-row x 32-job tile,

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "mueller.h"
@@ -120,18 +121,20 @@ static void graded_rule(int levels, int ng, bool log_inner, std::vector<double>&
   }
 }
 
+static Rules make_rules() {
+  Rules R;
+  gauss_legendre(P_NODES, R.x16, R.w16);
+  R.bary.resize(P_NODES);
+  for (int k = 0; k < P_NODES; ++k)
+    R.bary[k] = ((k % 2) ? -1.0 : 1.0) * std::sqrt((1.0 - R.x16[k] * R.x16[k]) * R.w16[k]);
+  graded_rule(10, 16, true, R.self_u, R.self_w);
+  graded_rule(5, 16, false, R.adj_u, R.adj_w);
+  return R;
+}
+
+// initialised once, thread-safely (concurrent builds on several streams)
 static const Rules& rules() {
-  static Rules R;
-  static bool init = false;
-  if (!init) {
-    gauss_legendre(P_NODES, R.x16, R.w16);
-    R.bary.resize(P_NODES);
-    for (int k = 0; k < P_NODES; ++k)
-      R.bary[k] = ((k % 2) ? -1.0 : 1.0) * std::sqrt((1.0 - R.x16[k] * R.x16[k]) * R.w16[k]);
-    graded_rule(10, 16, true, R.self_u, R.self_w);
-    graded_rule(5, 16, false, R.adj_u, R.adj_w);
-    init = true;
-  }
+  static const Rules R = make_rules();
   return R;
 }
 
@@ -416,13 +419,12 @@ static std::vector<double> s2_table(int nphi) {
 }
 
 static void ensure_tables() {
-  static bool done = false;
-  if (!done) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     SeriesTables t;
     fill_series_tables(&t);
     upload_series_tables(t);
-    done = true;
-  }
+  });
 }
 
 struct Timer {
@@ -727,7 +729,7 @@ static int n_theta_for(const Setup& S) {
 extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const double* pols, int nrhs,
                                      mueller_c128* rhs_dev, void* stream) {
   g_err.clear();
-  if (!c || !dirs || !pols || !rhs_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid rhs arguments");
+  if (!c || !dirs || !pols || !rhs_dev || (nrhs < 1 || nrhs > 65535)) return fail(MUELLER_EINVAL, "invalid rhs arguments");
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf tmp;
   double *dd, *dp;
@@ -744,7 +746,7 @@ extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const d
 extern "C" int mueller_rhs_fields(mueller_ctx* c, const mueller_c128* EH_dev, int nrhs, int n_theta,
                                   mueller_c128* rhs_dev, void* stream) {
   g_err.clear();
-  if (!c || !EH_dev || !rhs_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid field-sample arguments");
+  if (!c || !EH_dev || !rhs_dev || (nrhs < 1 || nrhs > 65535)) return fail(MUELLER_EINVAL, "invalid field-sample arguments");
   if (n_theta < 2 * c->S.M + 2 || n_theta > 2048)
     return fail(MUELLER_EINVAL, "n_theta must lie in [2M+2, 2048]");
   cudaStream_t s = (cudaStream_t)stream;
@@ -758,7 +760,7 @@ extern "C" int mueller_rhs_fields(mueller_ctx* c, const mueller_c128* EH_dev, in
 extern "C" int mueller_eval(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* targets, int ntargets,
                             int region, mueller_c128* out_dev, void* stream) {
   g_err.clear();
-  if (!c || !x_dev || !targets || !out_dev || nrhs < 1 || ntargets < 1 || (region != 0 && region != 1))
+  if (!c || !x_dev || !targets || !out_dev || (nrhs < 1 || nrhs > 65535) || ntargets < 1 || (region != 0 && region != 1))
     return fail(MUELLER_EINVAL, "invalid evaluation arguments");
   for (int p = 0; p < 3 * ntargets; ++p)
     if (!std::isfinite(targets[p])) return fail(MUELLER_EINVAL, "non-finite target coordinate");
@@ -790,7 +792,7 @@ extern "C" int mueller_eval(mueller_ctx* c, const mueller_c128* x_dev, int nrhs,
 extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* dirs_dev,
                                  int ndir, mueller_c128* E_dev, void* stream) {
   g_err.clear();
-  if (!c || !x_dev || !dirs_dev || !E_dev || nrhs < 1 || ndir < 1) return fail(MUELLER_EINVAL, "invalid far-field arguments");
+  if (!c || !x_dev || !dirs_dev || !E_dev || (nrhs < 1 || nrhs > 65535) || ndir < 1) return fail(MUELLER_EINVAL, "invalid far-field arguments");
   cudaStream_t s = (cudaStream_t)stream;
   int nth = n_theta_for(c->S);
   DevBuf tmp;
@@ -807,7 +809,7 @@ extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int 
 extern "C" int mueller_far_field_grid(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, int n_polar,
                                       int n_azim, mueller_c128* E_dev, void* stream) {
   g_err.clear();
-  if (!c || !x_dev || !E_dev || nrhs < 1 || n_polar < 1 || n_azim < 1 || n_azim > 8192)
+  if (!c || !x_dev || !E_dev || (nrhs < 1 || nrhs > 65535) || n_polar < 1 || n_azim < 1 || n_azim > 8192)
     return fail(MUELLER_EINVAL, "invalid far-field grid arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const int M = c->S.M, nth = n_theta_for(c->S);
