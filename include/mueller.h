@@ -175,9 +175,13 @@ int mueller_far_field_grid(mueller_ctx* ctx, const mueller_c128* x_dev, int nrhs
 /* Fields at points off the surface from modal currents (Section 3):
  * region 0 (the exterior medium) by eq. exteriorfield with k0; region 1 (the
  * body) by eq. interiorfield for the direct formulation or eq. interior_dual
- * for the indirect one, with k1.  The surface integrals use the nodes'
- * ds-weights along the curve and 2M + 2 ceil(|k| r_max) + 64 azimuths, so
- * points should lie a few node spacings away from the surface.  x_dev:
+ * for the indirect one, with k1.  The surface integrals are refined for the
+ * closest targets: each panel is split into up to 16 sub-panels of 16 Gauss
+ * points (more the closer a target is relative to the panel's length), with
+ * geometry and currents from the panel's degree-15 interpolants, and the
+ * azimuthal trapezoid rule has max(2M + 2 ceil(|k| r_max) + 64,
+ * 40 r_max / d_min) points (at most 8192), d_min the closest target-to-node
+ * distance.  A target on a node ring is rejected (MUELLER_EINVAL).  x_dev:
  * currents [2M+1][nrhs][4N]; targets: host [ntargets][3]; out_dev: device
  * [nrhs][ntargets][6] complex, (E, H) in Cartesian components. */
 int mueller_eval(mueller_ctx* ctx, const mueller_c128* x_dev, int nrhs, const double* targets, int ntargets,

@@ -20,8 +20,9 @@
     curl S J (x)      = int grad_x G x J da = int G (ik - 1/R) Rh x J da,
     curl curl S J (x) = int G [(k^2 + ik/R - 1/R^2) J + (-k^2 - 3ik/R + 3/R^2)(Rh.J) Rh] da,
   R = x - y, Rh = R/|R| (the second from curl curl = grad div + k^2 off the
-  surface).  Same surface rule as the far field, so the points must lie a
-  few node spacings away from the surface.
+  surface).  The surface rule is refined for points near the surface: each
+  panel split into sub-panels (geometry and currents from the panel's
+  interpolants), and more azimuths the closer the nearest point.
 * Modal data from sampled fields: the same traces and scaling as for the
   plane wave, from E and H given at the ring points.
 """
@@ -141,44 +142,63 @@ def field_coefficients(media, region, formulation=0):
     return k1, -1 / (1j * om * e0), u1 / u0, 1 / (1j * om * u0), e1 / e0   # eq. interior_dual
 
 
-def near_field(curve, media, M, x, targets, region, formulation=0, n_theta=None):
+def near_field(curve, media, M, x, targets, region, formulation=0, n_theta=None, upsample=8):
     """E, H [nrhs, nt, 3] at points targets [nt, 3] off the surface, from modal
-    currents x[q, 4N, nrhs]; region 0 = exterior, 1 = inside the body."""
+    currents x[q, 4N, nrhs]; region 0 = exterior, 1 = inside the body.  Each
+    panel is split into `upsample` sub-panels of 16 Gauss points, geometry
+    and currents from the panel's degree-15 interpolants of the node values;
+    the azimuthal rule has max(2M + 2 ceil(|k| r_max) + 64, 40 r_max / d)
+    points, d the smallest target-to-node distance in the meridian plane."""
+    from .gauss import gauss_legendre, lagrange_basis
     geo = node_geometry(curve)
     k, cJ, cM, dM, dJ = field_coefficients(media, region, formulation)
+    X = np.atleast_2d(np.asarray(targets, float))
+    rt, zt = np.hypot(X[:, 0], X[:, 1]), X[:, 2]
+    dmin = np.min(np.hypot(rt[:, None] - geo.r[None, :], zt[:, None] - geo.z[None, :]))
     if n_theta is None:
         n_theta = 2 * M + 2 * int(np.ceil(abs(k) * np.max(geo.r))) + 64
+        n_theta = max(n_theta, int(np.ceil(40 * np.max(geo.r) / dmin)))
+    xg, wg = gauss_legendre(16)
+    U = int(upsample)
+    tsub = np.concatenate([-1 + (2 * u + 1 + xg) / U for u in range(U)])      # [16U] in the panel parameter
+    wsub = np.concatenate([wg / U] * U)
+    Lr = lagrange_basis(xg, tsub)                                             # [16U, 16]
     th = 2 * np.pi * np.arange(n_theta) / n_theta
     er, et = _frame(th)
     ez = np.array([0.0, 0.0, 1.0])
     ms = np.arange(-M, M + 1)
     E_ph = np.exp(1j * np.outer(th, ms))                  # [theta, modes]
-    X = np.atleast_2d(np.asarray(targets, float))
     nrhs = x.shape[2]
     E = np.zeros((nrhs, len(X), 3), dtype=complex)
     H = np.zeros_like(E)
-    for i in range(curve.N):
-        y = geo.r[i] * er + geo.z[i] * ez                  # [T, 3]
-        t = geo.rp[i] * er + geo.zp[i] * ez
-        da = geo.w[i] * geo.r[i] * (2 * np.pi / n_theta)
-        cur = [E_ph @ x[:, 4 * i + a, :] for a in range(4)]           # 4 x [T, nrhs]
-        Jv = cur[0][..., None] * t[:, None, :] + cur[1][..., None] * et[:, None, :]   # [T, nrhs, 3]
-        Mv = cur[2][..., None] * t[:, None, :] + cur[3][..., None] * et[:, None, :]
-        Rv = X[None, :, :] - y[:, None, :]                 # [T, nt, 3]
-        R = np.linalg.norm(Rv, axis=-1)
-        Rh = Rv / R[..., None]
-        g = da * np.exp(1j * k * R) / (4 * np.pi * R)
-        c1 = g * (1j * k - 1 / R)
-        a = g * (k * k + 1j * k / R - 1 / R ** 2)
-        b = g * (-k * k - 3j * k / R + 3 / R ** 2)
+    for P in range(curve.n_panels):
+        sl = slice(16 * P, 16 * P + 16)
+        r_s, z_s = Lr @ curve.r[sl], Lr @ curve.z[sl]
+        dr_s, dz_s = Lr @ curve.dr[sl], Lr @ curve.dz[sl]
+        sp = np.hypot(dr_s, dz_s)
+        xs = np.einsum("sk,qkaw->qsaw", Lr, x[:, 64 * P:64 * (P + 1), :].reshape(len(ms), 16, 4, nrhs))
+        for i in range(len(tsub)):
+            y = r_s[i] * er + z_s[i] * ez                  # [T, 3]
+            t = (dr_s[i] / sp[i]) * er + (dz_s[i] / sp[i]) * ez
+            da = wsub[i] * sp[i] * r_s[i] * (2 * np.pi / n_theta)
+            cur = [E_ph @ xs[:, i, a, :] for a in range(4)]                   # 4 x [T, nrhs]
+            Jv = cur[0][..., None] * t[:, None, :] + cur[1][..., None] * et[:, None, :]   # [T, nrhs, 3]
+            Mv = cur[2][..., None] * t[:, None, :] + cur[3][..., None] * et[:, None, :]
+            Rv = X[None, :, :] - y[:, None, :]             # [T, nt, 3]
+            R = np.linalg.norm(Rv, axis=-1)
+            Rh = Rv / R[..., None]
+            g = da * np.exp(1j * k * R) / (4 * np.pi * R)
+            c1 = g * (1j * k - 1 / R)
+            a = g * (k * k + 1j * k / R - 1 / R ** 2)
+            b = g * (-k * k - 3j * k / R + 3 / R ** 2)
 
-        def curl(V):      # [nrhs, nt, 3]
-            return np.einsum("tp,twpk->wpk", c1, np.cross(Rh[:, None, :, :], V[:, :, None, :]))
+            def curl(V):      # [nrhs, nt, 3]
+                return np.einsum("tp,twpk->wpk", c1, np.cross(Rh[:, None, :, :], V[:, :, None, :]))
 
-        def curlcurl(V):
-            proj = np.einsum("tpk,twk->twp", Rh, V)
-            return (np.einsum("tp,twk->wpk", a, V) + np.einsum("tp,twp,tpk->wpk", b, proj, Rh))
+            def curlcurl(V):
+                proj = np.einsum("tpk,twk->twp", Rh, V)
+                return (np.einsum("tp,twk->wpk", a, V) + np.einsum("tp,twp,tpk->wpk", b, proj, Rh))
 
-        E += cJ * curlcurl(Jv) + cM * curl(Mv)
-        H += dM * curlcurl(Mv) + dJ * curl(Jv)
+            E += cJ * curlcurl(Jv) + cM * curl(Mv)
+            H += dM * curlcurl(Mv) + dJ * curl(Jv)
     return E, H

@@ -407,3 +407,27 @@ void launch_far_field_grid(const FieldGeom& g, int M, cd k0, double omega, cd ep
   cudaFuncSetAttribute(ffgrid_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
   ffgrid_synth_kernel<<<dim3(n_polar, nrhs), 256, smem3, s>>>(M, n_polar, n_azim, F, nrhs, E);
 }
+
+// Currents at refined nodes: xs[v][4s + a] = sum_k Lm[s][k] x[v][4 (node0[s] + k) + a]
+// (v over modes x right-hand sides; the 16 nodes of sub-node s's panel);
+// grid.y strides over the vectors.
+__global__ void interp_currents_kernel(const cd* __restrict__ x, int n, int nsub, const int* __restrict__ node0,
+                                       const double* __restrict__ Lm, long long nvec, cd* __restrict__ xs) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 4 * nsub) return;
+  const int s = idx >> 2, a = idx & 3;
+  const double* L = Lm + (size_t)s * 16;
+  for (long long v = blockIdx.y; v < nvec; v += gridDim.y) {
+    const cd* xv = x + v * n + 4 * node0[s] + a;
+    cd acc = C(0.0);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(L[k], xv[4 * k], acc);
+    xs[v * 4 * nsub + idx] = acc;
+  }
+}
+
+void launch_interp_currents(const cd* x, int n, int nsub, const int* node0, const double* Lm, long long nvec, cd* xs,
+                            cudaStream_t s) {
+  const unsigned gy = (unsigned)(nvec < 65535 ? nvec : 65535);
+  interp_currents_kernel<<<dim3((4 * nsub + 255) / 256, gy), 256, 0, s>>>(x, n, nsub, node0, Lm, nvec, xs);
+}

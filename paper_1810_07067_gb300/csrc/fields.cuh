@@ -30,3 +30,8 @@ void launch_near_field(const FieldGeom& g, int M, const cd* x, int nrhs, const d
 // E[rhs][p][s][3]; work buffers coef [n_polar][N][2M+3], F [rhs][n_polar][2M+1][3].
 void launch_far_field_grid(const FieldGeom& g, int M, cd k0, double omega, cd eps0, const cd* x, int nrhs,
                            int n_polar, int n_azim, int n_alpha, cd* coef, cd* F, cd* E, cudaStream_t s);
+
+// Currents x[v][n] at the nodes -> xs[v][4 nsub] at refined nodes (rows Lm[nsub][16]
+// of the panel interpolants, node0 = first node of each sub-node's panel).
+void launch_interp_currents(const cd* x, int n, int nsub, const int* node0, const double* Lm, long long nvec, cd* xs,
+                            cudaStream_t s);

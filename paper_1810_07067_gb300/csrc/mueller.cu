@@ -774,16 +774,79 @@ extern "C" int mueller_eval(mueller_ctx* c, const mueller_c128* x_dev, int nrhs,
   } else {  // eq. interior_dual
     k = S.k1; cJ = -(C(1.0) / (iw * S.eps0)); cM = S.mu1 / S.mu0; dM = C(1.0) / (iw * S.mu0); dJ = S.eps1 / S.eps0;
   }
-  const int nth = 2 * S.M + 2 * (int)std::ceil(cabs(k) * S.rmax) + 64;
+  // Quadrature refined for the closest targets: panel P is split into u_P
+  // sub-panels of 16 Gauss points (u_P = ceil(1.5 L_P / d_P), 1..16, L_P its
+  // length, d_P the smallest meridian-plane distance from a target to its
+  // nodes), geometry and currents from the panel's degree-15 interpolants;
+  // the azimuthal rule gets 40 r_max / d_min points where that exceeds the
+  // default 2M + 2 ceil(|k| r_max) + 64 (at most 8192).
+  const Rules& R = rules();
+  const int nP = S.nP;
+  std::vector<double> tr(ntargets), tz(ntargets);
+  for (int p = 0; p < ntargets; ++p) {
+    tr[p] = std::hypot(targets[3 * p], targets[3 * p + 1]);
+    tz[p] = targets[3 * p + 2];
+  }
+  std::vector<int> up(nP);
+  double dmin_all = 1e300;
+  int nsub = 0;
+  for (int P = 0; P < nP; ++P) {
+    double L = 0.0, d = 1e300;
+    for (int q = 0; q < P_NODES; ++q) {
+      const int j = P * P_NODES + q;
+      L += S.w[j];
+      for (int p = 0; p < ntargets; ++p) d = std::min(d, std::hypot(tr[p] - S.r[j], tz[p] - S.z[j]));
+    }
+    if (!(d > 0.0)) return fail(MUELLER_EINVAL, "a target lies on a node ring");
+    dmin_all = std::min(dmin_all, d);
+    up[P] = std::max(1, std::min(16, (int)std::ceil(1.5 * L / d)));
+    nsub += up[P] * P_NODES;
+  }
+  std::vector<double> gr(nsub), gz(nsub), grp(nsub), gzp(nsub), gw(nsub), Lm((size_t)nsub * P_NODES);
+  std::vector<int> node0(nsub);
+  {
+    int s_ = 0;
+    double Lrow[P_NODES];
+    for (int P = 0; P < nP; ++P) {
+      const int U = up[P], j0 = P * P_NODES;
+      for (int u = 0; u < U; ++u)
+        for (int q = 0; q < P_NODES; ++q, ++s_) {
+          const double tau = -1.0 + (2.0 * u + 1.0 + R.x16[q]) / U;
+          lagrange_row(R, tau, Lrow);
+          double r = 0, z = 0, dr = 0, dz = 0;
+          for (int k2 = 0; k2 < P_NODES; ++k2) {
+            const int j = j0 + k2;
+            const double sp = S.w[j] / R.w16[k2];  // |d gamma / d tau| at the node
+            r += Lrow[k2] * S.r[j]; z += Lrow[k2] * S.z[j];
+            dr += Lrow[k2] * S.rp[j] * sp; dz += Lrow[k2] * S.zp[j] * sp;
+            Lm[(size_t)s_ * P_NODES + k2] = Lrow[k2];
+          }
+          const double sp = std::hypot(dr, dz);
+          gr[s_] = r; gz[s_] = z; grp[s_] = dr / sp; gzp[s_] = dz / sp;
+          gw[s_] = R.w16[q] / U * sp;
+          node0[s_] = j0;
+        }
+    }
+  }
+  const int nth_base = 2 * S.M + 2 * (int)std::ceil(cabs(k) * S.rmax) + 64;
+  const int nth = std::max(nth_base, std::min(8192, (int)std::ceil(40.0 * S.rmax / dmin_all)));
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf tmp;
-  cd* cur;
-  double* X;
+  cd *cur, *xs;
+  double *X, *dgr, *dgz, *dgrp, *dgzp, *dgw, *dLm;
+  int* dn0;
   std::vector<double> vx(targets, targets + 3 * ntargets);
-  if (tmp.alloc(&cur, (size_t)nrhs * S.N * nth * 4) != cudaSuccess) return fail(MUELLER_ENOMEM, "ring buffer");
+  const long long nvec = (long long)(2 * S.M + 1) * nrhs;
+  if (tmp.alloc(&cur, (size_t)nrhs * nsub * nth * 4) != cudaSuccess ||
+      tmp.alloc(&xs, (size_t)nvec * 4 * nsub) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "evaluation buffers");
   CK(tmp.upload(&X, vx, s));
-  FieldGeom g{c->geo[0], c->geo[1], c->geo[2], c->geo[3], c->geo[4], S.N};
-  launch_near_field(g, S.M, (const cd*)x_dev, nrhs, X, ntargets, nth, k, cJ, cM, dM, dJ, cur, (cd*)out_dev, s);
+  CK(tmp.upload(&dgr, gr, s)); CK(tmp.upload(&dgz, gz, s)); CK(tmp.upload(&dgrp, grp, s));
+  CK(tmp.upload(&dgzp, gzp, s)); CK(tmp.upload(&dgw, gw, s)); CK(tmp.upload(&dLm, Lm, s));
+  CK(tmp.upload(&dn0, node0, s));
+  launch_interp_currents((const cd*)x_dev, 4 * S.N, nsub, dn0, dLm, nvec, xs, s);
+  FieldGeom g{dgr, dgz, dgrp, dgzp, dgw, nsub};
+  launch_near_field(g, S.M, xs, nrhs, X, ntargets, nth, k, cJ, cM, dM, dJ, cur, (cd*)out_dev, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return MUELLER_OK;
