@@ -647,24 +647,24 @@ __device__ __forceinline__ cd to_cd(cd a) { return a; }
 // then run in FP32 arithmetic on FP64 storage).  PHYS: right-hand sides and
 // solutions in physical unknowns (scaled by the sqrt weights here); otherwise
 // both are already in the weighted space.
-template <class TF, bool PHYS>
+template <class TF, bool PHYS, int SGT>
 __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict__ LU, const int* __restrict__ piv,
                                                             int n, int M, const double* __restrict__ sw,
                                                             const cd* __restrict__ rhs, cd* __restrict__ x,
                                                             int nrhs) {
   __shared__ TF Ls[SB][SB + 1];
-  __shared__ TF Xs[SB][SG];
+  __shared__ TF Xs[SB][SGT];
   extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation
   const int m = blockIdx.x;
-  const int job0 = blockIdx.y * SG;
+  const int job0 = blockIdx.y * SGT;
   const int njobs_all = (m == 0) ? nrhs : 2 * nrhs;
   if (job0 >= njobs_all) return;
-  const int G = min(SG, njobs_all - job0);
+  const int G = min(SGT, njobs_all - job0);
   const TF* L = LU + (size_t)m * n * n;
   const int* pv = piv + (size_t)m * n;
   const int tid = threadIdx.x, T = blockDim.x;
-  cd* X[SG];
-  for (int g = 0; g < SG; ++g) {
+  cd* X[SGT];
+  for (int g = 0; g < SGT; ++g) {
     int q, ri; bool neg;
     job_of(m, M, nrhs, job0 + (g < G ? g : 0), &q, &ri, &neg);
     X[g] = x + ((size_t)q * nrhs + ri) * n;
@@ -713,15 +713,17 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
       X[g][kb + r] = to_cd(Xs[r][g]);
     }
     for (int r = kb + bs + tid; r < n; r += T) {
-      TF acc[SG];
+      TF acc[SGT];
 #pragma unroll
-      for (int g = 0; g < SG; ++g) acc[g] = czero<TF>();
+      for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
       for (int c = 0; c < bs; ++c) {
         TF l = L[(size_t)(kb + c) * n + r];
 #pragma unroll
-        for (int g = 0; g < SG; ++g) acc[g] = fma(l, Xs[c][g], acc[g]);
+        for (int g = 0; g < SGT; ++g) acc[g] = fma(l, Xs[c][g], acc[g]);
       }
-      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - to_cd(acc[g]);
+#pragma unroll
+      for (int g = 0; g < SGT; ++g)
+        if (g < G) X[g][r] = X[g][r] - to_cd(acc[g]);
     }
     __syncthreads();
   }
@@ -752,15 +754,17 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
       X[g][kb + r] = to_cd(Xs[r][g]);
     }
     for (int r = tid; r < kb; r += T) {
-      TF acc[SG];
+      TF acc[SGT];
 #pragma unroll
-      for (int g = 0; g < SG; ++g) acc[g] = czero<TF>();
+      for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
       for (int c = 0; c < bs; ++c) {
         TF u = L[(size_t)(kb + c) * n + r];
 #pragma unroll
-        for (int g = 0; g < SG; ++g) acc[g] = fma(u, Xs[c][g], acc[g]);
+        for (int g = 0; g < SGT; ++g) acc[g] = fma(u, Xs[c][g], acc[g]);
       }
-      for (int g = 0; g < G; ++g) X[g][r] = X[g][r] - to_cd(acc[g]);
+#pragma unroll
+      for (int g = 0; g < SGT; ++g)
+        if (g < G) X[g][r] = X[g][r] - to_cd(acc[g]);
     }
     __syncthreads();
   }
@@ -774,18 +778,34 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
   }
 }
 
+// Vectors per CTA: 8, or 32 when that still leaves two CTAs per SM (many
+// right-hand sides: every group reads the whole factor, so wider groups read
+// it fewer times).
+template <class TF, bool PHYS>
+static void launch_solve_blocked(const TF* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x,
+                                 int nrhs, cudaStream_t s) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int smem = n * (int)sizeof(int);
+  const long long wide = (long long)(M + 1) * ((2 * nrhs + 31) / 32);
+  if (wide >= 2LL * sms) {
+    const int groups = (2 * nrhs + 31) / 32;
+    cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    solve_blocked_kernel<TF, PHYS, 32><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+  } else {
+    const int groups = (2 * nrhs + SG - 1) / SG;
+    cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    solve_blocked_kernel<TF, PHYS, SG><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+  }
+}
+
 void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
                     cudaStream_t s) {
-  int groups = (2 * nrhs + SG - 1) / SG;
-  int smem = n * (int)sizeof(int);
-  cudaFuncSetAttribute(solve_blocked_kernel<cd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  solve_blocked_kernel<cd, true><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+  launch_solve_blocked<cd, true>(LU, piv, n, M, sw, rhs, x, nrhs, s);
 }
 
 void lu_correction_solve_c64(const cf* LU, const int* piv, int n, int M, const cd* r, cd* d, int nrhs,
                              cudaStream_t s) {
-  int groups = (2 * nrhs + SG - 1) / SG;
-  int smem = n * (int)sizeof(int);
-  cudaFuncSetAttribute(solve_blocked_kernel<cf, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  solve_blocked_kernel<cf, false><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, nullptr, r, d, nrhs);
+  launch_solve_blocked<cf, false>(LU, piv, n, M, nullptr, r, d, nrhs, s);
 }
