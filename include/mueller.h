@@ -86,10 +86,17 @@ typedef struct {
   int refine_max_iter; /* mixed: cap on refinement steps                    */
   double split_eps;    /* kernel splitting when the plain trapezoid would
                           alias above this (default 1e-17 when <= 0)         */
+  int lu_tile;         /* mixed path: column tile of the tensor-core LU update,
+                          32, 64 or 128; 0 = chosen per step by the tile
+                          autotuner (timed once per process for each bucket
+                          of trailing size and matrix count, see
+                          mueller_lu_tile_table)                            */
 } mueller_options;
 
 typedef struct {
-  double ms_legendre, ms_far, ms_support, ms_near, ms_lu, ms_build;  /* stage times */
+  double ms_legendre, ms_far, ms_support, ms_near, ms_lu, ms_build;  /* stage times; ms_lu is the
+                                factorization alone, ms_build assembly (with the mixed path's
+                                complex64 copy and digit slices) plus ms_lu */
   double ms_solve;           /* last mueller_solve                           */
   int n_phi_used;
   long long n_split_pairs;   /* pairs evaluated with kernel splitting        */
@@ -107,6 +114,10 @@ typedef struct {
   double ms_residual;        /* precision 1: device time of the tensor-core residuals (incl. slicing) */
   int residual_launches;     /* precision 1: residual evaluations of the last solve */
   double residual_tc_flops;  /* precision 1: their BF16 tensor work (2 flops per MAC) */
+  int lu_graph;              /* 1: the LU steps ran as one captured CUDA graph */
+  int lu_tile_steps[3];      /* mixed path: LU steps whose update used column tiles 32, 64, 128 */
+  int lu_wave_bodies;        /* bodies factored together (mueller_build_many), else 1 */
+  int lu_launches;           /* kernel launches (graph nodes) of the factorization, shared by a wave */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;
@@ -123,6 +134,21 @@ typedef struct mueller_ctx mueller_ctx;
  * finished (stage times are measured with CUDA events). */
 int mueller_build(const mueller_curve* curve, const mueller_media* media, int M,
                   const mueller_options* opts, void* stream, mueller_ctx** out);
+
+/* Build a wave of bodies (Section 6's per-mode factorizations for several
+ * bodies at once): each body i (curves[i], media[i], modes 0..M[i], all with
+ * the same opts) is assembled in turn as in mueller_build; then the LU
+ * factorizations of all modes of all bodies run together, one launch per
+ * kernel and LU step over every (body, mode) matrix of any size, largest
+ * first, the whole step sequence captured into one CUDA graph and launched
+ * once on `stream`.  out[i] receives body i's context (the same factors a
+ * separate mueller_build gives with the same lu_tile); on failure every out[i]
+ * is NULL, except MUELLER_ESINGULAR, where all contexts are returned and the
+ * singular body's stats name the mode.  Stage times of each body: its own
+ * assembly; ms_lu is the wave's factorization.  At most 65535 mode matrices
+ * per wave.  Device memory: mueller_build_many_bytes. */
+int mueller_build_many(int count, const mueller_curve* curves, const mueller_media* media, const int* M,
+                       const mueller_options* opts, void* stream, mueller_ctx** out);
 
 /* Assemble only (no factorization) into a caller buffer A_dev
  * [M+1][4N][4N] column-major per mode, L2-weighted:
@@ -255,6 +281,20 @@ int mueller_lu_batched_c64(mueller_c64* A_dev, int n, int batch, int* piv_dev, i
  * scratch), *resident (if not null) what the context holds afterwards.  Used
  * to admit bodies under a memory budget; 0 for invalid sizes. */
 size_t mueller_build_bytes(int N, int M, int precision, size_t* resident);
+
+/* Peak device bytes of mueller_build_many for bodies of N[i] nodes and modes
+ * 0..M[i]: what every body holds through the wave's factorization (its
+ * resident bytes and LU workspace) plus the largest assembly-time surplus of
+ * one body (bodies are assembled one after another).  0 for invalid sizes. */
+size_t mueller_build_many_bytes(int count, const int* N, const int* M, int precision);
+
+/* The LU tile autotuner's decisions so far in this process: up to cap
+ * entries, each the upper end of a trailing-size bucket (rest_hi) and of a
+ * matrix-count bucket (count_hi), the column tile chosen (tile) and the
+ * measured milliseconds per matrix of one split + update step with tiles 32,
+ * 64 and 128 (ms_per_matrix[3k .. 3k+2]).  Returns the number of entries
+ * written, -1 for invalid arguments. */
+int mueller_lu_tile_table(int* rest_hi, int* count_hi, int* tile, float* ms_per_matrix, int cap);
 
 /* Bytes of complex128 factors for one body: 16 (4N)^2 (2M+1), the admission
  * unit named by the serving workload (the GPU path stores M+1 of them). */

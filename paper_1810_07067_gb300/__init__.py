@@ -40,7 +40,8 @@ class _Media(ct.Structure):
 
 class _Options(ct.Structure):
     _fields_ = [("n_phi", ct.c_int), ("formulation", ct.c_int), ("precision", ct.c_int),
-                ("refine_tol", ct.c_double), ("refine_max_iter", ct.c_int), ("split_eps", ct.c_double)]
+                ("refine_tol", ct.c_double), ("refine_max_iter", ct.c_int), ("split_eps", ct.c_double),
+                ("lu_tile", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -51,15 +52,25 @@ class Stats(ct.Structure):
                 ("singular_column", ct.c_int), ("device_bytes", ct.c_size_t), ("ms_lu_gemm", ct.c_double),
                 ("lu_gemm_flops", ct.c_double), ("lu_gemm_launches", ct.c_int), ("launches", ct.c_int),
                 ("solve_launches", ct.c_int), ("refine_iters", ct.c_int), ("backward_err_max", ct.c_double),
-                ("ms_residual", ct.c_double), ("residual_launches", ct.c_int), ("residual_tc_flops", ct.c_double)]
+                ("ms_residual", ct.c_double), ("residual_launches", ct.c_int), ("residual_tc_flops", ct.c_double),
+                ("lu_graph", ct.c_int), ("lu_tile_steps", ct.c_int * 3), ("lu_wave_bodies", ct.c_int),
+                ("lu_launches", ct.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["lu_tile_steps"] = list(d["lu_tile_steps"])
+        return d
 
 
 _vp = ct.c_void_p
 _lib.mueller_build.argtypes = [ct.POINTER(_Curve), ct.POINTER(_Media), ct.c_int, ct.POINTER(_Options), _vp,
                                ct.POINTER(_vp)]
+_lib.mueller_build_many.argtypes = [ct.c_int, ct.POINTER(_Curve), ct.POINTER(_Media), ct.POINTER(ct.c_int),
+                                    ct.POINTER(_Options), _vp, ct.POINTER(_vp)]
+_lib.mueller_build_many_bytes.argtypes = [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.c_int]
+_lib.mueller_build_many_bytes.restype = ct.c_size_t
+_lib.mueller_lu_tile_table.argtypes = [ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                       ct.POINTER(ct.c_float), ct.c_int]
 _lib.mueller_assemble.argtypes = [ct.POINTER(_Curve), ct.POINTER(_Media), ct.c_int, ct.POINTER(_Options), _vp, _vp]
 _lib.mueller_solve.argtypes = [_vp, _vp, ct.c_int, _vp, ct.POINTER(ct.c_double), _vp]
 _lib.mueller_rhs_planewave.argtypes = [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int, _vp, _vp]
@@ -86,6 +97,7 @@ _lib.mueller_last_error.restype = ct.c_char_p
 EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_planewave", "mueller_rhs_fields",
            "mueller_far_field", "mueller_far_field_grid", "mueller_eval",
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
+           "mueller_build_many", "mueller_build_many_bytes", "mueller_lu_tile_table",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
@@ -129,10 +141,11 @@ class Options:
     refine_tol: float = 1e-14
     refine_max_iter: int = 10
     split_eps: float = 1e-17
+    lu_tile: int = 0          # mixed path: LU update column tile 32 / 64 / 128, 0 = autotuned
 
     def _c(self):
         return _Options(self.n_phi, self.formulation, self.precision, self.refine_tol, self.refine_max_iter,
-                        self.split_eps)
+                        self.split_eps, self.lu_tile)
 
 
 def _curve_struct(curve):
@@ -148,7 +161,10 @@ def _media_struct(m):
 class Context:
     """Per-body factors of modes 0..M resident on the device."""
 
-    def __init__(self, curve, media, M: int, options: Options | None = None, stream=None):
+    def __init__(self, curve, media, M: int, options: Options | None = None, stream=None, _handle=None):
+        if _handle is not None:  # a context made by build_many
+            self._h, self.M, self.N, self._keep = _handle, int(M), int(curve.n_panels) * 16, None
+            return
         options = options or Options()
         cs, self._keep = _curve_struct(curve)
         ms = _media_struct(media)
@@ -214,6 +230,51 @@ class Context:
 
 def build(curve, media, M: int, options: Options | None = None, stream=None) -> Context:
     return Context(curve, media, M, options, stream)
+
+
+def build_many(bodies, options: Options | None = None, stream=None) -> list[Context]:
+    """Build a wave of bodies, given as (curve, media, M) triples: each is
+    assembled in turn, then all modes of all bodies are factored together in
+    one graph-launched LU (mueller_build_many)."""
+    options = options or Options()
+    count = len(bodies)
+    curves = (_Curve * count)()
+    medias = (_Media * count)()
+    Ms = (ct.c_int * count)()
+    keep = []
+    for i, (curve, media, M) in enumerate(bodies):
+        cs, arrs = _curve_struct(curve)
+        keep.append(arrs)
+        curves[i] = cs
+        medias[i] = _media_struct(media)
+        Ms[i] = int(M)
+    hs = (_vp * count)()
+    rc = _lib.mueller_build_many(count, curves, medias, Ms, ct.byref(options._c()), _stream(stream), hs)
+    ctxs = [Context(b[0], b[1], b[2], _handle=ct.c_void_p(hs[i])) for i, b in enumerate(bodies) if hs[i]]
+    if rc != 0:
+        for c in ctxs:
+            c.close()
+        raise MuellerError(rc)
+    return ctxs
+
+
+def build_many_bytes(N, M, precision: int) -> int:
+    """Peak device bytes of build_many for bodies of N[i] nodes and modes 0..M[i]."""
+    count = len(N)
+    n_arr = (ct.c_int * count)(*[int(v) for v in N])
+    m_arr = (ct.c_int * count)(*[int(v) for v in M])
+    return int(_lib.mueller_build_many_bytes(count, n_arr, m_arr, int(precision)))
+
+
+def lu_tile_table(cap: int = 256) -> list[dict]:
+    """The LU tile autotuner's decisions in this process (see mueller.h)."""
+    rh = (ct.c_int * cap)()
+    ch = (ct.c_int * cap)()
+    tl = (ct.c_int * cap)()
+    ms = (ct.c_float * (3 * cap))()
+    k = _lib.mueller_lu_tile_table(rh, ch, tl, ms, cap)
+    return [{"rest_hi": rh[i], "count_hi": ch[i], "tile": tl[i], "ms_per_matrix": list(ms[3 * i:3 * i + 3])}
+            for i in range(max(k, 0))]
 
 
 def assemble(curve, media, M: int, A, options: Options | None = None, stream=None):

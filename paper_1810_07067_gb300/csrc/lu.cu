@@ -5,7 +5,11 @@
 // (2) its row interchanges are applied to the other columns; (3) the block
 // row of U is formed by a unit-lower triangular solve; (4) the trailing matrix
 // is updated by a complex FP64 GEMM, batched over all matrices.
+#include <algorithm>
+#include <array>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 #include <cooperative_groups.h>
@@ -35,11 +39,14 @@ __device__ __forceinline__ void argmax_merge(V& v, int& idx, V v2, int i2) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, int k0, int nbk,
-                                                     int* __restrict__ piv, int* __restrict__ info) {
-  const int b = blockIdx.x;
-  T* M = A + (size_t)b * n * n;
-  int* pv = piv + (size_t)b * n;
+__global__ void __launch_bounds__(1024) panel_kernel(const LuMat* __restrict__ mats, int k0) {
+  const LuMat mat = mats[blockIdx.x];
+  const int n = mat.n;
+  if (k0 >= n) return;
+  const int nbk = min(LU_NB, n - k0);
+  T* M = (T*)mat.A;
+  int* pv = mat.piv;
+  int* info = mat.info;
   using V = typename Pivot<T>::V;
   __shared__ V red_v[32];
   __shared__ int red_i[32];
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, i
       if (lane == 0) {
         s_p = (best > V(0)) ? bi : -1;
         pv[c] = (best > V(0)) ? bi : c;
-        if (best <= V(0) && info[b] == 0) info[b] = c + 1;
+        if (best <= V(0) && info[0] == 0) info[0] = c + 1;
       }
     }
     __syncthreads();
@@ -116,15 +123,17 @@ __global__ void __launch_bounds__(1024) panel_kernel(T* __restrict__ A, int n, i
 #define PANEL_THREADS 512
 
 template <class T>
-__global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restrict__ A, int n, int k0, int nbk,
-                                                                      int R, int* __restrict__ piv,
-                                                                      int* __restrict__ info) {
+__global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(const LuMat* __restrict__ mats, int k0, int R) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int q = (int)cl.block_rank();
-  const int b = blockIdx.y;
-  T* M = A + (size_t)b * n * n;
-  int* pv = piv + (size_t)b * n;
+  const LuMat mat = mats[blockIdx.y];  // the whole cluster works on one matrix
+  const int n = mat.n;
+  if (k0 >= n) return;                 // every CTA of the cluster, before any cluster barrier
+  const int nbk = min(LU_NB, n - k0);
+  T* M = (T*)mat.A;
+  int* pv = mat.piv;
+  int* info = mat.info;
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T* a = (T*)panel_smem;  // [nbk][R]
   using V = typename Pivot<T>::V;
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restr
     const int p = (best > V(0)) ? bi : -1;
     if (q == 0 && tid == 0) {
       pv[c] = (p >= 0) ? p : c;
-      if (p < 0 && info[b] == 0) info[b] = c + 1;
+      if (p < 0 && info[0] == 0) info[0] = c + 1;
     }
     const int qp = (p >= 0) ? (p - k0) / R : -1, qc = (c - k0) / R;
     if (p >= 0) {
@@ -206,12 +215,13 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(T* __restr
   cl.sync();  // no CTA leaves while a peer could still address its shared memory
 }
 
-// Cluster size: the smallest of 1, 2, 4, 8 whose row slices fit PANEL_SMEM_MAX.
-// Returns false (nothing launched) when none fits or no such cluster can be
-// resident; the caller then uses panel_kernel.
+// Cluster size: the smallest of 1, 2, 4, 8 whose row slices of the largest
+// matrix (rows = its n - k0) fit PANEL_SMEM_MAX; smaller matrices of a ragged
+// batch own fewer rows of the same slices.  Returns false (nothing launched)
+// when none fits or no such cluster can be resident; the caller then uses
+// panel_kernel.
 template <class T>
-static bool launch_panel_cluster(T* A, int n, int k0, int nbk, int batch, int* piv, int* info, cudaStream_t s) {
-  const int rows = n - k0;
+static bool launch_panel_cluster(const LuMat* mats, int rows, int k0, int batch, cudaStream_t s) {
   int C = 1;
   while (C < 8 && (size_t)LU_NB * ((rows + C - 1) / C) * sizeof(T) > PANEL_SMEM_MAX) C *= 2;
   const int R = (rows + C - 1) / C;
@@ -243,7 +253,7 @@ static bool launch_panel_cluster(T* A, int n, int k0, int nbk, int batch, int* p
     cudaGetLastError();
     return false;
   }
-  if (cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, A, n, k0, nbk, R, piv, info) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, mats, k0, R) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -258,14 +268,17 @@ static bool launch_panel_cluster(T* A, int n, int k0, int nbk, int batch, int* p
 // (all loads before all stores).
 #define SWAP_COLS 64
 template <class T>
-__global__ void __launch_bounds__(256) swap_kernel(T* __restrict__ A, int n, int k0, int nbk,
-                                                   const int* __restrict__ piv) {
-  const int b = blockIdx.y;
+__global__ void __launch_bounds__(256) swap_kernel(const LuMat* __restrict__ mats, int k0) {
+  const LuMat mat = mats[blockIdx.y];
+  const int n = mat.n;
+  if (k0 >= n) return;
+  const int nbk = min(LU_NB, n - k0);
+  const int* piv = mat.piv;
   __shared__ int pos[2 * LU_NB], src[2 * LU_NB], slot[LU_NB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kend = k0 + nbk;
   if (warp == 0) {
-    const int p = (lane < nbk) ? piv[(size_t)b * n + k0 + lane] : -1;
+    const int p = (lane < nbk) ? piv[k0 + lane] : -1;
     const unsigned same = __match_any_sync(0xffffffffu, p);
     const bool below = p >= kend;
     const bool first = below && (__ffs(same) - 1 == lane);
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(256) swap_kernel(T* __restrict__ A, int n, int
     int c = blockIdx.x * SWAP_COLS + cc;
     if (c >= n - nbk) break;  // whole warp
     if (c >= k0) c += nbk;     // skip the panel's own columns
-    T* col = A + (size_t)b * n * n + (size_t)c * n;
+    T* col = (T*)mat.A + (size_t)c * n;
     T v0 = czero<T>(), v1 = czero<T>();
     if (d0 >= 0 && d0 != s0) v0 = col[s0];
     if (d1 >= 0 && d1 != s1) v1 = col[s1];
@@ -301,9 +314,12 @@ __global__ void __launch_bounds__(256) swap_kernel(T* __restrict__ A, int n, int
 
 // ---------------------------------------------------------------- U12 = L11^{-1} A12
 template <class T>
-__global__ void trsm_kernel(T* __restrict__ A, int n, int k0, int nbk) {
-  const int b = blockIdx.y;
-  T* M = A + (size_t)b * n * n;
+__global__ void trsm_kernel(const LuMat* __restrict__ mats, int k0) {
+  const LuMat mat = mats[blockIdx.y];
+  const int n = mat.n;
+  if (k0 + LU_NB >= n) return;  // no columns right of the block (or the block is the last)
+  const int nbk = LU_NB;
+  T* M = (T*)mat.A;
   __shared__ T L[LU_NB][LU_NB + 1];
   for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
     int r = t % nbk, cc = t / nbk;
@@ -331,10 +347,13 @@ __global__ void trsm_kernel(T* __restrict__ A, int n, int k0, int nbk) {
 // 256 threads, each 4x4 outputs: rows tx + 16a, columns ty + 16b.
 #define GT 64
 template <class T>
-__global__ void __launch_bounds__(256) gemm_update_kernel(T* __restrict__ A, int n, int k0, int nbk) {
-  const int b = blockIdx.z;
-  T* M = A + (size_t)b * n * n;
+__global__ void __launch_bounds__(256) gemm_update_kernel(const LuMat* __restrict__ mats, int k0) {
+  const LuMat mat = mats[blockIdx.z];
+  const int n = mat.n;
+  const int nbk = LU_NB;
   const int start = k0 + nbk;
+  if ((int)blockIdx.x * GT >= n - start || (int)blockIdx.y * GT >= n - start) return;
+  T* M = (T*)mat.A;
   const int i0 = start + blockIdx.x * GT, j0 = start + blockIdx.y * GT;
   __shared__ T As[LU_NB][GT];
   __shared__ T Bs[LU_NB][GT];
@@ -392,10 +411,18 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(T* __restrict__ A, int
 // matrix; 128 threads; operands are re-laid out into the MMA's K-major
 // no-swizzle core-matrix format in shared memory.
 #define TCU_M 128
-#define TCU_N 64
 #define TCU_ATILE (TCU_M * LU_NB)  // bf16 elements per piece tile of L (128 rows x 32 k)
-#define TCU_BTILE (TCU_N * LU_NB)  // of U (64 columns x 32 k)
-#define TCU_SMEM (6 * (TCU_ATILE + TCU_BTILE) * 2)
+
+// Column tile TN of the update: 32, 64 or 128 (chosen per step by the tile
+// autotuner below).  TMEM holds 4 TN accumulator columns; the launch's shared
+// memory is sized so that the CTAs resident on one SM never ask for more than
+// the 512 TMEM columns: 3 CTAs at TN = 32, 2 at 64, 1 at 128.
+template <int TN> struct TcuShape {
+  static constexpr int BTILE = TN * LU_NB;                        // bf16 elements per piece tile of U
+  static constexpr int SMEM = 6 * (TCU_ATILE + BTILE) * 2;        // both operands, six pieces each
+  static constexpr int SMEM_LAUNCH = TN == 32 ? 64 * 1024 : TN == 64 ? 100 * 1024 : 120 * 1024;
+  static constexpr int TMEM_COLS = 4 * TN;
+};
 
 __device__ __forceinline__ int tcu_off(int r, int k) {  // 4 core matrices along k
   return ((r >> 3) * (LU_NB / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
@@ -412,64 +439,69 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16* p) {
 // Per step, the L panel (rows start.., 32 columns) and the U panel (32 rows,
 // columns start..) are split once into their BF16 pieces, stored tile by tile
 // in exactly the shared-memory image the MMAs read: per matrix, ceil(n/128)
-// L tiles of [6 pieces][128 x 32], then ceil(n/64) U tiles of [6][64 x 32].
+// L tiles of [6 pieces][128 x 32], then ceil(n/TN) U tiles of [6][TN x 32]
+// (room for ceil(n/128) tiles of 128 columns, the largest TN).
 __host__ __device__ inline size_t tcu_ws_matrix_elems(int n) {
-  return (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)((n + TCU_N - 1) / TCU_N) * 6 * TCU_BTILE;
+  return (size_t)((n + TCU_M - 1) / TCU_M) * 6 * (TCU_ATILE + 128 * LU_NB);
 }
 
 size_t lu_c64_workspace_bytes(int n, int batch) { return tcu_ws_matrix_elems(n) * (size_t)batch * 2; }
 
-__global__ void __launch_bounds__(256) tcu_split_kernel(const cf* __restrict__ A, int n, int k0, int nbk, int nL,
-                                                       __nv_bfloat16* __restrict__ ws) {
-  const int b = blockIdx.y;
-  const cf* M = A + (size_t)b * n * n;
-  const int start = k0 + nbk;
-  __nv_bfloat16* W = ws + (size_t)b * tcu_ws_matrix_elems(n);
+template <int TN>
+__global__ void __launch_bounds__(256) tcu_split_kernel(const LuMat* __restrict__ mats, int k0, int nL) {
+  using S = TcuShape<TN>;
+  const LuMat mat = mats[blockIdx.y];
+  const int n = mat.n, nbk = LU_NB;
+  const int start = k0 + nbk, rest = n - start;
+  const cf* M = (const cf*)mat.A;
+  __nv_bfloat16* W = (__nv_bfloat16*)mat.ws;
   __nv_bfloat16 pr[3], pi[3];
   if ((int)blockIdx.x < nL) {
+    if ((int)blockIdx.x * TCU_M >= rest) return;
     const int r0 = start + blockIdx.x * TCU_M;
     __nv_bfloat16* dst = W + (size_t)blockIdx.x * 6 * TCU_ATILE;
     for (int t = threadIdx.x; t < TCU_M * LU_NB; t += 256) {
       int r = t % TCU_M, k = t / TCU_M;
-      cf v = (r0 + r < n && k < nbk) ? M[(size_t)(k0 + k) * n + r0 + r] : CF(0.f);
+      cf v = (r0 + r < n) ? M[(size_t)(k0 + k) * n + r0 + r] : CF(0.f);
       split3(v.x, pr); split3(v.y, pi);
       int off = tcu_off(r, k);
 #pragma unroll
       for (int q = 0; q < 3; ++q) { dst[q * TCU_ATILE + off] = pr[q]; dst[(3 + q) * TCU_ATILE + off] = pi[q]; }
     }
   } else {
-    const int y = blockIdx.x - nL, c0 = start + y * TCU_N;
-    __nv_bfloat16* dst = W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)y * 6 * TCU_BTILE;
-    for (int t = threadIdx.x; t < TCU_N * LU_NB; t += 256) {
+    const int y = blockIdx.x - nL;
+    if (y * TN >= rest) return;
+    const int c0 = start + y * TN;
+    __nv_bfloat16* dst = W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)y * 6 * S::BTILE;
+    for (int t = threadIdx.x; t < TN * LU_NB; t += 256) {
       int k = t % LU_NB, j = t / LU_NB;
-      cf v = (c0 + j < n && k < nbk) ? M[(size_t)(c0 + j) * n + k0 + k] : CF(0.f);
+      cf v = (c0 + j < n) ? M[(size_t)(c0 + j) * n + k0 + k] : CF(0.f);
       split3(v.x, pr); split3(v.y, pi);
       int off = tcu_off(j, k);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) { dst[q * TCU_BTILE + off] = pr[q]; dst[(3 + q) * TCU_BTILE + off] = pi[q]; }
+      for (int q = 0; q < 3; ++q) { dst[q * S::BTILE + off] = pr[q]; dst[(3 + q) * S::BTILE + off] = pi[q]; }
     }
   }
 }
 
-// Launched with TCU_SMEM_LAUNCH bytes of dynamic shared memory so that at
-// most two CTAs share an SM (each holds 256 TMEM columns of the 512).
-#define TCU_SMEM_LAUNCH (100 * 1024)
-
-__global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A, int n, int k0, int nbk,
-                                                            const __nv_bfloat16* __restrict__ ws,
+template <int TN>
+__global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __restrict__ mats, int k0,
                                                             int* __restrict__ err) {
+  using S = TcuShape<TN>;
+  const LuMat mat = mats[blockIdx.z];
+  const int n = mat.n, nbk = LU_NB;
+  const int start = k0 + nbk;
+  if ((int)blockIdx.x * TCU_M >= n - start || (int)blockIdx.y * TN >= n - start) return;  // before any allocation
   extern __shared__ __align__(1024) unsigned char smem[];
   __nv_bfloat16* As = (__nv_bfloat16*)smem;
   __nv_bfloat16* Bs = As + 6 * TCU_ATILE;
   __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
   __shared__ uint32_t tmem_base;
   __shared__ int s_ok;
-  const int b = blockIdx.z;
-  cf* M = A + (size_t)b * n * n;
-  const int start = k0 + nbk;
-  const int i0 = start + blockIdx.x * TCU_M, j0 = start + blockIdx.y * TCU_N;
+  cf* M = (cf*)mat.A;
+  const int i0 = start + blockIdx.x * TCU_M, j0 = start + blockIdx.y * TN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 4 * TCU_N);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, S::TMEM_COLS);
   if (tid == 0) {
     s_ok = 1;
     tc::mbar_init(&mbar_load, 1);
@@ -480,22 +512,22 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A,
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  // accumulator columns: [0,N) hh Re, [N,2N) hh Im, [2N,3N) corrections Re, [3N,4N) corrections Im
+  // accumulator columns: [0,TN) hh Re, [TN,2TN) hh Im, [2TN,3TN) corrections Re, [3TN,4TN) corrections Im
   if (tid == 0) {
-    const __nv_bfloat16* W = ws + (size_t)b * tcu_ws_matrix_elems(n);
+    const __nv_bfloat16* W = (const __nv_bfloat16*)mat.ws;
     const __nv_bfloat16* Lsrc = W + (size_t)blockIdx.x * 6 * TCU_ATILE;
     const __nv_bfloat16* Usrc =
-        W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)blockIdx.y * 6 * TCU_BTILE;
-    tc::mbar_expect_tx(&mbar_load, TCU_SMEM);
+        W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)blockIdx.y * 6 * S::BTILE;
+    tc::mbar_expect_tx(&mbar_load, S::SMEM);
     tc::bulk_g2s(As, Lsrc, 6 * TCU_ATILE * 2, &mbar_load);
-    tc::bulk_g2s(Bs, Usrc, 6 * TCU_BTILE * 2, &mbar_load);
+    tc::bulk_g2s(Bs, Usrc, 6 * S::BTILE * 2, &mbar_load);
     if (tc::mbar_wait(&mbar_load, 0)) {
       tc::fence_after();
-      const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TCU_N, false);
-      const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TCU_N, true);
+      const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TN, false);
+      const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TN, true);
       const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(As), 128, (LU_NB / 8) * 128);
       const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(Bs), 128, (LU_NB / 8) * 128);
-      const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(TCU_BTILE * 2 / 16);  // 16-byte units
+      const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(S::BTILE * 2 / 16);  // 16-byte units
       const int qa_[6] = {0, 0, 1, 0, 1, 2}, qb_[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
       for (int ks = 0; ks < LU_NB / 16; ++ks) {
@@ -504,7 +536,7 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A,
         for (int u = 0; u < 6; ++u) {
           const uint64_t are = a0 + qa_[u] * at + kof, aim = a0 + (3 + qa_[u]) * at + kof;
           const uint64_t bre = b0 + qb_[u] * bt + kof, bim = b0 + (3 + qb_[u]) * bt + kof;
-          const uint32_t dre = tmem + (u == 0 ? 0 : 2 * TCU_N), dim = tmem + (u == 0 ? TCU_N : 3 * TCU_N);
+          const uint32_t dre = tmem + (u == 0 ? 0 : 2 * TN), dim = tmem + (u == 0 ? TN : 3 * TN);
           const uint32_t acc = (ks == 0 && u <= 1) ? 0u : 1u;  // first write of each accumulator
           tc::mma_bf16(dre, are, bre, id_pos, acc);
           tc::mma_bf16(dre, aim, bim, id_neg, 1u);
@@ -534,7 +566,7 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A,
   if (ok) {
     const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TCU_N; c0 += 32) {
+    for (int c0 = 0; c0 < TN; c0 += 32) {
       if (c0 > 0) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -544,9 +576,9 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A,
       }
       float hr[32], hi[32], cr[32], ci[32];
       tc::tmem_ld32(tw + c0, hr);
-      tc::tmem_ld32(tw + TCU_N + c0, hi);
-      tc::tmem_ld32(tw + 2 * TCU_N + c0, cr);
-      tc::tmem_ld32(tw + 3 * TCU_N + c0, ci);
+      tc::tmem_ld32(tw + TN + c0, hi);
+      tc::tmem_ld32(tw + 2 * TN + c0, cr);
+      tc::tmem_ld32(tw + 3 * TN + c0, ci);
       if (i < n) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -558,52 +590,244 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(cf* __restrict__ A,
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 4 * TCU_N);
+  if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------- driver
+template <int TN>
+static void tc_update_tn(const LuMat* d, int k0, int rest, int active, int* tc_err, cudaStream_t s) {
+  const int nL = (rest + TCU_M - 1) / TCU_M, nU = (rest + TN - 1) / TN;
+  tcu_split_kernel<TN><<<dim3(nL + nU, active), 256, 0, s>>>(d, k0, nL);
+  gemm_update_tc_kernel<TN><<<dim3(nL, nU, active), 128, TcuShape<TN>::SMEM_LAUNCH, s>>>(d, k0, tc_err);
+}
+
+static void tc_update(int tn, const LuMat* d, int k0, int rest, int active, int* tc_err, cudaStream_t s) {
+  if (tn == 32) tc_update_tn<32>(d, k0, rest, active, tc_err, s);
+  else if (tn == 128) tc_update_tn<128>(d, k0, rest, active, tc_err, s);
+  else tc_update_tn<64>(d, k0, rest, active, tc_err, s);
+}
+
+static void tc_set_attributes() {
+  cudaFuncSetAttribute(gemm_update_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<32>::SMEM_LAUNCH);
+  cudaFuncSetAttribute(gemm_update_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<64>::SMEM_LAUNCH);
+  cudaFuncSetAttribute(gemm_update_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       TcuShape<128>::SMEM_LAUNCH);
+}
+
+__global__ void lu_info_zero_kernel(const LuMat* __restrict__ mats, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < count) mats[b].info[0] = 0;
+}
+
+// Tile autotuner.  The column tile TN of the tensor-core update is chosen per
+// LU step from the trailing size (rest) and the number of matrices in the
+// launch.  For each power-of-two bucket of rest ((64, 128], (128, 256], ...,
+// above 8192) and of the matrix count, the split + update pair is timed once
+// per process on scratch matrices of the bucket's middle size with TN = 32, 64
+// and 128 (CUDA events on the caller's stream, best of three after one
+// warm-up); the tile with the least time per matrix is kept, TN = 64 unless
+// another is at least 3 % faster.  Scratch is capped near 1 GiB by timing
+// fewer matrices of large sizes (their launches still fill the GPU).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune;
+std::map<std::pair<int, int>, std::array<float, 3>> g_tune_ms;
+int rest_bucket(int rest) { int b = 0; while (b < 7 && (128 << b) < rest) ++b; return b; }
+int count_bucket(int c) { int b = 0; while (b < 16 && (1 << b) < c) ++b; return b; }
+}  // namespace
+
+__global__ void tune_fill_kernel(cf* A, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 32);
+    h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+    A[i] = CF((float)(h & 0xffff) * (2.f / 65535.f) - 1.f, (float)(h >> 16) * (2.f / 65535.f) - 1.f);
+  }
+}
+
+static int measure_tile(int R, int count, cudaStream_t s, std::array<float, 3>& ms) {
+  const int n = R + LU_NB;
+  const size_t elems = (size_t)n * n, wse = tcu_ws_matrix_elems(n);
+  const size_t per = elems * sizeof(cf) + wse * 2;
+  const int c = (int)std::min<size_t>((size_t)count, std::max<size_t>(1, ((size_t)1 << 30) / per));
+  cf* A = nullptr;
+  __nv_bfloat16* ws = nullptr;
+  LuMat* d = nullptr;
+  int* err = nullptr;
+  ms = {-1.f, -1.f, -1.f};
+  if (cudaMallocAsync((void**)&A, elems * c * sizeof(cf), s) != cudaSuccess ||
+      cudaMallocAsync((void**)&ws, wse * c * 2, s) != cudaSuccess ||
+      cudaMallocAsync((void**)&d, sizeof(LuMat) * c, s) != cudaSuccess ||
+      cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    if (A) cudaFreeAsync(A, s);
+    if (ws) cudaFreeAsync(ws, s);
+    if (d) cudaFreeAsync(d, s);
+    if (err) cudaFreeAsync(err, s);
+    return 64;
+  }
+  std::vector<LuMat> it(c);
+  for (int i = 0; i < c; ++i) it[i] = LuMat{A + elems * i, nullptr, nullptr, ws + wse * i, n, 0};
+  cudaMemcpyAsync(d, it.data(), sizeof(LuMat) * c, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+  tune_fill_kernel<<<1024, 256, 0, s>>>(A, elems * c);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  const int tns[3] = {32, 64, 128};
+  for (int q = 0; q < 3; ++q) {
+    tc_update(tns[q], d, 0, R, c, err, s);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      tc_update(tns[q], d, 0, R, c, err, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, t);
+    }
+    ms[q] = best / c;
+  }
+  int herr = 0;
+  cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  cudaFreeAsync(A, s); cudaFreeAsync(ws, s); cudaFreeAsync(d, s); cudaFreeAsync(err, s);
+  if (cudaGetLastError() != cudaSuccess || herr) return 64;
+  int pick = 1;
+  for (int q : {0, 2})
+    if (ms[q] > 0.f && ms[q] < 0.97f * ms[pick]) pick = q;
+  return tns[pick];
+}
+
+static void autotune_tiles(int nmax, int count, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int cb = count_bucket(count);
+  for (int rb = 0; rb <= rest_bucket(nmax - LU_NB); ++rb) {
+    if (g_tune.count({rb, cb})) continue;
+    std::array<float, 3> ms;
+    const int tn = measure_tile(96 << rb, count, s, ms);
+    g_tune[{rb, cb}] = tn;
+    g_tune_ms[{rb, cb}] = ms;
+  }
+}
+
+static int tuned_tile(int rest, int count) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto f = g_tune.find({rest_bucket(rest), count_bucket(count)});
+  return f == g_tune.end() ? 64 : f->second;
+}
+
+int lu_tile_table(int* rest_hi, int* count_hi, int* tile, float* ms, int cap) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int k = 0;
+  for (const auto& e : g_tune) {
+    if (k >= cap) break;
+    rest_hi[k] = 128 << e.first.first;
+    count_hi[k] = 1 << e.first.second;
+    tile[k] = e.second;
+    const auto& m = g_tune_ms[e.first];
+    for (int q = 0; q < 3; ++q) ms[3 * k + q] = m[q];
+    ++k;
+  }
+  return k;
+}
+
+// Right-looking blocked LU of every matrix of the table, largest first: at
+// step k0 the launches cover the matrices with n > k0 (a prefix of the sorted
+// table), each kernel reading its matrix, size and pivots from the table.
 template <class T>
-static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm,
-                           int* tc_err = nullptr, __nv_bfloat16* ws = nullptr) {
-  cudaMemsetAsync(info, 0, sizeof(int) * batch, s);
-  if constexpr (std::is_same<T, cf>::value)
-    cudaFuncSetAttribute(gemm_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TCU_SMEM_LAUNCH);
-  std::vector<cudaEvent_t> ev;
-  int launches = 0;
-  for (int k0 = 0; k0 < n; k0 += LU_NB) {
-    int nbk = (n - k0 < LU_NB) ? n - k0 : LU_NB;
-    if (!launch_panel_cluster<T>(A, n, k0, nbk, batch, piv, info, s))
-      panel_kernel<T><<<batch, 1024, 0, s>>>(A, n, k0, nbk, piv, info);
-    ++launches;
-    int nother = n - nbk;
-    if (nother > 0) { swap_kernel<T><<<dim3((nother + SWAP_COLS - 1) / SWAP_COLS, batch), 256, 0, s>>>(A, n, k0, nbk, piv); ++launches; }
-    int rest = n - k0 - nbk;
-    if (rest > 0) {
-      trsm_kernel<T><<<dim3((rest + 127) / 128, batch), 128, 0, s>>>(A, n, k0, nbk);
-      int t = (rest + GT - 1) / GT;
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (tm) {
-        cudaEventCreate(&e0); cudaEventCreate(&e1);
-        cudaEventRecord(e0, s);
-      }
-      if constexpr (std::is_same<T, cf>::value) {
-        const int nL = (rest + TCU_M - 1) / TCU_M, nU = (rest + TCU_N - 1) / TCU_N;
-        tcu_split_kernel<<<dim3(nL + nU, batch), 256, 0, s>>>((const cf*)A, n, k0, nbk, nL, ws);
-        gemm_update_tc_kernel<<<dim3(nL, nU, batch), 128, TCU_SMEM_LAUNCH, s>>>((cf*)A, n, k0, nbk, ws, tc_err);
-        ++launches;
-      } else {
-        gemm_update_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, n, k0, nbk);
-      }
-      launches += 2;
-      if (tm) {
-        cudaEventRecord(e1, s);
-        ev.push_back(e0); ev.push_back(e1);
-        tm->gemm_flops += 8.0 * (double)rest * rest * nbk * batch;
-        tm->gemm_launches += 1;
-      }
+static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s, LuTiming* tm, int* tc_err, int tile,
+                                  bool graph) {
+  if (count <= 0) return cudaSuccess;
+  std::vector<LuMat> it(items, items + count);
+  std::stable_sort(it.begin(), it.end(), [](const LuMat& a, const LuMat& b) { return a.n > b.n; });
+  const int nmax = it[0].n;
+  LuMat* d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, sizeof(LuMat) * count, s);
+  if (e != cudaSuccess) return e;
+  cudaMemcpyAsync(d, it.data(), sizeof(LuMat) * count, cudaMemcpyHostToDevice, s);
+  lu_info_zero_kernel<<<(count + 255) / 256, 256, 0, s>>>(d, count);
+  constexpr bool c64 = std::is_same<T, cf>::value;
+  if constexpr (c64) {
+    tc_set_attributes();
+    if (tile == 0) autotune_tiles(nmax, count, s);
+  }
+  cudaStream_t ls = s, cs = nullptr;
+  if (graph) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      if (cs) cudaStreamDestroy(cs);
+      cs = nullptr;
+      graph = false;
+    } else {
+      ls = cs;
     }
   }
+  const bool timed = tm && !graph;
+  std::vector<cudaEvent_t> ev;
+  int launches = 1, gemm_launches = 0, tn_steps[3] = {0, 0, 0};
+  double gemm_flops = 0.0;
+  int active = count;
+  for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
+    while (active > 0 && it[active - 1].n <= k0) --active;
+    const int nbk = std::min(LU_NB, nmax - k0);
+    if (!launch_panel_cluster<T>(d, nmax - k0, k0, active, ls)) panel_kernel<T><<<active, 1024, 0, ls>>>(d, k0);
+    ++launches;
+    if (nmax - nbk > 0) {
+      swap_kernel<T><<<dim3((nmax - nbk + SWAP_COLS - 1) / SWAP_COLS, active), 256, 0, ls>>>(d, k0);
+      ++launches;
+    }
+    const int rest = nmax - k0 - nbk;
+    if (rest <= 0) continue;
+    trsm_kernel<T><<<dim3((rest + 127) / 128, active), 128, 0, ls>>>(d, k0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+      cudaEventCreate(&e0); cudaEventCreate(&e1);
+      cudaEventRecord(e0, ls);
+    }
+    if constexpr (c64) {
+      const int tn = tile ? tile : tuned_tile(rest, active);
+      tc_update(tn, d, k0, rest, active, tc_err, ls);
+      ++tn_steps[tn == 32 ? 0 : tn == 64 ? 1 : 2];
+      launches += 3;
+    } else {
+      const int t = (rest + GT - 1) / GT;
+      gemm_update_kernel<T><<<dim3(t, t, active), 256, 0, ls>>>(d, k0);
+      launches += 2;
+    }
+    if (timed) {
+      cudaEventRecord(e1, ls);
+      ev.push_back(e0); ev.push_back(e1);
+    }
+    for (int b = 0; b < active; ++b) {
+      const double rb = (double)(it[b].n - k0 - LU_NB);
+      if (rb > 0) gemm_flops += 8.0 * rb * rb * LU_NB;
+    }
+    ++gemm_launches;
+  }
+  if (graph) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, s);
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {  // nothing of the capture ran: factor with direct launches instead
+      cudaGetLastError();
+      cudaFreeAsync(d, s);
+      return lu_factor_impl<T>(items, count, s, tm, tc_err, tile, false);
+    }
+  }
+  cudaFreeAsync(d, s);
   if (tm) {
     tm->launches += launches;
+    tm->gemm_flops += gemm_flops;
+    tm->gemm_launches += gemm_launches;
+    tm->graph = graph ? 1 : 0;
+    for (int q = 0; q < 3; ++q) tm->tile_steps[q] += tn_steps[q];
     if (!ev.empty()) cudaEventSynchronize(ev.back());
     for (size_t q = 0; q + 1 < ev.size(); q += 2) {
       float ms = 0.f;
@@ -612,15 +836,28 @@ static void lu_factor_impl(T* A, int n, int batch, int* piv, int* info, cudaStre
       cudaEventDestroy(ev[q]); cudaEventDestroy(ev[q + 1]);
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t lu_factor_many(const LuMat* items, int count, bool c64, cudaStream_t s, LuTiming* tm, int* tc_err,
+                           int tile, bool graph) {
+  return c64 ? lu_factor_impl<cf>(items, count, s, tm, tc_err, tile, graph)
+             : lu_factor_impl<cd>(items, count, s, tm, nullptr, 0, graph);
 }
 
 void lu_factor_batched(cd* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm) {
-  lu_factor_impl<cd>(A, n, batch, piv, info, s, tm);
+  std::vector<LuMat> it(batch);
+  for (int b = 0; b < batch; ++b) it[b] = LuMat{A + (size_t)b * n * n, piv + (size_t)b * n, info + b, nullptr, n, 0};
+  lu_factor_impl<cd>(it.data(), batch, s, tm, nullptr, 0, false);
 }
 
 void lu_factor_batched_c64(cf* A, int n, int batch, int* piv, int* info, cudaStream_t s, LuTiming* tm,
-                           int* tc_err, void* ws) {
-  lu_factor_impl<cf>(A, n, batch, piv, info, s, tm, tc_err, (__nv_bfloat16*)ws);
+                           int* tc_err, void* ws, int tile) {
+  std::vector<LuMat> it(batch);
+  for (int b = 0; b < batch; ++b)
+    it[b] = LuMat{A + (size_t)b * n * n, piv + (size_t)b * n, info + b,
+                  (__nv_bfloat16*)ws + tcu_ws_matrix_elems(n) * b, n, 0};
+  lu_factor_impl<cf>(it.data(), batch, s, tm, tc_err, tile, false);
 }
 
 // ---------------------------------------------------------------- solves

@@ -506,29 +506,39 @@ struct mueller_ctx {
   int* piv = nullptr;
   int* info = nullptr;
   int* tc_err = nullptr;       // set by a timed-out device wait in tensor-core kernels
+  int lu_tile = 0;             // column tile of the complex64 update (0: autotuned)
+  int launches_pre = 0;        // launches between assembly and LU (norms, conversion, slices)
+  size_t bytes = 0;            // device bytes held after the build
   mueller_stats st{};
 };
 
-extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* media, int M,
-                             const mueller_options* opts, void* stream, mueller_ctx** out) {
-  g_err.clear();
-  if (!out) return fail(MUELLER_EINVAL, "null output pointer");
+// Build phases.  prepare: host set-up and the context's allocations;
+// assemble: matrices of modes 0..M (plus, mixed path, norms, the complex64
+// copy and the digit slices; precision 1 then frees the complex128 matrices);
+// factor: the LU of the body's modes (or of a whole wave, mueller_build_many);
+// finish: pivot and timeout checks, stats.
+static int build_prepare(const mueller_curve* curve, const mueller_media* media, int M, const mueller_options* opts,
+                         cudaStream_t s, mueller_ctx** out) {
   *out = nullptr;
   mueller_ctx* c = new mueller_ctx();
   int rc = setup_inputs(curve, media, M, opts, c->S);
   if (rc) { delete c; return rc; }
+  if (opts->lu_tile != 0 && opts->lu_tile != 32 && opts->lu_tile != 64 && opts->lu_tile != 128) {
+    delete c;
+    return fail(MUELLER_EINVAL, "lu_tile must be 0 (autotuned), 32, 64 or 128");
+  }
+  c->lu_tile = opts->lu_tile;
   setup_support(curve, c->S);
   setup_pairs(c->S);
-  cudaStream_t s = (cudaStream_t)stream;
   const size_t n = c->S.n;
   const bool mixed = c->S.precision != 0;
   const bool slices = c->S.precision == 1;
   c->npad = (int)((n + OZ_RT - 1) / OZ_RT * OZ_RT);
   const size_t slice_bytes = slices ? ozaki_matrix_slices_elems(c->npad, M + 1) * 2 : 0;
-  size_t bytes = (size_t)(M + 1) * n * n * (sizeof(cd) + (mixed ? sizeof(cf) : 0)) + slice_bytes;
+  c->bytes = (size_t)(M + 1) * n * n * (sizeof(cd) + (mixed ? sizeof(cf) : 0)) + slice_bytes;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
-  if (bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
+  if (c->bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
   if (c->keep.alloc(&c->A, (size_t)(M + 1) * n * n) != cudaSuccess ||
       c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess ||
       (mixed && (c->keep.alloc(&c->A32, (size_t)(M + 1) * n * n) != cudaSuccess ||
@@ -540,57 +550,178 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
     return fail(MUELLER_ENOMEM, "factor allocation");
   }
   cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
-  cudaEvent_t e0, e1, e2;
-  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+  *out = c;
+  return MUELLER_OK;
+}
+
+static int build_assemble(mueller_ctx* c, cudaStream_t s) {
+  const int M = c->S.M;
+  const size_t n = c->S.n;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  rc = assemble_core(c->S, c->A, s, &c->st, c->keep, c->geo);
-  if (rc) { delete c; return rc; }
-  cudaEventRecord(e1, s);
-  LuTiming lt;
-  DevBuf wsb;  // tensor-core LU workspace, freed after the factorisation has completed
-  if (mixed) {
+  int rc = assemble_core(c->S, c->A, s, &c->st, c->keep, c->geo);
+  if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+  if (c->S.precision != 0) {
     mixed_norm_inf(c->A, (int)n, M + 1, c->normA, s);
     mixed_convert(c->A, c->A32, (size_t)(M + 1) * n * n, s);
-    if (slices) {
+    c->launches_pre += 2;
+    if (c->S.precision == 1) {
       ozaki_slice_matrix(c->A, (int)n, c->npad, M + 1, c->Asl, c->rowscale, s);
-      lt.launches += 2;
+      c->launches_pre += 2;
     }
+  }
+  cudaEventRecord(e1, s);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(MUELLER_ECUDA, cudaGetErrorString(err));
+  c->st.ms_build = ms;
+  if (c->S.precision == 1) {  // the residuals use the slices; the complex128 matrices are no longer needed
+    cudaFree(c->A);
+    c->keep.ptrs.erase(std::find(c->keep.ptrs.begin(), c->keep.ptrs.end(), (void*)c->A));
+    c->A = nullptr;
+    c->bytes -= (size_t)(M + 1) * n * n * sizeof(cd);
+  }
+  return MUELLER_OK;
+}
+
+static int build_finish(mueller_ctx* c, const LuTiming& lt, double ms_lu, int wave_bodies) {
+  const int M = c->S.M;
+  c->st.ms_lu = ms_lu;
+  c->st.ms_build += ms_lu;
+  c->st.ms_lu_gemm = lt.gemm_ms; c->st.lu_gemm_flops = lt.gemm_flops; c->st.lu_gemm_launches = lt.gemm_launches;
+  c->st.launches = 4 + c->launches_pre + lt.launches;
+  c->st.lu_graph = lt.graph;
+  for (int q = 0; q < 3; ++q) c->st.lu_tile_steps[q] = lt.tile_steps[q];
+  c->st.lu_wave_bodies = wave_bodies;
+  c->st.lu_launches = lt.launches;
+  std::vector<int> info(M + 1);
+  CK(cudaMemcpy(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost));
+  int tce = 0;
+  CK(cudaMemcpy(&tce, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tce) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core LU update timed out");
+  c->st.singular_mode = -1; c->st.singular_column = -1;
+  for (int m = 0; m <= M; ++m)
+    if (info[m]) { c->st.singular_mode = m; c->st.singular_column = info[m] - 1; break; }
+  c->st.device_bytes = c->bytes;
+  return MUELLER_OK;
+}
+
+// The (mode) matrices of one body as LU table entries; ws_base: the body's
+// complex64 workspace (lu_c64_workspace_bytes(n, M + 1) bytes) or null.
+static void lu_items_of(mueller_ctx* c, unsigned char* ws_base, std::vector<LuMat>& items) {
+  const int n = c->S.n, M = c->S.M;
+  const bool mixed = c->S.precision != 0;
+  const size_t wsm = lu_c64_workspace_bytes(n, 1);
+  for (int m = 0; m <= M; ++m) {
+    void* A = mixed ? (void*)(c->A32 + (size_t)m * n * n) : (void*)(c->A + (size_t)m * n * n);
+    items.push_back(LuMat{A, c->piv + (size_t)m * n, c->info + m, ws_base ? ws_base + wsm * m : nullptr, n, 0});
+  }
+}
+
+extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* media, int M,
+                             const mueller_options* opts, void* stream, mueller_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(MUELLER_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!opts) return fail(MUELLER_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  mueller_ctx* c = nullptr;
+  int rc = build_prepare(curve, media, M, opts, s, &c);
+  if (rc) return rc;
+  rc = build_assemble(c, s);
+  if (rc) { delete c; return rc; }
+  const size_t n = c->S.n;
+  const bool mixed = c->S.precision != 0;
+  LuTiming lt;
+  DevBuf wsb;  // tensor-core LU workspace, freed after the factorisation has completed
+  cudaEvent_t e1, e2;
+  cudaEventCreate(&e1); cudaEventCreate(&e2);
+  cudaEventRecord(e1, s);
+  if (mixed) {
     unsigned char* ws = nullptr;
     if (wsb.alloc(&ws, lu_c64_workspace_bytes((int)n, M + 1)) != cudaSuccess) {
+      cudaEventDestroy(e1); cudaEventDestroy(e2);
       delete c;
       return fail(MUELLER_ENOMEM, "tensor-core LU workspace");
     }
-    lu_factor_batched_c64(c->A32, (int)n, M + 1, c->piv, c->info, s, &lt, c->tc_err, ws);
-    lt.launches += 2;
+    lu_factor_batched_c64(c->A32, (int)n, M + 1, c->piv, c->info, s, &lt, c->tc_err, ws, c->lu_tile);
   } else {
     lu_factor_batched(c->A, (int)n, M + 1, c->piv, c->info, s, &lt);
   }
   cudaEventRecord(e2, s);
   cudaError_t err = cudaStreamSynchronize(s);
+  float b = 0;
+  cudaEventElapsedTime(&b, e1, e2);
+  cudaEventDestroy(e1); cudaEventDestroy(e2);
   if (err != cudaSuccess) { delete c; return fail(MUELLER_ECUDA, cudaGetErrorString(err)); }
-  float a = 0, b = 0;
-  cudaEventElapsedTime(&a, e0, e1); cudaEventElapsedTime(&b, e1, e2);
-  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
-  c->st.ms_lu = b; c->st.ms_build = a + b;
-  c->st.ms_lu_gemm = lt.gemm_ms; c->st.lu_gemm_flops = lt.gemm_flops; c->st.lu_gemm_launches = lt.gemm_launches;
-  c->st.launches = 4 + lt.launches;
-  std::vector<int> info(M + 1);
-  cudaMemcpy(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost);
-  int tce = 0;
-  cudaMemcpy(&tce, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (tce) { delete c; return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core LU update timed out"); }
-  c->st.singular_mode = -1; c->st.singular_column = -1;
-  for (int m = 0; m <= M; ++m)
-    if (info[m]) { c->st.singular_mode = m; c->st.singular_column = info[m] - 1; break; }
-  if (slices) {  // the residuals use the slices; the complex128 matrices are no longer needed
-    cudaFree(c->A);
-    c->keep.ptrs.erase(std::find(c->keep.ptrs.begin(), c->keep.ptrs.end(), (void*)c->A));
-    c->A = nullptr;
-    bytes -= (size_t)(M + 1) * n * n * sizeof(cd);
-  }
-  c->st.device_bytes = bytes;
+  rc = build_finish(c, lt, b, 1);
+  if (rc) { delete c; return rc; }
   *out = c;
   if (c->st.singular_mode >= 0) return fail(MUELLER_ESINGULAR, "exact zero pivot");
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_build_many(int count, const mueller_curve* curves, const mueller_media* media, const int* M,
+                                  const mueller_options* opts, void* stream, mueller_ctx** out) {
+  g_err.clear();
+  if (!out || !curves || !media || !M || !opts) return fail(MUELLER_EINVAL, "null argument");
+  if (count < 1) return fail(MUELLER_EINVAL, "count must be >= 1");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<mueller_ctx*> cs(count, nullptr);
+  auto drop = [&](int rc) {
+    for (auto* c : cs) delete c;
+    return rc;
+  };
+  long long items_total = 0;
+  for (int i = 0; i < count; ++i) items_total += (long long)M[i] + 1;
+  if (items_total > 65535) return fail(MUELLER_EINVAL, "a wave holds at most 65535 mode matrices");
+  for (int i = 0; i < count; ++i) {
+    int rc = build_prepare(&curves[i], &media[i], M[i], opts, s, &cs[i]);
+    if (rc) return drop(rc);
+    rc = build_assemble(cs[i], s);
+    if (rc) return drop(rc);
+  }
+  const bool mixed = opts->precision != 0;
+  std::vector<LuMat> items;
+  items.reserve((size_t)items_total);
+  DevBuf wsb;
+  for (int i = 0; i < count; ++i) {
+    unsigned char* ws = nullptr;
+    if (mixed && wsb.alloc(&ws, lu_c64_workspace_bytes(cs[i]->S.n, M[i] + 1)) != cudaSuccess)
+      return drop(fail(MUELLER_ENOMEM, "tensor-core LU workspace"));
+    lu_items_of(cs[i], ws, items);
+  }
+  // one table entry per (body, mode); a body's timeout flag is shared by the wave
+  LuTiming lt;
+  cudaEvent_t e1, e2;
+  cudaEventCreate(&e1); cudaEventCreate(&e2);
+  cudaEventRecord(e1, s);
+  cudaError_t err = lu_factor_many(items.data(), (int)items.size(), mixed, s, &lt, cs[0]->tc_err,
+                                   opts->lu_tile, true);
+  cudaEventRecord(e2, s);
+  cudaError_t err2 = cudaStreamSynchronize(s);
+  float b = 0;
+  cudaEventElapsedTime(&b, e1, e2);
+  cudaEventDestroy(e1); cudaEventDestroy(e2);
+  if (err == cudaSuccess) err = err2;
+  if (err != cudaSuccess) return drop(fail(MUELLER_ECUDA, cudaGetErrorString(err)));
+  int tce = 0;
+  CK(cudaMemcpy(&tce, cs[0]->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < count; ++i) {
+    if (tce) cudaMemcpy(cs[i]->tc_err, cs[0]->tc_err, sizeof(int), cudaMemcpyDeviceToDevice);
+    int rc = build_finish(cs[i], lt, b, count);
+    if (rc) return drop(rc);
+  }
+  bool singular = false;
+  for (int i = 0; i < count; ++i) {
+    out[i] = cs[i];
+    singular = singular || cs[i]->st.singular_mode >= 0;
+  }
+  if (singular) return fail(MUELLER_ESINGULAR, "exact zero pivot in some body (see its stats)");
   return MUELLER_OK;
 }
 
@@ -973,6 +1104,27 @@ extern "C" size_t mueller_build_bytes(int N, int M, int precision, size_t* resid
   const size_t scratch = (size_t)N * NEAR_SLOTS * NFAM * (size_t)(M + 2) * sizeof(cd);
   if (resident) *resident = (precision == 1 ? 0 : A) + A32 + sl + small;
   return A + A32 + sl + small + scratch;
+}
+
+extern "C" size_t mueller_build_many_bytes(int count, const int* N, const int* M, int precision) {
+  if (count < 1 || !N || !M) return 0;
+  size_t held = 0, extra = 0;
+  for (int i = 0; i < count; ++i) {
+    size_t res = 0;
+    const size_t peak = mueller_build_bytes(N[i], M[i], precision, &res);
+    if (peak == 0) return 0;
+    // held through the wave's LU: the resident part, plus the complex128
+    // matrices where they stay, plus the LU workspace
+    const size_t ws = precision != 0 ? lu_c64_workspace_bytes(4 * N[i], M[i] + 1) : 0;
+    held += res + ws;
+    extra = std::max(extra, peak - res);  // a body's assembly-time surplus, one body at a time
+  }
+  return held + extra;
+}
+
+extern "C" int mueller_lu_tile_table(int* rest_hi, int* count_hi, int* tile, float* ms_per_matrix, int cap) {
+  if (cap < 0 || (cap > 0 && (!rest_hi || !count_hi || !tile || !ms_per_matrix))) return -1;
+  return lu_tile_table(rest_hi, count_hi, tile, ms_per_matrix, cap);
 }
 
 extern "C" size_t mueller_footprint_bytes(int N, int M) {

@@ -62,3 +62,31 @@ def test_worker_error_is_raised():
 
     with pytest.raises(RuntimeError):
         batch.run_batch(bodies, 10 ** 13, n_streams=2, process=bad)
+
+
+def test_wave_plan_covers_every_body_within_budget():
+    """Waves for build_many: every body in exactly one wave, largest first,
+    each wave's peak (the library's build_many_bytes) within the budget, and a
+    wave's peak between its largest member's build peak and the sum of the
+    members' build peaks."""
+    from paper_1810_07067_gb300 import build_many_bytes
+    sizes = [(1024, 96), (208, 32), (640, 64), (400, 40), (896, 120), (320, 48), (512, 32), (208, 128)]
+    bodies = _bodies(sizes)
+    peaks = [build_bytes(N, M, 1)[0] for N, M in sizes]
+    budget = int(1.6 * max(peaks))
+    plan = batch.plan_waves(bodies, budget, precision=1)
+    got = sorted(i for wave, _ in plan for i in wave)
+    assert got == list(range(len(sizes)))
+    assert plan[0][0][0] == max(range(len(sizes)), key=lambda i: peaks[i])
+    assert len(plan) < len(sizes)                     # bodies share waves
+    for wave, est in plan:
+        assert est == build_many_bytes([sizes[i][0] for i in wave], [sizes[i][1] for i in wave], 1)
+        assert est <= budget
+        assert max(peaks[i] for i in wave) <= est <= sum(peaks[i] for i in wave) + sum(
+            build_many_bytes([sizes[i][0]], [sizes[i][1]], 1) - peaks[i] for i in wave)
+
+
+def test_wave_plan_refuses_a_body_above_the_budget():
+    bodies = _bodies([(1024, 96), (208, 32)])
+    with pytest.raises(ValueError, match="budget"):
+        batch.plan_waves(bodies, build_bytes(1024, 96, 1)[0] // 2, precision=1)

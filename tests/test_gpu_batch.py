@@ -64,3 +64,85 @@ def test_batch_matches_bodies_alone(mb):
         assert np.array_equal(got[i], alone[i]), bodies[i].name
         assert r.backward_err <= 1e-14 and r.refine_iters >= 1
         assert r.resident_bytes <= r.peak_bytes
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wave_matches_bodies_alone(mb, precision):
+    """mueller_build_many factors all modes of several bodies of different
+    sizes in one graph-launched LU over a ragged table of matrices; with the
+    same LU tile each body's currents are bitwise those of its own build."""
+    bodies = _bodies()[:3] + _bodies()[4:5]          # N = 320, 160, 224 and a cylinder; M = 40, 16, 24, 20
+    opts = mb.Options(n_phi=16, precision=precision, lu_tile=64)
+
+    def solve(body, ctx):
+        n, nrhs = 4 * body.curve.N, len(body.waves)
+        rhs = torch.zeros((2 * body.M + 1, nrhs, n), dtype=torch.complex128, device=DEV)
+        ctx.rhs_planewave([w.d for w in body.waves], [w.e for w in body.waves], rhs)
+        x = torch.zeros_like(rhs)
+        be = np.zeros((2 * body.M + 1) * nrhs)
+        ctx.solve(rhs, x, backward_err=be)
+        return x.cpu().numpy(), be
+
+    alone = []
+    for b in bodies:
+        ctx = mb.build(b.curve, b.media, b.M, opts)
+        alone.append(solve(b, ctx))
+        assert ctx.stats()["lu_graph"] == 0
+        ctx.close()
+    ctxs = mb.build_many([(b.curve, b.media, b.M) for b in bodies], opts)
+    assert len(ctxs) == len(bodies)
+    for b, ctx, (xa, bea) in zip(bodies, ctxs, alone):
+        st = ctx.stats()
+        assert st["lu_graph"] == 1 and st["lu_wave_bodies"] == len(bodies)
+        if precision:
+            assert st["lu_tile_steps"][1] > 0 and st["lu_tile_steps"][0] == st["lu_tile_steps"][2] == 0
+        x, be = solve(b, ctx)
+        assert np.array_equal(x, xa), b.name
+        if precision:
+            assert be.max() <= 1e-14
+        ctx.close()
+
+
+def test_wave_bytes_bound_the_device_use(mb):
+    """The wave estimate covers what the contexts hold afterwards and at least
+    the largest single build's peak."""
+    bodies = _bodies()[:3]
+    est = mb.build_many_bytes([b.curve.N for b in bodies], [b.M for b in bodies], 1)
+    assert est >= max(mb.build_bytes(b.curve.N, b.M, 1)[0] for b in bodies)
+    ctxs = mb.build_many([(b.curve, b.media, b.M) for b in bodies], mb.Options(n_phi=16, precision=1))
+    held = sum(c.stats()["device_bytes"] for c in ctxs)
+    assert held <= est
+    for c in ctxs:
+        c.close()
+
+
+def test_waves_on_two_streams_match_bodies_alone(mb):
+    """run_waves: waves planned under half the budget each, two worker
+    streams admitted against the whole budget; with a fixed LU tile each
+    body's currents are bitwise those of its own build."""
+    from paper_1810_07067_gb300 import batch
+    bodies = _bodies()
+    alone = []
+    for body in bodies:
+        ctx = mb.build(body.curve, body.media, body.M, mb.Options(n_phi=body.n_phi, precision=1, lu_tile=64))
+        n, nrhs = 4 * body.curve.N, len(body.waves)
+        rhs = torch.zeros((2 * body.M + 1, nrhs, n), dtype=torch.complex128, device=DEV)
+        ctx.rhs_planewave([w.d for w in body.waves], [w.e for w in body.waves], rhs)
+        x = torch.zeros_like(rhs)
+        ctx.solve(rhs, x)
+        alone.append(x.cpu().numpy())
+        ctx.close()
+    got = {}
+
+    def check(i, body, ctx, x, stream):
+        stream.synchronize()
+        got[i] = x.cpu().numpy()
+        return {}
+
+    budget = 2 * mb.build_many_bytes([b.curve.N for b in bodies[:3]], [b.M for b in bodies[:3]], 1)
+    res, wall, plan, adm = batch.run_waves(bodies, budget, check=check, n_streams=2, lu_tile=64)
+    assert adm.high_water <= budget and adm.in_use == 0
+    assert len(plan) >= 2 and max(len(w) for w, _ in plan) >= 2
+    for i, r in enumerate(res):
+        assert np.array_equal(got[i], alone[i]), bodies[i].name
+        assert r.backward_err <= 1e-14 and r.extra["lu_graph"] == 1

@@ -63,6 +63,55 @@ def test_mixed_cylinder_full_size_vs_fp64(mb):
     assert _rel(a, r, M) < 1e-11
 
 
+@pytest.mark.parametrize("tile", [32, 64, 128])
+def test_mixed_lu_tiles(mb, tile):
+    """Each column tile of the tensor-core LU update (32, 64, 128 columns per
+    CTA) gives FP32-grade factors: refinement reaches 1e-14 in a few steps and
+    the currents agree with the FP64 path.  The body (N = 448, system 1792,
+    modes 0..12) spans 14 row tiles of 128 and a ragged last tile per step."""
+    body = W.random_body(28, seed=7)
+    media = W.Media.from_k(4.0, 6.0)
+    M, n = 12, 4 * body.N
+    waves = [W.paper_default_wave(), W.plane_wave([0.0, 0.0, 1.0], [1.0, 0.0, 0.0])]
+    c64 = mb.build(body, media, M, mb.Options(n_phi=64))
+    b = torch.zeros((2 * M + 1, len(waves), n), dtype=torch.complex128, device=DEV)
+    c64.rhs_planewave([w.d for w in waves], [w.e for w in waves], b)
+    x64 = torch.zeros_like(b)
+    c64.solve(b, x64)
+    c64.close()
+    cmx = mb.build(body, media, M, mb.Options(n_phi=64, precision=1, refine_tol=1e-14, lu_tile=tile))
+    st = cmx.stats()
+    q = {32: 0, 64: 1, 128: 2}[tile]
+    assert st["lu_tile_steps"][q] == sum(st["lu_tile_steps"]) == (n - 1) // 32
+    x = torch.zeros_like(b)
+    be = np.zeros((2 * M + 1) * len(waves))
+    cmx.solve(b, x, backward_err=be)
+    assert be.max() <= 1e-14 and cmx.stats()["refine_iters"] <= 3
+    assert _rel(x.cpu().numpy(), x64.cpu().numpy(), M) < 1e-11
+
+
+def test_tile_autotuner_table(mb):
+    """With lu_tile = 0 the update tile comes from the autotuner: every entry
+    holds measured times for the three tiles and keeps 64 unless another tile
+    was at least 3 % faster."""
+    body = W.random_body(28, seed=8)
+    ctx = mb.build(body, W.Media.from_k(4.0, 6.0), 12, mb.Options(n_phi=64, precision=1))
+    st = ctx.stats()
+    assert sum(st["lu_tile_steps"]) == (4 * body.N - 1) // 32
+    ctx.close()
+    table = mb.lu_tile_table()
+    assert table
+    for e in table:
+        t32, t64, t128 = e["ms_per_matrix"]
+        assert e["tile"] in (32, 64, 128)
+        if min(t32, t64, t128) > 0:
+            best = {32: t32, 64: t64, 128: t128}[e["tile"]]
+            if e["tile"] == 64:
+                assert t32 >= 0.97 * t64 and t128 >= 0.97 * t64
+            else:
+                assert best < 0.97 * t64
+
+
 def test_mixed_reports_no_convergence(mb):
     cur = W.sphere(2)
     med = W.Media.from_k(1.0, 1.5)
