@@ -123,9 +123,18 @@ __device__ __forceinline__ WarpSmem warp_smem(const GreenParams& gp, char* base)
 // The pair is the target (rt, zt) and the displacement (dr0, zd) = target - source.
 // Non-split pairs are sampled on every dec-th point of the n_phi grid
 // (dec = 1, 2, 4: a coarser grid for well-separated pairs, chosen so that the
-// trapezoid aliasing stays below the splitting threshold); split pairs use
-// the full grid.  The cosine transform folds samples j and n/2 - j (cos of
-// the mirrored angle is (-1)^m times the original), halving its work.
+// trapezoid aliasing stays below the splitting threshold) or, where it is
+// smaller still, on the compact grid of gp.nc points (returned as dec = 0);
+// split pairs use the full grid.  The cosine transform folds samples j and
+// n/2 - j (cos of the mirrored angle is (-1)^m times the original), halving
+// its work.
+//
+// Aliasing on an n-point grid: mode m <= M + 1 picks up the coefficients of
+// modes n - m and beyond, which decay like zeta^m (zeta = chi - sqrt(chi^2 - 1),
+// the singularity of 1/rho at cos phi = chi) once m exceeds the bandwidth of
+// the oscillating factor exp(i k rho), about |k| sqrt(r_t r_s).  The compact
+// grid is taken when (nc - M - 1 - K) ln(1/zeta) >= -ln(eps) with
+// K = 1.5 |k|max sqrt(r_t r_s) + 8, a margin over that bandwidth.
 __device__ int decimation(const GreenParams& gp, double rt, double dr0, double zd, bool split, double lneps) {
   if (split) return 1;
   const double d2 = dr0 * dr0 + zd * zd, B = 2.0 * rt * (rt - dr0);
@@ -137,15 +146,26 @@ __device__ int decimation(const GreenParams& gp, double rt, double dr0, double z
     if (nl < 16 || nl < 2 * gp.M + 4 || (double)(nl - gp.M - 1) * lz < lneps) break;
     dec *= 2;
   }
+  if (gp.nc > 0 && gp.nc < gp.nphi / dec) {
+    const double kmax = fmax(cabs(gp.kp0.k), cabs(gp.kp1.k));
+    const double K = 1.5 * kmax * sqrt(0.5 * B) + 8.0;
+    if ((double)(gp.nc - gp.M - 1) - K > 0.0 && ((double)(gp.nc - gp.M - 1) - K) * lz >= lneps) return 0;
+  }
   return dec;
 }
 
 __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
                                   long long sid, const double* __restrict__ leg, long long n_split,
                                   const double* __restrict__ cosT, const double* __restrict__ s2T,
-                                  const WarpSmem& W, int lane, int dec = 1) {
+                                  const WarpSmem& W, int lane, int dec = 1,
+                                  const double* __restrict__ cosC = nullptr, const double* __restrict__ s2C = nullptr) {
   const int Ms = gp.Ms, Mq = gp.Mq, mask = gp.nphi - 1;
-  const int nl = gp.nphi / dec;          // local grid size
+  const bool compact = dec == 0;
+  const int nl = compact ? gp.nc : gp.nphi / dec;  // local grid size
+  // local sample j sits at entry j * tstride of a table of T entries
+  const double* __restrict__ cosL = compact ? cosC : cosT;
+  const double* __restrict__ s2L = compact ? s2C : s2T;
+  const int T = compact ? gp.nc : gp.nphi, tstride = compact ? 1 : dec;
   const int H = nl / 2 + 1, Q = nl / 4;  // samples on [0, pi]; fold point
   const double rs = rt - dr0;
   const double d2 = dr0 * dr0 + zd * zd;
@@ -171,7 +191,7 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
   const cd g0 = gp.gamma0;
   const double kmin = fmin(cabs(gp.kp0.k), cabs(gp.kp1.k));
   for (int j = lane; j < H; j += 32) {
-    double s2 = s2T[j * dec];
+    double s2 = s2L[j * tstride];
     double u = d2 + 4.0 * rt * rs * s2;
     double su = sqrt(u);
     double rd = dr0 + 2.0 * rs * s2;
@@ -270,14 +290,18 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
     const int mm = it / 3, f0 = 3 * (it % 3);
     cd acc[3] = {C(0.0), C(0.0), C(0.0)};
     const bool odd = mm & 1;
+    const int step = (mm * tstride) % T;  // table index of cos(m phi_j) advances by step (mod T)
+    int idx = 0;
     for (int j = 0; j < Q; ++j) {
-      double c = cosT[(j * mm * dec) & mask];
+      double c = cosL[idx];
+      idx += step;
+      if (idx >= T) idx -= T;
       int jj = odd ? (H - 1 - j) : j;
 #pragma unroll
       for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + jj], acc[f]);
     }
     if (!odd) {  // centre sample j = n/4 pairs with itself (odd m: cos = 0)
-      double c = cosT[(Q * mm * dec) & mask];
+      double c = cosL[idx];
 #pragma unroll
       for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + Q], acc[f]);
     }
@@ -380,7 +404,7 @@ __global__ void far_kernel(BuildArgs a) {
     double rt = a.geo.r[i], rs = a.geo.r[j];
     const double dr0 = rt - rs, zd0 = a.geo.z[i] - a.geo.z[j];
     int dec = decimation(gp, rt, dr0, zd0, sid >= 0, a.lneps);
-    warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec);
+    warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec, a.cosC, a.s2C);
     const double w = a.geo.w[j], rps = a.geo.rp[j], zps = a.geo.zp[j];
     const double fac[3] = {w * rs * rps, w * rs, w * rs * zps};
     const cd* spec = W.spec;
@@ -436,7 +460,7 @@ __global__ void support_kernel(BuildArgs a) {
     if (slot < SELF_PTS) { dr0 = a.sup.dr[pid]; zd = a.sup.dz[pid]; }
     else { dr0 = rt - a.sup.r[pid]; zd = a.geo.z[i] - a.sup.z[pid]; }
     int dec = decimation(gp, rt, dr0, zd, sid >= 0, a.lneps);
-    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec);
+    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec, a.cosC, a.s2C);
     cd* dst = a.spec_sup + p * NFAM * gp.Ms;
     for (int t = lane; t < NFAM * gp.Ms; t += 32) dst[t] = W.spec[t];
     __syncwarp();
@@ -688,7 +712,7 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   cudaStream_t s = (cudaStream_t)stream;
   GreenParams gp{};
   cd K0{k0.re, k0.im}, K1{k1.re, k1.im};
-  gp.M = M; gp.Ms = Ms; gp.nphi = n_phi; gp.H = H; gp.Mq = Mq;
+  gp.M = M; gp.Ms = Ms; gp.nphi = n_phi; gp.H = H; gp.Mq = Mq; gp.nc = 0;
   gp.kp0 = kpow(K0); gp.kp1 = kpow(K1);
   gp.gamma0 = -0.25 * (K0 * K0 - K1 * K1);
   gp.k0_real = K0.y == 0.0; gp.k1_real = K1.y == 0.0;
