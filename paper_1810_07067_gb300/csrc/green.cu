@@ -326,6 +326,11 @@ __device__ __forceinline__ V2 operator-(V2 x, V2 y) { return v2(x.a - y.a, x.b -
 __device__ __forceinline__ V2 operator*(cd s, V2 x) { return v2(s * x.a, s * x.b); }
 __device__ __forceinline__ V2 operator*(double s, V2 x) { return v2(s * x.a, s * x.b); }
 
+// The block from the gathered coefficients c1, c2, c3 of the nine families.
+__device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
+                                                   const AsmParams& ap, double rt, double rpt, double zpt,
+                                                   cd out[4][4]);
+
 template <class Get>
 __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double rt, double rpt, double zpt,
                               cd out[4][4]) {
@@ -341,6 +346,32 @@ __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double r
     c2[f] = v2(mul_i(G3a), G2b);
     c3[f] = v2(R(2, f, a0), C(0.0));
   }
+  mueller_block_core(c1, c2, c3, m, ap, rt, rpt, zpt, out);
+}
+
+// The same block from one pair's unscaled spectra S[f * stride + (mode - base)]
+// and its three quadrature weights fac (sigma = 0, 1, 2): the weights multiply
+// the sums and differences of modes m +- 1 once instead of every term.
+__device__ __forceinline__ void mueller_block_spec(const cd* S, int stride, int base, const double fac[3], int m,
+                                                   const AsmParams& ap, double rt, double rpt, double zpt,
+                                                   cd out[4][4]) {
+  const int ap1 = m + 1 - base, am1 = ((m >= 1) ? m - 1 : 1) - base, a0 = m - base;
+  const double h0 = 0.5 * fac[0], h1 = 0.5 * fac[1];
+  V2 c1[NFAM], c2[NFAM], c3[NFAM];
+#pragma unroll
+  for (int f = 0; f < NFAM; ++f) {
+    const cd sp = S[f * stride + ap1], sm = S[f * stride + am1];
+    const cd sum = sp + sm, dif = sm - sp;
+    c1[f] = v2(h0 * sum, -mul_i(h1 * dif));
+    c2[f] = v2(mul_i(h0 * dif), h1 * sum);
+    c3[f] = v2(fac[2] * S[f * stride + a0], C(0.0));
+  }
+  mueller_block_core(c1, c2, c3, m, ap, rt, rpt, zpt, out);
+}
+
+__device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
+                                                   const AsmParams& ap, double rt, double rpt, double zpt,
+                                                   cd out[4][4]) {
   const double irt = 1.0 / rt, irt2 = irt * irt;
   const cd im = C(0.0, (double)m);
   const cd im_r = C(0.0, m * irt), im_r2 = C(0.0, m * irt2);
@@ -390,6 +421,12 @@ __device__ __forceinline__ bool near_panels(int Pi, int Pj, int nP, int closed) 
 
 // ---------------------------------------------------------------------------
 // Far panels: fused sampling, transform and assembly for one (i, j) pair per warp.
+// Modes 0..M are assembled one per lane.  When M + 1 leaves a partial last
+// round of tail = (M + 1) mod 32 modes (a.tq > 0), the tail modes are not
+// assembled with their pair: the pair's spectra of modes full - 1 .. M + 1 go
+// to a per-warp queue in global scratch, and once a.tq pairs are queued one
+// round assembles all their tail blocks (a.tq * tail <= 32 lanes busy instead
+// of tail lanes per pair).
 __global__ void far_kernel(BuildArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -397,7 +434,30 @@ __global__ void far_kernel(BuildArgs a) {
   WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
   const long long total = (long long)a.N * a.N;
   const int n = 4 * a.N;
-  for (long long p = (long long)blockIdx.x * wpb + wib; p < total; p += (long long)gridDim.x * wpb) {
+  const int tq = a.tq;
+  const int full = tq ? (gp.M + 1) / 32 * 32 : gp.M + 1;  // modes assembled with their pair
+  const int tail = gp.M + 1 - full, tw = tail + 2;         // queued modes, kept spectra per pair
+  const long long gw = (long long)blockIdx.x * wpb + wib;
+  cd* Qs = tq ? a.tailq + gw * (long long)tq * tw * NFAM : nullptr;
+  int* Qij = tq ? a.tailij + gw * 2LL * tq : nullptr;
+  int qn = 0;  // pairs in the queue (warp-uniform)
+  auto assemble = [&](const cd* S, int stride, int base, int i, int j, int m) {
+    const double rs = a.geo.r[j], w = a.geo.w[j];
+    const double fac[3] = {w * rs * a.geo.rp[j], w * rs, w * rs * a.geo.zp[j]};
+    cd blk[4][4];
+    mueller_block_spec(S, stride, base, fac, m, a.ap, a.geo.r[i], a.geo.rp[i], a.geo.zp[i], blk);
+    store_block(a.A, n, m, i, j, blk, a.geo.sw[i] / a.geo.sw[j]);
+  };
+  auto flush = [&]() {
+    __syncwarp();  // the queue's global writes are visible to the whole warp
+    for (int it = lane; it < qn * tail; it += 32) {
+      const int q = it / tail, m = full + it % tail;
+      assemble(Qs + (long long)q * tw * NFAM, tw, full - 1, Qij[2 * q], Qij[2 * q + 1], m);
+    }
+    __syncwarp();
+    qn = 0;
+  };
+  for (long long p = gw; p < total; p += (long long)gridDim.x * wpb) {
     int i = (int)(p / a.N), j = (int)(p % a.N);
     if (near_panels(i / P_NODES, j / P_NODES, a.n_panels, a.closed)) continue;
     long long sid = a.split_far[p];
@@ -405,19 +465,16 @@ __global__ void far_kernel(BuildArgs a) {
     const double dr0 = rt - rs, zd0 = a.geo.z[i] - a.geo.z[j];
     int dec = decimation(gp, rt, dr0, zd0, sid >= 0, a.lneps);
     warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec, a.cosC, a.s2C);
-    const double w = a.geo.w[j], rps = a.geo.rp[j], zps = a.geo.zp[j];
-    const double fac[3] = {w * rs * rps, w * rs, w * rs * zps};
-    const cd* spec = W.spec;
-    const int Ms = gp.Ms;
-    auto R = [&](int s, int f, int mm) { return fac[s] * spec[f * Ms + mm]; };
-    const double scale = a.geo.sw[i] / a.geo.sw[j];
-    for (int m = lane; m <= gp.M; m += 32) {
-      cd blk[4][4];
-      mueller_block(R, m, a.ap, rt, a.geo.rp[i], a.geo.zp[i], blk);
-      store_block(a.A, n, m, i, j, blk, scale);
+    for (int m = lane; m < full; m += 32) assemble(W.spec, gp.Ms, 0, i, j, m);
+    if (tq) {
+      cd* dst = Qs + (long long)qn * tw * NFAM;
+      for (int t = lane; t < NFAM * tw; t += 32) dst[t] = W.spec[(t / tw) * gp.Ms + full - 1 + t % tw];
+      if (lane == 0) { Qij[2 * qn] = i; Qij[2 * qn + 1] = j; }
+      if (++qn == tq) flush();
     }
     __syncwarp();
   }
+  if (tq && qn > 0) flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -583,6 +640,22 @@ static int grid_for(long long units, int wpb) {
   long long need = (units + wpb - 1) / wpb;
   long long cap = (long long)sms * 8;
   return (int)(need < cap ? need : cap);
+}
+
+// Tail queue of far_kernel: pairs per flush (0 = none) and its scratch, for
+// the launch shape launch_far_assembly uses.
+int far_tail_pairs(const GreenParams& gp) {
+  const int full = (gp.M + 1) / 32 * 32, tail = gp.M + 1 - full;
+  return (full >= 32 && tail > 0 && tail <= 16) ? 32 / tail : 0;
+}
+
+size_t far_tail_scratch(const BuildArgs& a, size_t* ij_elems) {
+  const int tq = far_tail_pairs(a.gp);
+  const int wpb = warps_per_block(a.gp);
+  const long long warps = (long long)grid_for((long long)a.N * a.N, wpb) * wpb;
+  const int tail = a.gp.M + 1 - (a.gp.M + 1) / 32 * 32;
+  *ij_elems = tq ? (size_t)warps * 2 * tq : 0;
+  return tq ? (size_t)warps * tq * (tail + 2) * NFAM : 0;
 }
 
 void launch_far_assembly(const BuildArgs& a, cudaStream_t s) {

@@ -64,6 +64,9 @@ struct BuildArgs {
   cd* A;                // [M+1][n][n] column-major per mode
   int kc;               // columns per CTA in the near contraction
   double lneps;         // -ln(split threshold): grid decimation criterion
+  int tq;               // far_kernel tail queue: pairs per flush (0 = none, see far_tail_pairs)
+  cd* tailq;            // its spectra scratch (far_tail_scratch elements)
+  int* tailij;          // its (target, source) scratch
 };
 
 // shared memory used by one warp of the pair-spectra routine (16-byte multiple)
@@ -78,6 +81,9 @@ __device__ void legendre_one(double rt, double dr, double dz, long long p, long 
 
 // host-side launchers (green.cu)
 void launch_legendre(const double* pairs, long long n_split, int Mq, int Ms, double* leg, cudaStream_t s);
+int far_tail_pairs(const GreenParams& gp);
+// elements of BuildArgs::tailq (return) and tailij (*ij_elems) for the launch of launch_far_assembly
+size_t far_tail_scratch(const BuildArgs& a, size_t* ij_elems);
 void launch_far_assembly(const BuildArgs& a, cudaStream_t s);
 void launch_support_spectra(const BuildArgs& a, cudaStream_t s);
 void launch_near_assembly(const BuildArgs& a, cudaStream_t s);

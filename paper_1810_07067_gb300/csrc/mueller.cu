@@ -474,6 +474,14 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   a.cosT = dcos; a.s2T = ds2; a.cosC = dcosC; a.s2C = ds2C; a.split_far = dsf; a.split_sup = dss; a.leg = dleg; a.n_split = n_split;
   a.spec_sup = dspec; a.A = A_dev;
   a.lneps = -std::log(S.split_eps);
+  a.tq = far_tail_pairs(S.gp);
+  a.tailq = nullptr; a.tailij = nullptr;
+  if (a.tq) {
+    size_t ij = 0;
+    const size_t q = far_tail_scratch(a, &ij);
+    if (tmp.alloc(&a.tailq, q) != cudaSuccess || tmp.alloc(&a.tailij, ij) != cudaSuccess)
+      return fail(MUELLER_ENOMEM, "far-pair tail queue scratch");
+  }
   int kc = 8;
   while (kc > 1 && kc * 3 * NFAM * Ms * 16 + SELF_PTS * kc * 3 * 8 > 200 * 1024) kc /= 2;
   a.kc = kc;
