@@ -268,6 +268,22 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
     W.smp[f * H + H - 1 - j] = a - b;
   }
   __syncwarp();
+  // second fold of the even-m sums E_j (j = 0..Q, E_Q the centre sample) at
+  // j <-> Q - j: cos(m phi_{Q-j}) = (-1)^{m/2} cos(m phi_j) for even m, so
+  // m = 0 mod 4 sums E_j + E_{Q-j} (kept at j) over j < Q/2 plus the centre
+  // E_{Q/2}, and m = 2 mod 4 sums E_j - E_{Q-j} (kept at Q - j) over j < Q/2
+  // (its centre cosine vanishes).  Needs Q even (grids of 8k points).
+  const int Q2 = Q / 2;
+  const bool fold2 = (Q & 1) == 0;
+  if (fold2) {
+    for (int t = lane; t < NFAM * Q2; t += 32) {
+      int f = t / Q2, j = t % Q2;
+      cd a = W.smp[f * H + j], b = W.smp[f * H + Q - j];
+      W.smp[f * H + j] = a + b;
+      W.smp[f * H + Q - j] = a - b;
+    }
+    __syncwarp();
+  }
   // cosine transform: spec_m = (1/n) sum_j w_j F_j cos(m phi_j) (the 4pi of G
   // is folded into the normalisation); the u^{-3/2} part is added exactly.
   const double inv = 1.0 / nl;
@@ -285,25 +301,35 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
   };
   const double* Shat = leg + (long long)(Mq + 1) * n_split;
   // one (mode, family triple) per lane and round: 3 (M+2) items keep the
-  // lanes busy where one mode per lane would leave most of the last round idle
+  // lanes busy where one mode per lane would leave most of the last round
+  // idle.  Items run odd modes first, then m = 2 mod 4, then m = 0 mod 4
+  // (with fold2), so that the lanes of a round mostly share a trip count.
+  const int n_odd = Ms / 2, n_2 = (Ms + 1) / 4;
   for (int it = lane; it < 3 * Ms; it += 32) {
-    const int mm = it / 3, f0 = 3 * (it % 3);
+    const int k = it / 3, f0 = 3 * (it % 3);
+    int mm, cls;  // cls 1: odd, 2: m = 2 mod 4, 0: m = 0 mod 4 (without fold2: 0 for every even m)
+    if (!fold2) { mm = k; cls = mm & 1; }
+    else if (k < n_odd) { mm = 2 * k + 1; cls = 1; }
+    else if (k < n_odd + n_2) { mm = 4 * (k - n_odd) + 2; cls = 2; }
+    else { mm = 4 * (k - n_odd - n_2); cls = 0; }
     cd acc[3] = {C(0.0), C(0.0), C(0.0)};
-    const bool odd = mm & 1;
+    const bool odd = cls == 1;
     const int step = (mm * tstride) % T;  // table index of cos(m phi_j) advances by step (mod T)
+    const int nj = odd ? Q : (fold2 ? Q2 : Q);
     int idx = 0;
-    for (int j = 0; j < Q; ++j) {
+    for (int j = 0; j < nj; ++j) {
       double c = cosL[idx];
       idx += step;
       if (idx >= T) idx -= T;
-      int jj = odd ? (H - 1 - j) : j;
+      int jj = odd ? (H - 1 - j) : (cls == 2 ? Q - j : j);
 #pragma unroll
       for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + jj], acc[f]);
     }
-    if (!odd) {  // centre sample j = n/4 pairs with itself (odd m: cos = 0)
+    if (cls == 0) {  // the centre sample (j = Q/2 after the second fold, else n/4) pairs with itself
       double c = cosL[idx];
+      const int jc = fold2 ? Q2 : Q;
 #pragma unroll
-      for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + Q], acc[f]);
+      for (int f = 0; f < 3; ++f) acc[f] = fma(c, W.smp[(f0 + f) * H + jc], acc[f]);
     }
     double Sm = split ? Shat[(long long)mm * n_split + sid] / FOUR_PI : 0.0;
 #pragma unroll

@@ -12,7 +12,7 @@ struct GreenParams {
   int nphi;    // azimuthal samples on [0, 2pi)
   int H;       // nphi/2 + 1 samples on [0, pi]
   int Mq;      // nphi/2 - 1: bandwidth of the Laplace coefficients
-  int nc;      // compact grid for well-separated pairs: the smallest multiple of 4
+  int nc;      // compact grid for well-separated pairs: the smallest multiple of 8
                // >= 2M + 4 (modes 0..M+1 stay distinct), 0 when not below nphi
   KPow kp0, kp1;
   cd gamma0;   // -(k0^2 - k1^2)/4

@@ -198,7 +198,7 @@ static void fill_green_params(GreenParams& gp, int M, int nphi, cd k0, cd k1) {
   gp.kp0 = kpow(k0); gp.kp1 = kpow(k1);
   gp.gamma0 = -0.25 * (k0 * k0 - k1 * k1);
   gp.k0_real = k0.y == 0.0; gp.k1_real = k1.y == 0.0;
-  gp.nc = (2 * M + 4 + 3) / 4 * 4;  // compact grid of the well-separated pairs
+  gp.nc = (2 * M + 4 + 7) / 8 * 8;  // compact grid of the well-separated pairs (8k: two folds)
   if (gp.nc >= nphi) gp.nc = 0;
 }
 
