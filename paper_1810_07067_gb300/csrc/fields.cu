@@ -5,19 +5,44 @@
 // ring at n_theta azimuths, then their Fourier coefficients for m = -M..M.
 // Fourier coefficients (1/n_theta) sum_t s_t e^{-i m theta_t} of the four ring
 // traces smp[n_theta][4] (twiddles tw[t] = e^{-2 pi i t/n_theta}), scaled by
-// sE (rows 0, 1) and sH (rows 2, 3): one (mode, row) per thread.
-__device__ void modal_dft(const cd* smp, const cd* tw, int n_theta, int M, int nrhs, int w, int i, int n, cd sE,
+// sE (rows 0, 1) and sH (rows 2, 3).  With n_theta = 2^L q (L <= 4), L
+// decimation-in-frequency stages first split each row into 2^L sub-sequences
+// of q samples (block bitrev(m mod 2^L) holds the terms of the modes of that
+// residue, twiddled), so each mode is a q-term sum instead of n_theta terms;
+// then one (mode, row) per thread.  Called by every thread of the CTA;
+// smp is overwritten.
+__device__ void modal_dft(cd* smp, const cd* tw, int n_theta, int M, int nrhs, int w, int i, int n, cd sE,
                           cd sH, cd* __restrict__ rhs) {
+  int L = 0;
+  while (L < 4 && ((n_theta >> L) & 1) == 0) ++L;
+  for (int st = 0, len = n_theta; st < L; ++st, len >>= 1) {
+    const int half = len >> 1, tstep = n_theta / len;
+    for (int item = threadIdx.x; item < 4 * (n_theta >> 1); item += blockDim.x) {
+      const int a = item & 3, bt = item >> 2;             // row, butterfly
+      const int blk = bt / half, t = bt % half;
+      const int i0 = blk * len + t, i1 = i0 + half;
+      const cd u = smp[4 * i0 + a], v = smp[4 * i1 + a];
+      smp[4 * i0 + a] = u + v;
+      smp[4 * i1 + a] = (u - v) * tw[t * tstep];
+    }
+    __syncthreads();
+  }
+  const int q = n_theta >> L, mask = (1 << L) - 1;
   const double inv = 1.0 / n_theta;
   for (int item = threadIdx.x; item < 4 * (2 * M + 1); item += blockDim.x) {
     const int mq = item >> 2, a = item & 3;
     const int m = mq - M;
     const int mm = ((m % n_theta) + n_theta) % n_theta;
+    const int r = mm & mask;
+    int blk = 0;
+    for (int bit = 0; bit < L; ++bit) blk |= ((r >> bit) & 1) << (L - 1 - bit);
+    const int step = (mm >> L) << L;  // twiddle index advance: (mm >> L) 2^L (mod n_theta)
+    const cd* x = smp + 4 * blk * q;
     cd acc = C(0.0);
     int idx = 0;
-    for (int t = 0; t < n_theta; ++t) {
-      acc = fma(smp[4 * t + a], tw[idx], acc);
-      idx += mm;
+    for (int t = 0; t < q; ++t) {
+      acc = fma(x[4 * t + a], tw[idx], acc);
+      idx += step;
       if (idx >= n_theta) idx -= n_theta;
     }
     rhs[((size_t)mq * nrhs + w) * n + 4 * i + a] = (a < 2 ? sE : sH) * (inv * acc);

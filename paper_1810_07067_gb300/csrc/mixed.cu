@@ -10,48 +10,57 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void convert_kernel(const cd* __restrict__ A, cf* __restrict__ B, size_t count) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    B[i] = to_cf(A[i]);
+// One pass over the complex128 matrices of the mixed path: the complex64
+// copy the LU factors, the infinity norm of every matrix (for the stopping
+// test) and, for the tensor-core residuals, every row's power-of-two scale
+// (the smallest 2^e with max(|Re a|, |Im a|) over the row below 2^e / 2;
+// 1 for empty rows and the padding rows n..npad-1).  32 rows x 8 column
+// slices per block: a warp reads 32 consecutive rows of one column.
+__device__ __forceinline__ double pow2_above_twice(double mx) {
+  if (!(mx > 0.0)) return 1.0;
+  int e;
+  frexp(mx, &e);             // mx = f 2^e, f in [1/2, 1)
+  return ldexp(1.0, e + 1);  // mx / scale < 1/2
 }
 
-void mixed_convert(const cd* A, cf* A32, size_t count, cudaStream_t s) {
-  convert_kernel<<<152 * 16, 256, 0, s>>>(A, A32, count);
-}
-
-// 32 rows x 8 column slices per block: each thread sums |a_ij| over its
-// slice of columns (a warp reads 32 consecutive rows of one column)
-__global__ void norm_inf_kernel(const cd* __restrict__ A, int n, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) row_pass_kernel(const cd* __restrict__ A, int n, int npad, cf* __restrict__ A32,
+                                                       double* __restrict__ normA, double* __restrict__ rowscale) {
   const int b = blockIdx.y;
-  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int slice = threadIdx.x >> 5;  // 0..7
-  const cd* M = A + (size_t)b * n * n;
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;  // slice 0..7
+  const int i = blockIdx.x * 32 + lane;
+  const cd* Mx = A + (size_t)b * n * n;
+  cf* My = A32 + (size_t)b * n * n;
   // |a| in FP32 (a norm for the stopping test needs no more), summed in FP64
-  double s = 0.0;
+  double s = 0.0, mx = 0.0;
   if (i < n) {
 #pragma unroll 4
     for (int j = slice; j < n; j += 8) {
-      const cd v = M[(size_t)j * n + i];
+      const cd v = Mx[(size_t)j * n + i];
+      My[(size_t)j * n + i] = to_cf(v);
       const float fx = fabsf((float)v.x), fy = fabsf((float)v.y);
       const float hi = fmaxf(fx, fy), lo = fminf(fx, fy);
       const float q = (hi > 0.f) ? lo / hi : 0.f;
       s += (double)(hi * sqrtf(1.f + q * q));
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
   }
-  __shared__ double part[8][32];
-  part[slice][threadIdx.x & 31] = s;
+  __shared__ double part[8][32], pmax[8][32];
+  part[slice][lane] = s;
+  pmax[slice][lane] = mx;
   __syncthreads();
   if (slice == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += part[q][threadIdx.x & 31];
+    double t = 0.0, m2 = 0.0;
+    for (int q = 0; q < 8; ++q) { t += part[q][lane]; m2 = fmax(m2, pmax[q][lane]); }
+    if (rowscale && i < npad) rowscale[(size_t)b * npad + i] = pow2_above_twice(m2);
     for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_pos(out + b, t);
+    if (lane == 0) atomic_max_pos(normA + b, t);
   }
 }
 
-void mixed_norm_inf(const cd* A, int n, int batch, double* out, cudaStream_t s) {
-  cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
-  norm_inf_kernel<<<dim3((n + 31) / 32, batch), 256, 0, s>>>(A, n, out);
+void mixed_prepare(const cd* A, int n, int batch, cf* A32, double* normA, double* rowscale, int npad, cudaStream_t s) {
+  cudaMemsetAsync(normA, 0, sizeof(double) * batch, s);
+  const int rows = rowscale ? npad : n;
+  row_pass_kernel<<<dim3((rows + 31) / 32, batch), 256, 0, s>>>(A, n, rowscale ? npad : n, A32, normA, rowscale);
 }
 
 // Vector kernels: grid.y strides over the (mode, right-hand side) vectors, so

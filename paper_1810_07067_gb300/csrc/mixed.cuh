@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 #include "cplx.cuh"
 
-void mixed_convert(const cd* A, cf* A32, size_t count, cudaStream_t s);
-// infinity norm of each weighted mode matrix (column-major n x n, batch of them)
-void mixed_norm_inf(const cd* A, int n, int batch, double* out, cudaStream_t s);
+// One pass over `batch` column-major n x n matrices: A32 = complex64 copy,
+// normA[b] = infinity norm of matrix b and, when rowscale is not null, the
+// power-of-two row scales of the tensor-core residuals for rows 0..npad-1
+// (rowscale[b * npad + i]; see ozaki_slice_matrix).
+void mixed_prepare(const cd* A, int n, int batch, cf* A32, double* normA, double* rowscale, int npad, cudaStream_t s);
 // bw = S b (physical -> weighted), infinity norm per vector into bnorm
 void mixed_scale(const cd* b, cd* bw, const double* sw, int n, long long nvec, double* bnorm, cudaStream_t s);
 // r = bw - A'_{+-m} y for all modes -M..M ([2M+1][nrhs][n]); infinity norm per vector into rnorm

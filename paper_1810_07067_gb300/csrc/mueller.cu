@@ -575,12 +575,11 @@ static int build_assemble(mueller_ctx* c, cudaStream_t s) {
   int rc = assemble_core(c->S, c->A, s, &c->st, c->keep, c->geo);
   if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
   if (c->S.precision != 0) {
-    mixed_norm_inf(c->A, (int)n, M + 1, c->normA, s);
-    mixed_convert(c->A, c->A32, (size_t)(M + 1) * n * n, s);
-    c->launches_pre += 2;
+    mixed_prepare(c->A, (int)n, M + 1, c->A32, c->normA, c->S.precision == 1 ? c->rowscale : nullptr, c->npad, s);
+    c->launches_pre += 1;
     if (c->S.precision == 1) {
       ozaki_slice_matrix(c->A, (int)n, c->npad, M + 1, c->Asl, c->rowscale, s);
-      c->launches_pre += 2;
+      c->launches_pre += 1;
     }
   }
   cudaEventRecord(e1, s);
@@ -865,8 +864,8 @@ extern "C" int mueller_solve(mueller_ctx* c, const mueller_c128* rhs_dev, int nr
   return MUELLER_OK;
 }
 
-static int n_theta_for(const Setup& S) {
-  return 2 * S.M + 2 * (int)std::ceil(cabs(S.k0) * S.rmax) + 64;
+static int n_theta_for(const Setup& S) {  // a multiple of 16: four transform stages in modal_dft
+  return (2 * S.M + 2 * (int)std::ceil(cabs(S.k0) * S.rmax) + 64 + 15) / 16 * 16;
 }
 
 extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const double* pols, int nrhs,

@@ -56,28 +56,31 @@ __device__ __forceinline__ double pow2_scale(double mx) {
   return ldexp(1.0, e + 1);    // |a| / scale < 1/2
 }
 
-// row maxima: thread per row, columns streamed
-__global__ void oz_rowscale_kernel(const cd* __restrict__ A, int n, int npad, double* __restrict__ rowscale) {
-  const int b = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npad) return;
-  double mx = 0.0;
-  if (i < n) {
-    const cd* M = A + (size_t)b * n * n;
-    for (int j = 0; j < n; ++j) {
-      cd v = M[(size_t)j * n + i];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-    }
+// thread per (row i, group of 8 consecutive k): 16 digit rows of 16 bytes.
+// The 16 values are held as fixed-point integers F = round(v 2^56) and
+// written in balanced base 128 from the least significant digit up, as in
+// digits(), on two 28-bit halves in 32-bit integer arithmetic:
+// d = ((F + 64) mod 128) - 64, F <- (F - d) / 128; the low half's carry joins
+// the high half, and the top digit ends in [-64, 64].  v = sum_s d_s 2^{-7(s+1)}
+// up to the rounding of F.
+__device__ __forceinline__ void digits28(long long F, int* d) {
+  int lo = (int)(F & 0xFFFFFFFll), hi = (int)(F >> 28);
+#pragma unroll
+  for (int s = OZ_S - 1; s >= OZ_S / 2; --s) {
+    const int dd = ((lo + 64) & 127) - 64;
+    d[s] = dd;
+    lo = (lo - dd) >> 7;
   }
-  rowscale[(size_t)b * npad + i] = pow2_scale(mx);
+  hi += lo;  // carry of the low half (0 or 1)
+#pragma unroll
+  for (int s = OZ_S / 2 - 1; s >= 1; --s) {
+    const int dd = ((hi + 64) & 127) - 64;
+    d[s] = dd;
+    hi = (hi - dd) >> 7;
+  }
+  d[0] = hi;
 }
 
-// thread per (row i, group of 8 consecutive k): 16 digit rows of 16 bytes.
-// The 16 values are held as fixed-point integers F = round(v 2^56) and their
-// balanced base-128 digits are taken from the top, one level at a time:
-// d = round-half-up(F / 2^(7 l)), F -= d 2^(7 l), for l = 7..1, then the last
-// digit is the remainder; every digit lies in [-64, 64] and
-// v = sum_s d_s 2^{-7(s+1)} up to the rounding of F.
 __global__ void __launch_bounds__(128) oz_slice_matrix_kernel(const cd* __restrict__ A, int n, int npad,
                                                               const double* __restrict__ rowscale,
                                                               __nv_bfloat16* __restrict__ Asl) {
@@ -87,42 +90,33 @@ __global__ void __launch_bounds__(128) oz_slice_matrix_kernel(const cd* __restri
   if (i >= npad) return;
   const int nrt = npad / OZ_RT, nkt = npad / OZ_KT;
   const double inv = 72057594037927936.0 / rowscale[(size_t)b * npad + i];  // 2^56 / scale
-  long long Fr[8], Fi[8];
+  int dr[8][OZ_S], di[8][OZ_S];
   const cd* M = A + (size_t)b * n * n;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     int k = kg * 8 + c;
     cd v = (i < n && k < n) ? M[(size_t)k * n + i] : C(0.0);
-    Fr[c] = __double2ll_rn(v.x * inv);
-    Fi[c] = __double2ll_rn(v.y * inv);
+    digits28(__double2ll_rn(v.x * inv), dr[c]);
+    digits28(__double2ll_rn(v.y * inv), di[c]);
   }
   const int rt = i / OZ_RT, r = i % OZ_RT, kt = (kg * 8) / OZ_KT, kk = (kg * 8) % OZ_KT;
   __nv_bfloat16* blk = Asl + (((size_t)b * nrt + rt) * nkt + kt) * OZ_ABLOCK;
   const int off = core_off(r, kk);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
-    const int sh = 7 * (OZ_S - 1 - s);
     __align__(16) __nv_bfloat16 re[8], im[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      long long dr = Fr[c], di = Fi[c];
-      if (sh > 0) {
-        dr = (Fr[c] + (1ll << (sh - 1))) >> sh;
-        di = (Fi[c] + (1ll << (sh - 1))) >> sh;
-        Fr[c] -= dr << sh;
-        Fi[c] -= di << sh;
-      }
-      re[c] = __float2bfloat16((float)dr);
-      im[c] = __float2bfloat16((float)di);
+      re[c] = __float2bfloat16((float)dr[c][s]);
+      im[c] = __float2bfloat16((float)di[c][s]);
     }
     *(uint4*)(blk + (0 * OZ_S + s) * OZ_ATILE + off) = *(uint4*)re;
     *(uint4*)(blk + (1 * OZ_S + s) * OZ_ATILE + off) = *(uint4*)im;
   }
 }
 
-void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* Asl, double* rowscale,
+void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* Asl, const double* rowscale,
                         cudaStream_t s) {
-  oz_rowscale_kernel<<<dim3((npad + 127) / 128, batch), 128, 0, s>>>(A, n, npad, rowscale);
   oz_slice_matrix_kernel<<<dim3((npad + 127) / 128, npad / 8, batch), 128, 0, s>>>(A, n, npad, rowscale, Asl);
 }
 

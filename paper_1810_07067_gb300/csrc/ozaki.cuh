@@ -15,8 +15,10 @@ size_t ozaki_matrix_slices_elems(int npad, int batch);  // bf16 elements
 size_t ozaki_vector_slices_elems(int npad, int batch, int njt);
 
 // Slices of the complex matrices A[batch][n][n] (column-major) for rows padded
-// to npad (multiple of 128); rowscale[batch][npad] = power-of-two row scales.
-void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* Asl, double* rowscale,
+// to npad (multiple of 128), given rowscale[batch][npad], the power-of-two
+// row scales (2^e with every |Re a|, |Im a| of the row below 2^e / 2; written
+// by mixed_prepare).
+void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* Asl, const double* rowscale,
                         cudaStream_t s);
 
 // r = b' - A'_{+-m} y for modes -M..M with the sliced matrices (see mixed.cu);
