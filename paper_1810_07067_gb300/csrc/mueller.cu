@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "mueller.h"
@@ -202,12 +203,36 @@ static void fill_green_params(GreenParams& gp, int M, int nphi, cd k0, cd k1) {
   if (gp.nc >= nphi) gp.nc = 0;
 }
 
-// split decision: plain trapezoid aliasing zeta^(nphi-M-1) above eps
-static bool needs_split(double rt, double dr, double dz, int nphi, int M, double eps) {
-  double d2 = dr * dr + dz * dz, B = 2.0 * rt * (rt - dr);
-  double cm1 = d2 / B, cp1 = 2.0 + cm1;
-  double lz = std::log1p(cm1 + std::sqrt(cm1 * cp1));
-  return (double)(nphi - M - 1) * lz < -std::log(eps);
+// Split decision: the plain trapezoid's aliasing zeta^(nphi-M-1) is above eps,
+// with zeta = e^{-l}, l = acosh(chi), chi = 1 + d^2 / (2 r_t r_s).  Since l
+// grows with chi, (nphi-M-1) l < -ln eps is chi - 1 < cosh(l_max) - 1 with
+// l_max = -ln(eps) / (nphi-M-1): a threshold on d^2 / (2 r_t r_s) fixed per build.
+struct SplitTest {
+  double cthr;  // cosh(l_max) - 1 = 2 sinh^2(l_max / 2); +inf when nphi <= M + 1
+  SplitTest(int nphi, int M, double eps) {
+    const int span = nphi - M - 1;
+    if (span <= 0) { cthr = HUGE_VAL; return; }
+    const double sh = std::sinh(0.5 * (-std::log(eps) / span));
+    cthr = 2.0 * sh * sh;
+  }
+  bool operator()(double rt, double dr, double dz) const {
+    const double d2 = dr * dr + dz * dz, B = 2.0 * rt * (rt - dr);
+    return d2 < cthr * B;
+  }
+};
+
+// Runs body(lo, hi) over [0, count) in contiguous chunks on up to 16 host threads.
+template <class F>
+static void parallel_chunks(int count, const F& body) {
+  const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const int nt = std::max(1, std::min(hw, count / 4));
+  if (nt == 1) { body(0, count); return; }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int lo = (int)((long long)count * t / nt), hi = (int)((long long)count * (t + 1) / nt);
+    th.emplace_back([&body, lo, hi] { body(lo, hi); });
+  }
+  for (auto& x : th) x.join();
 }
 
 static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M, const mueller_options* op,
@@ -304,7 +329,8 @@ static void setup_support(const mueller_curve* cv, Setup& S) {
   const size_t npts = (size_t)S.nP * PTS_PER_PANEL;
   S.sr.resize(npts); S.sz.resize(npts); S.srp.resize(npts); S.szp.resize(npts); S.sW.resize(npts);
   S.sdr.assign(npts, 0.0); S.sdz.assign(npts, 0.0);
-  for (int Q = 0; Q < S.nP; ++Q) {
+  parallel_chunks(S.nP, [&](int q_lo, int q_hi) {
+  for (int Q = q_lo; Q < q_hi; ++Q) {
     const double* r = cv->r + Q * P_NODES;
     const double* z = cv->z + Q * P_NODES;
     const double* dr = cv->dr + Q * P_NODES;
@@ -334,6 +360,7 @@ static void setup_support(const mueller_curve* cv, Setup& S) {
       }
     }
   }
+  });
 }
 
 static bool near_panels_h(int Pi, int Pj, int nP, int closed) {
@@ -356,36 +383,69 @@ static long long support_pid(const Setup& S, int i, int slot) {
   return (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + (slot - SELF_PTS - ADJ_PTS);
 }
 
+// Split pairs get ids in a fixed order: far pairs (i, j) row-major, then
+// support pairs (i, slot) row-major.  Rows are classified on host threads
+// (flags and per-row counts), then numbered from the prefix sums.
 static void setup_pairs(Setup& S) {
   const int N = S.N;
+  const SplitTest split(S.nphi, S.M, S.split_eps);
   S.split_far.assign((size_t)N * N, -1);
   S.split_sup.assign((size_t)N * NEAR_SLOTS, -1);
-  S.split_pairs.clear();
-  long long id = 0;
+  std::vector<long long> cnt_far(N + 1, 0), cnt_sup(N + 1, 0), nfar(N, 0), nsup(N, 0);
+  auto sup_disp = [&](int i, int slot, long long pid, double* dr, double* dz) {
+    if (slot < SELF_PTS) { *dr = S.sdr[pid]; *dz = S.sdz[pid]; }
+    else { *dr = S.r[i] - S.sr[pid]; *dz = S.z[i] - S.sz[pid]; }
+  };
+  parallel_chunks(N, [&](int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      long long cf = 0, cs = 0;
+      for (int j = 0; j < N; ++j) {
+        if (near_panels_h(i / P_NODES, j / P_NODES, S.nP, S.closed)) continue;
+        ++nfar[i];
+        if (split(S.r[i], S.r[i] - S.r[j], S.z[i] - S.z[j])) { S.split_far[(size_t)i * N + j] = 0; ++cf; }
+      }
+      for (int slot = 0; slot < NEAR_SLOTS; ++slot) {
+        long long pid = support_pid(S, i, slot);
+        if (pid < 0) continue;
+        ++nsup[i];
+        double dr, dz;
+        sup_disp(i, slot, pid, &dr, &dz);
+        if (split(S.r[i], dr, dz)) { S.split_sup[(size_t)i * NEAR_SLOTS + slot] = 0; ++cs; }
+      }
+      cnt_far[i + 1] = cf;
+      cnt_sup[i + 1] = cs;
+    }
+  });
+  for (int i = 0; i < N; ++i) cnt_far[i + 1] += cnt_far[i];
+  cnt_sup[0] = cnt_far[N];
+  for (int i = 0; i < N; ++i) cnt_sup[i + 1] += cnt_sup[i];
   S.n_far = 0; S.n_sup = 0;
-  for (int i = 0; i < N; ++i)
-    for (int j = 0; j < N; ++j) {
-      if (near_panels_h(i / P_NODES, j / P_NODES, S.nP, S.closed)) continue;
-      ++S.n_far;
-      double dr = S.r[i] - S.r[j], dz = S.z[i] - S.z[j];
-      if (needs_split(S.r[i], dr, dz, S.nphi, S.M, S.split_eps)) {
-        S.split_far[(size_t)i * N + j] = (int)id++;
-        S.split_pairs.insert(S.split_pairs.end(), {S.r[i], S.z[i], dr, dz});
+  for (int i = 0; i < N; ++i) { S.n_far += nfar[i]; S.n_sup += nsup[i]; }
+  S.split_pairs.assign((size_t)cnt_sup[N] * 4, 0.0);
+  parallel_chunks(N, [&](int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      long long id = cnt_far[i];
+      for (int j = 0; j < N; ++j) {
+        int& f = S.split_far[(size_t)i * N + j];
+        if (f < 0) continue;
+        f = (int)id;
+        const double v[4] = {S.r[i], S.z[i], S.r[i] - S.r[j], S.z[i] - S.z[j]};
+        std::copy(v, v + 4, &S.split_pairs[(size_t)id * 4]);
+        ++id;
+      }
+      id = cnt_sup[i];
+      for (int slot = 0; slot < NEAR_SLOTS; ++slot) {
+        int& f = S.split_sup[(size_t)i * NEAR_SLOTS + slot];
+        if (f < 0) continue;
+        f = (int)id;
+        double dr, dz;
+        sup_disp(i, slot, support_pid(S, i, slot), &dr, &dz);
+        const double v[4] = {S.r[i], S.z[i], dr, dz};
+        std::copy(v, v + 4, &S.split_pairs[(size_t)id * 4]);
+        ++id;
       }
     }
-  for (int i = 0; i < N; ++i)
-    for (int slot = 0; slot < NEAR_SLOTS; ++slot) {
-      long long pid = support_pid(S, i, slot);
-      if (pid < 0) continue;
-      ++S.n_sup;
-      double dr, dz;
-      if (slot < SELF_PTS) { dr = S.sdr[pid]; dz = S.sdz[pid]; }
-      else { dr = S.r[i] - S.sr[pid]; dz = S.z[i] - S.sz[pid]; }
-      if (needs_split(S.r[i], dr, dz, S.nphi, S.M, S.split_eps)) {
-        S.split_sup[(size_t)i * NEAR_SLOTS + slot] = (int)id++;
-        S.split_pairs.insert(S.split_pairs.end(), {S.r[i], S.z[i], dr, dz});
-      }
-    }
+  });
 }
 
 // ---------------------------------------------------------------- device staging
@@ -1052,11 +1112,12 @@ extern "C" int mueller_modal_kernels(const double* pairs_host, long long npairs,
   std::vector<int> sid(npairs, -1);
   std::vector<double> sp, vp(4 * npairs);
   long long ns = 0;
+  const SplitTest split(nphi, M, eps);
   for (long long p = 0; p < npairs; ++p) {
     const double* q = pairs_host + 4 * p;
     double* v = &vp[4 * p];
     v[0] = q[0]; v[1] = q[1]; v[2] = q[0] - q[2]; v[3] = q[1] - q[3];  // target, target - source
-    if (needs_split(v[0], v[2], v[3], nphi, M, eps)) {
+    if (split(v[0], v[2], v[3])) {
       sid[p] = (int)ns++;
       sp.insert(sp.end(), v, v + 4);
     }
