@@ -351,6 +351,10 @@ __device__ __forceinline__ V2 operator+(V2 x, V2 y) { return v2(x.a + y.a, x.b +
 __device__ __forceinline__ V2 operator-(V2 x, V2 y) { return v2(x.a - y.a, x.b - y.b); }
 __device__ __forceinline__ V2 operator*(cd s, V2 x) { return v2(s * x.a, s * x.b); }
 __device__ __forceinline__ V2 operator*(double s, V2 x) { return v2(s * x.a, s * x.b); }
+__device__ __forceinline__ V2 operator-(V2 x) { return v2(-x.a, -x.b); }
+// (i y) x for real y: two multiplies per complex entry instead of a complex product
+__device__ __forceinline__ cd iy(double y, cd a) { return cd{-y * a.y, y * a.x}; }
+__device__ __forceinline__ V2 iy(double y, V2 x) { return v2(iy(y, x.a), iy(y, x.b)); }
 
 // The block from the gathered coefficients c1, c2, c3 of the nine families.
 __device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
@@ -399,26 +403,25 @@ __device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, c
                                                    const AsmParams& ap, double rt, double rpt, double zpt,
                                                    cd out[4][4]) {
   const double irt = 1.0 / rt, irt2 = irt * irt;
-  const cd im = C(0.0, (double)m);
-  const cd im_r = C(0.0, m * irt), im_r2 = C(0.0, m * irt2);
+  const double mr = m * irt, mr2 = m * irt2;  // i m / r_t and i m / r_t^2 act as iy(mr, .), iy(mr2, .)
   V2 Nt[2], Nth[2];
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
     int g = kk, dr = 2 + 2 * kk, dz = 3 + 2 * kk;
     Nt[kk] = c1[dz] - c3[dr];
-    V2 t1 = c2[g] + rt * c2[dr] - im * c1[g];
-    V2 t2 = im_r * c3[g] - c2[dz];
-    Nth[kk] = C(-1.0) * ((zpt * irt) * t1 + rpt * t2);
+    V2 t1 = c2[g] + rt * c2[dr] - iy((double)m, c1[g]);
+    V2 t2 = iy(mr, c3[g]) - c2[dz];
+    Nth[kk] = -((zpt * irt) * t1 + rpt * t2);
   }
   V2 c1D = c1[0] - c1[1], c2D = c2[0] - c2[1];
   V2 c1rD = c1[2] - c1[4], c2rD = c2[2] - c2[4];
   V2 c1zD = c1[3] - c1[5], c2zD = c2[3] - c2[5], c3zD = c3[3] - c3[5];
-  V2 Kt = ap.k0sq * c2[0] - ap.k1sq * c2[1] + im_r2 * c1D + im_r * c1rD - (double(m) * m * irt2) * c2D +
-          im_r * c3zD;
-  V2 dPr = C(-irt2) * c1D + irt * c1rD + c1[6] - im_r2 * c2D + im_r * c2rD + c3[7];
-  V2 dPz = irt * c1zD + c1[7] + im_r * c2zD + c3[8];
-  V2 Kth = C(-1.0) * (rpt * (ap.k0sq * c1[0] - ap.k1sq * c1[1] + dPr) +
-                      zpt * (ap.k0sq * c3[0] - ap.k1sq * c3[1] + dPz));
+  V2 Kt = ap.k0sq * c2[0] - ap.k1sq * c2[1] + iy(mr2, c1D) + iy(mr, c1rD) - (double(m) * m * irt2) * c2D +
+          iy(mr, c3zD);
+  V2 dPr = (-irt2) * c1D + irt * c1rD + c1[6] - iy(mr2, c2D) + iy(mr, c2rD) + c3[7];
+  V2 dPz = irt * c1zD + c1[7] + iy(mr, c2zD) + c3[8];
+  V2 Kth = -(rpt * (ap.k0sq * c1[0] - ap.k1sq * c1[1] + dPr) +
+             zpt * (ap.k0sq * c3[0] - ap.k1sq * c3[1] + dPz));
   V2 EM_t = ap.cEM0 * Nt[0] + ap.cEM1 * Nt[1], EM_th = ap.cEM0 * Nth[0] + ap.cEM1 * Nth[1];
   V2 HJ_t = ap.cHJ0 * Nt[0] + ap.cHJ1 * Nt[1], HJ_th = ap.cHJ0 * Nth[0] + ap.cHJ1 * Nth[1];
   out[0][0] = ap.aEJ * Kt.a;  out[0][1] = ap.aEJ * Kt.b;  out[0][2] = EM_t.a;  out[0][3] = EM_t.b;

@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
                                                             int nrhs) {
   __shared__ TF Ls[SB][SB + 1];
   __shared__ TF Xs[SB][SGT];
-  extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation
+  extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation; then pv_s [n]
   const int m = blockIdx.x;
   const int job0 = blockIdx.y * SGT;
   const int njobs_all = (m == 0) ? nrhs : 2 * nrhs;
@@ -907,11 +907,12 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
     X[g] = x + ((size_t)q * nrhs + ri) * n;
   }
   // row interchanges (LAPACK order) composed into perm: (P b)[r] = b[perm[r]]
-  for (int r = tid; r < n; r += T) perm[r] = r;
+  int* pv_s = perm + n;  // the pivots staged in shared memory for the serial composition
+  for (int r = tid; r < n; r += T) { perm[r] = r; pv_s[r] = pv[r]; }
   __syncthreads();
   if (tid == 0) {
     for (int k = 0; k < n; ++k) {
-      int p = pv[k];
+      int p = pv_s[k];
       if (p != k) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
     }
   }
@@ -1015,26 +1016,31 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
   }
 }
 
-// Vectors per CTA: 8, or 32 when that still leaves two CTAs per SM (many
+// Vectors per CTA: 32 when that still leaves two CTAs per SM (many
 // right-hand sides: every group reads the whole factor, so wider groups read
-// it fewer times).
+// it fewer times), else 8 when that leaves four, else 4 (more CTAs hide the
+// latency of the per-block triangle steps; measured on the cylinder's 65
+// modes x 32 vectors: 4 vectors 53 ms, 8 vectors 63 ms, 2 vectors 75 ms for
+// the three correction solves with residuals).
+template <class TF, bool PHYS, int W>
+static void launch_solve_w(const TF* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
+                           int smem, cudaStream_t s) {
+  const int groups = (2 * nrhs + W - 1) / W;
+  cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  solve_blocked_kernel<TF, PHYS, W><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+}
+
 template <class TF, bool PHYS>
 static void launch_solve_blocked(const TF* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x,
                                  int nrhs, cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int smem = n * (int)sizeof(int);
-  const long long wide = (long long)(M + 1) * ((2 * nrhs + 31) / 32);
-  if (wide >= 2LL * sms) {
-    const int groups = (2 * nrhs + 31) / 32;
-    cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    solve_blocked_kernel<TF, PHYS, 32><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
-  } else {
-    const int groups = (2 * nrhs + SG - 1) / SG;
-    cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    solve_blocked_kernel<TF, PHYS, SG><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
-  }
+  const int smem = 2 * n * (int)sizeof(int);
+  const long long modes = M + 1;
+  if (modes * ((2 * nrhs + 31) / 32) >= 2LL * sms) launch_solve_w<TF, PHYS, 32>(LU, piv, n, M, sw, rhs, x, nrhs, smem, s);
+  else if (modes * ((2 * nrhs + SG - 1) / SG) >= 4LL * sms) launch_solve_w<TF, PHYS, SG>(LU, piv, n, M, sw, rhs, x, nrhs, smem, s);
+  else launch_solve_w<TF, PHYS, 4>(LU, piv, n, M, sw, rhs, x, nrhs, smem, s);
 }
 
 void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,

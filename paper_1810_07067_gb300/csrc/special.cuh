@@ -21,6 +21,8 @@ struct SeriesTables {
   double sig2[SPECIAL_NTERM];
   double phi2[SPECIAL_NTERM];
   double phi3[SPECIAL_NTERM];
+  double hsinc[SPECIAL_NTERM];  // sinc[p] / 4^p: sinc at x/2 as a series in x^2
+  double hsig1[SPECIAL_NTERM];  // sig1[p] / 4^p
 };
 
 // Fill the series tables on the host (exact rationals evaluated in double).
@@ -43,6 +45,8 @@ inline void fill_series_tables(SeriesTables* t) {
     t->sig2[p] = 2.0 * n2 * (2.0 * n2 - 2.0) * sg2 / fact[2 * n2 + 1];
     t->phi2[p] = sg2 * (n2 - 0.5) / fact[2 * n2];
     t->phi3[p] = sg2 * (n2 - 0.5) * (n2 - 1.0) / fact[2 * n2];
+    t->hsinc[p] = std::ldexp(t->sinc[p], -2 * p);  // exact: a power of two
+    t->hsig1[p] = std::ldexp(t->sig1[p], -2 * p);
   }
 }
 
@@ -110,9 +114,22 @@ HD Ent entire(const SeriesTables& T, const KPow& kp, double su) {
   double ax = cabs(x);
   SphFun fx, fh;
   cd cosx;
+  cd phi2, phi3;
   if (ax < 2.0) {
-    fx = sph_series(T, x2);
-    fh = sph_series(T, 0.25 * x2, false);
+    // the seven series in x^2 share one table of powers: per term one complex
+    // product for the power and a real-times-complex update per series
+    // (half-argument series from the coefficients scaled by 4^-p)
+    const int nt = series_terms(ax * ax);
+    cd P = C(1.0), s0 = C(0.0), s1 = C(0.0), s2 = C(0.0), h0 = C(0.0), h1 = C(0.0), p2 = C(0.0), p3 = C(0.0);
+    for (int p = 0; p < nt; ++p) {
+      s0 = fma(T.sinc[p], P, s0); s1 = fma(T.sig1[p], P, s1); s2 = fma(T.sig2[p], P, s2);
+      h0 = fma(T.hsinc[p], P, h0); h1 = fma(T.hsig1[p], P, h1);
+      p2 = fma(T.phi2[p], P, p2); p3 = fma(T.phi3[p], P, p3);
+      P = P * x2;
+    }
+    fx.sinc = s0; fx.sig1 = s1; fx.sig2 = s2;
+    fh.sinc = h0; fh.sig1 = h1; fh.sig2 = C(0.0);
+    phi2 = p2; phi3 = p3;
   } else {
     cd sh, chh;
     csincos(h, &sh, &chh);
@@ -124,12 +141,7 @@ HD Ent entire(const SeriesTables& T, const KPow& kp, double su) {
   }
   // cos x = 1 - 2 sin^2(x/2) = 1 - (x^2/2) sinc(x/2)^2  (stable for all x)
   cosx = C(1.0) - 0.5 * (x2 * (fh.sinc * fh.sinc));
-  cd phi2, phi3;
-  if (ax < 2.0) {
-    int nt = series_terms(ax * ax);
-    phi2 = horner(T.phi2, x2, nt);
-    phi3 = horner(T.phi3, x2, nt);
-  } else {
+  if (ax >= 2.0) {
     phi2 = (C(1.0) + fh.sinc * fh.sinc - 2.0 * fx.sinc) / (4.0 * x2);
     phi3 = (0.5 * (fh.sinc * fh.sig1) - 2.0 * fx.sig1) * 0.125;
   }
