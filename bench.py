@@ -171,6 +171,7 @@ def run_batched(args):
     bodies = W.config_batch()
     if args.bodies:
         bodies = bodies[:args.bodies]
+    mb.cache_limit(0)                                   # bodies of distinct sizes: nothing to reuse, keep the budget whole
     free, total = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * 1e9) if args.budget_gb > 0 else int(0.9 * free)
     small = sorted(bodies, key=lambda c: mb.build_bytes(c.N, c.M, 1)[0])[:max(args.warmup, 0)]
@@ -235,12 +236,14 @@ def run_serving(args):
     requests on the smallest body, untimed.  value = p99 latency."""
     import torch
     import workloads as W
+    import paper_1810_07067_gb300 as mb
     from paper_1810_07067_gb300 import serving
     if args.impl == "reference":
         print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no oracle timing "
                           "(the oracle is timed on the cylinder workload)"}))
         return
     pool = W.config_pool(32)
+    mb.cache_limit(0)                                   # the admission budget accounts for every device byte
     free, _ = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * 1e9) if args.budget_gb > 0 else int(0.9 * free)
     srv = serving.Server(pool, budget, precision=1, max_rhs=args.max_rhs, grid=(180, 360))

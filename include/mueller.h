@@ -300,6 +300,21 @@ int mueller_lu_tile_table(int* rest_hi, int* count_hi, int* tile, float* ms_per_
  * unit named by the serving workload (the GPU path stores M+1 of them). */
 size_t mueller_footprint_bytes(int N, int M);
 
+/* Device-memory cache.  Buffers of at least 64 MiB that a build, a solve or
+ * a destroyed context releases are kept by the library (per device, up to
+ * the cap) and reused for requests of the same size rounded up to 2 MiB, so
+ * repeated builds of similar bodies skip the driver's allocation and
+ * release of several GB each.  A release synchronizes the device first (as
+ * cudaFree does).  When an allocation fails, the cache is emptied and the
+ * allocation retried.  mueller_cache_limit sets the cap (default 32 GiB; 0
+ * disables caching) and returns the previous one; mueller_cache_trim returns
+ * every cached block to the driver; mueller_cache_bytes reports the bytes
+ * held.  Callers that budget device memory themselves should leave the cap
+ * as headroom or trim first. */
+void mueller_cache_trim(void);
+size_t mueller_cache_limit(size_t bytes);
+size_t mueller_cache_bytes(void);
+
 int mueller_stats_get(const mueller_ctx* ctx, mueller_stats* out);
 void mueller_destroy(mueller_ctx* ctx);
 const char* mueller_strerror(int status);

@@ -71,6 +71,12 @@ _lib.mueller_build_many_bytes.argtypes = [ct.c_int, ct.POINTER(ct.c_int), ct.POI
 _lib.mueller_build_many_bytes.restype = ct.c_size_t
 _lib.mueller_lu_tile_table.argtypes = [ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                        ct.POINTER(ct.c_float), ct.c_int]
+_lib.mueller_cache_trim.argtypes = []
+_lib.mueller_cache_trim.restype = None
+_lib.mueller_cache_limit.argtypes = [ct.c_size_t]
+_lib.mueller_cache_limit.restype = ct.c_size_t
+_lib.mueller_cache_bytes.argtypes = []
+_lib.mueller_cache_bytes.restype = ct.c_size_t
 _lib.mueller_assemble.argtypes = [ct.POINTER(_Curve), ct.POINTER(_Media), ct.c_int, ct.POINTER(_Options), _vp, _vp]
 _lib.mueller_solve.argtypes = [_vp, _vp, ct.c_int, _vp, ct.POINTER(ct.c_double), _vp]
 _lib.mueller_rhs_planewave.argtypes = [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int, _vp, _vp]
@@ -98,6 +104,7 @@ EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_pl
            "mueller_far_field", "mueller_far_field_grid", "mueller_eval",
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
            "mueller_build_many", "mueller_build_many_bytes", "mueller_lu_tile_table",
+           "mueller_cache_trim", "mueller_cache_limit", "mueller_cache_bytes",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
@@ -324,6 +331,20 @@ def build_bytes(N: int, M: int, precision: int) -> tuple[int, int]:
     res = ct.c_size_t(0)
     peak = int(_lib.mueller_build_bytes(int(N), int(M), int(precision), ct.byref(res)))
     return peak, int(res.value)
+
+
+def cache_trim() -> None:
+    """Return every cached device block to the driver (see mueller_cache_limit)."""
+    _lib.mueller_cache_trim()
+
+
+def cache_limit(nbytes: int) -> int:
+    """Cap on the library's cache of freed device blocks; returns the previous cap."""
+    return int(_lib.mueller_cache_limit(int(nbytes)))
+
+
+def cache_bytes() -> int:
+    return int(_lib.mueller_cache_bytes())
 
 
 def footprint_bytes(N: int, M: int) -> int:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -449,14 +450,114 @@ static void setup_pairs(Setup& S) {
 }
 
 // ---------------------------------------------------------------- device staging
+// Process-wide cache of freed device blocks.  Builds allocate and free
+// buffers of several GB (matrices, complex64 copies, residual slices, spectra
+// scratch), and mapping or unmapping one costs milliseconds; released blocks
+// of at least 64 MiB are kept, per device, up to a cap (32 GiB by default,
+// mueller_cache_limit) and handed out again for a request of the same size
+// (rounded up to 2 MiB).  Releasing synchronizes the device first, as
+// cudaFree does, so no kernel still uses a block when it is reused.  When an
+// allocation fails the cache is emptied and the allocation retried.
+namespace devcache {
+constexpr size_t kMinBlock = (size_t)64 << 20, kRound = (size_t)2 << 20;
+std::mutex mu;
+std::multimap<std::pair<int, size_t>, void*> blocks;  // (device, bytes) -> block
+size_t cached = 0, cap = (size_t)32 << 30;
+
+inline size_t rounded(size_t b) { return (b + kRound - 1) / kRound * kRound; }
+
+void trim() {
+  std::lock_guard<std::mutex> lk(mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& e : blocks) {
+    cudaSetDevice(e.first.first);
+    cudaFree(e.second);
+  }
+  cudaSetDevice(cur);
+  blocks.clear();
+  cached = 0;
+}
+
+size_t bytes_held() {
+  std::lock_guard<std::mutex> lk(mu);
+  return cached;
+}
+
+cudaError_t alloc(void** p, size_t bytes) {
+  const bool big = bytes >= kMinBlock;
+  const size_t req = big ? rounded(bytes) : bytes;
+  if (big) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = blocks.find({dev, req});
+    if (it != blocks.end()) {
+      *p = it->second;
+      blocks.erase(it);
+      cached -= req;
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMalloc(p, req);
+  if (e != cudaSuccess && bytes_held() > 0) {
+    cudaGetLastError();
+    trim();
+    e = cudaMalloc(p, req);
+  }
+  return e;
+}
+
+void release(void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes >= kMinBlock) {
+    const size_t req = rounded(bytes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> lk(mu);
+    if (cached + req <= cap) {
+      blocks.insert({{dev, req}, p});
+      cached += req;
+      return;
+    }
+  }
+  cudaFree(p);
+}
+}  // namespace devcache
+
+extern "C" void mueller_cache_trim(void) { devcache::trim(); }
+
+extern "C" size_t mueller_cache_limit(size_t bytes) {
+  size_t old;
+  {
+    std::lock_guard<std::mutex> lk(devcache::mu);
+    old = devcache::cap;
+    devcache::cap = bytes;
+  }
+  if (devcache::bytes_held() > bytes) devcache::trim();
+  return old;
+}
+
+extern "C" size_t mueller_cache_bytes(void) { return devcache::bytes_held(); }
+
 struct DevBuf {
-  std::vector<void*> ptrs;
-  ~DevBuf() { for (void* p : ptrs) cudaFree(p); }
+  std::vector<std::pair<void*, size_t>> ptrs;
+  ~DevBuf() { for (auto& e : ptrs) devcache::release(e.first, e.second); }
   template <class T>
   cudaError_t alloc(T** p, size_t count) {
-    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
-    if (e == cudaSuccess) ptrs.push_back(*p);
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = devcache::alloc((void**)p, bytes);
+    if (e == cudaSuccess) ptrs.push_back({*p, bytes});
     return e;
+  }
+  void release(void* p) {  // give one buffer back before the others
+    for (size_t k = 0; k < ptrs.size(); ++k)
+      if (ptrs[k].first == p) {
+        devcache::release(p, ptrs[k].second);
+        ptrs.erase(ptrs.begin() + k);
+        return;
+      }
   }
   template <class T>
   cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t s) {
@@ -610,6 +711,7 @@ static int build_prepare(const mueller_curve* curve, const mueller_media* media,
   c->bytes = (size_t)(M + 1) * n * n * (sizeof(cd) + (mixed ? sizeof(cf) : 0)) + slice_bytes;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
+  freeb += devcache::bytes_held();  // cached blocks are returned when an allocation needs the room
   if (c->bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
   if (c->keep.alloc(&c->A, (size_t)(M + 1) * n * n) != cudaSuccess ||
       c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess ||
@@ -650,8 +752,7 @@ static int build_assemble(mueller_ctx* c, cudaStream_t s) {
   if (err != cudaSuccess) return fail(MUELLER_ECUDA, cudaGetErrorString(err));
   c->st.ms_build = ms;
   if (c->S.precision == 1) {  // the residuals use the slices; the complex128 matrices are no longer needed
-    cudaFree(c->A);
-    c->keep.ptrs.erase(std::find(c->keep.ptrs.begin(), c->keep.ptrs.end(), (void*)c->A));
+    c->keep.release(c->A);
     c->A = nullptr;
     c->bytes -= (size_t)(M + 1) * n * n * sizeof(cd);
   }
