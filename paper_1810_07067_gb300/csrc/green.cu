@@ -34,8 +34,12 @@ void upload_series_tables(const SeriesTables& t) { cudaMemcpyToSymbol(c_tab, &t,
 // Laplace-type modal coefficients, one thread per split pair.
 // pairs: [n][4] = (r_t, z_t, r_t - r_s, z_t - z_s); leg: [(Mq+1)+Ms][n] index-major:
 // rows 0..Mq hold P^_n = P_n / sqrt(B), rows Mq+1.. hold S^_m = S_m / B^{3/2}.
+// rinv[k] = 1 / (2k + 1) for k < nr (shared memory): the recurrences divide by
+// odd integers at every step, and FP64 division costs several dependent
+// operations, so the quotients are multiplications by the table's entries.
 __device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms,
-                             double* __restrict__ leg) {
+                             double* __restrict__ leg, const double* rinv, int nr) {
+  auto inv_odd = [&](int k) { return k < nr ? rinv[k] : 1.0 / (2.0 * k + 1.0); };  // 1 / (2k + 1)
   double rs = rt - dr;
   double d2 = dr * dr + dz * dz, B = 2.0 * rt * rs;
   double c = d2 / B, cp1 = 2.0 + c;          // chi - 1, chi + 1
@@ -58,7 +62,7 @@ __device__ void legendre_one(double rt, double dr, double dz, long long p, long 
       if (m < Ms) Sv[(long long)m * n + p] = D;
       double Pn = P - D;                              // P_m
       Pv[(long long)m * n + p] = Pn;
-      D = ((2.0 * m - 1.0) * D - 4.0 * m * c * Pn) / (2.0 * m + 1.0);  // D_{m+1}
+      D = ((2.0 * m - 1.0) * D - 4.0 * m * c * Pn) * inv_odd(m);  // D_{m+1}
       P = Pn;
     }
   } else {
@@ -69,7 +73,7 @@ __device__ void legendre_one(double rt, double dr, double dz, long long p, long 
       double Pm = Pn + Dn;
       if (m <= Mq) Pv[(long long)m * n + p] = Pm;
       if (m >= 1) {
-        double Dm = ((2.0 * m + 1.0) * Dn + 4.0 * m * c * Pm) / (2.0 * m - 1.0);
+        double Dm = ((2.0 * m + 1.0) * Dn + 4.0 * m * c * Pm) * inv_odd(m - 1);
         if (m < Ms) Sv[(long long)m * n + p] = Dm;
         Pn = Pm; Dn = Dm;
       }
@@ -81,24 +85,41 @@ __device__ void legendre_one(double rt, double dr, double dz, long long p, long 
   // S_m = (1 - 2m)(chi P_m - P_{m-1})/(chi^2 - 1) = (2m - 1)(D_m - c P_m)/(c (c + 2))
   double isB = 1.0 / sqrt(B), isB3 = isB * isB * isB;
   Sv[p] = 4.0 * E / (c * sqrt(cp1)) * isB3;
+  const double sfac = isB3 / (c * cp1);
   for (int m = 1; m < Ms; ++m) {
     double D = Sv[(long long)m * n + p], P = Pv[(long long)m * n + p];
-    Sv[(long long)m * n + p] = (2.0 * m - 1.0) * (D - c * P) / (c * cp1) * isB3;
+    Sv[(long long)m * n + p] = (2.0 * m - 1.0) * (D - c * P) * sfac;
   }
   for (int m = 0; m <= Mq; ++m) Pv[(long long)m * n + p] *= isB;
 }
 
+// Entries of the reciprocal table: the largest index either recurrence reaches
+// (the Miller start Mq + ceil(19.6 / ln(1/zeta)) + 2 with ln(1/zeta) above
+// ln(32) / (2 Mq) on that branch), capped at 96 KiB of shared memory.
+static int legendre_table_entries(int Mq) {
+  const long long need = (long long)Mq + (long long)(19.6 * 2.0 * Mq / 3.4657359027997265) + 4;
+  return (int)std::min<long long>(need, 96 * 1024 / 8);
+}
+
+__device__ __forceinline__ void fill_odd_reciprocals(double* rinv, int nr) {
+  for (int k = threadIdx.x; k < nr; k += blockDim.x) rinv[k] = 1.0 / (2.0 * k + 1.0);
+  __syncthreads();
+}
+
 __global__ void legendre_kernel(const double* __restrict__ pairs, long long n, int Mq, int Ms,
-                                double* __restrict__ leg) {
+                                double* __restrict__ leg, int nr) {
+  extern __shared__ double rinv[];
+  fill_odd_reciprocals(rinv, nr);
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= n) return;
-  legendre_one(pairs[4 * p], pairs[4 * p + 2], pairs[4 * p + 3], p, n, Mq, Ms, leg);
+  legendre_one(pairs[4 * p], pairs[4 * p + 2], pairs[4 * p + 3], p, n, Mq, Ms, leg, rinv, nr);
 }
 
 void launch_legendre(const double* pairs, long long n, int Mq, int Ms, double* leg, cudaStream_t s) {
   if (n <= 0) return;
-  int tpb = 128;
-  legendre_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, s>>>(pairs, n, Mq, Ms, leg);
+  const int tpb = 128, nr = legendre_table_entries(Mq);
+  cudaFuncSetAttribute(legendre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, nr * 8);
+  legendre_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, nr * 8, s>>>(pairs, n, Mq, Ms, leg, nr);
 }
 
 // ---------------------------------------------------------------------------
@@ -759,10 +780,12 @@ __global__ void noalloc_prep_kernel(const double* __restrict__ pairs, long long 
 }
 
 __global__ void noalloc_legendre_kernel(const double* __restrict__ disp, const int* __restrict__ sid, long long n,
-                                        int Mq, int Ms, double* __restrict__ leg) {
+                                        int Mq, int Ms, double* __restrict__ leg, int nr) {
+  extern __shared__ double rinv[];
+  fill_odd_reciprocals(rinv, nr);
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= n || sid[p] < 0) return;
-  legendre_one(disp[4 * p], disp[4 * p + 2], disp[4 * p + 3], p, n, Mq, Ms, leg);
+  legendre_one(disp[4 * p], disp[4 * p + 2], disp[4 * p + 3], p, n, Mq, Ms, leg, rinv, nr);
 }
 
 static int noalloc_fail(const char* msg, int code = MUELLER_EINVAL) {
@@ -822,7 +845,9 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   noalloc_tables_kernel<<<(n_phi + 255) / 256, 256, 0, s>>>(n_phi, cosT, s2T);
   unsigned blocks = (unsigned)((npairs + 127) / 128);
   noalloc_prep_kernel<<<blocks, 128, 0, s>>>(pairs_dev, npairs, n_phi, M, -log(eps), disp, sid);
-  noalloc_legendre_kernel<<<blocks, 128, 0, s>>>(disp, sid, npairs, Mq, Ms, leg);
+  const int nr = legendre_table_entries(Mq);
+  cudaFuncSetAttribute(noalloc_legendre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, nr * 8);
+  noalloc_legendre_kernel<<<blocks, 128, nr * 8, s>>>(disp, sid, npairs, Mq, Ms, leg, nr);
   launch_pair_spectra(gp, disp, sid, leg, npairs, npairs, cosT, s2T, (cd*)out_dev, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(cudaGetErrorString(e), MUELLER_ECUDA);
