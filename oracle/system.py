@@ -70,11 +70,15 @@ def panel_support(curve, target_panel: int, target_local: int, Q: int):
     if Q == target_panel:
         tau, wt = gauss.self_rule(target_local)
     else:
-        nxt = target_panel + 1 if target_panel + 1 < nP else (0 if curve.closed else None)
-        prv = target_panel - 1 if target_panel - 1 >= 0 else (nP - 1 if curve.closed else None)
-        if Q == nxt and nP > 2:
+        # panels sharing an endpoint with the target's panel take the near
+        # rule (Section 5); a closed curve also wraps around, which needs at
+        # least 3 panels for the two neighbours to be distinct
+        wrap = curve.closed and nP > 2
+        nxt = target_panel + 1 if target_panel + 1 < nP else (0 if wrap else None)
+        prv = target_panel - 1 if target_panel - 1 >= 0 else (nP - 1 if wrap else None)
+        if Q == nxt:
             tau, wt = gauss.adjacent_rule(-1)
-        elif Q == prv and nP > 2:
+        elif Q == prv:
             tau, wt = gauss.adjacent_rule(+1)
         else:
             return None

@@ -215,6 +215,31 @@ def test_mie_far_field(sphere_oracle):
         assert np.linalg.norm(Ef[w_i] - Em) / np.linalg.norm(Em) < 1e-12
 
 
+def test_mie_far_field_two_panels():
+    """Two panels meeting at the equator share an endpoint, so each is the
+    other's adjacent panel and takes the near-singular rule (Section 5): the
+    whole oracle on this 2 x 16-node sphere still matches the Mie series.
+    With plain Gauss-Legendre on the neighbour instead, the far field is off
+    by about 2e-6; with the near rule it agrees to about 3e-15."""
+    cur = W.sphere(2)
+    med = W.Media.from_k(1.0, 1.5)
+    M = 8
+    wv = W.PlaneWave(np.array([0.6, 0.0, 0.8]), np.array([0.8, 0.0, -0.6]))
+    A = system.assemble(cur, med, M)
+    b = fields.modal_rhs(cur, med, M, [wv])
+    sw = system.l2_weights(cur)
+    Aw = system.weight_matrix(A, sw)
+    x = np.zeros_like(b)
+    for q in range(2 * M + 1):
+        LU, piv = linalg.lu_factor(Aw[q])
+        x[q] = linalg.lu_solve(LU, piv, b[q] * sw[:, None]) / sw[:, None]
+    th = np.linspace(0.1, np.pi - 0.1, 7)
+    dirs = np.array([[math.sin(t), 0.0, math.cos(t)] for t in th])
+    Ef = fields.far_field(cur, med, M, x, dirs)[0]
+    Em = mie.far_field(1.0, 1.5, 1.0, wv.d, wv.e, dirs)
+    assert np.linalg.norm(Ef - Em) / np.linalg.norm(Em) < 1e-8
+
+
 def test_mie_against_rayleigh_limit():
     """Mie amplitudes for a small sphere reduce to the Rayleigh dipole:
     S1 = -i x^3 (m^2-1)/(m^2+2), S2 = S1 cos(Theta) to leading order."""
