@@ -39,7 +39,7 @@ def _dist():
 # DRAM bytes per (far pair, mode) of far_kernel, from one ncu capture
 # (profiles/far_kernel_random_N256_M32.md); the launch writes the pairs' 4x4
 # blocks of every mode.
-FAR_TRAFFIC_PER_PAIR_MODE = 402.8e6 / (53760 * 33)
+FAR_TRAFFIC_PER_PAIR_MODE = 424.7e6 / (53760 * 33)
 
 
 def reduce_max(values, dist=None, device="cpu"):
@@ -490,7 +490,7 @@ def main():
                              "frac": far_tflops / FP64_PEAK_TFLOPS,
                              "traffic": st["n_far_pairs"] * (M + 1) * FAR_TRAFFIC_PER_PAIR_MODE,
                              "traffic_source": "ncu dram__bytes_read+write of one far_kernel launch on the "
-                                               "N=256, M=32 body (402.8 MB / (53760 far pairs x 33 modes)), "
+                                               "N=256, M=32 body (424.7 MB / (53760 far pairs x 33 modes)), "
                                                "scaled by far pairs x modes",
                              "algorithmic_flops_per_far_pair": per_pair,
                              "peak_source": "nominal FP64 of the profiling recipe (no FP64 entry in "
