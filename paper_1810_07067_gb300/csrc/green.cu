@@ -578,7 +578,7 @@ __global__ void support_kernel(BuildArgs a) {
 // Near panels: R_k(sigma, f, m) = sum_s W_s L_k(tau_s) sigma_s F_f(s, m)
 // (eqs. eq_nyslike, eq_nyslike2 with sum_j U_jk P_j = L_k), then the blocks of
 // the panel's columns k.  One CTA per (target, near panel, chunk of kc columns).
-__global__ void near_kernel(BuildArgs a) {
+__global__ void __launch_bounds__(384) near_kernel(BuildArgs a) {
   extern __shared__ __align__(16) char smem[];
   const GreenParams& gp = a.gp;
   const int kc = a.kc, nchunk = P_NODES / kc;
@@ -722,10 +722,16 @@ void launch_support_spectra(const BuildArgs& a, cudaStream_t s) {
   support_kernel<<<grid_for((long long)a.N * NEAR_SLOTS, wpb), wpb * 32, smem, s>>>(a);
 }
 
+// Threads per CTA: the fewest rounds (at most 384 threads) over the larger
+// of the contraction's NFAM (M+2) items and the kc (M+1) blocks, so that the
+// last round is not nearly empty (one CTA per SM: its shared memory).
 void launch_near_assembly(const BuildArgs& a, cudaStream_t s) {
   int smem = a.kc * 3 * NFAM * a.gp.Ms * 16 + SELF_PTS * a.kc * 3 * 8;
+  const int items = std::max(NFAM * a.gp.Ms, a.kc * (a.gp.M + 1));
+  const int rounds = (items + 383) / 384;
+  const int threads = std::min(384, ((items + rounds - 1) / rounds + 31) / 32 * 32);
   cudaFuncSetAttribute(near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  near_kernel<<<a.N * 3 * (P_NODES / a.kc), 256, smem, s>>>(a);
+  near_kernel<<<a.N * 3 * (P_NODES / a.kc), threads, smem, s>>>(a);
 }
 
 void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* sidx, const double* leg,
