@@ -24,6 +24,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+
+def _log_dir() -> str:
+    """Directory for the clock-sample CSV files (BENCH_LOG_DIR, else the temp dir)."""
+    import tempfile
+    d = os.environ.get("BENCH_LOG_DIR") or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
 import numpy as np  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table); DFMA loop measured 1.19
@@ -185,7 +194,7 @@ def run_batched(args):
 
     one_pass(small)
     torch.cuda.synchronize()
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    clk_path = os.path.join(_log_dir(),
                             "clocks_batched.csv")
     sampler = _clock_sampler(clk_path)
     time.sleep(0.3)
@@ -254,7 +263,7 @@ def run_serving(args):
     srv.close()
     reqs = serving.poisson_requests(len(pool), args.rate, args.duration, seed=5, zipf=args.zipf,
                                     max_rhs=args.max_rhs)
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    clk_path = os.path.join(_log_dir(),
                             "clocks_serving.csv")
     sampler = _clock_sampler(clk_path)
     torch.cuda.synchronize()
@@ -423,7 +432,7 @@ def main():
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    clk_path = os.path.join(_log_dir(),
                             f"clocks_rank{rank}.csv")
     sampler = _clock_sampler(clk_path)
     time.sleep(0.3)
