@@ -63,3 +63,18 @@ def test_build_rejects_bad_inputs_before_device_work(lib):
         mb.build(bad, W.Media.from_k(1.0, 1.5), 2, stream=0)
     with pytest.raises(mb.MuellerError, match="FP64"):
         mb.build(cur, W.Media.from_k(1.0, 1.5), 2, mb.Options(precision=7), stream=0)
+    with pytest.raises(mb.MuellerError, match="lu_tile"):
+        mb.build(cur, W.Media.from_k(1.0, 1.5), 2, mb.Options(precision=1, lu_tile=48), stream=0)
+
+
+def test_build_many_rejects_bad_inputs_before_device_work(lib):
+    """Wave builds check the count and every body on the host first."""
+    import paper_1810_07067_gb300 as mb
+    import workloads as W
+    cur = W.sphere(2)
+    with pytest.raises(mb.MuellerError, match="count"):
+        mb.build_many([], stream=0)
+    with pytest.raises(mb.MuellerError, match="omega"):
+        mb.build_many([(cur, W.Media(omega=0.0), 2), (cur, W.Media.from_k(1.0, 1.5), 2)], stream=0)
+    assert mb.build_many_bytes([64, 32], [10, 4], 1) >= max(mb.build_bytes(64, 10, 1)[0], mb.build_bytes(32, 4, 1)[0])
+    assert mb.build_many_bytes([], [], 1) == 0
