@@ -2,12 +2,17 @@
 
 One step = mueller_build (modal Green's functions, assembly and LU of modes
 0..M) + mueller_rhs_planewave (modal incident data) + mueller_solve for all
-plane waves of the workload.  Default workload:
-finite cylinder radius 1, height 2, edge-graded panels (N = 576 nodes, system
-2304 x 2304 complex128 per mode), modes -64..64, 256 azimuthal samples,
-k0 = 5, k1 = 7.5 + 0.01i, 8 incidence angles x 2 polarisations.
+plane waves of the workload.  Default workload: the smooth random body
+r = sin t (1 + sum_{j<=6} a_j cos jt), z = -cos t, a_j ~ U(-0.08, 0.08) from
+default_rng(1810), 64 panels (N = 1024 nodes, system 4096 x 4096 complex128
+per mode), modes -128..128, 512 azimuthal samples, k0 = 10, k1 = 15, two
+plane waves.  The headline value is the mixed path (complex64 LU + FP64
+refinement); the FP64 path is timed beside it, and both are compared with
+the oracle's stored solution of the same body (per-mode current errors and
+the far field).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--workload random|cylinder|sphere|small|batched|serving|tables]
 Under torchrun each rank solves its own copy of the body (weak scaling).
 """
 from __future__ import annotations
@@ -35,20 +40,11 @@ def _log_dir() -> str:
 
 import numpy as np  # noqa: E402
 
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table); DFMA loop measured 1.19
-
-
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-# DRAM bytes per (far pair, mode) of far_kernel, from one ncu capture
-# (profiles/far_kernel_random_N256_M32.md); the launch writes the pairs' 4x4
-# blocks of every mode.
-FAR_TRAFFIC_PER_PAIR_MODE = 424.7e6 / (53760 * 33)
 
 
 def reduce_max(values, dist=None, device="cpu"):
@@ -97,48 +93,114 @@ def _clock_summary(path, gpu_index):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons)}
 
 
-def _oracle_baseline(cfg, budget_s=25.0):
-    """The oracle (as it stands) on a bounded sample of the workload, scaled to
-    one step: assembly of two target rows for all 2M+1 modes, one naive LU of
-    a full-size mode matrix (the sample's time scales by N rows and 2M+1 modes)."""
-    from oracle import system, linalg
-    N, M, n = cfg.N, cfg.M, 4 * cfg.N
-    rows = [N // 6, N // 2]
+def _workload(name):
+    import workloads as W
+    if name == "random":
+        return W.config_random()
+    if name == "cylinder":
+        return W.config_cylinder(7)
+    if name == "sphere":
+        return W.config_sphere()
+    if name == "small":
+        return W.config_random(16, 1810, 32, 128)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _oracle_pool_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+
+
+def _oracle_rows(args):
+    """Worker: the oracle assembles the given target rows (all 2M+1 modes)."""
+    name, rows = args
+    from oracle import system
+    cfg = _workload(name)
+    geo = system.node_geometry(cfg.curve)
     t0 = time.perf_counter()
-    system.assemble(cfg.curve, cfg.media, M, rows=rows)
-    t_rows = (time.perf_counter() - t0) / len(rows)
-    rng = np.random.default_rng(0)
+    for i in rows:
+        system.assemble_row(cfg.curve, cfg.media, cfg.M, int(i), 0, None, geo)
+    return time.perf_counter() - t0
+
+
+def _oracle_lu_steps(args):
+    """Worker: the first k elimination steps of the oracle's naive LU on a
+    full-size matrix (the oracle's LU restarted on the leading steps only)."""
+    n, k, seed = args
+    from oracle import linalg
+    rng = np.random.default_rng(seed)
     A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + n * np.eye(n)
     t0 = time.perf_counter()
-    LU, piv = linalg.lu_factor(A)
-    t_lu = time.perf_counter() - t0
-    b = rng.standard_normal((n, len(cfg.waves))) + 0j
-    t0 = time.perf_counter()
-    linalg.lu_solve(LU, piv, b)
-    t_solve = time.perf_counter() - t0
-    total = t_rows * N + (t_lu + t_solve) * (2 * M + 1)
-    sample = (f"oracle assembly of {len(rows)} of {N} target rows (all {2 * M + 1} modes) and one naive LU + "
-              f"{len(cfg.waves)}-rhs solve of a {n}x{n} mode; scaled by {N} rows and {2 * M + 1} modes")
-    return total, sample, time.perf_counter()
+    linalg.lu_factor(A, steps=k)
+    return time.perf_counter() - t0
+
+
+def _lu_fraction(n, k):
+    """Share of the naive LU's work (sum over steps j of (n - j - 1)^2) in its first k steps."""
+    j = np.arange(n, dtype=np.float64)
+    w = (n - j - 1) ** 2
+    return float(w[:k].sum() / w.sum())
+
+
+class OracleBaseline:
+    """The oracle (as it stands) on the host cores, on a bounded sample of the
+    workload, projected to one step: every worker assembles `rows` target rows
+    (all 2M+1 modes) and runs the first `lu_steps` steps of one full-size
+    naive LU, all workers at once; the step is N rows and 2M+1 LUs spread over
+    the same workers."""
+
+    def __init__(self, name, cores=None):
+        import multiprocessing as mp
+        self.name = name
+        self.cfg = _workload(name)
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_pool_init)
+        self.pool.map(_oracle_rows, [(name, []) for _ in range(self.cores)])   # imports done before timing
+
+    def sample(self, budget_s):
+        cfg, P = self.cfg, self.cores
+        N, M, n = cfg.N, cfg.M, 4 * cfg.N
+        rows = np.linspace(0, N - 1, P).astype(int)
+        # workers run at once; the slowest one's compute time is the sample's wall time
+        t_row = max(self.pool.map(_oracle_rows, [(self.name, [int(r)]) for r in rows]))
+        if getattr(self, "k", None) is None:            # elimination steps that fill about half the budget
+            t8 = max(self.pool.map(_oracle_lu_steps, [(n, 8, s) for s in range(P)]))
+            self.k = int(max(8, min(n, 8 * 0.5 * budget_s / max(t8, 1e-3))))
+        k = self.k
+        t_lu = max(self.pool.map(_oracle_lu_steps, [(n, k, s) for s in range(P)]))
+        frac = _lu_fraction(n, k)
+        value = t_row * N / P + (t_lu / frac) * (2 * M + 1) / P
+        sample = (f"projection from a sample: {P} host processes each assembled 1 of {N} target rows (all "
+                  f"{2 * M + 1} modes; {t_row:.2f} s wall) and ran the first {k} of {n} steps of the naive LU of "
+                  f"a {n}x{n} matrix ({t_lu:.2f} s wall, {100 * frac:.2f}% of its work); step = {N} rows + "
+                  f"{2 * M + 1} LUs over {P} processes")
+        return value, sample
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
 
 
 def run_reference(args, cfg):
     ws, rank, _ = _dist()
     if rank != 0:
         return
+    ob = OracleBaseline(args.workload)
+    budget = max(2.0, min(25.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        ob.sample(budget)
     vals = []
     sample = ""
-    for _ in range(args.warmup_ref):
-        pass
-    for _ in range(max(1, args.steps_ref)):
-        v, sample, _ = _oracle_baseline(cfg)
+    for _ in range(max(1, args.steps)):
+        v, sample = ob.sample(budget)
         vals.append(v)
+    ob.close()
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": len(vals), "warmup": 0, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "steps": len(vals), "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": _config(cfg),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": ob.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -150,15 +212,100 @@ METRIC = ("modal assemble+solve time (mueller_build + mueller_solve) at backward
 def _config(cfg):
     if cfg.name.startswith("cylinder"):
         body = "finite cylinder R=1 H=2, edge-graded panels"
+    elif cfg.name.startswith("sphere"):
+        body = "dielectric unit sphere"
     else:
-        body = "smooth random body r = sin t (1 + sum a_j cos jt)"
+        body = "smooth random body r = sin t (1 + sum_{j<=6} a_j cos jt), a_j ~ U(-0.08, 0.08)"
     k0 = cfg.media.omega
     k1 = k0 * complex(cfg.media.eps1) ** 0.5
     fb = 16 * (4 * cfg.N) ** 2 * (cfg.M + 1) / 1e9
     return {"workload": f"{cfg.name}: {body}, N={cfg.N} nodes (system {4 * cfg.N}x{4 * cfg.N} c128 per mode), "
                         f"modes -{cfg.M}..{cfg.M}, n_phi={cfg.n_phi}, k0={k0:g}, k1={k1:.4g}, "
                         f"{len(cfg.waves)} plane waves",
-            "precision": "fp64", "l2_flush": f"inputs larger than L2 ({fb:.2g} GB of factors per step)"}
+            "precision": "mixed", "l2_flush": f"inputs larger than L2 ({fb:.2g} GB of matrices per step)"}
+
+
+def _golden(cfg, name):
+    """The oracle's stored full-size solution of this workload (written by
+    tests/golden/make_fullsize.py), if it exists and describes the same body."""
+    path = os.path.join(ROOT, "tests", "golden", f"fullsize_{name}.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    if g["r"].shape != cfg.curve.r.shape or int(g["M"]) != cfg.M:
+        return None
+    if max(np.abs(g["r"] - cfg.curve.r).max(), np.abs(g["z"] - cfg.curve.z).max()) > 1e-13:
+        return None
+    return g
+
+
+def _errors_vs_oracle(ctx, x, g, M, dev):
+    """Per stored mode: relative l2 error of the currents (max over the stored
+    waves), and the relative l2 error of the far field of the stored modes'
+    currents at the stored directions."""
+    import torch
+    modes, waves = [int(m) for m in g["modes"]], [int(w) for w in g["waves"]]
+    xg = x.cpu().numpy()
+    per_mode = {}
+    for qi, m in enumerate(modes):
+        e = max(np.linalg.norm(xg[m + M, w] - g["x"][qi, wi]) / np.linalg.norm(g["x"][qi, wi])
+                for wi, w in enumerate(waves))
+        per_mode[str(m)] = float(e)
+    keep = torch.zeros_like(x)
+    for m in [int(v) for v in g["solved_modes"]]:
+        keep[m + M] = x[m + M]
+    dirs = torch.tensor(g["ff_dirs"], device=dev)
+    E = torch.zeros((x.shape[1], len(dirs), 3), dtype=torch.complex128, device=dev)
+    ctx.far_field(keep, dirs, E)
+    Eg = E.cpu().numpy()
+    ff = float(np.linalg.norm(Eg - g["ff"]) / np.linalg.norm(g["ff"]))
+    return {"currents_rel_l2_per_mode": per_mode, "currents_rel_l2_max": max(per_mode.values()),
+            "far_field_rel_l2": ff,
+            "far_field_modes": "all" if len(g["solved_modes"]) == 2 * M + 1 else
+            [int(v) for v in g["solved_modes"]]}
+
+
+def _kernel_rooflines(st, M, N, fp64_peak, hbm_peak):
+    """Per kernel: device time (ms) from the build's CUDA events and the
+    algorithmic work it stands for.
+
+    FP64 stages (kernel evaluation and assembly), per pair:
+      far_kernel      9 FFT-class transforms 9 * 2.5 n log2 n, sampling
+                      (n/2 + 1) * 140 flops (both wavenumbers), assembly
+                      256 flops per mode, n = n_phi;
+      support_kernel  the same without assembly, plus 6 convolution
+                      transforms 6 * 2.5 n log2 n for split pairs;
+      near_kernel     the rule contraction, 4 flops per (support point,
+                      column, family x weight, mode), and 16 x 3 blocks of
+                      256 flops per mode for every target;
+      legendre_kernel 10 flops per recurrence step, n/2 steps per split pair.
+    LU trailing update (mixed path): read + write of the trailing complex64
+    matrix per step, 16 bytes per entry (HBM bound)."""
+    nphi = st["n_phi_used"]
+    fft = 2.5 * nphi * math.log2(nphi)
+    samp = (nphi // 2 + 1) * 140
+    out = {}
+    far = st["n_far_pairs"] * (9 * fft + samp + 256 * (M + 1))
+    out["far_kernel"] = (st["ms_far"], far, "alu")
+    n_split = st["n_split_pairs"]
+    sup = st["n_support_pairs"] * (9 * fft + samp) + 6 * fft * min(n_split, st["n_support_pairs"])
+    out["support_kernel"] = (st["ms_support"], sup, "alu")
+    near = st["n_support_pairs"] * 16 * 27 * 4 * (M + 2) + N * 48 * (M + 1) * 256
+    out["near_kernel"] = (st["ms_near"], near, "alu")
+    out["legendre_kernel"] = (st["ms_legendre"], n_split * 10 * (nphi // 2), "alu")
+    res = {}
+    for k, (ms, work, bound) in out.items():
+        if ms <= 0:
+            continue
+        ach = work / (ms * 1e-3) / 1e12
+        res[k] = {"ms": ms, "bound": bound, "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                  "frac": ach / fp64_peak, "algorithmic_flops": work}
+    if st.get("ms_lu_gemm", 0) > 0 and st.get("lu_gemm_bytes", 0) > 0:
+        ach = st["lu_gemm_bytes"] / (st["ms_lu_gemm"] * 1e-3) / 1e9
+        res["gemm_update_tc_kernel"] = {"ms": st["ms_lu_gemm"], "bound": "hbm", "achieved": ach,
+                                        "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                                        "algorithmic_bytes": st["lu_gemm_bytes"]}
+    return res
 
 
 def run_batched(args):
@@ -355,48 +502,10 @@ def run_tables(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "small", "batched", "serving", "tables"],
-                    help="small: random smooth body N=256, M=32 (profiling captures); batched: the 72-body "
-                         "batch under a memory budget; serving: Poisson request stream with a factor cache")
-    ap.add_argument("--bodies", type=int, default=0, help="batched: only the first K bodies (0 = all)")
-    ap.add_argument("--streams", type=int, default=2, help="batched: concurrent bodies (CUDA streams)")
-    ap.add_argument("--schedule", default="waves", choices=["waves", "streams"],
-                    help="batched: waves = bodies grouped under the budget, each wave's modes factored in one "
-                         "graph-launched LU (build_many); streams = one body per concurrent stream")
-    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
-    ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window in seconds")
-    ap.add_argument("--zipf", type=float, default=1.1, help="serving: body choice Zipf exponent (0 = uniform)")
-    ap.add_argument("--max-rhs", type=int, default=256, help="serving: right-hand sides per request at most")
-    ap.add_argument("--drain", type=float, default=120.0, help="serving: seconds after the last arrival to finish")
-    ap.add_argument("--budget-gb", type=float, default=0.0,
-                    help="batched/serving: device-memory budget (0 = 90%% of the free memory)")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                    help="path timed for the headline value (the other path is timed once beside it)")
-    args = ap.parse_args()
-    args.steps_ref = args.steps
-    args.warmup_ref = args.warmup
-    import workloads as W
-    if args.workload == "batched":
-        run_batched(args)
-        return
-    if args.workload == "serving":
-        run_serving(args)
-        return
-    if args.workload == "tables":
-        run_tables(args)
-        return
-    cfg = W.config_cylinder(7) if args.workload == "cylinder" else W.config_random(16, 1810, 32, 128)
-    if args.impl == "reference":
-        run_reference(args, cfg)
-        return
-
+def run_single(args, cfg):
+    """One body per rank: build (assembly + LU of modes 0..M) + plane-wave
+    data + solve of all waves, mixed path timed over args.steps steps (the
+    headline value), the FP64 path over args.fp64_steps steps beside it."""
     import torch
     import paper_1810_07067_gb300 as mb
     ws, rank, local = _dist()
@@ -406,41 +515,41 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    # the oracle's worker pool starts (spawn) before the first GPU call
+    ob = OracleBaseline(args.workload) if (ws == 1 and not args.no_cpu_baseline) else None
     stream = torch.cuda.current_stream(dev)
     M, n = cfg.M, 4 * cfg.N
     nrhs = len(cfg.waves)
     dirs = np.array([w.d for w in cfg.waves]); pols = np.array([w.e for w in cfg.waves])
-    prec = 1 if args.precision == "mixed" else 0
-    opts = mb.Options(n_phi=cfg.n_phi, precision=prec, refine_tol=1e-14)
-    opts_other = mb.Options(n_phi=cfg.n_phi, precision=1 - prec, refine_tol=1e-14)
+    opts = {1: mb.Options(n_phi=cfg.n_phi, precision=1, refine_tol=1e-14),
+            0: mb.Options(n_phi=cfg.n_phi, precision=0)}
     rhs = torch.zeros((2 * M + 1, nrhs, n), dtype=torch.complex128, device=dev)
     x = torch.zeros_like(rhs)
-    ctx0 = mb.build(cfg.curve, cfg.media, M, opts)
-    ctx0.rhs_planewave(dirs, pols, rhs)
-    ctx0.close()
 
-    def step(o=opts, out=x):
-        ctx = mb.build(cfg.curve, cfg.media, M, o)
+    def step(prec, out=x, keep=False):
+        ctx = mb.build(cfg.curve, cfg.media, M, opts[prec])
         ctx.rhs_planewave(dirs, pols, rhs)
         ctx.solve(rhs, out)
         st = ctx.stats()
+        if keep:
+            return st, ctx
         ctx.close()
         return st
 
+    fp64_peak = mb.fp64_peak()
     for _ in range(args.warmup):
-        step()
+        step(1)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    clk_path = os.path.join(_log_dir(),
-                            f"clocks_rank{rank}.csv")
+    clk_path = os.path.join(_log_dir(), f"clocks_rank{rank}.csv")
     sampler = _clock_sampler(clk_path)
     time.sleep(0.3)
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed_step")            # lets a profiler select the timed launches
     e0.record(stream)
-    stats = [step() for _ in range(args.steps)]
+    stats = [step(1) for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
@@ -453,83 +562,155 @@ def main():
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx = mb.build(cfg.curve, cfg.media, M, opts)
+        ctx = mb.build(cfg.curve, cfg.media, M, opts[1])
         ctx.rhs_planewave(dirs, pols, rhs)
         ctx.solve(rhs, x)
         x_host.copy_(x, non_blocking=True)
         torch.cuda.synchronize(dev)
         ctx.close()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    # the other path once, same inputs: time and agreement of the currents
-    x_other = torch.zeros_like(x)
-    ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    st_other = step(opts_other, x_other)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    other_s = ev0.elapsed_time(ev1) / 1e3
-    num = max(float((x[q] - x_other[q]).norm()) for q in range(2 * M + 1))
-    den = max(float(x_other[q].norm()) for q in range(2 * M + 1))
+    # the FP64 path on the same inputs: one untimed warm-up, then fp64_steps timed steps
+    x64 = torch.zeros_like(x)
+    fp64 = None
+    if args.fp64_steps > 0:
+        step(0, x64)
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st64 = [step(0, x64) for _ in range(args.fp64_steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64 = {"s": ev0.elapsed_time(ev1) / 1e3 / args.fp64_steps, "steps": args.fp64_steps, "warmup": 1,
+                "stages_ms": {k: round(st64[-1][k], 3) for k in
+                              ("ms_legendre", "ms_far", "ms_support", "ms_near", "ms_lu", "ms_lu_gemm", "ms_solve")},
+                "lu_trailing_update_tflops": st64[-1]["lu_gemm_flops"] / (st64[-1]["ms_lu_gemm"] * 1e-3) / 1e12
+                if st64[-1]["ms_lu_gemm"] > 0 else None}
     if sampler:
         sampler.terminate()
         sampler.wait()
     clocks = _clock_summary(clk_path, local)
+    # accuracy, untimed: both paths against the oracle's stored solution
+    accuracy = None
+    g = _golden(cfg, args.workload)
+    if g is not None:
+        accuracy = {}
+        for prec, name in ((1, "mixed"), (0, "fp64")):
+            if prec == 0 and args.fp64_steps <= 0:
+                continue
+            xx = torch.zeros_like(x)
+            _, ctx = step(prec, xx, keep=True)
+            accuracy[name] = _errors_vs_oracle(ctx, xx, g, M, dev)
+            ctx.close()
+        accuracy["oracle"] = {"modes": [int(v) for v in g["modes"]], "waves": [int(v) for v in g["waves"]],
+                              "solved_modes": len(g["solved_modes"]),
+                              "oracle_backward_err_max": float(np.max(g["backward_err"])),
+                              "source": "tests/golden/fullsize_%s.npz (oracle only)" % args.workload}
+    num = den = None
+    if fp64 is not None:
+        num = max(float((x[q] - x64[q]).norm()) for q in range(2 * M + 1))
+        den = max(float(x64[q].norm()) for q in range(2 * M + 1))
     dev_s, e2e_s = reduce_max([dev_s, e2e_s], dist, dev)
     if rank == 0:
         st = stats[-1]
         launches = st["launches"] + st["solve_launches"] + 1  # + rhs_kernel
-        # dominant kernel: far_kernel (FP64 pipe).  Algorithmic flops per far
-        # pair: 9 FFT-based cosine transforms 9 * 2.5 n_phi log2 n_phi, sampling
-        # (n_phi/2 + 1) * 140 (both wavenumbers), assembly 256 per mode.
-        nphi = st["n_phi_used"]
-        per_pair = 9 * 2.5 * nphi * math.log2(nphi) + (nphi // 2 + 1) * 140 + 256 * (M + 1)
-        far_tflops = st["n_far_pairs"] * per_pair / (st["ms_far"] * 1e-3) / 1e12
+        hbm = _measured_peaks().get("hbm_gbs", 6790.3)
+        kr = _kernel_rooflines(st, M, cfg.N, fp64_peak, hbm)
+        top = max(kr, key=lambda k: kr[k]["ms"])
+        roof = dict(kr[top], kernel=top)
+        roof["peak_source"] = ("measured live: DFMA register loop (mueller_fp64_peak)" if roof["bound"] == "alu"
+                               else "MEASURED_PEAKS.json hbm_gbs")
+        roof["traffic"] = None
+        roof["traffic_note"] = "per-launch DRAM bytes: profiles/ (ncu captures of this kernel)"
         h2d = 8 * 4 * cfg.N + 8 * 6 * nrhs
         d2h = 16 * (2 * M + 1) * nrhs * n
         line = {"metric": METRIC, "value": dev_s, "unit": "s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dev_s * 1e3, "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)", "data": "synthetic",
-                "config": dict(_config(cfg), precision=args.precision),
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64 LU + c128 (fp64) refinement", "data": "synthetic",
+                "config": _config(cfg),
                 "bodies_per_s": job_throughput(ws, dev_s),
                 "stages_ms": {k: round(st[k], 3) for k in ("ms_legendre", "ms_far", "ms_support", "ms_near",
                                                            "ms_lu", "ms_lu_gemm", "ms_solve")},
-                "roofline": {"bound": "alu", "kernel": "far_kernel (far pairs: sampling, cosine transform, "
-                                                       "assembly; FP64)",
-                             "achieved": far_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": far_tflops / FP64_PEAK_TFLOPS,
-                             "traffic": st["n_far_pairs"] * (M + 1) * FAR_TRAFFIC_PER_PAIR_MODE,
-                             "traffic_source": "ncu dram__bytes_read+write of one far_kernel launch on the "
-                                               "N=256, M=32 body (424.7 MB / (53760 far pairs x 33 modes)), "
-                                               "scaled by far pairs x modes",
-                             "algorithmic_flops_per_far_pair": per_pair,
-                             "peak_source": "nominal FP64 of the profiling recipe (no FP64 entry in "
-                                            "MEASURED_PEAKS.json); a DFMA register loop measured 1.19"},
-                "lu_trailing_update": {"tflops": st["lu_gemm_flops"] / (st["ms_lu_gemm"] * 1e-3) / 1e12,
+                "roofline": roof,
+                "kernels": kr,
+                "fp64_peak_tflops_measured": fp64_peak,
+                "lu_trailing_update": {"tflops": st["lu_gemm_flops"] / (st["ms_lu_gemm"] * 1e-3) / 1e12
+                                       if st["ms_lu_gemm"] > 0 else None,
                                        "ms": st["ms_lu_gemm"],
-                                       "arith": ("complex64 as exact 3-piece split BF16 on tcgen05, FP32 "
-                                                 "accumulation" if prec else "complex128 DFMA"),
-                                       "tile_steps_32_64_128": st["lu_tile_steps"] if prec else None,
-                                       "tile_table": mb.lu_tile_table() if prec else None},
+                                       "arith": "complex64 as exact 3-piece split BF16 on tcgen05, FP32 accumulation",
+                                       "tile_steps_32_64_128": st["lu_tile_steps"]},
                 "refine_iters": st["refine_iters"], "backward_err_max": st["backward_err_max"],
                 "tensor_core_residual": ({"ms": st["ms_residual"], "launches": st["residual_launches"],
                                           "bf16_tflops": st["residual_tc_flops"] / (st["ms_residual"] * 1e-3) / 1e12,
-                                          "peak_bf16_tflops": 1915.0,
-                                          "peak_source": "bf16 burst of the profiling recipe (fallback; "
-                                                         "MEASURED_PEAKS.json absent)"}
+                                          "peak_bf16_tflops": _measured_peaks().get("bf16_tflops", 1872.0),
+                                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
                                          if st["ms_residual"] > 0 else None),
-                "other_path": {"precision": "fp64" if prec else "mixed", "s": other_s,
-                               "stages_ms": {k: round(st_other[k], 3) for k in
-                                             ("ms_far", "ms_support", "ms_near", "ms_lu", "ms_solve")}},
-                "currents_rel_diff_vs_other_path": num / den,
+                "fp64_path": fp64,
+                "mixed_over_fp64_speedup": (fp64["s"] / dev_s) if fp64 else None,
+                "currents_rel_diff_mixed_vs_fp64": (num / den) if num is not None else None,
+                "accuracy_vs_oracle": accuracy,
                 "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * args.steps,
                 "clocks": clocks}
-        if ws == 1 and not args.no_cpu_baseline:
-            v, sample, _ = _oracle_baseline(cfg)
-            line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+        if ob is not None:
+            v, sample = ob.sample(20.0)
+            line["cpu_baseline"] = {"value": v, "unit": "s", "cores": ob.cores, "kind": "oracle", "sample": sample}
         print(json.dumps(line), flush=True)
+    if ob is not None:
+        ob.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the FP64 path beside the mixed headline (after one warm-up; 0 = skip)")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="random",
+                    choices=["random", "cylinder", "sphere", "small", "batched", "serving", "tables"],
+                    help="random: smooth random body N=1024, M=128, n_phi=512, k0=10, k1=15 (default); "
+                         "cylinder: edge-graded cylinder N=576, M=64; sphere: N=64, M=10; small: random body "
+                         "N=256, M=32 (profiling captures); batched: the 72-body batch under a memory budget; "
+                         "serving: Poisson request stream with a factor cache; tables: the paper's four examples")
+    ap.add_argument("--bodies", type=int, default=0, help="batched: only the first K bodies (0 = all)")
+    ap.add_argument("--streams", type=int, default=2, help="batched: concurrent bodies (CUDA streams)")
+    ap.add_argument("--schedule", default="waves", choices=["waves", "streams"],
+                    help="batched: waves = bodies grouped under the budget, each wave's modes factored in one "
+                         "graph-launched LU (build_many); streams = one body per concurrent stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window in seconds")
+    ap.add_argument("--zipf", type=float, default=1.1, help="serving: body choice Zipf exponent (0 = uniform)")
+    ap.add_argument("--max-rhs", type=int, default=256, help="serving: right-hand sides per request at most")
+    ap.add_argument("--drain", type=float, default=120.0, help="serving: seconds after the last arrival to finish")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="batched/serving: device-memory budget (0 = 90%% of the free memory)")
+    args = ap.parse_args()
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
+        return
+    if args.workload == "tables":
+        run_tables(args)
+        return
+    cfg = _workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+    run_single(args, cfg)
 
 
 if __name__ == "__main__":

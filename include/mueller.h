@@ -43,7 +43,11 @@ typedef enum {
   MUELLER_ENOMEM = 2,     /* device or host allocation failed                  */
   MUELLER_ESINGULAR = 3,  /* exact zero pivot in some mode (see stats)         */
   MUELLER_ENOCONV = 4,    /* iterative refinement hit its cap                  */
-  MUELLER_ETIMEOUT = 5,   /* a bounded device-side wait gave up                */
+  MUELLER_ETIMEOUT = 5,   /* a bounded device-side wait gave up (for tests,
+                             the environment variable MUELLER_FAULT_INJECT =
+                             "lu_timeout" and/or "residual_timeout" makes the
+                             host set that status word before reading it, so
+                             the error path runs without a device fault)     */
   MUELLER_ECUDA = 6       /* CUDA runtime error                                */
 } mueller_status;
 
@@ -76,7 +80,11 @@ typedef struct {
 typedef struct {
   int n_phi;           /* azimuthal samples (power of two >= 16); raised
                           automatically when too small for M and k (see
-                          stats.n_phi_used)                                 */
+                          stats.n_phi_used).  One warp's shared memory,
+                          80 n_phi + 144 M + 440 bytes, must fit the device's
+                          opt-in limit per CTA (232,448 bytes on GB300, e.g.
+                          n_phi = 2048 with M <= 473); larger requests fail
+                          with MUELLER_EINVAL before any device work         */
   int formulation;     /* 0 direct (eq. mullerrep), 1 indirect (eq. dualmullrep) */
   int precision;       /* 0 FP64; 1 mixed: complex64 LU + iterative refinement
                           whose complex128-accurate residuals run on BF16
@@ -118,6 +126,7 @@ typedef struct {
   int lu_tile_steps[3];      /* mixed path: LU steps whose update used column tiles 32, 64, 128 */
   int lu_wave_bodies;        /* bodies factored together (mueller_build_many), else 1 */
   int lu_launches;           /* kernel launches (graph nodes) of the factorization, shared by a wave */
+  double lu_gemm_bytes;      /* bytes of the trailing matrices the updates read and write (once each) */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;
@@ -240,7 +249,8 @@ int mueller_modal_kernels(const double* pairs_host, long long npairs, mueller_c1
  *  - pairs_dev is a DEVICE array [npairs][4] = (r_t, z_t, r_s, z_s), with
  *    r_t, r_s > 0 and distinct points (not checked on the host; a bad pair
  *    yields non-finite values in its own output rows);
- *  - n_phi is used as given (power of two in [16, 8192], >= 2M + 4); unlike
+ *  - n_phi is used as given (power of two in [16, 8192], >= 2M + 4, and
+ *    within the shared-memory bound stated at mueller_options.n_phi); unlike
  *    mueller_modal_kernels it is not raised automatically, so the caller
  *    picks it large enough for the wavenumbers (see stats.n_phi_used of a
  *    build for a safe value);
@@ -314,6 +324,14 @@ size_t mueller_footprint_bytes(int N, int M);
 void mueller_cache_trim(void);
 size_t mueller_cache_limit(size_t bytes);
 size_t mueller_cache_bytes(void);
+
+/* Measured FP64 arithmetic peak of the current device in TFLOP/s: the best
+ * of five timed launches of a register loop of independent fused
+ * multiply-adds (8 chains per thread, 8 CTAs of 256 threads per SM; 2 flops
+ * per FMA).  The paper's kernel evaluation and assembly (Sections 4-5) run on
+ * the FP64 pipe; this is the denominator of their roofline.  Runs on `stream`
+ * and synchronises it (about 2 s). */
+int mueller_fp64_peak(double* tflops, void* stream);
 
 int mueller_stats_get(const mueller_ctx* ctx, mueller_stats* out);
 void mueller_destroy(mueller_ctx* ctx);

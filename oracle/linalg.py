@@ -8,13 +8,14 @@ from __future__ import annotations
 import numpy as np
 
 
-def lu_factor(A):
+def lu_factor(A, steps=None):
     """In-place-style LU of a copy of A: returns (LU, piv) with P A = L U,
-    L unit lower triangular stored below the diagonal."""
+    L unit lower triangular stored below the diagonal.  ``steps`` stops the
+    elimination after that many columns (used to time a sample of it)."""
     A = np.array(A, dtype=complex, copy=True)
     n = A.shape[0]
     piv = np.arange(n)
-    for k in range(n):
+    for k in range(n if steps is None else min(int(steps), n)):
         p = k + int(np.argmax(np.abs(A[k:, k])))
         if A[p, k] == 0:
             raise ZeroDivisionError(f"exact zero pivot in column {k}")

@@ -54,7 +54,7 @@ class Stats(ct.Structure):
                 ("solve_launches", ct.c_int), ("refine_iters", ct.c_int), ("backward_err_max", ct.c_double),
                 ("ms_residual", ct.c_double), ("residual_launches", ct.c_int), ("residual_tc_flops", ct.c_double),
                 ("lu_graph", ct.c_int), ("lu_tile_steps", ct.c_int * 3), ("lu_wave_bodies", ct.c_int),
-                ("lu_launches", ct.c_int)]
+                ("lu_launches", ct.c_int), ("lu_gemm_bytes", ct.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +94,7 @@ _lib.mueller_footprint_bytes.argtypes = [ct.c_int, ct.c_int]
 _lib.mueller_build_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
 _lib.mueller_build_bytes.restype = ct.c_size_t
 _lib.mueller_footprint_bytes.restype = ct.c_size_t
+_lib.mueller_fp64_peak.argtypes = [ct.POINTER(ct.c_double), _vp]
 _lib.mueller_stats_get.argtypes = [_vp, ct.POINTER(Stats)]
 _lib.mueller_destroy.argtypes = [_vp]
 _lib.mueller_strerror.restype = ct.c_char_p
@@ -105,7 +106,7 @@ EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_pl
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
            "mueller_build_many", "mueller_build_many_bytes", "mueller_lu_tile_table",
            "mueller_cache_trim", "mueller_cache_limit", "mueller_cache_bytes",
-           "mueller_destroy", "mueller_strerror", "mueller_last_error"]
+           "mueller_fp64_peak", "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
 class MuellerError(RuntimeError):
@@ -295,8 +296,28 @@ def assemble(curve, media, M: int, A, options: Options | None = None, stream=Non
     return A
 
 
+def _check_spectra_out(out, npairs: int, M: int):
+    """out must hold npairs x 9 x (M + 2) complex128 values (the kernels write all of them)."""
+    import torch
+    if out.dtype != torch.complex128:
+        raise ValueError(f"out must be complex128, got {out.dtype}")
+    if M < 0 or out.numel() < npairs * 9 * (M + 2):
+        raise ValueError(f"out holds {out.numel()} values; {npairs} pairs x 9 families x (M + 2) need "
+                         f"{npairs * 9 * (M + 2)}")
+
+
+def _check_current_device(*tensors):
+    import torch
+    cur = torch.cuda.current_device()
+    for t in tensors:
+        if not t.is_cuda or t.device.index != cur:
+            raise ValueError(f"tensors must be on the current CUDA device (cuda:{cur}), got {t.device}")
+
+
 def modal_kernels(pairs: np.ndarray, k0, k1, M: int, n_phi: int, out, split_eps: float = 1e-17, stream=None):
     p = np.ascontiguousarray(np.asarray(pairs, np.float64).reshape(-1, 4))
+    _check_spectra_out(out, len(p), int(M))
+    _check_current_device(out)
     _check(_lib.mueller_modal_kernels(_dptr(p), len(p), _c(k0), _c(k1), int(M), int(n_phi), float(split_eps),
                                       _ptr(out), _stream(stream)))
     return out
@@ -305,6 +326,12 @@ def modal_kernels(pairs: np.ndarray, k0, k1, M: int, n_phi: int, out, split_eps:
 def modal_kernels_noalloc(pairs_dev, k0, k1, M: int, n_phi: int, out, split_eps: float = 1e-17, stream=None):
     """Same spectra as ``modal_kernels`` for pairs already on the device, using
     the library's fixed scratch array instead of allocating (see mueller.h)."""
+    import torch
+    if pairs_dev.dtype != torch.float64 or pairs_dev.dim() != 2 or pairs_dev.shape[1] != 4:
+        raise ValueError(f"pairs_dev must be float64 of shape (npairs, 4), got {pairs_dev.dtype} "
+                         f"{tuple(pairs_dev.shape)}")
+    _check_spectra_out(out, pairs_dev.shape[0], int(M))
+    _check_current_device(pairs_dev, out)
     _check(_lib.mueller_modal_kernels_noalloc(_ptr(pairs_dev), pairs_dev.shape[0], _c(k0), _c(k1), int(M),
                                               int(n_phi), float(split_eps), _ptr(out), _stream(stream)))
     return out
@@ -345,6 +372,13 @@ def cache_limit(nbytes: int) -> int:
 
 def cache_bytes() -> int:
     return int(_lib.mueller_cache_bytes())
+
+
+def fp64_peak(stream=None) -> float:
+    """Measured FP64 peak of the current device, TFLOP/s (DFMA register loop)."""
+    v = ct.c_double(0.0)
+    _check(_lib.mueller_fp64_peak(ct.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 def footprint_bytes(N: int, M: int) -> int:

@@ -683,6 +683,14 @@ static int warps_per_block(const GreenParams& gp) {
   return w;
 }
 
+bool green_fits_smem(const GreenParams& gp) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+    optin = 227 * 1024;
+  return green_smem_bytes(gp) <= optin;
+}
+
 static int grid_for(long long units, int wpb) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -751,12 +759,16 @@ void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* 
 // coefficients) lives in one fixed file-scope device array instead of memory
 // from cudaMalloc.  Host code must not use the array's name as a device
 // address: its address is fetched once per device with cudaGetSymbolAddress.
+#include <mutex>
 #include "mueller.h"
 
 #define NOALLOC_SCRATCH_DOUBLES ((size_t)2 * 1024 * 1024)  // 16 MiB
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
 #define NOALLOC_MAX_DEVICES 64
+// Per-device set-up state, written under g_noalloc_mu: the scratch array's
+// device address and whether the series tables were uploaded to that device.
+static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
 static bool g_noalloc_tables[NOALLOC_MAX_DEVICES] = {false};
 // message reported by mueller_last_error (defined with the other ABI functions)
@@ -809,6 +821,11 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   if (k0.im < 0 || k1.im < 0) return noalloc_fail("wavenumbers need Im k >= 0");
   if (npairs == 0) return MUELLER_OK;
   const int Mq = n_phi / 2 - 1, Ms = M + 2, H = n_phi / 2 + 1;
+  {
+    GreenParams g{};
+    g.Ms = Ms; g.H = H; g.Mq = Mq;
+    if (!green_fits_smem(g)) return noalloc_fail("n_phi and M need more shared memory per warp than a CTA can have");
+  }
   auto up32 = [](size_t v) { return (v + 31) & ~(size_t)31; };
   const size_t o_cos = 0, o_s2 = o_cos + up32(n_phi), o_disp = o_s2 + up32(H);
   const size_t o_sid = o_disp + up32(4 * (size_t)npairs);
@@ -822,19 +839,23 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail("no current CUDA device");
-  if (!g_noalloc_ptr[dev]) {  // one-time set-up on this device
-    double* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return noalloc_fail(cudaGetErrorString(e), MUELLER_ECUDA);
-    g_noalloc_ptr[dev] = p;
+  double* base = nullptr;
+  {  // one-time set-up on this device (host threads serialised)
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      double* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) return noalloc_fail(cudaGetErrorString(e), MUELLER_ECUDA);
+      g_noalloc_ptr[dev] = p;
+    }
+    if (!g_noalloc_tables[dev]) {
+      SeriesTables t;
+      fill_series_tables(&t);
+      if (cudaMemcpyToSymbol(c_tab, &t, sizeof(SeriesTables)) != cudaSuccess) return noalloc_fail("series tables");
+      g_noalloc_tables[dev] = true;
+    }
+    base = g_noalloc_ptr[dev];
   }
-  if (!g_noalloc_tables[dev]) {
-    SeriesTables t;
-    fill_series_tables(&t);
-    if (cudaMemcpyToSymbol(c_tab, &t, sizeof(SeriesTables)) != cudaSuccess) return noalloc_fail("series tables");
-    g_noalloc_tables[dev] = true;
-  }
-  double* base = g_noalloc_ptr[dev];
   double* cosT = base + o_cos;
   double* s2T = base + o_s2;
   double* disp = base + o_disp;

@@ -93,3 +93,5 @@ void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* 
                          cd* out, cudaStream_t s);
 void upload_series_tables(const SeriesTables& t);
 int green_smem_per_warp(const GreenParams& gp);
+// whether one warp's shared memory (green_smem_bytes) fits the device's per-CTA opt-in limit
+bool green_fits_smem(const GreenParams& gp);

@@ -767,7 +767,7 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
   const bool timed = tm && !graph;
   std::vector<cudaEvent_t> ev;
   int launches = 1, gemm_launches = 0, tn_steps[3] = {0, 0, 0};
-  double gemm_flops = 0.0;
+  double gemm_flops = 0.0, gemm_bytes = 0.0;
   int active = count;
   for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
     while (active > 0 && it[active - 1].n <= k0) --active;
@@ -802,7 +802,10 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
     }
     for (int b = 0; b < active; ++b) {
       const double rb = (double)(it[b].n - k0 - LU_NB);
-      if (rb > 0) gemm_flops += 8.0 * rb * rb * LU_NB;
+      if (rb > 0) {
+        gemm_flops += 8.0 * rb * rb * LU_NB;
+        gemm_bytes += 2.0 * sizeof(T) * rb * rb;   // the trailing matrix read and written once
+      }
     }
     ++gemm_launches;
   }
@@ -825,6 +828,7 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
   if (tm) {
     tm->launches += launches;
     tm->gemm_flops += gemm_flops;
+    tm->gemm_bytes += gemm_bytes;
     tm->gemm_launches += gemm_launches;
     tm->graph = graph ? 1 : 0;
     for (int q = 0; q < 3; ++q) tm->tile_steps[q] += tn_steps[q];

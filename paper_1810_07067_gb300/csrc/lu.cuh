@@ -11,6 +11,7 @@
 struct LuTiming {
   double gemm_ms = 0.0;      // summed device time of the trailing-update launches (0 when graph-launched)
   double gemm_flops = 0.0;   // their algorithmic flops (8 per complex multiply-add)
+  double gemm_bytes = 0.0;   // the trailing matrices' bytes, read and written once per update
   int gemm_launches = 0;     // steps with a trailing update
   int launches = 0;          // all kernel launches of the factorization
   int graph = 0;             // 1: the steps ran as one captured CUDA graph

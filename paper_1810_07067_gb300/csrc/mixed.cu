@@ -1,4 +1,4 @@
-// Mixed-precision solves (BASELINE precision pattern of the method's use):
+// Mixed-precision solves (complex64 factors, FP64-accurate answers):
 // the modes are factored in complex64 and every solve is refined with
 // residuals of the complex128 L2-weighted matrices,
 //   y_0 = LU32^{-1} b',  r_i = b' - A' y_i (FP64),  y_{i+1} = y_i + LU32^{-1} r_i,

@@ -1,0 +1,161 @@
+"""Write the oracle's full-size reference solutions used by the GPU parity
+tests and by the bench's per-mode error report.
+
+Only the oracle (``oracle/``) computes anything here; ``workloads`` supplies
+the seeded synthetic inputs.  For one named workload the script
+
+1. assembles the per-mode Mueller matrices (eq. mullerrep, Lemma 1, the
+   modal N and K operators, the near-panel rules of Section 5) row by row
+   with ``oracle.system.assemble_row``, target rows spread over worker
+   processes;
+2. applies the L2 weighting (Section 6 remark), factors every requested mode
+   with the oracle's naive partial-pivot LU and solves for the plane-wave
+   data of eq. pw (``oracle.fields.modal_rhs``);
+3. evaluates the far field (eq. farfieldform, magnetic current in the last
+   term) of the solved currents at fixed directions.
+
+Workloads:
+  cylinder  finite cylinder R = 1, H = 2, 7 dyadic levels at each edge
+            (N = 576), k0 = 5, k1 = 7.5 + 0.01i, all modes -64..64, 16 plane
+            waves; the far field is that of the complete solution.
+  random    smooth random body (seed 1810, N = 1024), k0 = 10, k1 = 15,
+            modes -128, -1, 0, 1, 64, 128, two plane waves; the far field is
+            that of the listed modes' currents (the other modes set to zero).
+
+Usage: python tests/golden/make_fullsize.py cylinder|random [--workers K]
+Writes tests/golden/fullsize_<workload>.npz.  The whole run takes about
+15-25 minutes on 8 cores.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# currents kept in the file (the far field covers every solved mode)
+KEEP = {
+    "cylinder": dict(modes=[-64, -1, 0, 1, 32, 64], waves=[0, 1, 6, 7, 14, 15]),
+    "random": dict(modes=[-128, -1, 0, 1, 64, 128], waves=[0, 1]),
+}
+
+
+def workload(name):
+    import workloads as W
+    if name == "cylinder":
+        cfg = W.config_cylinder(7)
+        modes = list(range(-cfg.M, cfg.M + 1))
+    elif name == "random":
+        cfg = W.config_random()
+        modes = KEEP["random"]["modes"]
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return cfg, modes
+
+
+def far_directions():
+    """48 directions: 6 polar angles x 6 azimuths plus 12 scattered ones."""
+    th = (np.arange(6) + 0.5) * np.pi / 6
+    ph = np.arange(6) * 2 * np.pi / 6 + 0.3
+    T, Pp = np.meshgrid(th, ph, indexing="ij")
+    d = np.stack([np.sin(T) * np.cos(Pp), np.sin(T) * np.sin(Pp), np.cos(T)], -1).reshape(-1, 3)
+    rng = np.random.default_rng(48)
+    e = rng.standard_normal((12, 3))
+    e /= np.linalg.norm(e, axis=1, keepdims=True)
+    return np.concatenate([d, e])
+
+
+def _rows_job(args):
+    name, rows, modes, path = args
+    from oracle import system
+    cfg, _ = workload(name)
+    A = np.load(path, mmap_mode="r+")
+    geo = system.node_geometry(cfg.curve)
+    for i in rows:
+        A[:, 4 * i:4 * i + 4, :] = system.assemble_row(cfg.curve, cfg.media, cfg.M, i, 0, modes, geo)
+    A.flush()
+    return len(rows)
+
+
+def _solve_job(args):
+    name, qi, path, b = args
+    from oracle import system, linalg
+    cfg, _ = workload(name)
+    A = np.array(np.load(path, mmap_mode="r")[qi])
+    sw = system.l2_weights(cfg.curve)
+    Aw = A * sw[:, None] / sw[None, :]
+    LU, piv = linalg.lu_factor(Aw)
+    bw = b * sw[:, None]
+    y = linalg.lu_solve(LU, piv, bw)
+    res = np.abs(Aw @ y - bw).max() / (np.abs(Aw).sum(1).max() * np.abs(y).max() + np.abs(bw).max())
+    return qi, y / sw[:, None], float(res)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["cylinder", "random"])
+    ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
+    ap.add_argument("--tmp", default=tempfile.gettempdir())
+    args = ap.parse_args()
+    import multiprocessing as mp
+    from oracle import fields
+    name = args.workload
+    cfg, modes = workload(name)
+    N, M, n = cfg.N, cfg.M, 4 * cfg.N
+    t0 = time.time()
+    path = os.path.join(args.tmp, f"oracle_A_{name}_{os.getpid()}.npy")
+    A = np.lib.format.open_memmap(path, mode="w+", dtype=np.complex128, shape=(len(modes), n, n))
+    del A
+    ctx = mp.get_context("spawn")
+    chunks = [list(range(i, N, 4 * args.workers)) for i in range(4 * args.workers)]
+    with ctx.Pool(args.workers) as pool:
+        done = 0
+        for k in pool.imap_unordered(_rows_job, [(name, c, modes, path) for c in chunks if c]):
+            done += k
+            print(f"[{time.time() - t0:7.0f} s] assembled {done}/{N} rows", flush=True)
+        b_all = fields.modal_rhs(cfg.curve, cfg.media, M, cfg.waves)     # [2M+1, n, nrhs]
+        jobs = [(name, qi, path, b_all[m + M]) for qi, m in enumerate(modes)]
+        x = np.zeros((len(modes), n, len(cfg.waves)), dtype=complex)
+        berr = np.zeros(len(modes))
+        for qi, xq, res in pool.imap_unordered(_solve_job, jobs):
+            x[qi] = xq
+            berr[qi] = res
+            print(f"[{time.time() - t0:7.0f} s] solved mode {modes[qi]} (backward error {res:.1e})", flush=True)
+    os.remove(path)
+    # far field of the solved modes (the others zero)
+    xf = np.zeros((2 * M + 1, n, len(cfg.waves)), dtype=complex)
+    for qi, m in enumerate(modes):
+        xf[m + M] = x[qi]
+    dirs = far_directions()
+    ff = fields.far_field(cfg.curve, cfg.media, M, xf, dirs)          # [nrhs, nd, 3]
+    keep = KEEP[name]
+    kq = [modes.index(m) for m in keep["modes"]]
+    out = os.path.join(HERE, f"fullsize_{name}.npz")
+    np.savez_compressed(
+        out,
+        workload=name, n_panels=cfg.curve.n_panels, closed=int(cfg.curve.closed),
+        r=cfg.curve.r, z=cfg.curve.z, dr=cfg.curve.dr, dz=cfg.curve.dz,
+        omega=cfg.media.omega, eps0=complex(cfg.media.eps0), mu0=complex(cfg.media.mu0),
+        eps1=complex(cfg.media.eps1), mu1=complex(cfg.media.mu1), M=M, n_phi=cfg.n_phi,
+        wave_d=np.array([w.d for w in cfg.waves]), wave_e=np.array([w.e for w in cfg.waves]),
+        solved_modes=np.array(modes), backward_err=berr,
+        modes=np.array(keep["modes"]), waves=np.array(keep["waves"]),
+        x=x[kq][:, :, keep["waves"]].transpose(0, 2, 1).copy(),     # [modes, waves, 4N]
+        ff_dirs=dirs, ff=ff, seconds=time.time() - t0)
+    print(f"wrote {out} in {time.time() - t0:.0f} s; max oracle backward error {berr.max():.1e}")
+
+
+if __name__ == "__main__":
+    main()

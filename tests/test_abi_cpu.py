@@ -78,3 +78,29 @@ def test_build_many_rejects_bad_inputs_before_device_work(lib):
         mb.build_many([(cur, W.Media(omega=0.0), 2), (cur, W.Media.from_k(1.0, 1.5), 2)], stream=0)
     assert mb.build_many_bytes([64, 32], [10, 4], 1) >= max(mb.build_bytes(64, 10, 1)[0], mb.build_bytes(32, 4, 1)[0])
     assert mb.build_many_bytes([], [], 1) == 0
+
+
+def test_modal_kernel_wrappers_check_buffers_before_the_call(lib):
+    """A wrongly typed or too small buffer is refused on the host: the kernels
+    would otherwise read or write past it."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    import paper_1810_07067_gb300 as mb
+    M, n = 4, 3
+    good_pairs = torch.ones((n, 4), dtype=torch.float64)
+    good_out = torch.zeros((n, 9, M + 2), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="float64"):
+        mb.modal_kernels_noalloc(good_pairs.float(), 1.0, 1.5, M, 64, good_out)
+    with pytest.raises(ValueError, match="shape"):
+        mb.modal_kernels_noalloc(torch.ones((n, 3), dtype=torch.float64), 1.0, 1.5, M, 64, good_out)
+    with pytest.raises(ValueError, match="complex128"):
+        mb.modal_kernels_noalloc(good_pairs, 1.0, 1.5, M, 64, good_out.to(torch.complex64))
+    with pytest.raises(ValueError, match="need"):
+        mb.modal_kernels_noalloc(good_pairs, 1.0, 1.5, M + 1, 64, good_out)
+    with pytest.raises(ValueError, match="need"):
+        mb.modal_kernels(np.ones((n, 4)), 1.0, 1.5, M, 64, good_out[:2])
+    with pytest.raises(ValueError, match="complex128"):
+        mb.modal_kernels(np.ones((n, 4)), 1.0, 1.5, M, 64, good_out.real.contiguous())
+    if not torch.cuda.is_available():  # CPU tensors of the right type and size: refused as off-device
+        with pytest.raises((ValueError, RuntimeError, AssertionError)):
+            mb.modal_kernels_noalloc(good_pairs, 1.0, 1.5, M, 64, good_out)

@@ -182,3 +182,33 @@ def test_lu_c64_zero_pivot_in_cluster_panel(mb):
     info = torch.zeros(1, dtype=torch.int32, device=DEV)
     mb.lu_batched_c64(At, piv, info)
     assert info.item() == 701
+
+
+@pytest.mark.parametrize("word,where", [("lu_timeout", "build"), ("residual_timeout", "solve")])
+def test_timeout_status_reaches_the_api(mb, monkeypatch, word, where):
+    """A device-side wait that gives up leaves 1 in a status word; the host
+    must turn it into MUELLER_ETIMEOUT.  The word is set from the host
+    (MUELLER_FAULT_INJECT), so no device wait is shortened and nothing faults."""
+    cfg = W.config_sphere()
+    M = 4
+    opts = mb.Options(n_phi=cfg.n_phi, precision=1, refine_tol=1e-14)
+    if where == "build":
+        monkeypatch.setenv("MUELLER_FAULT_INJECT", word)
+        with pytest.raises(mb.MuellerError, match="timed out") as ei:
+            mb.build(cfg.curve, cfg.media, M, opts)
+        assert ei.value.status == 5
+        monkeypatch.delenv("MUELLER_FAULT_INJECT")
+        mb.build(cfg.curve, cfg.media, M, opts).close()     # the context stays usable
+        return
+    ctx = mb.build(cfg.curve, cfg.media, M, opts)
+    n = 4 * cfg.N
+    rhs = torch.zeros((2 * M + 1, 1, n), dtype=torch.complex128, device=DEV)
+    ctx.rhs_planewave(cfg.waves[0].d[None], cfg.waves[0].e[None], rhs)
+    x = torch.zeros_like(rhs)
+    monkeypatch.setenv("MUELLER_FAULT_INJECT", word)
+    with pytest.raises(mb.MuellerError, match="timed out") as ei:
+        ctx.solve(rhs, x)
+    assert ei.value.status == 5
+    monkeypatch.delenv("MUELLER_FAULT_INJECT")
+    ctx.solve(rhs, x)
+    ctx.close()
