@@ -1,0 +1,125 @@
+"""Full-size parity of modal currents and far fields against the oracle.
+
+The oracle's solutions of the full-size cylinder (N = 576, modes -64..64,
+16 plane waves) and random body (N = 1024, modes -128, -1, 0, 1, 64, 128,
+two plane waves) are stored in tests/golden/fullsize_*.npz, written by
+tests/golden/make_fullsize.py from the oracle alone (direct azimuthal
+quadrature, plain assembly by Lemma 1 and the modal N and K operators, naive
+partial-pivot LU).  The GPU builds the same body from the stored curve and
+solves through the C ABI, FP64 and mixed paths; the currents of every stored
+mode and the far field of the stored modes are compared.
+
+Tolerances (the build's targets): FP64 path 1e-10, mixed path 1e-9, relative
+l2 per mode and plane wave, normalised by the largest mode's currents (a
+mode with tiny currents is compared on the scale of the solution; the plain
+per-mode relative error is bounded separately for modes above 1e-6 of the
+largest); far field relative l2 over all directions and components.
+
+Also: a closed curve (torus, Section 6) with sampled 4x4 blocks across the
+wrap-around, where the first and last panels are neighbours.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+from oracle import system
+
+DEV = "cuda:0"
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_07067_gb300 as m
+    return m
+
+
+def _load(name):
+    path = os.path.join(HERE, "golden", f"fullsize_{name}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    g = np.load(path)
+    curve = W.Curve(int(g["n_panels"]), g["r"].copy(), g["z"].copy(), g["dr"].copy(), g["dz"].copy(),
+                    bool(int(g["closed"])))
+    media = W.Media(float(g["omega"]), complex(g["eps0"]), complex(g["mu0"]), complex(g["eps1"]), complex(g["mu1"]))
+    return g, curve, media
+
+
+def _check(mb, name, precision, tol):
+    g, curve, media = _load(name)
+    M, n_phi = int(g["M"]), int(g["n_phi"])
+    n = 4 * curve.N
+    ctx = mb.build(curve, media, M, mb.Options(n_phi=n_phi, precision=precision, refine_tol=1e-14))
+    nrhs = len(g["wave_d"])
+    b = torch.zeros((2 * M + 1, nrhs, n), dtype=torch.complex128, device=DEV)
+    ctx.rhs_planewave(g["wave_d"], g["wave_e"], b)
+    x = torch.zeros_like(b)
+    ctx.solve(b, x)
+    xg = x.cpu().numpy()
+    modes, waves = [int(m) for m in g["modes"]], [int(w) for w in g["waves"]]
+    xo = g["x"]                                     # [modes, waves, 4N]
+    top = max(np.linalg.norm(xo[qi, wi]) for qi in range(len(modes)) for wi in range(len(waves)))
+    worst_global = worst_plain = 0.0
+    for qi, m in enumerate(modes):
+        for wi, w in enumerate(waves):
+            d = np.linalg.norm(xg[m + M, w] - xo[qi, wi])
+            worst_global = max(worst_global, d / top)
+            if np.linalg.norm(xo[qi, wi]) > 1e-6 * top:
+                worst_plain = max(worst_plain, d / np.linalg.norm(xo[qi, wi]))
+    keep = torch.zeros_like(x)
+    for m in [int(v) for v in g["solved_modes"]]:
+        keep[m + M] = x[m + M]
+    dirs = torch.tensor(g["ff_dirs"], device=DEV)
+    E = torch.zeros((nrhs, len(dirs), 3), dtype=torch.complex128, device=DEV)
+    ctx.far_field(keep, dirs, E)
+    ff = np.linalg.norm(E.cpu().numpy() - g["ff"]) / np.linalg.norm(g["ff"])
+    ctx.close()
+    print(f"{name} precision {precision}: currents {worst_global:.2e} (plain per mode {worst_plain:.2e}), "
+          f"far field {ff:.2e}")
+    assert worst_global < tol, worst_global
+    assert worst_plain < 100 * tol, worst_plain
+    assert ff < tol, ff
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_cylinder_currents_and_far_field_vs_oracle(mb, precision, tol):
+    """Edge-graded cylinder, every mode solved by the oracle: stored modes'
+    currents and the far field of the complete solution."""
+    _check(mb, "cylinder", precision, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_random_body_currents_and_far_field_vs_oracle(mb, precision, tol):
+    """Random body (N = 1024, 4096 x 4096 per mode), modes -128, -1, 0, 1,
+    64, 128: currents, and the far field of those modes' currents."""
+    _check(mb, "random", precision, tol)
+
+
+def test_torus_blocks_across_the_wraparound(mb):
+    """Closed curve: the first and last panels are neighbours, so their
+    blocks take the adjacent-panel rule; blocks of the self panel, the two
+    neighbours across the seam and far panels against the oracle."""
+    curve = W.torus(6)
+    media = W.Media.from_k(2.0, 3.0)
+    M = 6
+    n = 4 * curve.N
+    A = torch.zeros((M + 1, n, n), dtype=torch.complex128, device=DEV)
+    mb.assemble(curve, media, M, A, mb.Options(n_phi=64))
+    sw = system.l2_weights(curve)
+    modes = np.array([0, 1, 6])
+    scale = max(float(A[q].abs().max()) for q in modes)
+    N = curve.N
+    samples = [(0, N - 1), (3, N - 16), (N - 1, 0), (N - 5, 7), (2, 2), (N - 2, N - 3), (0, 40), (50, 10)]
+    for (i, j) in samples:
+        ref, noise = system.block(curve, media, M, i, j, modes=modes, noise=True)
+        s = sw[4 * i] / sw[4 * j]
+        got = np.stack([A[q, 4 * j:4 * j + 4, 4 * i:4 * i + 4].cpu().numpy().T for q in modes])
+        ok = np.abs(got - ref * s) <= 1e-12 * scale + 20 * noise.max() * s
+        assert ok.all(), (i, j, (np.abs(got - ref * s) / scale).max())
