@@ -9,28 +9,46 @@ eq_nyslike2); since sum_j U_jk P_j(y) is the Lagrange basis polynomial L_k(y),
 the quadrature kernel is Q(x, y_k) = sum_s W_s g(x, y_s) L_k(y_s).
 
 The paper's generalized Gaussian tables come from external code and are not
-reproduced.  These rules are written out from their definition instead; they
-integrate p(y) log|x-y| + q(y) (the form in the Remark of Section 5) to about
-machine precision:
+reproduced.  The rules used instead integrate p(y) log|x-y| + q(y) (the form
+in the Remark of Section 5):
 
 * self rule, target at tau_i: split [-1, 1] at tau_i; on each side of length
-  L map u in [0, 1] to distance L*u from tau_i and use the reference rule
-  R_self on [0, 1]: for j = 0..9 the interval [4^-(j+1), 4^-j] with 16 Gauss
-  points, plus [0, 4^-10] with 4 nodes at the 4 Gauss points whose weights
-  make the rule exact for {1, u, log u, u log u}.  164 nodes per side.
+  L map u in [0, 1] to distance L*u from tau_i and use the reference rule on
+  [0, 1]: the 16-node generalized Gaussian rule that integrates P_j(2u-1)
+  and P_j(2u-1) log u, j < 16, exactly.  Its nodes and weights are data of
+  the discretisation, read from include/mueller_near_rules.h (the table the
+  CUDA library compiles in); tests/test_oracle_pins.py checks them against
+  the closed-form moments.  32 nodes per target.
 * adjacent rule: graded toward the shared endpoint: u in [0, 1] -> tau =
   -1 + 2u (or 1 - 2u); intervals [4^-(j+1), 4^-j], j = 0..4, and [0, 4^-5],
   each with 16 Gauss points.  96 nodes, target independent.
 """
 from __future__ import annotations
 
+import os
+import re
+
 import numpy as np
 
 P = 16
-SELF_LEVELS = 10
-SELF_GAUSS = 16
 ADJ_LEVELS = 5
 ADJ_GAUSS = 16
+RULES_HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "mueller_near_rules.h")
+
+
+def near_rule_table(name: str) -> np.ndarray:
+    """The array MUELLER_<name> of the near-rule data file, as float64."""
+    text = open(RULES_HEADER).read()
+    m = re.search(r"MUELLER_" + name + r"\[[^\]]*\]\s*=\s*\{([^}]*)\}", text)
+    if m is None:
+        raise KeyError(name)
+    return np.array([float(v) for v in m.group(1).replace("\n", " ").split(",") if v.strip()])
+
+
+def self_side_rule():
+    """Generalized Gaussian reference rule (u, w) on [0, 1] for one side of the self panel."""
+    return near_rule_table("SELF_U"), near_rule_table("SELF_W")
 
 
 def gauss_legendre(n: int, a: float = -1.0, b: float = 1.0):
@@ -51,30 +69,13 @@ def lagrange_basis(nodes: np.ndarray, t: np.ndarray) -> np.ndarray:
     return L
 
 
-def log_end_rule():
-    """4-node rule on [0, 1] at the Gauss points, exact for 1, u, log u, u log u."""
-    x, _ = gauss_legendre(4, 0.0, 1.0)
-    V = np.vstack([np.ones(4), x, np.log(x), x * np.log(x)])
-    mom = np.array([1.0, 0.5, -1.0, -0.25])
-    return x, np.linalg.solve(V, mom)
-
-
-def graded_rule(levels: int, n_gauss: int, inner: str):
-    """Reference rule on [0, 1] graded toward 0 with ratio 4.
-
-    inner = 'log': innermost [0, 4^-levels] uses the 4-node log rule;
-    inner = 'gauss': innermost interval uses n_gauss Gauss points."""
+def graded_rule(levels: int, n_gauss: int):
+    """Reference rule on [0, 1] graded toward 0 with ratio 4: intervals
+    [4^-(j+1), 4^-j] (j < levels) and [0, 4^-levels], n_gauss Gauss points each."""
     us, ws = [], []
-    for j in range(levels):
-        a, b = 4.0 ** -(j + 1), 4.0 ** -j
+    for j in range(levels + 1):
+        a, b = (4.0 ** -(j + 1) if j < levels else 0.0), 4.0 ** -j
         x, w = gauss_legendre(n_gauss, a, b)
-        us.append(x); ws.append(w)
-    h = 4.0 ** -levels
-    if inner == "log":
-        x, w = log_end_rule()
-        us.append(h * x); ws.append(h * w)
-    else:
-        x, w = gauss_legendre(n_gauss, 0.0, h)
         us.append(x); ws.append(w)
     u = np.concatenate(us); w = np.concatenate(ws)
     order = np.argsort(u)
@@ -84,7 +85,7 @@ def graded_rule(levels: int, n_gauss: int, inner: str):
 def self_rule(i: int):
     """Support nodes tau_s and tau-weights for a target at node i of its own panel."""
     x, _ = gauss_legendre(P)
-    u, w = graded_rule(SELF_LEVELS, SELF_GAUSS, "log")
+    u, w = self_side_rule()
     ti = x[i]
     Lm, Lp = ti + 1.0, 1.0 - ti
     tau = np.concatenate([ti - Lm * u, ti + Lp * u])
@@ -95,7 +96,7 @@ def self_rule(i: int):
 def adjacent_rule(shared_end: int):
     """Support nodes for a neighbouring panel whose endpoint tau = shared_end
     (-1 or +1) touches the target's panel."""
-    u, w = graded_rule(ADJ_LEVELS, ADJ_GAUSS, "gauss")
+    u, w = graded_rule(ADJ_LEVELS, ADJ_GAUSS)
     if shared_end < 0:
         return -1.0 + 2.0 * u, 2.0 * w
     return 1.0 - 2.0 * u, 2.0 * w

@@ -734,7 +734,7 @@ void launch_support_spectra(const BuildArgs& a, cudaStream_t s) {
 // of the contraction's NFAM (M+2) items and the kc (M+1) blocks, so that the
 // last round is not nearly empty (one CTA per SM: its shared memory).
 void launch_near_assembly(const BuildArgs& a, cudaStream_t s) {
-  int smem = a.kc * 3 * NFAM * a.gp.Ms * 16 + SELF_PTS * a.kc * 3 * 8;
+  int smem = a.kc * 3 * NFAM * a.gp.Ms * 16 + NEAR_MAX_PTS * a.kc * 3 * 8;
   const int items = std::max(NFAM * a.gp.Ms, a.kc * (a.gp.M + 1));
   const int rounds = (items + 383) / 384;
   const int threads = std::min(384, ((items + rounds - 1) / rounds + 31) / 32 * 32);

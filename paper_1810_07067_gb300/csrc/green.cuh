@@ -39,9 +39,14 @@ struct SupportTable {
   const double* Ladj;                 // [2][ADJ_PTS][16]  (0: shared end -1, 1: shared end +1)
 };
 
-#define SELF_SIDE 164
+#include "mueller_near_rules.h"
+// support points of the near-panel rules (Section 5): the target's own panel
+// takes the generalized Gaussian rule on each side of the target (the table
+// of mueller_near_rules.h), each neighbouring panel a graded composite rule
+#define SELF_SIDE MUELLER_SELF_SIDE
 #define SELF_PTS (2 * SELF_SIDE)
 #define ADJ_PTS 96
+#define NEAR_MAX_PTS (SELF_PTS > ADJ_PTS ? SELF_PTS : ADJ_PTS)  // the largest rule
 #define PTS_PER_PANEL (P_NODES * SELF_PTS + 2 * ADJ_PTS)
 #define NEAR_SLOTS (SELF_PTS + 2 * ADJ_PTS)   // support points per target
 

@@ -70,56 +70,17 @@ struct Rules {
   std::vector<double> adj_u, adj_w;     // reference adjacent rule on [0, 1]
 };
 
-// 4x4 solve by Gaussian elimination with partial pivoting
-static void solve4(double A[4][4], double b[4]) {
-  for (int k = 0; k < 4; ++k) {
-    int p = k;
-    for (int r = k + 1; r < 4; ++r)
-      if (std::fabs(A[r][k]) > std::fabs(A[p][k])) p = r;
-    for (int c = 0; c < 4; ++c) std::swap(A[k][c], A[p][c]);
-    std::swap(b[k], b[p]);
-    for (int r = k + 1; r < 4; ++r) {
-      double f = A[r][k] / A[k][k];
-      for (int c = k; c < 4; ++c) A[r][c] -= f * A[k][c];
-      b[r] -= f * b[k];
-    }
-  }
-  for (int k = 3; k >= 0; --k) {
-    for (int c = k + 1; c < 4; ++c) b[k] -= A[k][c] * b[c];
-    b[k] /= A[k][k];
-  }
-}
-
-// Reference rule on [0, 1] graded toward 0: intervals [4^-(j+1), 4^-j] with
-// ng Gauss points; innermost [0, 4^-levels] either ng Gauss points or 4 nodes
-// exact for {1, u, log u, u log u}.
-static void graded_rule(int levels, int ng, bool log_inner, std::vector<double>& u, std::vector<double>& w) {
+// Reference rule on [0, 1] graded toward 0: intervals [4^-(j+1), 4^-j] and
+// the innermost [0, 4^-levels], ng Gauss points each.
+static void graded_rule(int levels, int ng, std::vector<double>& u, std::vector<double>& w) {
   std::vector<double> x, wx;
   gauss_legendre(ng, x, wx);
   u.clear(); w.clear();
-  for (int j = 0; j < levels; ++j) {
-    double a = std::pow(4.0, -(j + 1)), b = std::pow(4.0, -j);
+  for (int j = 0; j <= levels; ++j) {
+    const double a = j < levels ? std::pow(4.0, -(j + 1)) : 0.0, b = std::pow(4.0, -j);
     for (int q = 0; q < ng; ++q) {
       u.push_back(0.5 * (a + b) + 0.5 * (b - a) * x[q]);
       w.push_back(0.5 * (b - a) * wx[q]);
-    }
-  }
-  double h = std::pow(4.0, -levels);
-  if (log_inner) {
-    std::vector<double> x4, w4;
-    gauss_legendre(4, x4, w4);
-    double V[4][4], mom[4] = {1.0, 0.5, -1.0, -0.25};
-    double xs[4];
-    for (int q = 0; q < 4; ++q) {
-      xs[q] = 0.5 + 0.5 * x4[q];
-      V[0][q] = 1.0; V[1][q] = xs[q]; V[2][q] = std::log(xs[q]); V[3][q] = xs[q] * std::log(xs[q]);
-    }
-    solve4(V, mom);
-    for (int q = 0; q < 4; ++q) { u.push_back(h * xs[q]); w.push_back(h * mom[q]); }
-  } else {
-    for (int q = 0; q < ng; ++q) {
-      u.push_back(0.5 * h + 0.5 * h * x[q]);
-      w.push_back(0.5 * h * wx[q]);
     }
   }
 }
@@ -130,8 +91,9 @@ static Rules make_rules() {
   R.bary.resize(P_NODES);
   for (int k = 0; k < P_NODES; ++k)
     R.bary[k] = ((k % 2) ? -1.0 : 1.0) * std::sqrt((1.0 - R.x16[k] * R.x16[k]) * R.w16[k]);
-  graded_rule(10, 16, true, R.self_u, R.self_w);
-  graded_rule(5, 16, false, R.adj_u, R.adj_w);
+  R.self_u.assign(MUELLER_SELF_U, MUELLER_SELF_U + MUELLER_SELF_SIDE);
+  R.self_w.assign(MUELLER_SELF_W, MUELLER_SELF_W + MUELLER_SELF_SIDE);
+  graded_rule(5, 16, R.adj_u, R.adj_w);
   return R;
 }
 
@@ -670,7 +632,7 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
       return fail(MUELLER_ENOMEM, "far-pair tail queue scratch");
   }
   int kc = 8;
-  while (kc > 1 && kc * 3 * NFAM * Ms * 16 + SELF_PTS * kc * 3 * 8 > 200 * 1024) kc /= 2;
+  while (kc > 1 && kc * 3 * NFAM * Ms * 16 + NEAR_MAX_PTS * kc * 3 * 8 > 200 * 1024) kc /= 2;
   a.kc = kc;
   Timer T(s);
   T.mark();
