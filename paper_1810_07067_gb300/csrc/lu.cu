@@ -398,28 +398,98 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const LuMat* __restric
   }
 }
 
-// ---------------------------------------------------------------- tensor-core trailing update
-// Complex64 trailing update C -= L U on tcgen05: every FP32 operand is split
-// exactly into three BF16 pieces (x = hi + mid + lo, 24 bits), and the six
-// piece products whose sum carries FP32 precision (hh, hm, mh, hl, mm, lh) are
-// accumulated in FP32 tensor memory (-L_im U_im via the MMA's A-negation).
-// The hi*hi products and the five smaller corrections go to separate
-// accumulators (Re and Im each, four in all) that are added in registers:
-// sharing one accumulator loses about two bits to the tensor core's
-// accumulation, which measured 4x the error of a plain FP32 update, while the
-// split form measured half of it.  One CTA per 128 x 64 output tile of one
-// matrix; 128 threads; operands are re-laid out into the MMA's K-major
-// no-swizzle core-matrix format in shared memory.
-#define TCU_M 128
-#define TCU_ATILE (TCU_M * LU_NB)  // bf16 elements per piece tile of L (128 rows x 32 k)
+// ---------------------------------------------------------------- two-level blocking (complex64)
+// The complex64 factorization works on outer blocks of LU_OB = 4 LU_NB
+// columns.  Inside a block each LU_NB panel is factored, its interchanges
+// applied, its rows of U formed, and only two thin strips are updated at
+// once: the rest of the block's columns (all rows below, "R1") and the rest
+// of the block's rows (all columns right of the block, "R2").  The trailing
+// matrix right of and below the block ("R3") receives the four panels'
+// updates together, as one rank-LU_OB product on the tensor cores, so it is
+// read and written once per LU_OB columns instead of once per LU_NB.
+#define LU_OB 128
+#define LU_OB_CHUNKS (LU_OB / LU_NB)
 
-// Column tile TN of the update: 32, 64 or 128 (chosen per step by the tile
+// Strip update on the CUDA cores (FP32 arithmetic): C -= L U with
+// L = A[r0..r1, k..k+LU_NB), U = A[k..k+LU_NB, c0..c1); which = 1 gives the
+// block-column strip (rows k+LU_NB..n, columns k+LU_NB..min(K0+LU_OB, n)),
+// which = 2 the block-row strip (rows k+LU_NB..min(K0+LU_OB, n), columns
+// K0+LU_OB..n).  64 x 64 output tiles, 256 threads with 4 x 4 outputs each.
+template <class T>
+__global__ void __launch_bounds__(256) strip_update_kernel(const LuMat* __restrict__ mats, int K0, int k, int which) {
+  const LuMat mat = mats[blockIdx.z];
+  const int n = mat.n;
+  if (k + LU_NB >= n) return;
+  const int bend = min(K0 + LU_OB, n);
+  const int r0 = k + LU_NB, r1 = which == 1 ? n : bend;
+  const int c0 = which == 1 ? k + LU_NB : K0 + LU_OB, c1 = which == 1 ? bend : n;
+  const int i0 = r0 + blockIdx.x * GT, j0 = c0 + blockIdx.y * GT;
+  if (i0 >= r1 || j0 >= c1) return;
+  T* M = (T*)mat.A;
+  __shared__ T As[LU_NB][GT];
+  __shared__ T Bs[LU_NB][GT];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int t = tid; t < LU_NB * GT; t += 256) {
+    const int r = t % GT, kk = t / GT;
+    As[kk][r] = (i0 + r < r1) ? M[(size_t)(k + kk) * n + i0 + r] : czero<T>();
+    const int kb = t % LU_NB, cj = t / LU_NB;
+    Bs[kb][cj] = (j0 + cj < c1) ? M[(size_t)(j0 + cj) * n + k + kb] : czero<T>();
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = czero<T>();
+#pragma unroll 4
+  for (int kk = 0; kk < LU_NB; ++kk) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gj = j0 + ty + 16 * c;
+    if (gj >= c1) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int gi = i0 + tx + 16 * a;
+      if (gi < r1) {
+        T* d = M + (size_t)gj * n + gi;
+        *d = *d - acc[a][c];
+      }
+    }
+  }
+}
+
+// Tensor-core update of R3: C -= L U with L = A[K0+LU_OB.., K0..K0+LU_OB) and
+// U = A[K0..K0+LU_OB, K0+LU_OB..).  Every FP32 operand is split exactly into
+// three BF16 pieces (x = hi + mid + lo, 24 bits), and the six piece products
+// whose sum carries FP32 precision (hh, hm, mh, hl, mm, lh) are accumulated
+// in FP32 tensor memory (-L_im U_im via the MMA's A-negation).  The hi*hi
+// products and the five smaller corrections go to separate accumulators (Re
+// and Im each, four in all) that are added in registers: sharing one
+// accumulator loses about two bits to the tensor core's accumulation, which
+// measured 4x the error of a plain FP32 update, while the split form measured
+// half of it.  One CTA per 128 x TN output tile of one matrix; 128 threads;
+// the operands arrive in LU_OB_CHUNKS chunks of LU_NB k-columns, each in the
+// MMA's K-major no-swizzle core-matrix format, through one shared buffer.
+#define TCU_M 128
+#define TCU_ATILE (TCU_M * LU_NB)  // bf16 elements per piece chunk of an L tile (128 rows x 32 k)
+
+// Column tile TN of the update: 32, 64 or 128 (chosen per block by the tile
 // autotuner below).  TMEM holds 4 TN accumulator columns; the launch's shared
 // memory is sized so that the CTAs resident on one SM never ask for more than
 // the 512 TMEM columns: 3 CTAs at TN = 32, 2 at 64, 1 at 128.
 template <int TN> struct TcuShape {
-  static constexpr int BTILE = TN * LU_NB;                        // bf16 elements per piece tile of U
-  static constexpr int SMEM = 6 * (TCU_ATILE + BTILE) * 2;        // both operands, six pieces each
+  static constexpr int BTILE = TN * LU_NB;                        // bf16 elements per piece chunk of a U tile
+  static constexpr int SMEM = 6 * (TCU_ATILE + BTILE) * 2;        // one chunk of both operands, six pieces each
   static constexpr int SMEM_LAUNCH = TN == 32 ? 64 * 1024 : TN == 64 ? 100 * 1024 : 120 * 1024;
   static constexpr int TMEM_COLS = 4 * TN;
 };
@@ -436,66 +506,69 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16* p) {
   p[0] = h; p[1] = m; p[2] = __float2bfloat16_rn(r2);
 }
 
-// Per step, the L panel (rows start.., 32 columns) and the U panel (32 rows,
-// columns start..) are split once into their BF16 pieces, stored tile by tile
-// in exactly the shared-memory image the MMAs read: per matrix, ceil(n/128)
-// L tiles of [6 pieces][128 x 32], then ceil(n/TN) U tiles of [6][TN x 32]
-// (room for ceil(n/128) tiles of 128 columns, the largest TN).
+// Workspace of one matrix: the L block column (rows K0+LU_OB.., LU_OB
+// k-columns) and the U block row (LU_OB k-rows, columns K0+LU_OB..) split
+// into their BF16 pieces, stored tile by tile in exactly the shared-memory
+// image the MMAs read: ceil(n/128) L tiles of [LU_OB_CHUNKS][6 pieces][128 x 32],
+// then ceil(n/TN) U tiles of [LU_OB_CHUNKS][6][TN x 32] (room for ceil(n/128)
+// tiles of 128 columns, the largest TN).
 __host__ __device__ inline size_t tcu_ws_matrix_elems(int n) {
-  return (size_t)((n + TCU_M - 1) / TCU_M) * 6 * (TCU_ATILE + 128 * LU_NB);
+  return (size_t)((n + TCU_M - 1) / TCU_M) * LU_OB_CHUNKS * 6 * (TCU_ATILE + 128 * LU_NB);
 }
 
 size_t lu_c64_workspace_bytes(int n, int batch) { return tcu_ws_matrix_elems(n) * (size_t)batch * 2; }
 
 template <int TN>
-__global__ void __launch_bounds__(256) tcu_split_kernel(const LuMat* __restrict__ mats, int k0, int nL) {
+__global__ void __launch_bounds__(256) tcu_split_kernel(const LuMat* __restrict__ mats, int K0, int nL) {
   using S = TcuShape<TN>;
   const LuMat mat = mats[blockIdx.y];
-  const int n = mat.n, nbk = LU_NB;
-  const int start = k0 + nbk, rest = n - start;
+  const int n = mat.n;
+  const int start = K0 + LU_OB, rest = n - start;
+  if (rest <= 0) return;
   const cf* M = (const cf*)mat.A;
   __nv_bfloat16* W = (__nv_bfloat16*)mat.ws;
   __nv_bfloat16 pr[3], pi[3];
   if ((int)blockIdx.x < nL) {
     if ((int)blockIdx.x * TCU_M >= rest) return;
     const int r0 = start + blockIdx.x * TCU_M;
-    __nv_bfloat16* dst = W + (size_t)blockIdx.x * 6 * TCU_ATILE;
-    for (int t = threadIdx.x; t < TCU_M * LU_NB; t += 256) {
-      int r = t % TCU_M, k = t / TCU_M;
-      cf v = (r0 + r < n) ? M[(size_t)(k0 + k) * n + r0 + r] : CF(0.f);
+    __nv_bfloat16* dst = W + (size_t)blockIdx.x * LU_OB_CHUNKS * 6 * TCU_ATILE;
+    for (int t = threadIdx.x; t < TCU_M * LU_OB; t += 256) {
+      const int r = t % TCU_M, kb = t / TCU_M, ch = kb / LU_NB, k = kb % LU_NB;
+      const cf v = (r0 + r < n) ? M[(size_t)(K0 + kb) * n + r0 + r] : CF(0.f);
       split3(v.x, pr); split3(v.y, pi);
-      int off = tcu_off(r, k);
+      __nv_bfloat16* d = dst + (size_t)ch * 6 * TCU_ATILE + tcu_off(r, k);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) { dst[q * TCU_ATILE + off] = pr[q]; dst[(3 + q) * TCU_ATILE + off] = pi[q]; }
+      for (int q = 0; q < 3; ++q) { d[q * TCU_ATILE] = pr[q]; d[(3 + q) * TCU_ATILE] = pi[q]; }
     }
   } else {
     const int y = blockIdx.x - nL;
     if (y * TN >= rest) return;
     const int c0 = start + y * TN;
-    __nv_bfloat16* dst = W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)y * 6 * S::BTILE;
-    for (int t = threadIdx.x; t < TN * LU_NB; t += 256) {
-      int k = t % LU_NB, j = t / LU_NB;
-      cf v = (c0 + j < n) ? M[(size_t)(c0 + j) * n + k0 + k] : CF(0.f);
+    __nv_bfloat16* dst = W + (size_t)((n + TCU_M - 1) / TCU_M) * LU_OB_CHUNKS * 6 * TCU_ATILE +
+                         (size_t)y * LU_OB_CHUNKS * 6 * S::BTILE;
+    for (int t = threadIdx.x; t < TN * LU_OB; t += 256) {
+      const int kb = t % LU_OB, j = t / LU_OB, ch = kb / LU_NB, k = kb % LU_NB;
+      const cf v = (c0 + j < n) ? M[(size_t)(c0 + j) * n + K0 + kb] : CF(0.f);
       split3(v.x, pr); split3(v.y, pi);
-      int off = tcu_off(j, k);
+      __nv_bfloat16* d = dst + (size_t)ch * 6 * S::BTILE + tcu_off(j, k);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) { dst[q * S::BTILE + off] = pr[q]; dst[(3 + q) * S::BTILE + off] = pi[q]; }
+      for (int q = 0; q < 3; ++q) { d[q * S::BTILE] = pr[q]; d[(3 + q) * S::BTILE] = pi[q]; }
     }
   }
 }
 
 template <int TN>
-__global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __restrict__ mats, int k0,
+__global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __restrict__ mats, int K0,
                                                             int* __restrict__ err) {
   using S = TcuShape<TN>;
   const LuMat mat = mats[blockIdx.z];
-  const int n = mat.n, nbk = LU_NB;
-  const int start = k0 + nbk;
+  const int n = mat.n;
+  const int start = K0 + LU_OB;
   if ((int)blockIdx.x * TCU_M >= n - start || (int)blockIdx.y * TN >= n - start) return;  // before any allocation
   extern __shared__ __align__(1024) unsigned char smem[];
   __nv_bfloat16* As = (__nv_bfloat16*)smem;
   __nv_bfloat16* Bs = As + 6 * TCU_ATILE;
-  __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
+  __shared__ __align__(8) uint64_t mbar_load, mbar_mma, mbar_done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_ok;
   cf* M = (cf*)mat.A;
@@ -506,6 +579,7 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __rest
     s_ok = 1;
     tc::mbar_init(&mbar_load, 1);
     tc::mbar_init(&mbar_mma, 1);
+    tc::mbar_init(&mbar_done, 1);
     tc::mbar_fence_init();
   }
   tc::fence_before();
@@ -515,20 +589,27 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __rest
   // accumulator columns: [0,TN) hh Re, [TN,2TN) hh Im, [2TN,3TN) corrections Re, [3TN,4TN) corrections Im
   if (tid == 0) {
     const __nv_bfloat16* W = (const __nv_bfloat16*)mat.ws;
-    const __nv_bfloat16* Lsrc = W + (size_t)blockIdx.x * 6 * TCU_ATILE;
-    const __nv_bfloat16* Usrc =
-        W + (size_t)((n + TCU_M - 1) / TCU_M) * 6 * TCU_ATILE + (size_t)blockIdx.y * 6 * S::BTILE;
-    tc::mbar_expect_tx(&mbar_load, S::SMEM);
-    tc::bulk_g2s(As, Lsrc, 6 * TCU_ATILE * 2, &mbar_load);
-    tc::bulk_g2s(Bs, Usrc, 6 * S::BTILE * 2, &mbar_load);
-    if (tc::mbar_wait(&mbar_load, 0)) {
+    const __nv_bfloat16* Lsrc = W + (size_t)blockIdx.x * LU_OB_CHUNKS * 6 * TCU_ATILE;
+    const __nv_bfloat16* Usrc = W + (size_t)((n + TCU_M - 1) / TCU_M) * LU_OB_CHUNKS * 6 * TCU_ATILE +
+                                (size_t)blockIdx.y * LU_OB_CHUNKS * 6 * S::BTILE;
+    const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TN, false);
+    const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TN, true);
+    const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(As), 128, (LU_NB / 8) * 128);
+    const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(Bs), 128, (LU_NB / 8) * 128);
+    const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(S::BTILE * 2 / 16);  // 16-byte units
+    const int qa_[6] = {0, 0, 1, 0, 1, 2}, qb_[6] = {0, 1, 0, 2, 1, 0};
+    bool ok = true;
+    for (int ch = 0; ch < LU_OB_CHUNKS; ++ch) {
+      // the buffer is free: chunk 0 is the first use, later chunks waited for the previous MMAs below
+      tc::mbar_expect_tx(&mbar_load, S::SMEM);
+      tc::bulk_g2s(As, Lsrc + (size_t)ch * 6 * TCU_ATILE, 6 * TCU_ATILE * 2, &mbar_load);
+      tc::bulk_g2s(Bs, Usrc + (size_t)ch * 6 * S::BTILE, 6 * S::BTILE * 2, &mbar_load);
+      if (!tc::mbar_wait(&mbar_load, ch & 1)) {
+        ok = false;
+        tc::mbar_wait(&mbar_load, ch & 1);  // let copies still in flight land before the CTA can exit
+        break;
+      }
       tc::fence_after();
-      const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TN, false);
-      const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TN, true);
-      const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(As), 128, (LU_NB / 8) * 128);
-      const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(Bs), 128, (LU_NB / 8) * 128);
-      const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(S::BTILE * 2 / 16);  // 16-byte units
-      const int qa_[6] = {0, 0, 1, 0, 1, 2}, qb_[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
       for (int ks = 0; ks < LU_NB / 16; ++ks) {
         const uint64_t kof = (uint64_t)(ks * 256 / 16);  // two core matrices along k
@@ -537,18 +618,20 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __rest
           const uint64_t are = a0 + qa_[u] * at + kof, aim = a0 + (3 + qa_[u]) * at + kof;
           const uint64_t bre = b0 + qb_[u] * bt + kof, bim = b0 + (3 + qb_[u]) * bt + kof;
           const uint32_t dre = tmem + (u == 0 ? 0 : 2 * TN), dim = tmem + (u == 0 ? TN : 3 * TN);
-          const uint32_t acc = (ks == 0 && u <= 1) ? 0u : 1u;  // first write of each accumulator
+          const uint32_t acc = (ch == 0 && ks == 0 && u <= 1) ? 0u : 1u;  // first write of each accumulator
           tc::mma_bf16(dre, are, bre, id_pos, acc);
           tc::mma_bf16(dre, aim, bim, id_neg, 1u);
           tc::mma_bf16(dim, are, bim, id_pos, acc);
           tc::mma_bf16(dim, aim, bre, id_pos, 1u);
         }
       }
-    } else {
-      s_ok = 0;
-      tc::mbar_wait(&mbar_load, 0);  // let copies still in flight land before the CTA can exit
+      if (ch + 1 < LU_OB_CHUNKS) {  // the next chunk overwrites the buffer these MMAs read
+        tc::commit(&mbar_mma);
+        if (!tc::mbar_wait(&mbar_mma, ch & 1)) { ok = false; break; }
+      }
     }
-    tc::commit(&mbar_mma);
+    if (!ok) s_ok = 0;
+    tc::commit(&mbar_done);  // arrives once every MMA issued above has completed
   }
   // while the MMAs run: fetch this thread's row of the first 32 output columns
   const int i = i0 + warp * 32 + lane;
@@ -558,7 +641,7 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __rest
     int j = j0 + c;
     cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
   }
-  const bool done = tc::mbar_wait(&mbar_mma, 0);
+  const bool done = tc::mbar_wait(&mbar_done, 0);
   tc::fence_after();
   __syncthreads();
   const bool ok = done && s_ok;
@@ -594,17 +677,19 @@ __global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __rest
 }
 
 // ---------------------------------------------------------------- driver
+// R3 of outer block K0 for the matrices 0..active-1 (those with n > K0 + LU_OB);
+// rest = nmax - K0 - LU_OB is the largest trailing size.
 template <int TN>
-static void tc_update_tn(const LuMat* d, int k0, int rest, int active, int* tc_err, cudaStream_t s) {
+static void tc_update_tn(const LuMat* d, int K0, int rest, int active, int* tc_err, cudaStream_t s) {
   const int nL = (rest + TCU_M - 1) / TCU_M, nU = (rest + TN - 1) / TN;
-  tcu_split_kernel<TN><<<dim3(nL + nU, active), 256, 0, s>>>(d, k0, nL);
-  gemm_update_tc_kernel<TN><<<dim3(nL, nU, active), 128, TcuShape<TN>::SMEM_LAUNCH, s>>>(d, k0, tc_err);
+  tcu_split_kernel<TN><<<dim3(nL + nU, active), 256, 0, s>>>(d, K0, nL);
+  gemm_update_tc_kernel<TN><<<dim3(nL, nU, active), 128, TcuShape<TN>::SMEM_LAUNCH, s>>>(d, K0, tc_err);
 }
 
-static void tc_update(int tn, const LuMat* d, int k0, int rest, int active, int* tc_err, cudaStream_t s) {
-  if (tn == 32) tc_update_tn<32>(d, k0, rest, active, tc_err, s);
-  else if (tn == 128) tc_update_tn<128>(d, k0, rest, active, tc_err, s);
-  else tc_update_tn<64>(d, k0, rest, active, tc_err, s);
+static void tc_update(int tn, const LuMat* d, int K0, int rest, int active, int* tc_err, cudaStream_t s) {
+  if (tn == 32) tc_update_tn<32>(d, K0, rest, active, tc_err, s);
+  else if (tn == 128) tc_update_tn<128>(d, K0, rest, active, tc_err, s);
+  else tc_update_tn<64>(d, K0, rest, active, tc_err, s);
 }
 
 static void tc_set_attributes() {
@@ -645,7 +730,7 @@ __global__ void tune_fill_kernel(cf* A, size_t count) {
 }
 
 static int measure_tile(int R, int count, cudaStream_t s, std::array<float, 3>& ms) {
-  const int n = R + LU_NB;
+  const int n = R + LU_OB;
   const size_t elems = (size_t)n * n, wse = tcu_ws_matrix_elems(n);
   const size_t per = elems * sizeof(cf) + wse * 2;
   const int c = (int)std::min<size_t>((size_t)count, std::max<size_t>(1, ((size_t)1 << 30) / per));
@@ -702,10 +787,10 @@ static int measure_tile(int R, int count, cudaStream_t s, std::array<float, 3>& 
 static void autotune_tiles(int nmax, int count, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const int cb = count_bucket(count);
-  for (int rb = 0; rb <= rest_bucket(nmax - LU_NB); ++rb) {
+  for (int rb = 0; rb <= rest_bucket(nmax - LU_OB); ++rb) {
     if (g_tune.count({rb, cb})) continue;
     std::array<float, 3> ms;
-    const int tn = measure_tile(96 << rb, count, s, ms);
+    const int tn = measure_tile(96 << rb, count, s, ms);  // the bucket's middle trailing size
     g_tune[{rb, cb}] = tn;
     g_tune_ms[{rb, cb}] = ms;
   }
@@ -769,7 +854,20 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
   int launches = 1, gemm_launches = 0, tn_steps[3] = {0, 0, 0};
   double gemm_flops = 0.0, gemm_bytes = 0.0;
   int active = count;
-  for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
+  auto timed_launch = [&](auto&& launch) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+      cudaEventCreate(&e0); cudaEventCreate(&e1);
+      cudaEventRecord(e0, ls);
+    }
+    launch();
+    if (timed) {
+      cudaEventRecord(e1, ls);
+      ev.push_back(e0); ev.push_back(e1);
+    }
+  };
+  // one LU_NB panel at column k0: factor, interchange, rows of U right of it
+  auto panel_step = [&](int k0) -> int {
     while (active > 0 && it[active - 1].n <= k0) --active;
     const int nbk = std::min(LU_NB, nmax - k0);
     if (!launch_panel_cluster<T>(d, nmax - k0, k0, active, ls)) panel_kernel<T><<<active, 1024, 0, ls>>>(d, k0);
@@ -779,35 +877,67 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
       ++launches;
     }
     const int rest = nmax - k0 - nbk;
-    if (rest <= 0) continue;
-    trsm_kernel<T><<<dim3((rest + 127) / 128, active), 128, 0, ls>>>(d, k0);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timed) {
-      cudaEventCreate(&e0); cudaEventCreate(&e1);
-      cudaEventRecord(e0, ls);
+    if (rest > 0) {
+      trsm_kernel<T><<<dim3((rest + 127) / 128, active), 128, 0, ls>>>(d, k0);
+      ++launches;
     }
-    if constexpr (c64) {
-      const int tn = tile ? tile : tuned_tile(rest, active);
-      tc_update(tn, d, k0, rest, active, tc_err, ls);
-      ++tn_steps[tn == 32 ? 0 : tn == 64 ? 1 : 2];
-      launches += 3;
-    } else {
-      const int t = (rest + GT - 1) / GT;
-      gemm_update_kernel<T><<<dim3(t, t, active), 256, 0, ls>>>(d, k0);
-      launches += 2;
-    }
-    if (timed) {
-      cudaEventRecord(e1, ls);
-      ev.push_back(e0); ev.push_back(e1);
-    }
-    for (int b = 0; b < active; ++b) {
-      const double rb = (double)(it[b].n - k0 - LU_NB);
-      if (rb > 0) {
-        gemm_flops += 8.0 * rb * rb * LU_NB;
-        gemm_bytes += 2.0 * sizeof(T) * rb * rb;   // the trailing matrix read and written once
+    return rest;
+  };
+  if constexpr (c64) {
+    // two-level: LU_NB panels inside LU_OB blocks, one rank-LU_OB tensor-core update per block
+    for (int K0 = 0; K0 < nmax; K0 += LU_OB) {
+      for (int p = 0; p < LU_OB_CHUNKS; ++p) {
+        const int k0 = K0 + p * LU_NB;
+        if (k0 >= nmax) break;
+        if (panel_step(k0) <= 0) continue;
+        const int rows = nmax - k0 - LU_NB;                       // R1: block columns right of the panel
+        const int bcols = std::min(K0 + LU_OB, nmax) - k0 - LU_NB;
+        if (bcols > 0) {
+          strip_update_kernel<T><<<dim3((rows + GT - 1) / GT, (bcols + GT - 1) / GT, active), 256, 0, ls>>>(
+              d, K0, k0, 1);
+          ++launches;
+        }
+        const int tail = nmax - K0 - LU_OB;                         // R2: block rows below the panel
+        if (bcols > 0 && tail > 0) {
+          strip_update_kernel<T><<<dim3((bcols + GT - 1) / GT, (tail + GT - 1) / GT, active), 256, 0, ls>>>(
+              d, K0, k0, 2);
+          ++launches;
+        }
       }
+      const int rest = nmax - K0 - LU_OB;                            // R3
+      if (rest <= 0) continue;
+      int a3 = active;
+      while (a3 > 0 && it[a3 - 1].n <= K0 + LU_OB) --a3;
+      if (a3 <= 0) continue;
+      const int tn = tile ? tile : tuned_tile(rest, a3);
+      timed_launch([&] { tc_update(tn, d, K0, rest, a3, tc_err, ls); });
+      ++tn_steps[tn == 32 ? 0 : tn == 64 ? 1 : 2];
+      launches += 2;
+      for (int b = 0; b < a3; ++b) {
+        const double rb = (double)(it[b].n - K0 - LU_OB);
+        if (rb > 0) {
+          gemm_flops += 8.0 * rb * rb * LU_OB;
+          gemm_bytes += 2.0 * sizeof(T) * rb * rb;   // the trailing matrix read and written once
+        }
+      }
+      ++gemm_launches;
     }
-    ++gemm_launches;
+  } else {
+    for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
+      const int rest = panel_step(k0);
+      if (rest <= 0) continue;
+      const int t = (rest + GT - 1) / GT;
+      timed_launch([&] { gemm_update_kernel<T><<<dim3(t, t, active), 256, 0, ls>>>(d, k0); });
+      ++launches;
+      for (int b = 0; b < active; ++b) {
+        const double rb = (double)(it[b].n - k0 - LU_NB);
+        if (rb > 0) {
+          gemm_flops += 8.0 * rb * rb * LU_NB;
+          gemm_bytes += 2.0 * sizeof(T) * rb * rb;
+        }
+      }
+      ++gemm_launches;
+    }
   }
   if (graph) {
     cudaGraph_t g = nullptr;

@@ -12,7 +12,11 @@ the seeded synthetic inputs.  For one named workload the script
    with the oracle's naive partial-pivot LU and solves for the plane-wave
    data of eq. pw (``oracle.fields.modal_rhs``);
 3. evaluates the far field (eq. farfieldform, magnetic current in the last
-   term) of the solved currents at fixed directions.
+   term) of the solved currents at fixed directions;
+4. for the modes whose currents are kept, also solves two seeded random
+   right-hand sides (complex normal entries, numpy default_rng(7000 + m)),
+   so that modes whose plane-wave data are below rounding are still
+   compared on solutions of full size.
 
 Workloads:
   cylinder  finite cylinder R = 1, H = 2, 7 dyadic levels at each edge
@@ -90,7 +94,7 @@ def _rows_job(args):
 
 
 def _solve_job(args):
-    name, qi, path, b = args
+    name, qi, path, b, brand = args
     from oracle import system, linalg
     cfg, _ = workload(name)
     A = np.array(np.load(path, mmap_mode="r")[qi])
@@ -100,7 +104,10 @@ def _solve_job(args):
     bw = b * sw[:, None]
     y = linalg.lu_solve(LU, piv, bw)
     res = np.abs(Aw @ y - bw).max() / (np.abs(Aw).sum(1).max() * np.abs(y).max() + np.abs(bw).max())
-    return qi, y / sw[:, None], float(res)
+    xr = None
+    if brand is not None:
+        xr = linalg.lu_solve(LU, piv, brand * sw[:, None]) / sw[:, None]
+    return qi, y / sw[:, None], float(res), xr
 
 
 def main():
@@ -126,12 +133,20 @@ def main():
             done += k
             print(f"[{time.time() - t0:7.0f} s] assembled {done}/{N} rows", flush=True)
         b_all = fields.modal_rhs(cfg.curve, cfg.media, M, cfg.waves)     # [2M+1, n, nrhs]
-        jobs = [(name, qi, path, b_all[m + M]) for qi, m in enumerate(modes)]
+        keep = KEEP[name]
+        brand = {}
+        for m in keep["modes"]:
+            rng = np.random.default_rng(7000 + m)
+            brand[m] = rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2))
+        jobs = [(name, qi, path, b_all[m + M], brand.get(m)) for qi, m in enumerate(modes)]
         x = np.zeros((len(modes), n, len(cfg.waves)), dtype=complex)
+        xrand = {}
         berr = np.zeros(len(modes))
-        for qi, xq, res in pool.imap_unordered(_solve_job, jobs):
+        for qi, xq, res, xr in pool.imap_unordered(_solve_job, jobs):
             x[qi] = xq
             berr[qi] = res
+            if xr is not None:
+                xrand[modes[qi]] = xr
             print(f"[{time.time() - t0:7.0f} s] solved mode {modes[qi]} (backward error {res:.1e})", flush=True)
     os.remove(path)
     # far field of the solved modes (the others zero)
@@ -140,7 +155,6 @@ def main():
         xf[m + M] = x[qi]
     dirs = far_directions()
     ff = fields.far_field(cfg.curve, cfg.media, M, xf, dirs)          # [nrhs, nd, 3]
-    keep = KEEP[name]
     kq = [modes.index(m) for m in keep["modes"]]
     out = os.path.join(HERE, f"fullsize_{name}.npz")
     np.savez_compressed(
@@ -153,7 +167,10 @@ def main():
         solved_modes=np.array(modes), backward_err=berr,
         modes=np.array(keep["modes"]), waves=np.array(keep["waves"]),
         x=x[kq][:, :, keep["waves"]].transpose(0, 2, 1).copy(),     # [modes, waves, 4N]
-        ff_dirs=dirs, ff=ff, seconds=time.time() - t0)
+        ff_dirs=dirs, ff=ff,
+        b_rand=np.stack([brand[m].T for m in keep["modes"]]),      # [modes, 2, 4N]
+        x_rand=np.stack([xrand[m].T for m in keep["modes"]]),
+        seconds=time.time() - t0)
     print(f"wrote {out} in {time.time() - t0:.0f} s; max oracle backward error {berr.max():.1e}")
 
 

@@ -13,7 +13,10 @@ Tolerances (the build's targets): FP64 path 1e-10, mixed path 1e-9, relative
 l2 per mode and plane wave, normalised by the largest mode's currents (a
 mode with tiny currents is compared on the scale of the solution; the plain
 per-mode relative error is bounded separately for modes above 1e-6 of the
-largest); far field relative l2 over all directions and components.
+largest); far field relative l2 over all directions and components; and,
+per stored mode, the solutions of two seeded random right-hand sides, plain
+relative l2 (these are full-size solutions for every mode, including those
+whose plane-wave data are below rounding).
 
 Also: a closed curve (torus, Section 6) with sampled 4x4 blocks across the
 wrap-around, where the first and last panels are neighbours.
@@ -80,12 +83,22 @@ def _check(mb, name, precision, tol):
     E = torch.zeros((nrhs, len(dirs), 3), dtype=torch.complex128, device=DEV)
     ctx.far_field(keep, dirs, E)
     ff = np.linalg.norm(E.cpu().numpy() - g["ff"]) / np.linalg.norm(g["ff"])
+    # seeded random right-hand sides of the stored modes: every mode's solution has full size
+    br = torch.zeros((2 * M + 1, 2, n), dtype=torch.complex128, device=DEV)
+    for qi, m in enumerate(modes):
+        br[m + M] = torch.tensor(g["b_rand"][qi], device=DEV)
+    xr = torch.zeros_like(br)
+    ctx.solve(br, xr)
+    xr = xr.cpu().numpy()
+    worst_rand = max(np.linalg.norm(xr[m + M, c] - g["x_rand"][qi, c]) / np.linalg.norm(g["x_rand"][qi, c])
+                     for qi, m in enumerate(modes) for c in range(2))
     ctx.close()
     print(f"{name} precision {precision}: currents {worst_global:.2e} (plain per mode {worst_plain:.2e}), "
-          f"far field {ff:.2e}")
+          f"far field {ff:.2e}, random right-hand sides per mode {worst_rand:.2e}")
     assert worst_global < tol, worst_global
     assert worst_plain < 100 * tol, worst_plain
     assert ff < tol, ff
+    assert worst_rand < tol, worst_rand
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])

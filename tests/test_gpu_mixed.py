@@ -68,7 +68,8 @@ def test_mixed_lu_tiles(mb, tile):
     """Each column tile of the tensor-core LU update (32, 64, 128 columns per
     CTA) gives FP32-grade factors: refinement reaches 1e-14 in a few steps and
     the currents agree with the FP64 path.  The body (N = 448, system 1792,
-    modes 0..12) spans 14 row tiles of 128 and a ragged last tile per step."""
+    modes 0..12) spans 14 row tiles of 128 and a ragged last tile per step;
+    the factorization updates the trailing matrix once per 128 columns."""
     body = W.random_body(28, seed=7)
     media = W.Media.from_k(4.0, 6.0)
     M, n = 12, 4 * body.N
@@ -82,7 +83,8 @@ def test_mixed_lu_tiles(mb, tile):
     cmx = mb.build(body, media, M, mb.Options(n_phi=64, precision=1, refine_tol=1e-14, lu_tile=tile))
     st = cmx.stats()
     q = {32: 0, 64: 1, 128: 2}[tile]
-    assert st["lu_tile_steps"][q] == sum(st["lu_tile_steps"]) == (n - 1) // 32
+    # one tensor-core update per 128-column block with a trailing matrix
+    assert st["lu_tile_steps"][q] == sum(st["lu_tile_steps"]) == (n - 1) // 128
     x = torch.zeros_like(b)
     be = np.zeros((2 * M + 1) * len(waves))
     cmx.solve(b, x, backward_err=be)
@@ -97,7 +99,7 @@ def test_tile_autotuner_table(mb):
     body = W.random_body(28, seed=8)
     ctx = mb.build(body, W.Media.from_k(4.0, 6.0), 12, mb.Options(n_phi=64, precision=1))
     st = ctx.stats()
-    assert sum(st["lu_tile_steps"]) == (4 * body.N - 1) // 32
+    assert sum(st["lu_tile_steps"]) == (4 * body.N - 1) // 128
     ctx.close()
     table = mb.lu_tile_table()
     assert table
