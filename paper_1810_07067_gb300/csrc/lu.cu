@@ -19,6 +19,10 @@
 
 namespace cg = cooperative_groups;
 
+// Outer block of the complex64 factorization (see "two-level blocking" below).
+#define LU_OB 128
+#define LU_OB_CHUNKS (LU_OB / LU_NB)
+
 // ---------------------------------------------------------------- panel
 // Pivot measure: |a|^2 in FP64 for complex128; |Re a| + |Im a| in FP32 for
 // complex64 (LAPACK's complex pivot measure; GB300's FP64 pipe is too slow to
@@ -266,13 +270,21 @@ static bool launch_panel_cluster(const LuMat* mats, int rows, int k0, int batch,
 // below it (slot nbk + lane of the first interchange naming it).  One warp
 // forms it per CTA; each warp then moves the affected entries of its columns
 // (all loads before all stores).
+//
+// Columns (mode): 0 all but the panel's own; 1 those left of the panel and
+// the rest of its LU_OB block (columns < min(K0 + LU_OB, n)); 2 those right
+// of the block.
 #define SWAP_COLS 64
 template <class T>
-__global__ void __launch_bounds__(256) swap_kernel(const LuMat* __restrict__ mats, int k0) {
+__global__ void __launch_bounds__(256) swap_kernel(const LuMat* __restrict__ mats, int k0, int K0, int mode) {
   const LuMat mat = mats[blockIdx.y];
   const int n = mat.n;
   if (k0 >= n) return;
   const int nbk = min(LU_NB, n - k0);
+  const int bend = min(K0 + LU_OB, n);
+  const int lo = mode == 2 ? bend : 0, hi = mode == 1 ? bend : n;
+  const bool skip = mode != 2;  // the panel's columns lie inside [lo, hi)
+  const int ncols = hi - lo - (skip ? nbk : 0);
   const int* piv = mat.piv;
   __shared__ int pos[2 * LU_NB], src[2 * LU_NB], slot[LU_NB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -298,9 +310,10 @@ __global__ void __launch_bounds__(256) swap_kernel(const LuMat* __restrict__ mat
   __syncthreads();
   const int d0 = pos[lane], d1 = pos[lane + 32], s0 = src[lane], s1 = src[lane + 32];
   for (int cc = warp; cc < SWAP_COLS; cc += 8) {
-    int c = blockIdx.x * SWAP_COLS + cc;
-    if (c >= n - nbk) break;  // whole warp
-    if (c >= k0) c += nbk;     // skip the panel's own columns
+    const int idx = blockIdx.x * SWAP_COLS + cc;
+    if (idx >= ncols) break;  // whole warp
+    int c = lo + idx;
+    if (skip && c >= k0) c += nbk;  // skip the panel's own columns
     T* col = (T*)mat.A + (size_t)c * n;
     T v0 = czero<T>(), v1 = czero<T>();
     if (d0 >= 0 && d0 != s0) v0 = col[s0];
@@ -313,12 +326,16 @@ __global__ void __launch_bounds__(256) swap_kernel(const LuMat* __restrict__ mat
 }
 
 // ---------------------------------------------------------------- U12 = L11^{-1} A12
+// Columns (mode): 0 all right of the panel; 1 those right of the panel
+// inside its LU_OB block; 2 those right of the block.
 template <class T>
-__global__ void trsm_kernel(const LuMat* __restrict__ mats, int k0) {
+__global__ void trsm_kernel(const LuMat* __restrict__ mats, int k0, int K0, int mode) {
   const LuMat mat = mats[blockIdx.y];
   const int n = mat.n;
-  if (k0 + LU_NB >= n) return;  // no columns right of the block (or the block is the last)
+  if (k0 + LU_NB >= n) return;  // no columns right of the panel (or the panel is the last)
   const int nbk = LU_NB;
+  const int bend = min(K0 + LU_OB, n);
+  const int clo = mode == 2 ? bend : k0 + nbk, chi = mode == 1 ? bend : n;
   T* M = (T*)mat.A;
   __shared__ T L[LU_NB][LU_NB + 1];
   for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
@@ -326,8 +343,8 @@ __global__ void trsm_kernel(const LuMat* __restrict__ mats, int k0) {
     L[r][cc] = M[(size_t)(k0 + cc) * n + k0 + r];
   }
   __syncthreads();
-  int c = k0 + nbk + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+  const int c = clo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= chi) return;
   T* col = M + (size_t)c * n + k0;
   T x[LU_NB];
 #pragma unroll
@@ -400,15 +417,19 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const LuMat* __restric
 
 // ---------------------------------------------------------------- two-level blocking (complex64)
 // The complex64 factorization works on outer blocks of LU_OB = 4 LU_NB
-// columns.  Inside a block each LU_NB panel is factored, its interchanges
-// applied, its rows of U formed, and only two thin strips are updated at
-// once: the rest of the block's columns (all rows below, "R1") and the rest
-// of the block's rows (all columns right of the block, "R2").  The trailing
-// matrix right of and below the block ("R3") receives the four panels'
-// updates together, as one rank-LU_OB product on the tensor cores, so it is
-// read and written once per LU_OB columns instead of once per LU_NB.
-#define LU_OB 128
-#define LU_OB_CHUNKS (LU_OB / LU_NB)
+// columns.  Inside a block, each LU_NB panel is factored, its interchanges
+// are applied to the columns left of it and to the rest of the block, its
+// rows of U are formed within the block, and the block's remaining columns
+// are updated (all rows below: "R1").  Then the columns right of the block
+// take the block's interchanges, in order, and the block's rows of U there
+// are formed panel by panel (each panel's triangular solve followed by the
+// update of the block's remaining rows: "R2").  Last, the trailing matrix
+// right of and below the block ("R3") receives the four panels' updates
+// together, as one rank-LU_OB product on the tensor cores, so it is read and
+// written once per LU_OB columns instead of once per LU_NB.  (The columns
+// right of the block must not take a panel's interchanges before the block
+// is done: a row from below the block, without the deferred updates, would
+// trade places with a row inside it, with them.)
 
 // Strip update on the CUDA cores (FP32 arithmetic): C -= L U with
 // L = A[r0..r1, k..k+LU_NB), U = A[k..k+LU_NB, c0..c1); which = 1 gives the
@@ -867,18 +888,20 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
     }
   };
   // one LU_NB panel at column k0: factor, interchange, rows of U right of it
-  auto panel_step = [&](int k0) -> int {
+  // (mode 0: all columns; mode 1: within the LU_OB block starting at K0)
+  auto panel_step = [&](int k0, int K0, int mode) -> int {
     while (active > 0 && it[active - 1].n <= k0) --active;
     const int nbk = std::min(LU_NB, nmax - k0);
     if (!launch_panel_cluster<T>(d, nmax - k0, k0, active, ls)) panel_kernel<T><<<active, 1024, 0, ls>>>(d, k0);
     ++launches;
-    if (nmax - nbk > 0) {
-      swap_kernel<T><<<dim3((nmax - nbk + SWAP_COLS - 1) / SWAP_COLS, active), 256, 0, ls>>>(d, k0);
+    const int hi = mode == 1 ? std::min(K0 + LU_OB, nmax) : nmax;
+    if (hi - nbk > 0) {
+      swap_kernel<T><<<dim3((hi - nbk + SWAP_COLS - 1) / SWAP_COLS, active), 256, 0, ls>>>(d, k0, K0, mode);
       ++launches;
     }
-    const int rest = nmax - k0 - nbk;
+    const int rest = hi - k0 - nbk;
     if (rest > 0) {
-      trsm_kernel<T><<<dim3((rest + 127) / 128, active), 128, 0, ls>>>(d, k0);
+      trsm_kernel<T><<<dim3((rest + 127) / 128, active), 128, 0, ls>>>(d, k0, K0, mode);
       ++launches;
     }
     return rest;
@@ -889,26 +912,34 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
       for (int p = 0; p < LU_OB_CHUNKS; ++p) {
         const int k0 = K0 + p * LU_NB;
         if (k0 >= nmax) break;
-        if (panel_step(k0) <= 0) continue;
-        const int rows = nmax - k0 - LU_NB;                       // R1: block columns right of the panel
-        const int bcols = std::min(K0 + LU_OB, nmax) - k0 - LU_NB;
-        if (bcols > 0) {
-          strip_update_kernel<T><<<dim3((rows + GT - 1) / GT, (bcols + GT - 1) / GT, active), 256, 0, ls>>>(
-              d, K0, k0, 1);
-          ++launches;
-        }
-        const int tail = nmax - K0 - LU_OB;                         // R2: block rows below the panel
-        if (bcols > 0 && tail > 0) {
-          strip_update_kernel<T><<<dim3((bcols + GT - 1) / GT, (tail + GT - 1) / GT, active), 256, 0, ls>>>(
+        const int bcols = panel_step(k0, K0, 1);                    // R1: block columns right of the panel
+        if (bcols <= 0) continue;
+        const int rows = nmax - k0 - LU_NB;
+        strip_update_kernel<T><<<dim3((rows + GT - 1) / GT, (bcols + GT - 1) / GT, active), 256, 0, ls>>>(
+            d, K0, k0, 1);
+        ++launches;
+      }
+      const int rest = nmax - K0 - LU_OB;                           // columns right of the block
+      if (rest <= 0) continue;
+      int a3 = active;                                               // the matrices that have them
+      while (a3 > 0 && it[a3 - 1].n <= K0 + LU_OB) --a3;
+      if (a3 <= 0) continue;
+      for (int p = 0; p < LU_OB_CHUNKS; ++p) {                      // the block's interchanges, in order
+        swap_kernel<T><<<dim3((rest + SWAP_COLS - 1) / SWAP_COLS, a3), 256, 0, ls>>>(d, K0 + p * LU_NB, K0, 2);
+        ++launches;
+      }
+      for (int p = 0; p < LU_OB_CHUNKS; ++p) {                      // rows of U right of the block; R2
+        const int k0 = K0 + p * LU_NB;
+        trsm_kernel<T><<<dim3((rest + 127) / 128, a3), 128, 0, ls>>>(d, k0, K0, 2);
+        ++launches;
+        const int brows = LU_OB - (p + 1) * LU_NB;
+        if (brows > 0) {
+          strip_update_kernel<T><<<dim3((brows + GT - 1) / GT, (rest + GT - 1) / GT, a3), 256, 0, ls>>>(
               d, K0, k0, 2);
           ++launches;
         }
       }
-      const int rest = nmax - K0 - LU_OB;                            // R3
-      if (rest <= 0) continue;
-      int a3 = active;
-      while (a3 > 0 && it[a3 - 1].n <= K0 + LU_OB) --a3;
-      if (a3 <= 0) continue;
+      // R3
       const int tn = tile ? tile : tuned_tile(rest, a3);
       timed_launch([&] { tc_update(tn, d, K0, rest, a3, tc_err, ls); });
       ++tn_steps[tn == 32 ? 0 : tn == 64 ? 1 : 2];
@@ -924,7 +955,7 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
     }
   } else {
     for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
-      const int rest = panel_step(k0);
+      const int rest = panel_step(k0, 0, 0);
       if (rest <= 0) continue;
       const int t = (rest + GT - 1) / GT;
       timed_launch([&] { gemm_update_kernel<T><<<dim3(t, t, active), 256, 0, ls>>>(d, k0); });
