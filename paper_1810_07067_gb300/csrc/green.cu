@@ -142,51 +142,61 @@ __device__ __forceinline__ WarpSmem warp_smem(const GreenParams& gp, char* base)
 }
 
 // The pair is the target (rt, zt) and the displacement (dr0, zd) = target - source.
-// Non-split pairs are sampled on every dec-th point of the n_phi grid
-// (dec = 1, 2, 4: a coarser grid for well-separated pairs, chosen so that the
-// trapezoid aliasing stays below the splitting threshold) or, where it is
-// smaller still, on the compact grid of gp.nc points (returned as dec = 0);
-// split pairs use the full grid.  The cosine transform folds samples j and
-// n/2 - j (cos of the mirrored angle is (-1)^m times the original), halving
-// its work.
-//
-// Aliasing on an n-point grid: mode m <= M + 1 picks up the coefficients of
-// modes n - m and beyond, which decay like zeta^m (zeta = chi - sqrt(chi^2 - 1),
-// the singularity of 1/rho at cos phi = chi) once m exceeds the bandwidth of
-// the oscillating factor exp(i k rho), about |k| sqrt(r_t r_s).  The compact
-// grid is taken when (nc - M - 1 - K) ln(1/zeta) >= -ln(eps) with
-// K = 1.5 |k|max sqrt(r_t r_s) + 8, a margin over that bandwidth.
-__device__ int decimation(const GreenParams& gp, double rt, double dr0, double zd, bool split, double lneps) {
-  if (split) return 1;
+// Split pairs are sampled on the full n_phi grid and keep all modes 0..M+1.
+// A non-split pair's spectra decay like zeta^(m - K) past the band of the
+// oscillating factor exp(i k rho) (zeta = chi - sqrt(chi^2 - 1), the
+// singularity of 1/rho at cos phi = chi; the band is about |k| sqrt(r_t r_s),
+// with margin K = 1.5 |k|max sqrt(r_t r_s) + 8).  So
+//  - modes above mc = min(M + 1, ceil(K + ln(1/eps) / ln(1/zeta))) are below
+//    eps of the family's largest coefficient and are set to zero;
+//  - on an n-point grid, mode m <= mc picks up the aliases of modes n - m and
+//    beyond, below eps once n >= mc + K + ln(1/eps) / ln(1/zeta);
+// and the pair is sampled on the smallest grid of the ladder (every multiple
+// of 8 below n_phi: two folds) that keeps modes 0..mc distinct (n >= 2 mc + 2)
+// and the aliases below eps, or on the full grid when none does.  eps is the
+// splitting threshold.  Neither choice changes the computed quantity by more
+// than eps of a family's largest coefficient.  The cosine transform folds
+// samples j and n/2 - j (cos of the mirrored angle is (-1)^m times the
+// original), halving its work.
+struct PairGrid {
+  int nl;        // grid size
+  int mc;        // highest mode computed (modes above are zero)
+  const double* cosL;  // cos(2 pi t / nl), t < nl
+  const double* s2L;   // sin^2(pi j / nl), j <= nl / 2
+};
+
+__device__ __forceinline__ PairGrid full_grid(const GreenParams& gp, const double* cosT, const double* s2T) {
+  return PairGrid{gp.nphi, gp.Ms - 1, cosT, s2T};
+}
+
+__device__ PairGrid pair_grid(const GreenParams& gp, double rt, double dr0, double zd, bool split, double lneps,
+                              const double* cosT, const double* s2T, const double* ladC, const double* ladS) {
+  if (split || gp.qmax < 2) return full_grid(gp, cosT, s2T);
   const double d2 = dr0 * dr0 + zd * zd, B = 2.0 * rt * (rt - dr0);
   const double c = d2 / B;
   const double lz = log1p(c + sqrt(c * (2.0 + c)));
-  int dec = 1;
-  while (dec < 4) {
-    int nl = gp.nphi / (2 * dec);
-    if (nl < 16 || nl < 2 * gp.M + 4 || (double)(nl - gp.M - 1) * lz < lneps) break;
-    dec *= 2;
-  }
-  if (gp.nc > 0 && gp.nc < gp.nphi / dec) {
-    const double kmax = fmax(cabs(gp.kp0.k), cabs(gp.kp1.k));
-    const double K = 1.5 * kmax * sqrt(0.5 * B) + 8.0;
-    if ((double)(gp.nc - gp.M - 1) - K > 0.0 && ((double)(gp.nc - gp.M - 1) - K) * lz >= lneps) return 0;
-  }
-  return dec;
+  const double kmax = fmax(cabs(gp.kp0.k), cabs(gp.kp1.k));
+  const double K = 1.5 * kmax * sqrt(0.5 * B) + 8.0;
+  const double span = lneps / lz;
+  const int mc = (int)fmin((double)(gp.Ms - 1), ceil(K + span));
+  const double need = fmax(2.0 * mc + 2.0, fmax(16.0, ceil(mc + K + span)));
+  const int q = (int)ceil(need / 8.0);
+  if (q > gp.qmax) return full_grid(gp, cosT, s2T);
+  // ladder tables: sizes 8q' for q' = 2..qmax, cos tables then s2 tables
+  const int offc = 4 * (q - 1) * q - 8, offs = 2 * (q - 1) * q - 4 + (q - 2);
+  return PairGrid{8 * q, mc, ladC + offc, ladS + offs};
 }
 
 __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
                                   long long sid, const double* __restrict__ leg, long long n_split,
                                   const double* __restrict__ cosT, const double* __restrict__ s2T,
-                                  const WarpSmem& W, int lane, int dec = 1,
-                                  const double* __restrict__ cosC = nullptr, const double* __restrict__ s2C = nullptr) {
+                                  const WarpSmem& W, int lane, const PairGrid& g) {
   const int Ms = gp.Ms, Mq = gp.Mq, mask = gp.nphi - 1;
-  const bool compact = dec == 0;
-  const int nl = compact ? gp.nc : gp.nphi / dec;  // local grid size
-  // local sample j sits at entry j * tstride of a table of T entries
-  const double* __restrict__ cosL = compact ? cosC : cosT;
-  const double* __restrict__ s2L = compact ? s2C : s2T;
-  const int T = compact ? gp.nc : gp.nphi, tstride = compact ? 1 : dec;
+  const int nl = g.nl;  // local grid size; sample j sits at entry j of its tables
+  const double* __restrict__ cosL = g.cosL;
+  const double* __restrict__ s2L = g.s2L;
+  const int T = nl, tstride = 1;
+  const int Me = g.mc + 1;  // modes 0..mc computed, the rest zero
   const int H = nl / 2 + 1, Q = nl / 4;  // samples on [0, pi]; fold point
   const double rs = rt - dr0;
   const double d2 = dr0 * dr0 + zd * zd;
@@ -325,8 +335,9 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
   // lanes busy where one mode per lane would leave most of the last round
   // idle.  Items run odd modes first, then m = 2 mod 4, then m = 0 mod 4
   // (with fold2), so that the lanes of a round mostly share a trip count.
-  const int n_odd = Ms / 2, n_2 = (Ms + 1) / 4;
-  for (int it = lane; it < 3 * Ms; it += 32) {
+  const int n_odd = Me / 2, n_2 = (Me + 1) / 4;
+  for (int t = lane; t < NFAM * (Ms - Me); t += 32) W.spec[(t / (Ms - Me)) * Ms + Me + t % (Ms - Me)] = C(0.0);
+  for (int it = lane; it < 3 * Me; it += 32) {
     const int k = it / 3, f0 = 3 * (it % 3);
     int mm, cls;  // cls 1: odd, 2: m = 2 mod 4, 0: m = 0 mod 4 (without fold2: 0 for every even m)
     if (!fold2) { mm = k; cls = mm & 1; }
@@ -462,6 +473,16 @@ __device__ __forceinline__ void store_block(cd* __restrict__ A, int n, int m, in
   }
 }
 
+__device__ __forceinline__ void store_zero_block(cd* __restrict__ A, int n, int m, int i, int j) {
+  size_t base = (size_t)m * n * n;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    double2* dst = (double2*)(A + base + (size_t)(4 * j + b) * n + 4 * i);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) dst[a] = make_double2(0.0, 0.0);
+  }
+}
+
 __device__ __forceinline__ bool near_panels(int Pi, int Pj, int nP, int closed) {
   int d = Pi - Pj;
   if (d >= -1 && d <= 1) return true;
@@ -513,14 +534,23 @@ __global__ void far_kernel(BuildArgs a) {
     long long sid = a.split_far[p];
     double rt = a.geo.r[i], rs = a.geo.r[j];
     const double dr0 = rt - rs, zd0 = a.geo.z[i] - a.geo.z[j];
-    int dec = decimation(gp, rt, dr0, zd0, sid >= 0, a.lneps);
-    warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec, a.cosC, a.s2C);
-    for (int m = lane; m < full; m += 32) assemble(W.spec, gp.Ms, 0, i, j, m);
+    const PairGrid g = pair_grid(gp, rt, dr0, zd0, sid >= 0, a.lneps, a.cosT, a.s2T, a.ladC, a.ladS);
+    warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, g);
+    // modes above mz have zero spectra at m - 1, m and m + 1: their blocks are zero
+    const int mz = min(gp.M, g.mc + 1);
+    for (int m = lane; m < full; m += 32) {
+      if (m <= mz) assemble(W.spec, gp.Ms, 0, i, j, m);
+      else store_zero_block(a.A, n, m, i, j);
+    }
     if (tq) {
-      cd* dst = Qs + (long long)qn * tw * NFAM;
-      for (int t = lane; t < NFAM * tw; t += 32) dst[t] = W.spec[(t / tw) * gp.Ms + full - 1 + t % tw];
-      if (lane == 0) { Qij[2 * qn] = i; Qij[2 * qn + 1] = j; }
-      if (++qn == tq) flush();
+      if (mz >= full) {
+        cd* dst = Qs + (long long)qn * tw * NFAM;
+        for (int t = lane; t < NFAM * tw; t += 32) dst[t] = W.spec[(t / tw) * gp.Ms + full - 1 + t % tw];
+        if (lane == 0) { Qij[2 * qn] = i; Qij[2 * qn + 1] = j; }
+        if (++qn == tq) flush();
+      } else {
+        for (int m = full + lane; m <= gp.M; m += 32) store_zero_block(a.A, n, m, i, j);
+      }
     }
     __syncwarp();
   }
@@ -566,8 +596,8 @@ __global__ void support_kernel(BuildArgs a) {
     double rt = a.geo.r[i], dr0, zd;
     if (slot < SELF_PTS) { dr0 = a.sup.dr[pid]; zd = a.sup.dz[pid]; }
     else { dr0 = rt - a.sup.r[pid]; zd = a.geo.z[i] - a.sup.z[pid]; }
-    int dec = decimation(gp, rt, dr0, zd, sid >= 0, a.lneps);
-    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, dec, a.cosC, a.s2C);
+    const PairGrid g = pair_grid(gp, rt, dr0, zd, sid >= 0, a.lneps, a.cosT, a.s2T, a.ladC, a.ladS);
+    warp_pair_spectra(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, g);
     cd* dst = a.spec_sup + p * NFAM * gp.Ms;
     for (int t = lane; t < NFAM * gp.Ms; t += 32) dst[t] = W.spec[t];
     __syncwarp();
@@ -667,7 +697,7 @@ __global__ void pair_spectra_kernel(GreenParams gp, const double* __restrict__ p
   WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
   for (long long p = (long long)blockIdx.x * wpb + wib; p < npairs; p += (long long)gridDim.x * wpb) {
     const double* q = pairs + 4 * p;  // (r_t, z_t, r_t - r_s, z_t - z_s)
-    warp_pair_spectra(gp, q[0], q[2], q[3], sidx[p], leg, n_split, cosT, s2T, W, lane);
+    warp_pair_spectra(gp, q[0], q[2], q[3], sidx[p], leg, n_split, cosT, s2T, W, lane, full_grid(gp, cosT, s2T));
     cd* dst = out + p * NFAM * gp.Ms;
     for (int t = lane; t < NFAM * gp.Ms; t += 32) dst[t] = W.spec[t];
     __syncwarp();
@@ -864,7 +894,7 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   cudaStream_t s = (cudaStream_t)stream;
   GreenParams gp{};
   cd K0{k0.re, k0.im}, K1{k1.re, k1.im};
-  gp.M = M; gp.Ms = Ms; gp.nphi = n_phi; gp.H = H; gp.Mq = Mq; gp.nc = 0;
+  gp.M = M; gp.Ms = Ms; gp.nphi = n_phi; gp.H = H; gp.Mq = Mq; gp.qmax = 0;
   gp.kp0 = kpow(K0); gp.kp1 = kpow(K1);
   gp.gamma0 = -0.25 * (K0 * K0 - K1 * K1);
   gp.k0_real = K0.y == 0.0; gp.k1_real = K1.y == 0.0;

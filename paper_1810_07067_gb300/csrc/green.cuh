@@ -12,8 +12,7 @@ struct GreenParams {
   int nphi;    // azimuthal samples on [0, 2pi)
   int H;       // nphi/2 + 1 samples on [0, pi]
   int Mq;      // nphi/2 - 1: bandwidth of the Laplace coefficients
-  int nc;      // compact grid for well-separated pairs: the smallest multiple of 8
-               // >= 2M + 4 (modes 0..M+1 stay distinct), 0 when not below nphi
+  int qmax;    // grid ladder for non-split pairs: sizes 8q, q = 2..qmax (8 qmax < nphi; 0: none)
   KPow kp0, kp1;
   cd gamma0;   // -(k0^2 - k1^2)/4
   int k0_real, k1_real;  // real wavenumbers take the real-arithmetic path
@@ -58,8 +57,8 @@ struct BuildArgs {
   int N, n_panels, closed;
   const double* cosT;   // [nphi] cos(2 pi t / nphi)
   const double* s2T;    // [H] sin^2(pi j / nphi)
-  const double* cosC;   // [nc] cos(2 pi t / nc) (compact grid; null when nc = 0)
-  const double* s2C;    // [nc/2 + 1] sin^2(pi j / nc)
+  const double* ladC;   // grid ladder: cos(2 pi t / 8q), t < 8q, for q = 2..qmax, concatenated
+  const double* ladS;   // sin^2(pi j / 8q), j <= 4q, for q = 2..qmax, concatenated
   const int* split_far; // [N*N] split id or -1 (far-panel pairs)
   const int* split_sup; // [N*NEAR_SLOTS] split id or -1
   const double* leg;    // Legendre scratch: [(Mq+1) + Ms][n_split] (index-major)

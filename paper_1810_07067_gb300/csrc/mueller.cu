@@ -163,8 +163,7 @@ static void fill_green_params(GreenParams& gp, int M, int nphi, cd k0, cd k1) {
   gp.kp0 = kpow(k0); gp.kp1 = kpow(k1);
   gp.gamma0 = -0.25 * (k0 * k0 - k1 * k1);
   gp.k0_real = k0.y == 0.0; gp.k1_real = k1.y == 0.0;
-  gp.nc = (2 * M + 4 + 7) / 8 * 8;  // compact grid of the well-separated pairs (8k: two folds)
-  if (gp.nc >= nphi) gp.nc = 0;
+  gp.qmax = (nphi - 1) / 8;  // grid ladder 16, 24, .., below nphi (multiples of 8: two folds)
 }
 
 // Split decision: the plain trapezoid's aliasing zeta^(nphi-M-1) is above eps,
@@ -608,8 +607,16 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   CK(tmp.upload(&ssdr, S.sdr, s)); CK(tmp.upload(&ssdz, S.sdz, s));
   CK(tmp.upload(&sLs, S.Lself, s)); CK(tmp.upload(&sLa, S.Ladj, s));
   CK(tmp.upload(&dcos, cos_table(S.nphi), s)); CK(tmp.upload(&ds2, s2_table(S.nphi), s));
-  double *dcosC = nullptr, *ds2C = nullptr;
-  if (S.gp.nc > 0) { CK(tmp.upload(&dcosC, cos_table(S.gp.nc), s)); CK(tmp.upload(&ds2C, s2_table(S.gp.nc), s)); }
+  double *dladC = nullptr, *dladS = nullptr;
+  if (S.gp.qmax >= 2) {
+    std::vector<double> lc, ls;
+    for (int q = 2; q <= S.gp.qmax; ++q) {
+      const std::vector<double> c = cos_table(8 * q), t = s2_table(8 * q);
+      lc.insert(lc.end(), c.begin(), c.end());
+      ls.insert(ls.end(), t.begin(), t.end());
+    }
+    CK(tmp.upload(&dladC, lc, s)); CK(tmp.upload(&dladS, ls, s));
+  }
   CK(tmp.upload(&dsf, S.split_far, s)); CK(tmp.upload(&dss, S.split_sup, s));
   CK(tmp.upload(&dpairs, S.split_pairs, s));
   const long long n_split = (long long)S.split_pairs.size() / 4;
@@ -620,7 +627,7 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   if (tmp.alloc(&dspec, (size_t)S.N * NEAR_SLOTS * NFAM * Ms) != cudaSuccess)
     return fail(MUELLER_ENOMEM, "support spectra scratch");
   a.sup = SupportTable{ssr, ssz, ssrp, sszp, ssW, ssdr, ssdz, sLs, sLa};
-  a.cosT = dcos; a.s2T = ds2; a.cosC = dcosC; a.s2C = ds2C; a.split_far = dsf; a.split_sup = dss; a.leg = dleg; a.n_split = n_split;
+  a.cosT = dcos; a.s2T = ds2; a.ladC = dladC; a.ladS = dladS; a.split_far = dsf; a.split_sup = dss; a.leg = dleg; a.n_split = n_split;
   a.spec_sup = dspec; a.A = A_dev;
   a.lneps = -std::log(S.split_eps);
   a.tq = far_tail_pairs(S.gp);

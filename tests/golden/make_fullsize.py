@@ -16,7 +16,8 @@ the seeded synthetic inputs.  For one named workload the script
 4. for the modes whose currents are kept, also solves two seeded random
    right-hand sides (complex normal entries, numpy default_rng(7000 + m)),
    so that modes whose plane-wave data are below rounding are still
-   compared on solutions of full size.
+   compared on solutions of full size, and records the 1-norm condition
+   number of those modes' weighted matrices.
 
 Workloads:
   cylinder  finite cylinder R = 1, H = 2, 7 dyadic levels at each edge
@@ -104,10 +105,13 @@ def _solve_job(args):
     bw = b * sw[:, None]
     y = linalg.lu_solve(LU, piv, bw)
     res = np.abs(Aw @ y - bw).max() / (np.abs(Aw).sum(1).max() * np.abs(y).max() + np.abs(bw).max())
-    xr = None
+    xr, kappa = None, None
     if brand is not None:
         xr = linalg.lu_solve(LU, piv, brand * sw[:, None]) / sw[:, None]
-    return qi, y / sw[:, None], float(res), xr
+        # 1-norm condition number of the weighted matrix (LAPACK inverse; a
+        # diagnostic of how far rounding-level differences can move x)
+        kappa = float(np.linalg.norm(Aw, 1) * np.linalg.norm(np.linalg.inv(Aw), 1))
+    return qi, y / sw[:, None], float(res), xr, kappa
 
 
 def main():
@@ -140,13 +144,14 @@ def main():
             brand[m] = rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2))
         jobs = [(name, qi, path, b_all[m + M], brand.get(m)) for qi, m in enumerate(modes)]
         x = np.zeros((len(modes), n, len(cfg.waves)), dtype=complex)
-        xrand = {}
+        xrand, kappa = {}, {}
         berr = np.zeros(len(modes))
-        for qi, xq, res, xr in pool.imap_unordered(_solve_job, jobs):
+        for qi, xq, res, xr, kp in pool.imap_unordered(_solve_job, jobs):
             x[qi] = xq
             berr[qi] = res
             if xr is not None:
                 xrand[modes[qi]] = xr
+                kappa[modes[qi]] = kp
             print(f"[{time.time() - t0:7.0f} s] solved mode {modes[qi]} (backward error {res:.1e})", flush=True)
     os.remove(path)
     # far field of the solved modes (the others zero)
@@ -170,6 +175,7 @@ def main():
         ff_dirs=dirs, ff=ff,
         b_rand=np.stack([brand[m].T for m in keep["modes"]]),      # [modes, 2, 4N]
         x_rand=np.stack([xrand[m].T for m in keep["modes"]]),
+        kappa1=np.array([kappa[m] for m in keep["modes"]]),        # 1-norm condition numbers of A'_m
         seconds=time.time() - t0)
     print(f"wrote {out} in {time.time() - t0:.0f} s; max oracle backward error {berr.max():.1e}")
 
