@@ -127,6 +127,8 @@ typedef struct {
   int lu_wave_bodies;        /* bodies factored together (mueller_build_many), else 1 */
   int lu_launches;           /* kernel launches (graph nodes) of the factorization, shared by a wave */
   double lu_gemm_bytes;      /* bytes of the trailing matrices the updates read and write (once each) */
+  int spilled;               /* 1 while the device buffers are in host memory (mueller_ctx_spill) */
+  size_t host_bytes;         /* pinned host bytes held while spilled */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;
@@ -332,6 +334,32 @@ size_t mueller_cache_bytes(void);
  * the FP64 pipe; this is the denominator of their roofline.  Runs on `stream`
  * and synchronises it (about 2 s). */
 int mueller_fp64_peak(double* tflops, void* stream);
+
+/* Host-spilled factor cache.  mueller_ctx_spill copies every device buffer
+ * of the context (factors, residual slices, geometry, pivots) to pinned host
+ * memory on `stream`, waits for the copies and releases the device buffers,
+ * so that a caller keeping many bodies (a serving cache) can park the factors
+ * of a body it evicts in host memory, over the CPU-GPU link, instead of
+ * destroying them; mueller_ctx_restore allocates device buffers again and
+ * copies the factors back (bit-identical), far cheaper than a new build.
+ * While spilled, mueller_solve, mueller_rhs_*, mueller_eval and
+ * mueller_far_field* return MUELLER_EINVAL; stats report spilled = 1, the
+ * host bytes, and device_bytes = 0.  Both calls synchronise `stream`; both
+ * are no-ops when the context is already in the requested place.  ENOMEM
+ * leaves the context where it was. */
+int mueller_ctx_spill(mueller_ctx* ctx, void* stream);
+int mueller_ctx_restore(mueller_ctx* ctx, void* stream);
+
+/* Checkpoints.  mueller_ctx_save writes to `path` the build's inputs (curve,
+ * media, M, options) and every device buffer of the context (from host memory
+ * when spilled); mueller_ctx_load reads such a file, checks the inputs as
+ * mueller_build does and allocates and fills the device buffers, giving a
+ * context whose solves are bit-identical to the saved one's, without the
+ * assembly and factorization.  The file format is this library's own (not
+ * portable across versions of it); MUELLER_EINVAL on a file that does not
+ * match, MUELLER_ENOMEM when the device cannot hold the factors. */
+int mueller_ctx_save(const mueller_ctx* ctx, const char* path);
+int mueller_ctx_load(const char* path, void* stream, mueller_ctx** out);
 
 int mueller_stats_get(const mueller_ctx* ctx, mueller_stats* out);
 void mueller_destroy(mueller_ctx* ctx);

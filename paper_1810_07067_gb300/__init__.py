@@ -54,7 +54,8 @@ class Stats(ct.Structure):
                 ("solve_launches", ct.c_int), ("refine_iters", ct.c_int), ("backward_err_max", ct.c_double),
                 ("ms_residual", ct.c_double), ("residual_launches", ct.c_int), ("residual_tc_flops", ct.c_double),
                 ("lu_graph", ct.c_int), ("lu_tile_steps", ct.c_int * 3), ("lu_wave_bodies", ct.c_int),
-                ("lu_launches", ct.c_int), ("lu_gemm_bytes", ct.c_double)]
+                ("lu_launches", ct.c_int), ("lu_gemm_bytes", ct.c_double), ("spilled", ct.c_int),
+                ("host_bytes", ct.c_size_t)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +96,10 @@ _lib.mueller_build_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct
 _lib.mueller_build_bytes.restype = ct.c_size_t
 _lib.mueller_footprint_bytes.restype = ct.c_size_t
 _lib.mueller_fp64_peak.argtypes = [ct.POINTER(ct.c_double), _vp]
+_lib.mueller_ctx_spill.argtypes = [_vp, _vp]
+_lib.mueller_ctx_restore.argtypes = [_vp, _vp]
+_lib.mueller_ctx_save.argtypes = [_vp, ct.c_char_p]
+_lib.mueller_ctx_load.argtypes = [ct.c_char_p, _vp, ct.POINTER(_vp)]
 _lib.mueller_stats_get.argtypes = [_vp, ct.POINTER(Stats)]
 _lib.mueller_destroy.argtypes = [_vp]
 _lib.mueller_strerror.restype = ct.c_char_p
@@ -106,7 +111,8 @@ EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_pl
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
            "mueller_build_many", "mueller_build_many_bytes", "mueller_lu_tile_table",
            "mueller_cache_trim", "mueller_cache_limit", "mueller_cache_bytes",
-           "mueller_fp64_peak", "mueller_destroy", "mueller_strerror", "mueller_last_error"]
+           "mueller_fp64_peak", "mueller_ctx_spill", "mueller_ctx_restore", "mueller_ctx_save", "mueller_ctx_load",
+           "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
 class MuellerError(RuntimeError):
@@ -218,6 +224,30 @@ class Context:
         _check(_lib.mueller_far_field(self._h, _ptr(x), x.shape[1], _ptr(dirs), dirs.shape[0], _ptr(E),
                                       _stream(stream)))
         return E
+
+    def spill(self, stream=None):
+        """Move the factors to pinned host memory and free their device memory."""
+        _check(_lib.mueller_ctx_spill(self._h, _stream(stream)))
+
+    def restore(self, stream=None):
+        """Bring spilled factors back to the device."""
+        _check(_lib.mueller_ctx_restore(self._h, _stream(stream)))
+
+    def save(self, path: str):
+        """Write a checkpoint (build inputs + factors) to path."""
+        _check(_lib.mueller_ctx_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Context":
+        """A context from a checkpoint written by save (no assembly or factorization)."""
+        h = _vp()
+        _check(_lib.mueller_ctx_load(os.fsencode(path), _stream(stream), ct.byref(h)))
+        ctx = cls.__new__(cls)
+        ctx._h, ctx._keep = h, None
+        with open(path, "rb") as f:                      # header: magic, version, panels, closed, M, N
+            head = np.frombuffer(f.read(28)[8:], dtype="<i4")
+        ctx.M, ctx.N = int(head[3]), int(head[4])
+        return ctx
 
     def stats(self) -> dict:
         st = Stats()

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -516,6 +518,11 @@ struct DevBuf {
     if (e == cudaSuccess) ptrs.push_back({*p, bytes});
     return e;
   }
+  size_t size_of(const void* p) const {
+    for (const auto& e : ptrs)
+      if (e.first == p) return e.second;
+    return 0;
+  }
   void release(void* p) {  // give one buffer back before the others
     for (size_t k = 0; k < ptrs.size(); ++k)
       if (ptrs[k].first == p) {
@@ -678,7 +685,29 @@ struct mueller_ctx {
   int launches_pre = 0;        // launches between assembly and LU (norms, conversion, slices)
   size_t bytes = 0;            // device bytes held after the build
   mueller_stats st{};
+  // the build's inputs, kept for mueller_ctx_save
+  int rec_np = 0, rec_closed = 0, rec_M = 0;
+  std::vector<double> rec_r, rec_z, rec_dr, rec_dz;
+  mueller_media rec_media{};
+  mueller_options rec_opts{};
+  // device buffers moved to pinned host memory by mueller_ctx_spill: (field id, bytes, host copy)
+  struct HostCopy { int field; size_t bytes; void* host; };
+  std::vector<HostCopy> spilled;
+  bool is_spilled = false;
+  ~mueller_ctx() {
+    for (auto& h : spilled) cudaFreeHost(h.host);
+  }
 };
+
+// The context's device buffers, by a fixed field id (the order of the save file).
+static std::vector<void**> ctx_fields(mueller_ctx* c) {
+  return {(void**)&c->geo[0], (void**)&c->geo[1], (void**)&c->geo[2], (void**)&c->geo[3], (void**)&c->geo[4],
+          (void**)&c->geo[5], (void**)&c->A, (void**)&c->A32, (void**)&c->normA, (void**)&c->Asl,
+          (void**)&c->rowscale, (void**)&c->piv, (void**)&c->info, (void**)&c->tc_err};
+}
+
+#define SPILLED_CHECK(c) \
+  if ((c) && (c)->is_spilled) return fail(MUELLER_EINVAL, "the context's factors are in host memory: call mueller_ctx_restore first")
 
 // Build phases.  prepare: host set-up and the context's allocations;
 // assemble: matrices of modes 0..M (plus, mixed path, norms, the complex64
@@ -696,6 +725,10 @@ static int build_prepare(const mueller_curve* curve, const mueller_media* media,
     return fail(MUELLER_EINVAL, "lu_tile must be 0 (autotuned), 32, 64 or 128");
   }
   c->lu_tile = opts->lu_tile;
+  c->rec_np = curve->n_panels; c->rec_closed = curve->closed; c->rec_M = M;
+  c->rec_r.assign(curve->r, curve->r + c->S.N); c->rec_z.assign(curve->z, curve->z + c->S.N);
+  c->rec_dr.assign(curve->dr, curve->dr + c->S.N); c->rec_dz.assign(curve->dz, curve->dz + c->S.N);
+  c->rec_media = *media; c->rec_opts = *opts;
   setup_support(curve, c->S);
   setup_pairs(c->S);
   const size_t n = c->S.n;
@@ -1002,6 +1035,7 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
 extern "C" int mueller_solve(mueller_ctx* c, const mueller_c128* rhs_dev, int nrhs, mueller_c128* x_dev,
                              double* backward_err, void* stream) {
   g_err.clear();
+  SPILLED_CHECK(c);
   if (!c || !rhs_dev || !x_dev || nrhs < 1) return fail(MUELLER_EINVAL, "invalid solve arguments");
   if ((const void*)rhs_dev == (const void*)x_dev) return fail(MUELLER_EINVAL, "rhs and x must not alias");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1030,6 +1064,7 @@ static int n_theta_for(const Setup& S) {  // a multiple of 16: four transform st
 extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const double* pols, int nrhs,
                                      mueller_c128* rhs_dev, void* stream) {
   g_err.clear();
+  SPILLED_CHECK(c);
   if (!c || !dirs || !pols || !rhs_dev || (nrhs < 1 || nrhs > 65535)) return fail(MUELLER_EINVAL, "invalid rhs arguments");
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf tmp;
@@ -1047,6 +1082,7 @@ extern "C" int mueller_rhs_planewave(mueller_ctx* c, const double* dirs, const d
 extern "C" int mueller_rhs_fields(mueller_ctx* c, const mueller_c128* EH_dev, int nrhs, int n_theta,
                                   mueller_c128* rhs_dev, void* stream) {
   g_err.clear();
+  SPILLED_CHECK(c);
   if (!c || !EH_dev || !rhs_dev || (nrhs < 1 || nrhs > 65535)) return fail(MUELLER_EINVAL, "invalid field-sample arguments");
   if (n_theta < 2 * c->S.M + 2 || n_theta > 2048)
     return fail(MUELLER_EINVAL, "n_theta must lie in [2M+2, 2048]");
@@ -1061,6 +1097,7 @@ extern "C" int mueller_rhs_fields(mueller_ctx* c, const mueller_c128* EH_dev, in
 extern "C" int mueller_eval(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* targets, int ntargets,
                             int region, mueller_c128* out_dev, void* stream) {
   g_err.clear();
+  SPILLED_CHECK(c);
   if (!c || !x_dev || !targets || !out_dev || (nrhs < 1 || nrhs > 65535) || ntargets < 1 || (region != 0 && region != 1))
     return fail(MUELLER_EINVAL, "invalid evaluation arguments");
   for (int p = 0; p < 3 * ntargets; ++p)
@@ -1156,6 +1193,7 @@ extern "C" int mueller_eval(mueller_ctx* c, const mueller_c128* x_dev, int nrhs,
 extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, const double* dirs_dev,
                                  int ndir, mueller_c128* E_dev, void* stream) {
   g_err.clear();
+  SPILLED_CHECK(c);
   if (!c || !x_dev || !dirs_dev || !E_dev || (nrhs < 1 || nrhs > 65535) || ndir < 1) return fail(MUELLER_EINVAL, "invalid far-field arguments");
   cudaStream_t s = (cudaStream_t)stream;
   int nth = n_theta_for(c->S);
@@ -1173,6 +1211,7 @@ extern "C" int mueller_far_field(mueller_ctx* c, const mueller_c128* x_dev, int 
 extern "C" int mueller_far_field_grid(mueller_ctx* c, const mueller_c128* x_dev, int nrhs, int n_polar,
                                       int n_azim, mueller_c128* E_dev, void* stream) {
   g_err.clear();
+  SPILLED_CHECK(c);
   if (!c || !x_dev || !E_dev || (nrhs < 1 || nrhs > 65535) || n_polar < 1 || n_azim < 1 || n_azim > 8192)
     return fail(MUELLER_EINVAL, "invalid far-field grid arguments");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1308,6 +1347,190 @@ extern "C" size_t mueller_footprint_bytes(int N, int M) {
 extern "C" int mueller_stats_get(const mueller_ctx* c, mueller_stats* out) {
   if (!c || !out) return fail(MUELLER_EINVAL, "null argument");
   *out = c->st;
+  out->spilled = c->is_spilled ? 1 : 0;
+  out->host_bytes = 0;
+  for (const auto& h : c->spilled) out->host_bytes += h.bytes;
+  if (c->is_spilled) out->device_bytes = 0;
+  return MUELLER_OK;
+}
+
+// ---------------------------------------------------------------- host spill and checkpoints
+extern "C" int mueller_ctx_spill(mueller_ctx* c, void* stream) {
+  g_err.clear();
+  if (!c) return fail(MUELLER_EINVAL, "null context");
+  if (c->is_spilled) return MUELLER_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::vector<void**> fields = ctx_fields(c);
+  std::vector<mueller_ctx::HostCopy> copies;
+  for (int f = 0; f < (int)fields.size(); ++f) {
+    void* p = *fields[f];
+    if (!p) continue;
+    const size_t bytes = c->keep.size_of(p);
+    void* h = nullptr;
+    if (cudaMallocHost(&h, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      for (auto& x : copies) cudaFreeHost(x.host);
+      return fail(MUELLER_ENOMEM, "pinned host memory for the spilled factors");
+    }
+    copies.push_back({f, bytes, h});
+    cudaMemcpyAsync(h, p, bytes, cudaMemcpyDeviceToHost, s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    for (auto& x : copies) cudaFreeHost(x.host);
+    return fail(MUELLER_ECUDA, cudaGetErrorString(e));
+  }
+  for (auto& x : copies) {
+    c->keep.release(*fields[x.field]);
+    *fields[x.field] = nullptr;
+  }
+  c->spilled = std::move(copies);
+  c->is_spilled = true;
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_ctx_restore(mueller_ctx* c, void* stream) {
+  g_err.clear();
+  if (!c) return fail(MUELLER_EINVAL, "null context");
+  if (!c->is_spilled) return MUELLER_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::vector<void**> fields = ctx_fields(c);
+  std::vector<void*> got;
+  for (const auto& x : c->spilled) {
+    char* p = nullptr;
+    if (c->keep.alloc(&p, x.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      for (void* q : got) c->keep.release(q);
+      return fail(MUELLER_ENOMEM, "device memory for the restored factors");
+    }
+    got.push_back(p);
+    cudaMemcpyAsync(p, x.host, x.bytes, cudaMemcpyHostToDevice, s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    for (void* q : got) c->keep.release(q);
+    return fail(MUELLER_ECUDA, cudaGetErrorString(e));
+  }
+  for (size_t k = 0; k < c->spilled.size(); ++k) {
+    *fields[c->spilled[k].field] = got[k];
+    cudaFreeHost(c->spilled[k].host);
+  }
+  c->spilled.clear();
+  c->is_spilled = false;
+  return MUELLER_OK;
+}
+
+static const char kCkptMagic[8] = {'M', 'U', 'E', 'L', 'C', 'T', 'X', '1'};
+
+extern "C" int mueller_ctx_save(const mueller_ctx* cc, const char* path) {
+  g_err.clear();
+  if (!cc || !path) return fail(MUELLER_EINVAL, "null argument");
+  mueller_ctx* c = const_cast<mueller_ctx*>(cc);  // device pointers are only read
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(MUELLER_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = true;
+  auto put = [&](const void* p, size_t b) { if (ok && b && std::fwrite(p, 1, b, f) != b) ok = false; };
+  const int32_t version = 1, N = c->S.N;
+  put(kCkptMagic, 8); put(&version, 4);
+  put(&c->rec_np, 4); put(&c->rec_closed, 4); put(&c->rec_M, 4); put(&N, 4);
+  put(c->rec_r.data(), 8 * N); put(c->rec_z.data(), 8 * N); put(c->rec_dr.data(), 8 * N); put(c->rec_dz.data(), 8 * N);
+  put(&c->rec_media, sizeof(mueller_media)); put(&c->rec_opts, sizeof(mueller_options));
+  put(&c->npad, 4); put(&c->lu_tile, 4); put(&c->launches_pre, 4); put(&c->bytes, 8);
+  put(&c->st, sizeof(mueller_stats));
+  const std::vector<void**> fields = ctx_fields(c);
+  int32_t nf = 0;
+  for (int k = 0; k < (int)fields.size(); ++k) nf += (*fields[k] != nullptr) ? 1 : 0;
+  nf += (int32_t)c->spilled.size();
+  put(&nf, 4);
+  std::vector<char> buf;
+  for (int k = 0; k < (int)fields.size() && ok; ++k) {
+    const void* p = *fields[k];
+    const void* host = nullptr;
+    uint64_t bytes = 0;
+    if (p) {
+      bytes = c->keep.size_of(p);
+    } else {
+      for (const auto& h : c->spilled)
+        if (h.field == k) { host = h.host; bytes = h.bytes; }
+      if (!host) continue;
+    }
+    const int32_t id = k;
+    put(&id, 4); put(&bytes, 8);
+    if (host) { put(host, bytes); continue; }
+    const size_t chunk = (size_t)256 << 20;
+    buf.resize(std::min<size_t>(chunk, bytes));
+    for (size_t o = 0; o < bytes && ok; o += chunk) {
+      const size_t b = std::min<size_t>(chunk, bytes - o);
+      if (cudaMemcpy(buf.data(), (const char*)p + o, b, cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+      put(buf.data(), b);
+    }
+  }
+  if (std::fclose(f) != 0) ok = false;
+  if (!ok) return fail(MUELLER_EINVAL, std::string("writing ") + path + " failed");
+  return MUELLER_OK;
+}
+
+extern "C" int mueller_ctx_load(const char* path, void* stream, mueller_ctx** out) {
+  g_err.clear();
+  if (!path || !out) return fail(MUELLER_EINVAL, "null argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(MUELLER_EINVAL, std::string("cannot open ") + path);
+  bool ok = true;
+  auto get = [&](void* p, size_t b) { if (ok && b && std::fread(p, 1, b, f) != b) ok = false; };
+  char magic[8] = {0};
+  int32_t version = 0, np = 0, closed = 0, M = 0, N = 0;
+  get(magic, 8); get(&version, 4);
+  if (!ok || std::memcmp(magic, kCkptMagic, 8) != 0 || version != 1) {
+    std::fclose(f);
+    return fail(MUELLER_EINVAL, std::string(path) + " is not a context checkpoint of this library");
+  }
+  get(&np, 4); get(&closed, 4); get(&M, 4); get(&N, 4);
+  if (!ok || np < 1 || N != 16 * np) { std::fclose(f); return fail(MUELLER_EINVAL, "corrupt checkpoint header"); }
+  std::vector<double> r(N), z(N), dr(N), dz(N);
+  mueller_media media{};
+  mueller_options opts{};
+  get(r.data(), 8 * N); get(z.data(), 8 * N); get(dr.data(), 8 * N); get(dz.data(), 8 * N);
+  get(&media, sizeof(media)); get(&opts, sizeof(opts));
+  if (!ok) { std::fclose(f); return fail(MUELLER_EINVAL, "truncated checkpoint"); }
+  mueller_curve cv{np, closed, r.data(), z.data(), dr.data(), dz.data()};
+  mueller_ctx* c = new mueller_ctx();
+  int rc = setup_inputs(&cv, &media, M, &opts, c->S);
+  if (rc) { std::fclose(f); delete c; return rc; }
+  c->rec_np = np; c->rec_closed = closed; c->rec_M = M;
+  c->rec_r = r; c->rec_z = z; c->rec_dr = dr; c->rec_dz = dz;
+  c->rec_media = media; c->rec_opts = opts;
+  get(&c->npad, 4); get(&c->lu_tile, 4); get(&c->launches_pre, 4); get(&c->bytes, 8);
+  get(&c->st, sizeof(mueller_stats));
+  int32_t nf = 0;
+  get(&nf, 4);
+  const std::vector<void**> fields = ctx_fields(c);
+  std::vector<char> buf;
+  for (int q = 0; q < nf && ok; ++q) {
+    int32_t id = -1;
+    uint64_t bytes = 0;
+    get(&id, 4); get(&bytes, 8);
+    if (!ok || id < 0 || id >= (int)fields.size() || bytes == 0) { ok = false; break; }
+    char* p = nullptr;
+    if (c->keep.alloc(&p, bytes) != cudaSuccess) {
+      std::fclose(f); delete c;
+      return fail(MUELLER_ENOMEM, "device memory for the checkpoint's factors");
+    }
+    *fields[id] = p;
+    const size_t chunk = (size_t)256 << 20;
+    buf.resize(std::min<size_t>(chunk, bytes));
+    for (size_t o = 0; o < bytes && ok; o += chunk) {
+      const size_t b = std::min<size_t>(chunk, bytes - o);
+      get(buf.data(), b);
+      if (ok && cudaMemcpy(p + o, buf.data(), b, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+    }
+  }
+  std::fclose(f);
+  if (!ok) { delete c; return fail(MUELLER_EINVAL, std::string("reading ") + path + " failed"); }
+  (void)stream;
+  *out = c;
   return MUELLER_OK;
 }
 

@@ -6,7 +6,12 @@ least-recently-used cache whose resident bytes stay within a budget (the
 budget is charged with a build's peak while it runs, mueller_build_bytes).
 A request for a key that is not resident starts its build on a separate CUDA
 stream in a builder thread, while the serving thread keeps solving requests
-of resident keys on its own stream.  Requests of one key that are waiting
+of resident keys on its own stream.  With a host budget, an evicted key's
+factors are moved to pinned host memory (mueller_ctx_spill) instead of being
+destroyed, and a later miss on it copies them back (mueller_ctx_restore)
+instead of building; with a checkpoint directory, every build is saved there
+(mueller_ctx_save) and a miss on a key with a saved checkpoint loads it
+(mueller_ctx_load), so a restarted server resumes without rebuilding.  Requests of one key that are waiting
 together are solved as one batch of right-hand sides (continuous batching, up
 to max_rhs columns); each request's far field is then evaluated on its grid
 and copied to pinned host memory.  Latency is completion minus arrival.
@@ -87,6 +92,9 @@ class ServeStats:
     done: list = field(default_factory=list)
     unfinished: int = 0
     builds: int = 0
+    restores: int = 0            # misses served from the host cache
+    loads: int = 0               # misses served from a checkpoint file
+    spills: int = 0              # evictions parked in host memory
     evictions: int = 0
     build_s: float = 0.0
     batches: int = 0
@@ -99,10 +107,18 @@ class Server:
     """pool: list of workloads.Config-like bodies (curve, media, M, n_phi)."""
 
     def __init__(self, pool, budget_bytes: int, precision: int = 1, max_rhs: int = 256,
-                 grid=(180, 360), refine_tol: float = 1e-14):
+                 grid=(180, 360), refine_tol: float = 1e-14, host_budget_bytes: int = 0,
+                 checkpoint_dir: str | None = None):
         import torch
         from . import build_bytes
         self.pool = pool
+        self.host_budget = int(host_budget_bytes)
+        self.host_cache: OrderedDict[int, _Entry] = OrderedDict()   # spilled keys, least recently used first
+        self.host_charged = 0
+        self.checkpoint_dir = checkpoint_dir
+        if checkpoint_dir:
+            import os
+            os.makedirs(checkpoint_dir, exist_ok=True)
         self.precision = precision
         self.max_rhs = max_rhs
         self.grid = grid
@@ -123,6 +139,7 @@ class Server:
         self._lock = threading.Lock()
         self._built = deque()             # (key, ctx or exception, seconds)
         self._building = None             # key being built
+        self._charged_now = 0             # bytes charged for the running build / restore / load
 
     # ---------------------------------------------------------------- builds
     def _evict_for(self, nbytes, st, keep=()):
@@ -134,33 +151,79 @@ class Server:
             if key in keep:
                 continue
             e = self.cache.pop(key)
-            e.ctx.close()
             self.charged -= e.resident
             st.evictions += 1
+            if self.host_budget > 0 and e.resident <= self.host_budget:
+                while self.host_cache and self.host_charged + e.resident > self.host_budget:
+                    _, old = self.host_cache.popitem(last=False)
+                    old.ctx.close()
+                    self.host_charged -= old.resident
+                e.ctx.spill(stream=self.serve_stream)
+                self.host_cache[key] = e
+                self.host_charged += e.resident
+                st.spills += 1
+            else:
+                e.ctx.close()
         return self.charged + nbytes <= self.budget
 
+    def _checkpoint_path(self, key):
+        """File of a key's checkpoint: named by a hash of everything the build depends on."""
+        import hashlib
+        import os
+        b = self.pool[key]
+        h = hashlib.sha1()
+        for a in (b.curve.r, b.curve.z, b.curve.dr, b.curve.dz):
+            h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+        m = b.media
+        h.update(repr((int(b.curve.n_panels), bool(getattr(b.curve, "closed", False)), float(m.omega),
+                       complex(m.eps0), complex(m.mu0), complex(m.eps1), complex(m.mu1), int(b.M),
+                       int(b.n_phi), self.precision, self.refine_tol)).encode())
+        return os.path.join(self.checkpoint_dir, f"key{key}_{h.hexdigest()[:16]}.ctx")
+
     def _start_build(self, key, st, keep=()):
-        from . import Options, build
-        peak = self.peaks[key]
-        if not self._evict_for(peak, st, keep):
+        """Make a key resident: restore it from the host cache, load its
+        checkpoint, or build it; runs in a builder thread."""
+        import os
+        from . import Context, Options, build
+        spilled = self.host_cache.pop(key, None)
+        ckpt = self._checkpoint_path(key) if self.checkpoint_dir else None
+        from_file = spilled is None and ckpt is not None and os.path.exists(ckpt)
+        # a restore or a load needs the context's resident bytes; a build its peak
+        need = spilled.resident if spilled is not None else self.peaks[key]
+        if spilled is not None:
+            self.host_charged -= spilled.resident
+        if not self._evict_for(need, st, keep):
+            if spilled is not None:                      # back to the host cache; retry later
+                self.host_cache[key] = spilled
+                self.host_charged += spilled.resident
             return False
-        self.charged += peak
+        self.charged += need
+        self._charged_now = need
         st.high_water = max(st.high_water, self.charged)
         self._building = key
         body = self.pool[key]
 
         def run():
             t = time.perf_counter()
+            kind = "build"
             try:
                 with self._torch().cuda.stream(self.build_stream):
-                    ctx = build(body.curve, body.media, body.M,
-                                Options(n_phi=body.n_phi, precision=self.precision, refine_tol=self.refine_tol),
-                                stream=self.build_stream)
+                    if spilled is not None:
+                        spilled.ctx.restore(stream=self.build_stream)
+                        ctx, kind = spilled.ctx, "restore"
+                    elif from_file:
+                        ctx, kind = Context.load(ckpt, stream=self.build_stream), "load"
+                    else:
+                        ctx = build(body.curve, body.media, body.M,
+                                    Options(n_phi=body.n_phi, precision=self.precision, refine_tol=self.refine_tol),
+                                    stream=self.build_stream)
+                        if ckpt is not None:
+                            ctx.save(ckpt)
                 res = ctx
             except BaseException as e:  # handed to the serving thread
                 res = e
             with self._lock:
-                self._built.append((key, res, time.perf_counter() - t))
+                self._built.append((key, res, time.perf_counter() - t, kind))
 
         threading.Thread(target=run, daemon=True).start()
         return True
@@ -174,15 +237,20 @@ class Server:
         with self._lock:
             items = list(self._built)
             self._built.clear()
-        for key, res, secs in items:
+        for key, res, secs, kind in items:
             self._building = None
-            self.charged -= self.peaks[key]
+            self.charged -= self._charged_now
             if isinstance(res, BaseException):
                 raise res
             resident = int(res.stats()["device_bytes"])
             self.cache[key] = _Entry(res, resident, now)
             self.charged += resident
-            st.builds += 1
+            if kind == "restore":
+                st.restores += 1
+            elif kind == "load":
+                st.loads += 1
+            else:
+                st.builds += 1
             st.build_s += secs
 
     # ---------------------------------------------------------------- serving
@@ -272,10 +340,12 @@ class Server:
         return (st, results) if keep_results else st
 
     def close(self):
-        for e in self.cache.values():
+        for e in list(self.cache.values()) + list(self.host_cache.values()):
             e.ctx.close()
         self.cache.clear()
+        self.host_cache.clear()
         self.charged = 0
+        self.host_charged = 0
 
 
 def summarize(st: ServeStats, n_offered: int, duration: float) -> dict:
@@ -285,7 +355,8 @@ def summarize(st: ServeStats, n_offered: int, duration: float) -> dict:
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "solves_per_s": nrhs / st.wall if st.wall else 0.0,
             "hit_rate": float(np.mean([d.hit for d in st.done])) if st.done else 0.0,
-            "builds": st.builds, "evictions": st.evictions, "batches": st.batches,
+            "builds": st.builds, "restores_from_host": st.restores, "loads_from_checkpoint": st.loads,
+            "spills_to_host": st.spills, "evictions": st.evictions, "batches": st.batches,
             "mean_batch_rhs": float(np.mean([d.batch_rhs for d in st.done])) if st.done else 0.0,
             "build_s_total": st.build_s, "wall_s": st.wall, "arrival_window_s": duration,
             "budget_gb": st.budget / 1e9, "high_water_gb": st.high_water / 1e9}

@@ -78,3 +78,75 @@ def test_served_equals_alone(mb, tight):
         ref = _alone(mb, pool[r.key], r)
         got = res[r.id].numpy()
         assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), r.id
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_spill_restore_and_checkpoint_roundtrip(mb, tmp_path, precision):
+    """Factors parked in host memory and brought back, or written to a
+    checkpoint and loaded in a new context, give bit-identical solves; a
+    spilled context refuses to solve until restored."""
+    body = _pool()[1]
+    ctx = mb.build(body.curve, body.media, body.M, mb.Options(n_phi=body.n_phi, precision=precision))
+    n = 4 * body.curve.N
+    rhs = torch.zeros((2 * body.M + 1, 3, n), dtype=torch.complex128, device=DEV)
+    d = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8], [0.0, 1.0, 0.0]])
+    p = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [1.0, 0.0, 0.0]])
+    ctx.rhs_planewave(d, p, rhs)
+    x0 = torch.zeros_like(rhs)
+    ctx.solve(rhs, x0)
+    dev_bytes = ctx.stats()["device_bytes"]
+    ctx.spill()
+    st = ctx.stats()
+    assert st["spilled"] == 1 and st["device_bytes"] == 0 and st["host_bytes"] >= dev_bytes
+    with pytest.raises(mb.MuellerError, match="restore"):
+        ctx.solve(rhs, torch.zeros_like(rhs))
+    path = str(tmp_path / "body.ctx")
+    ctx.save(path)                                      # from the host copies
+    ctx.restore()
+    assert ctx.stats()["spilled"] == 0
+    x1 = torch.zeros_like(rhs)
+    ctx.solve(rhs, x1)
+    assert torch.equal(x0, x1)
+    ctx.close()
+    loaded = mb.Context.load(path)
+    x2 = torch.zeros_like(rhs)
+    loaded.solve(rhs, x2)
+    assert torch.equal(x0, x2)
+    assert loaded.stats()["device_bytes"] == dev_bytes
+    loaded.close()
+
+
+def test_served_with_host_cache_and_checkpoints(mb, tmp_path):
+    """A device budget for one key at a time: with a host cache every key is
+    built once and evicted keys come back from host memory; with a checkpoint
+    directory a second server loads every key instead of building it.  Every
+    request's far field still equals the same request solved alone."""
+    from paper_1810_07067_gb300 import serving
+    pool = _pool()
+    reqs = _requests(serving)
+    peaks = [mb.build_bytes(b.curve.N, b.M, 1)[0] for b in pool]
+    probe = serving.Server(pool, 10 ** 13, max_rhs=16, grid=GRID)
+    head = probe.headroom
+    probe.close()
+    budget = head + max(peaks) + 1
+    srv = serving.Server(pool, budget, max_rhs=16, grid=GRID, host_budget_bytes=4 * sum(peaks))
+    st, res = srv.run(reqs, keep_results=True)
+    srv.close()
+    assert len(st.done) == len(reqs) and st.unfinished == 0
+    assert st.builds == 3 and st.spills >= 2 and st.restores >= 1
+    refs = {r.id: _alone(mb, pool[r.key], r) for r in reqs}
+    for r in reqs:
+        got = res[r.id].numpy()
+        assert np.abs(got - refs[r.id]).max() <= 1e-11 * np.abs(refs[r.id]).max(), r.id
+    ck = str(tmp_path / "ckpt")
+    first = serving.Server(pool, head + 4 * sum(peaks), max_rhs=16, grid=GRID, checkpoint_dir=ck)
+    st1 = first.run(reqs)
+    first.close()
+    assert st1.builds == 3 and st1.loads == 0
+    second = serving.Server(pool, head + 4 * sum(peaks), max_rhs=16, grid=GRID, checkpoint_dir=ck)
+    st2, res2 = second.run(reqs, keep_results=True)
+    second.close()
+    assert st2.builds == 0 and st2.loads == 3
+    for r in reqs:
+        got = res2[r.id].numpy()
+        assert np.abs(got - refs[r.id]).max() <= 1e-11 * np.abs(refs[r.id]).max(), r.id
