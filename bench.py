@@ -605,6 +605,7 @@ def run_single(args, cfg):
     clocks = _clock_summary(clk_path, local)
     # accuracy, untimed: both paths against the oracle's stored solution
     accuracy = None
+    cond = None
     g = _golden(cfg, args.workload)
     if g is not None:
         accuracy = {}
@@ -614,11 +615,29 @@ def run_single(args, cfg):
             xx = torch.zeros_like(x)
             _, ctx = step(prec, xx, keep=True)
             accuracy[name] = _errors_vs_oracle(ctx, xx, g, M, dev)
+            if prec == 1:
+                kap = ctx.cond_estimate()
+                cond = {"kappa_inf_mode0": float(kap[0]), "kappa_inf_max": float(kap.max()),
+                        "mode_of_max": int(kap.argmax()), "ms": ctx.stats()["ms_cond"],
+                        "kind": "Hager estimate of ||A'^-1||_inf from the complex64 factors x ||A'||_inf, "
+                                "per mode (mueller_cond_estimate)"}
             ctx.close()
         accuracy["oracle"] = {"modes": [int(v) for v in g["modes"]], "waves": [int(v) for v in g["waves"]],
+                              "kappa1_per_mode": ([float(v) for v in g["kappa1"]] if "kappa1" in g.files else None),
+                              "noise1_per_mode": ([float(v) for v in g["noise1"]] if "noise1" in g.files else None),
+                              "noise1_meaning": "relative 1-norm difference of the oracle's 32- and 24-point "
+                                                "matrices (its own rounding noise)",
                               "solved_modes": len(g["solved_modes"]),
                               "oracle_backward_err_max": float(np.max(g["backward_err"])),
                               "source": "tests/golden/fullsize_%s.npz (oracle only)" % args.workload}
+    if cond is None:                                    # no stored oracle solution: estimate on its own
+        _, ctx = step(1, torch.zeros_like(x), keep=True)
+        kap = ctx.cond_estimate()
+        cond = {"kappa_inf_mode0": float(kap[0]), "kappa_inf_max": float(kap.max()), "mode_of_max": int(kap.argmax()),
+                "ms": ctx.stats()["ms_cond"],
+                "kind": "Hager estimate of ||A'^-1||_inf from the complex64 factors x ||A'||_inf, per mode "
+                        "(mueller_cond_estimate)"}
+        ctx.close()
     num = den = None
     if fp64 is not None:
         num = max(float((x[q] - x64[q]).norm()) for q in range(2 * M + 1))
@@ -662,6 +681,7 @@ def run_single(args, cfg):
                 "mixed_over_fp64_speedup": (fp64["s"] / dev_s) if fp64 else None,
                 "currents_rel_diff_mixed_vs_fp64": (num / den) if num is not None else None,
                 "accuracy_vs_oracle": accuracy,
+                "condition_estimate": cond,
                 "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * args.steps,
                 "clocks": clocks}

@@ -129,6 +129,10 @@ typedef struct {
   double lu_gemm_bytes;      /* bytes of the trailing matrices the updates read and write (once each) */
   int spilled;               /* 1 while the device buffers are in host memory (mueller_ctx_spill) */
   size_t host_bytes;         /* pinned host bytes held while spilled */
+  double kappa_mode0;        /* last mueller_cond_estimate: kappa_inf of mode 0 ...   */
+  double kappa_max;          /* ... the largest over modes 0..M ...                   */
+  int kappa_max_mode;        /* ... and its mode (-1 before any estimate)             */
+  double ms_cond;            /* device time of that estimate                          */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;
@@ -334,6 +338,17 @@ size_t mueller_cache_bytes(void);
  * the FP64 pipe; this is the denominator of their roofline.  Runs on `stream`
  * and synchronises it (about 2 s). */
 int mueller_fp64_peak(double* tflops, void* stream);
+
+/* Condition estimate of every mode's system (the paper reports LAPACK
+ * ZGESVX condition numbers of its mode-0 systems, Section 6): kappa[m] for
+ * m = 0..M (host array, may be NULL) = ||A'_m||_inf times Hager's estimate
+ * (the iteration of LAPACK's xLACN2) of ||A'_m^{-1}||_inf, from the build's
+ * LU factors (complex64 ones on the mixed paths), A'_m the L2-weighted
+ * matrix (mode -m has the same value: A'_{-m} is A'_m with rows and columns
+ * multiplied by +-1).  The estimate is a lower bound, in practice within a
+ * small factor.  Also sets kappa_mode0, kappa_max, kappa_max_mode and
+ * ms_cond in the stats.  One CTA per mode; synchronises `stream`. */
+int mueller_cond_estimate(mueller_ctx* ctx, double* kappa, void* stream);
 
 /* Host-spilled factor cache.  mueller_ctx_spill copies every device buffer
  * of the context (factors, residual slices, geometry, pivots) to pinned host

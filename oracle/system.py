@@ -170,15 +170,25 @@ def coefficients(media, formulation: int):
                 dHJ=-0.5j * om * (e0 + e1), aHM=-e0 / u0, sE=1j * om * u0, sH=1j * om * e0)
 
 
-def assemble_row(curve, media, M: int, i: int, formulation: int = 0, modes=None, geo=None):
+def assemble_row(curve, media, M: int, i: int, formulation: int = 0, modes=None, geo=None, lo_modes=None):
     """Rows 4i..4i+3 of the per-mode matrices (unweighted) for target node i:
-    an array [len(modes), 4, 4N] (default all signed modes -M..M)."""
+    an array [len(modes), 4, 4N] (default all signed modes -M..M).  With
+    ``lo_modes`` (a list of signed modes) also those modes' rows from the
+    24-point azimuthal rule (see green.modal_families_batch), returned second:
+    their difference from the same rows of the first is the oracle's own noise."""
+    R = _assemble_row(curve, media, M, i, formulation, modes, geo, lo_modes)
+    return R if lo_modes is not None else R[0]
+
+
+def _assemble_row(curve, media, M, i, formulation, modes, geo, lo_modes):
     geo = node_geometry(curve) if geo is None else geo
     k0, k1 = wavenumbers(media)
     co = coefficients(media, formulation)
     N = curve.N
     ms = np.arange(-M, M + 1) if modes is None else np.asarray(modes)
-    R = np.zeros((len(ms), 4, 4 * N), dtype=complex)
+    with_lo = lo_modes is not None
+    mss = [ms] + ([np.asarray(lo_modes)] if with_lo else [])
+    Rs = [np.zeros((len(m_), 4, 4 * N), dtype=complex) for m_ in mss]
     om = media.omega
     Pt, a = divmod(i, P)
     rt, zt, rpt, zpt = geo.r[i], geo.z[i], geo.rp[i], geo.zp[i]
@@ -191,26 +201,28 @@ def assemble_row(curve, media, M: int, i: int, formulation: int = 0, modes=None,
             L = np.eye(P)
         else:
             rs, zs, rps, zps, W, L, disp = sup
-        F = modal_families_batch(rt, zt, rs, zs, k0, k1, M, disp=disp)
-        N0, N1, KD = operator_blocks(F, rs, rps, zps, rt, rpt, zpt, k0, k1, ms)
-        x0, x1 = co["x"]; y0, y1 = co["y"]
-        EM = -1j * om * (x0 * N0 - x1 * N1)
-        HJ = -1j * om * (y0 * N0 - y1 * N1)
-        blk = np.zeros(N0.shape[:2] + (4, 4), dtype=complex)
-        blk[..., 0:2, 0:2] = co["aEJ"] * KD
-        blk[..., 0:2, 2:4] = EM
-        blk[..., 2:4, 0:2] = HJ
-        blk[..., 2:4, 2:4] = co["aHM"] * KD
-        # contract support points into the panel's 16 columns
-        contrib = np.einsum("s,sk,sqab->qkab", W, L, blk)
-        for k in range(P):
-            j = Q * P + k
-            R[:, :, 4 * j:4 * j + 4] += contrib[:, k]
-    R[:, 0, 4 * i + 2] += co["dEM"]
-    R[:, 1, 4 * i + 3] += co["dEM"]
-    R[:, 2, 4 * i + 0] += co["dHJ"]
-    R[:, 3, 4 * i + 1] += co["dHJ"]
-    return R
+        Fs = modal_families_batch(rt, zt, rs, zs, k0, k1, M, disp=disp, return_lo=with_lo)
+        for R, F, m_ in zip(Rs, Fs if with_lo else (Fs,), mss):
+            N0, N1, KD = operator_blocks(F, rs, rps, zps, rt, rpt, zpt, k0, k1, m_)
+            x0, x1 = co["x"]; y0, y1 = co["y"]
+            EM = -1j * om * (x0 * N0 - x1 * N1)
+            HJ = -1j * om * (y0 * N0 - y1 * N1)
+            blk = np.zeros(N0.shape[:2] + (4, 4), dtype=complex)
+            blk[..., 0:2, 0:2] = co["aEJ"] * KD
+            blk[..., 0:2, 2:4] = EM
+            blk[..., 2:4, 0:2] = HJ
+            blk[..., 2:4, 2:4] = co["aHM"] * KD
+            # contract support points into the panel's 16 columns
+            contrib = np.einsum("s,sk,sqab->qkab", W, L, blk)
+            for k in range(P):
+                j = Q * P + k
+                R[:, :, 4 * j:4 * j + 4] += contrib[:, k]
+    for R in Rs:
+        R[:, 0, 4 * i + 2] += co["dEM"]
+        R[:, 1, 4 * i + 3] += co["dEM"]
+        R[:, 2, 4 * i + 0] += co["dHJ"]
+        R[:, 3, 4 * i + 1] += co["dHJ"]
+    return Rs
 
 
 def assemble(curve, media, M: int, formulation: int = 0, modes=None, rows=None, progress=None):

@@ -55,7 +55,8 @@ class Stats(ct.Structure):
                 ("ms_residual", ct.c_double), ("residual_launches", ct.c_int), ("residual_tc_flops", ct.c_double),
                 ("lu_graph", ct.c_int), ("lu_tile_steps", ct.c_int * 3), ("lu_wave_bodies", ct.c_int),
                 ("lu_launches", ct.c_int), ("lu_gemm_bytes", ct.c_double), ("spilled", ct.c_int),
-                ("host_bytes", ct.c_size_t)]
+                ("host_bytes", ct.c_size_t), ("kappa_mode0", ct.c_double), ("kappa_max", ct.c_double),
+                ("kappa_max_mode", ct.c_int), ("ms_cond", ct.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -96,6 +97,7 @@ _lib.mueller_build_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct
 _lib.mueller_build_bytes.restype = ct.c_size_t
 _lib.mueller_footprint_bytes.restype = ct.c_size_t
 _lib.mueller_fp64_peak.argtypes = [ct.POINTER(ct.c_double), _vp]
+_lib.mueller_cond_estimate.argtypes = [_vp, ct.POINTER(ct.c_double), _vp]
 _lib.mueller_ctx_spill.argtypes = [_vp, _vp]
 _lib.mueller_ctx_restore.argtypes = [_vp, _vp]
 _lib.mueller_ctx_save.argtypes = [_vp, ct.c_char_p]
@@ -111,7 +113,7 @@ EXPORTS = ["mueller_build", "mueller_assemble", "mueller_solve", "mueller_rhs_pl
            "mueller_modal_kernels", "mueller_modal_kernels_noalloc", "mueller_lu_batched", "mueller_lu_batched_c64", "mueller_footprint_bytes", "mueller_build_bytes", "mueller_stats_get",
            "mueller_build_many", "mueller_build_many_bytes", "mueller_lu_tile_table",
            "mueller_cache_trim", "mueller_cache_limit", "mueller_cache_bytes",
-           "mueller_fp64_peak", "mueller_ctx_spill", "mueller_ctx_restore", "mueller_ctx_save", "mueller_ctx_load",
+           "mueller_fp64_peak", "mueller_cond_estimate", "mueller_ctx_spill", "mueller_ctx_restore", "mueller_ctx_save", "mueller_ctx_load",
            "mueller_destroy", "mueller_strerror", "mueller_last_error"]
 
 
@@ -224,6 +226,12 @@ class Context:
         _check(_lib.mueller_far_field(self._h, _ptr(x), x.shape[1], _ptr(dirs), dirs.shape[0], _ptr(E),
                                       _stream(stream)))
         return E
+
+    def cond_estimate(self, stream=None) -> np.ndarray:
+        """kappa_inf of the weighted system of every mode 0..M (Hager's estimate from the factors)."""
+        k = np.zeros(self.M + 1)
+        _check(_lib.mueller_cond_estimate(self._h, k.ctypes.data_as(ct.POINTER(ct.c_double)), _stream(stream)))
+        return k
 
     def spill(self, stream=None):
         """Move the factors to pinned host memory and free their device memory."""

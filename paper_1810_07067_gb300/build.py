@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libmueller.so")
-SOURCES = ["green.cu", "lu.cu", "fields.cu", "mixed.cu", "ozaki.cu", "mueller.cu", "probe.cu"]
+SOURCES = ["green.cu", "lu.cu", "fields.cu", "mixed.cu", "ozaki.cu", "mueller.cu", "probe.cu", "cond.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

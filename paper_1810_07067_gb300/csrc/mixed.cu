@@ -29,14 +29,14 @@ __global__ void __launch_bounds__(256) row_pass_kernel(const cd* __restrict__ A,
   const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;  // slice 0..7
   const int i = blockIdx.x * 32 + lane;
   const cd* Mx = A + (size_t)b * n * n;
-  cf* My = A32 + (size_t)b * n * n;
+  cf* My = A32 ? A32 + (size_t)b * n * n : nullptr;  // null: norms only
   // |a| in FP32 (a norm for the stopping test needs no more), summed in FP64
   double s = 0.0, mx = 0.0;
   if (i < n) {
 #pragma unroll 4
     for (int j = slice; j < n; j += 8) {
       const cd v = Mx[(size_t)j * n + i];
-      My[(size_t)j * n + i] = to_cf(v);
+      if (My) My[(size_t)j * n + i] = to_cf(v);
       const float fx = fabsf((float)v.x), fy = fabsf((float)v.y);
       const float hi = fmaxf(fx, fy), lo = fminf(fx, fy);
       const float q = (hi > 0.f) ? lo / hi : 0.f;

@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include "cplx.cuh"
 
-// One pass over `batch` column-major n x n matrices: A32 = complex64 copy,
+// One pass over `batch` column-major n x n matrices: A32 = complex64 copy (skipped when A32 is null),
 // normA[b] = infinity norm of matrix b and, when rowscale is not null, the
 // power-of-two row scales of the tensor-core residuals for rows 0..npad-1
 // (rowscale[b * npad + i]; see ozaki_slice_matrix).

@@ -743,8 +743,8 @@ static int build_prepare(const mueller_curve* curve, const mueller_media* media,
   if (c->bytes + ((size_t)1 << 30) > freeb) { delete c; return fail(MUELLER_ENOMEM, "factors exceed free device memory"); }
   if (c->keep.alloc(&c->A, (size_t)(M + 1) * n * n) != cudaSuccess ||
       c->keep.alloc(&c->piv, (size_t)(M + 1) * n) != cudaSuccess || c->keep.alloc(&c->info, M + 1) != cudaSuccess ||
-      (mixed && (c->keep.alloc(&c->A32, (size_t)(M + 1) * n * n) != cudaSuccess ||
-                 c->keep.alloc(&c->normA, M + 1) != cudaSuccess)) ||
+      c->keep.alloc(&c->normA, M + 1) != cudaSuccess ||
+      (mixed && c->keep.alloc(&c->A32, (size_t)(M + 1) * n * n) != cudaSuccess) ||
       (slices && (c->keep.alloc(&c->Asl, ozaki_matrix_slices_elems(c->npad, M + 1)) != cudaSuccess ||
                   c->keep.alloc(&c->rowscale, (size_t)(M + 1) * c->npad) != cudaSuccess)) ||
       c->keep.alloc(&c->tc_err, 1) != cudaSuccess) {
@@ -764,7 +764,10 @@ static int build_assemble(mueller_ctx* c, cudaStream_t s) {
   cudaEventRecord(e0, s);
   int rc = assemble_core(c->S, c->A, s, &c->st, c->keep, c->geo);
   if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-  if (c->S.precision != 0) {
+  if (c->S.precision == 0) {  // ||A'_m||_inf for the condition estimate (mueller_cond_estimate)
+    mixed_prepare(c->A, (int)n, M + 1, nullptr, c->normA, nullptr, (int)n, s);
+    c->launches_pre += 1;
+  } else {
     mixed_prepare(c->A, (int)n, M + 1, c->A32, c->normA, c->S.precision == 1 ? c->rowscale : nullptr, c->npad, s);
     c->launches_pre += 1;
     if (c->S.precision == 1) {
@@ -805,6 +808,7 @@ static int build_finish(mueller_ctx* c, const LuTiming& lt, double ms_lu, int wa
   CK(cudaMemcpy(&tce, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (tce) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core LU update timed out");
   c->st.singular_mode = -1; c->st.singular_column = -1;
+  c->st.kappa_max_mode = -1;
   for (int m = 0; m <= M; ++m)
     if (info[m]) { c->st.singular_mode = m; c->st.singular_column = info[m] - 1; break; }
   c->st.device_bytes = c->bytes;
@@ -1351,6 +1355,46 @@ extern "C" int mueller_stats_get(const mueller_ctx* c, mueller_stats* out) {
   out->host_bytes = 0;
   for (const auto& h : c->spilled) out->host_bytes += h.bytes;
   if (c->is_spilled) out->device_bytes = 0;
+  return MUELLER_OK;
+}
+
+// ---------------------------------------------------------------- condition estimate
+void launch_cond_estimate(const void* LU, bool c64, const int* piv, int n, int modes, const double* normA, cd* work,
+                          double* kappa, cudaStream_t s);
+
+extern "C" int mueller_cond_estimate(mueller_ctx* c, double* kappa, void* stream) {
+  g_err.clear();
+  if (!c) return fail(MUELLER_EINVAL, "null context");
+  SPILLED_CHECK(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int M = c->S.M, n = c->S.n;
+  const bool c64 = c->S.precision != 0;
+  const void* LU = c64 ? (const void*)c->A32 : (const void*)c->A;
+  if (!LU || !c->normA) return fail(MUELLER_EINVAL, "the context holds no factors");
+  DevBuf tmp;
+  cd* work;
+  double* dk;
+  if (tmp.alloc(&work, (size_t)(M + 1) * n) != cudaSuccess || tmp.alloc(&dk, M + 1) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "condition-estimate scratch");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  launch_cond_estimate(LU, c64, c->piv, n, M + 1, c->normA, work, dk, s);
+  cudaEventRecord(e1, s);
+  std::vector<double> hk(M + 1);
+  cudaError_t err = cudaMemcpyAsync(hk.data(), dk, sizeof(double) * (M + 1), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(MUELLER_ECUDA, cudaGetErrorString(err));
+  c->st.kappa_max = -1.0;
+  c->st.kappa_max_mode = -1;
+  for (int m = 0; m <= M; ++m)
+    if (hk[m] > c->st.kappa_max) { c->st.kappa_max = hk[m]; c->st.kappa_max_mode = m; }
+  c->st.kappa_mode0 = hk[0];
+  c->st.ms_cond = ms;
+  if (kappa) std::copy(hk.begin(), hk.end(), kappa);
   return MUELLER_OK;
 }
 

@@ -146,3 +146,64 @@ def test_waves_on_two_streams_match_bodies_alone(mb):
     for i, r in enumerate(res):
         assert np.array_equal(got[i], alone[i]), bodies[i].name
         assert r.backward_err <= 1e-14 and r.extra["lu_graph"] == 1
+
+
+def test_batch_sample_vs_oracle(mb):
+    """The seeded 8-body sample of the batched workload (6 random bodies, a
+    5-level and an 11-level cylinder; oracle solutions in
+    tests/golden/fullsize_batch<index>.npz, written by
+    tests/golden/make_fullsize.py batch): all eight built together by one
+    mueller_build_many (mixed path, one graph-launched LU over every mode of
+    every body), then modes -1, 0 and M of each compared with the oracle --
+    plane-wave currents to 1e-9 of the body's largest mode, the far field of
+    those modes to 1e-9, and the solutions of two seeded random right-hand
+    sides per mode to max(1e-9, 10 kappa_1 noise_1) (kappa_1 the mode's
+    condition number and noise_1 the relative difference of the oracle's 32-
+    and 24-point matrices, both from the oracle's file)."""
+    import glob
+    import os
+    files = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "fullsize_batch*.npz")))
+    if len(files) < 8:
+        pytest.skip("batch oracle files not generated")
+    gs = [np.load(f) for f in files]
+    bodies = []
+    for g in gs:
+        curve = W.Curve(int(g["n_panels"]), g["r"].copy(), g["z"].copy(), g["dr"].copy(), g["dz"].copy(),
+                        bool(int(g["closed"])))
+        media = W.Media(float(g["omega"]), complex(g["eps0"]), complex(g["mu0"]), complex(g["eps1"]),
+                        complex(g["mu1"]))
+        bodies.append((curve, media, int(g["M"])))
+    ctxs = mb.build_many(bodies, mb.Options(n_phi=int(gs[0]["n_phi"]), precision=1, refine_tol=1e-14))
+    tol = 1e-9
+    for g, (curve, media, M), ctx in zip(gs, bodies, ctxs):
+        n = 4 * curve.N
+        nrhs = len(g["wave_d"])
+        b = torch.zeros((2 * M + 1, nrhs, n), dtype=torch.complex128, device=DEV)
+        ctx.rhs_planewave(g["wave_d"], g["wave_e"], b)
+        x = torch.zeros_like(b)
+        ctx.solve(b, x)
+        xg = x.cpu().numpy()
+        modes, waves = [int(m) for m in g["modes"]], [int(w) for w in g["waves"]]
+        top = max(np.linalg.norm(g["x"][qi, wi]) for qi in range(len(modes)) for wi in range(len(waves)))
+        for qi, m in enumerate(modes):
+            for wi, w in enumerate(waves):
+                assert np.linalg.norm(xg[m + M, w] - g["x"][qi, wi]) < tol * top, (g["workload"], m, w)
+        keep = torch.zeros_like(x)
+        for m in modes:
+            keep[m + M] = x[m + M]
+        dirs = torch.tensor(g["ff_dirs"], device=DEV)
+        E = torch.zeros((nrhs, len(dirs), 3), dtype=torch.complex128, device=DEV)
+        ctx.far_field(keep, dirs, E)
+        assert np.linalg.norm(E.cpu().numpy() - g["ff"]) < tol * np.linalg.norm(g["ff"]), g["workload"]
+        br = torch.zeros((2 * M + 1, 2, n), dtype=torch.complex128, device=DEV)
+        for qi, m in enumerate(modes):
+            br[m + M] = torch.tensor(g["b_rand"][qi], device=DEV)
+        xr = torch.zeros_like(br)
+        ctx.solve(br, xr)
+        xr = xr.cpu().numpy()
+        for qi, m in enumerate(modes):
+            err = max(np.linalg.norm(xr[m + M, c] - g["x_rand"][qi, c]) / np.linalg.norm(g["x_rand"][qi, c])
+                      for c in range(2))
+            bound = max(tol, 10.0 * float(g["kappa1"][qi]) * max(float(g["noise1"][qi]), 1e-15))
+            assert err < bound, (str(g["workload"]), m, err)
+        ctx.close()

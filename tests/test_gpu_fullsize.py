@@ -16,8 +16,9 @@ per-mode relative error is bounded separately for modes above 1e-6 of the
 largest); far field relative l2 over all directions and components; and,
 per stored mode, the solutions of two seeded random right-hand sides, plain
 relative l2 (these are full-size solutions for every mode, including those
-whose plane-wave data are below rounding), held to max(tol, 1e-13 kappa_1)
-with kappa_1 the mode's condition number (see _check).
+whose plane-wave data are below rounding), held to the tolerance or to the
+mode's condition number times the oracle's own noise level, whichever is
+larger (see _check).
 
 Also: a closed curve (torus, Section 6) with sampled 4x4 blocks across the
 wrap-around, where the first and last panels are neighbours.
@@ -102,15 +103,17 @@ def _check(mb, name, precision, tol):
     assert worst_global < tol, worst_global
     assert worst_plain < 100 * tol, worst_plain
     assert ff < tol, ff
-    # A solution moves by up to kappa (dA/A + backward errors) when the matrix
-    # moves by dA: the two sides' kernels agree to ~1e-14 of each family's
-    # largest coefficient, the LUs are backward stable to ~1e-15, so a mode
-    # of condition number kappa is held to max(tol, 1e-13 kappa_1), kappa_1
-    # the 1-norm condition number of the oracle's weighted matrix.
-    if "kappa1" in g.files:
+    # A solution moves by up to kappa dA/A when the matrix moves by dA.  In
+    # high modes, rows of targets next to the axis carry factors m/r and
+    # m^2/r^2 (up to ~1e11) on spectral coefficients far below rounding, so
+    # those entries are rounding noise on both sides; the oracle measures its
+    # own noise as the difference of its 32- and 24-point matrices (noise1).
+    # Each mode is held to max(tol, 10 kappa_1 max(noise1, 1e-15)).
+    if "kappa1" in g.files and "noise1" in g.files:
         for qi, m in enumerate(modes):
-            bound = max(tol, 1e-13 * float(g["kappa1"][qi]))
-            assert err_rand[qi] < bound, (m, err_rand[qi], float(g["kappa1"][qi]))
+            kap, nz = float(g["kappa1"][qi]), float(g["noise1"][qi])
+            bound = max(tol, 10.0 * kap * max(nz, 1e-15))
+            assert err_rand[qi] < bound, (m, err_rand[qi], kap, nz)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])

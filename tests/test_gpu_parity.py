@@ -274,3 +274,25 @@ def test_random_body_full_size(mb):
     num = max(float((xs[1][q] - xs[0][q]).norm()) for q in range(2 * M + 1))
     den = max(float(xs[0][q].norm()) for q in range(2 * M + 1))
     assert num / den < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_condition_estimate_vs_exact(mb, precision):
+    """mueller_cond_estimate (Hager's estimate of ||A'^{-1}||_inf from the LU
+    factors, times ||A'||_inf) against the exact kappa_inf of the same
+    weighted matrices (numpy, from the matrices mueller_assemble gives): a
+    lower bound, within a factor 3 (the estimator's usual accuracy; on small
+    well-behaved matrices it is typically exact)."""
+    cfg = W.config_sphere()
+    M, n = cfg.M, 4 * cfg.N
+    A = torch.zeros((M + 1, n, n), dtype=torch.complex128, device=DEV)
+    mb.assemble(cfg.curve, cfg.media, M, A, mb.Options(n_phi=cfg.n_phi))
+    ctx = mb.build(cfg.curve, cfg.media, M, mb.Options(n_phi=cfg.n_phi, precision=precision))
+    est = ctx.cond_estimate()
+    st = ctx.stats()
+    ctx.close()
+    Ah = A.cpu().numpy()
+    exact = np.array([np.linalg.cond(Ah[m].T, np.inf) for m in range(M + 1)])
+    assert (est <= exact * (1 + 1e-5)).all() and (est >= exact / 3).all(), (est / exact)
+    assert st["kappa_max_mode"] == int(np.argmax(est)) and abs(st["kappa_max"] - est.max()) <= 1e-12 * est.max()
+    assert abs(st["kappa_mode0"] - est[0]) <= 1e-12 * est[0]
