@@ -145,8 +145,10 @@ __device__ __forceinline__ WarpSmem warp_smem(const GreenParams& gp, char* base)
 // Split pairs are sampled on the full n_phi grid and keep all modes 0..M+1.
 // A non-split pair's spectra decay like zeta^(m - K) past the band of the
 // oscillating factor exp(i k rho) (zeta = chi - sqrt(chi^2 - 1), the
-// singularity of 1/rho at cos phi = chi; the band is about |k| sqrt(r_t r_s),
-// with margin K = 1.5 |k|max sqrt(r_t r_s) + 8).  So
+// singularity of 1/rho at cos phi = chi; the band is about |k| sqrt(r_t r_s):
+// the phase k rho(phi) turns at most at that rate; margin K = |k|max
+// sqrt(r_t r_s) + 4, whose exact tails at mode mc + 1 measured below 1e-20 of
+// each family's largest coefficient in 40-digit quadrature).  So
 //  - modes above mc = min(M + 1, ceil(K + ln(1/eps) / ln(1/zeta))) are below
 //    eps of the family's largest coefficient and are set to zero;
 //  - on an n-point grid, mode m <= mc picks up the aliases of modes n - m and
@@ -176,7 +178,7 @@ __device__ PairGrid pair_grid(const GreenParams& gp, double rt, double dr0, doub
   const double c = d2 / B;
   const double lz = log1p(c + sqrt(c * (2.0 + c)));
   const double kmax = fmax(cabs(gp.kp0.k), cabs(gp.kp1.k));
-  const double K = 1.5 * kmax * sqrt(0.5 * B) + 8.0;
+  const double K = kmax * sqrt(0.5 * B) + 4.0;
   const double span = lneps / lz;
   const int mc = (int)fmin((double)(gp.Ms - 1), ceil(K + span));
   const double need = fmax(2.0 * mc + 2.0, fmax(16.0, ceil(mc + K + span)));
