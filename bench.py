@@ -106,9 +106,7 @@ def _workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def _oracle_pool_init():
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+_ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
 def _oracle_rows(args):
@@ -154,7 +152,18 @@ class OracleBaseline:
         self.name = name
         self.cfg = _workload(name)
         self.cores = cores or os.cpu_count() or 1
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_pool_init)
+        # one BLAS thread per process: the spawned workers import numpy before any
+        # initializer runs, so the environment is set before they start
+        saved = {k: os.environ.get(k) for k in _ONE_THREAD}
+        os.environ.update(_ONE_THREAD)
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
         self.pool.map(_oracle_rows, [(name, []) for _ in range(self.cores)])   # imports done before timing
 
     def sample(self, budget_s):
@@ -416,7 +425,8 @@ def run_serving(args):
     mb.cache_limit(0)                                   # the admission budget accounts for every device byte
     free, _ = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * 1e9) if args.budget_gb > 0 else int(0.9 * free)
-    srv = serving.Server(pool, budget, precision=1, max_rhs=args.max_rhs, grid=(180, 360))
+    srv = serving.Server(pool, budget, precision=1, max_rhs=args.max_rhs, grid=(180, 360),
+                         host_budget_bytes=int(args.host_budget_gb * 1e9))
     smallest = min(range(len(pool)), key=lambda k: srv.peaks[k])
     warm = [serving.Request(i, smallest, 0.0, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
             for i in range(max(args.warmup, 1))]
@@ -438,7 +448,8 @@ def run_serving(args):
             "value": summ["p99_latency_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": len(warm),
             "ms_per_step": st.wall * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 factors + c128 refinement", "data": "synthetic",
-            "config": {"workload": f"serving: 32-body pool (workloads.config_pool), Poisson {args.rate:g}/s for "
+            "config": {"workload": f"serving: 32-body pool (workloads.config_pool: random bodies N=1024, "
+                                   f"modes -128..128, k0=10, k1=15), Poisson {args.rate:g}/s for "
                                    f"{args.duration:g} s, Zipf({args.zipf:g}) bodies, nrhs U{{1..{args.max_rhs}}}, "
                                    f"far field 180x360 per request", "budget_gb": budget / 1e9,
                        "l2_flush": "inputs larger than L2 (factors of every key)"},
@@ -728,6 +739,8 @@ def main():
     ap.add_argument("--zipf", type=float, default=1.1, help="serving: body choice Zipf exponent (0 = uniform)")
     ap.add_argument("--max-rhs", type=int, default=256, help="serving: right-hand sides per request at most")
     ap.add_argument("--drain", type=float, default=120.0, help="serving: seconds after the last arrival to finish")
+    ap.add_argument("--host-budget-gb", type=float, default=0.0,
+                    help="serving: pinned host memory for factors evicted from the device (0 = none)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="batched/serving: device-memory budget (0 = 90%% of the free memory)")
     args = ap.parse_args()

@@ -19,9 +19,15 @@ in the Remark of Section 5):
   the discretisation, read from include/mueller_near_rules.h (the table the
   CUDA library compiles in); tests/test_oracle_pins.py checks them against
   the closed-form moments.  32 nodes per target.
-* adjacent rule: graded toward the shared endpoint: u in [0, 1] -> tau =
-  -1 + 2u (or 1 - 2u); intervals [4^-(j+1), 4^-j], j = 0..4, and [0, 4^-5],
-  each with 16 Gauss points.  96 nodes, target independent.
+* adjacent rules, target independent, in u in [0, 1] -> tau = -1 + 2u (or
+  1 - 2u), u the distance from the shared endpoint: where the curve is
+  smooth across the junction, the 26-node rule of the near-rule data, exact
+  (to 3e-14) for P_j(2u-1) and P_j(2u-1) log|u - s| with the singular point
+  s off the panel near the extension of the curve (the table's comment gives
+  the family); at a corner (the end tangents of the two panels differ by more
+  than 10 degrees) a rule graded toward the shared endpoint, intervals
+  [4^-(j+1), 4^-j], j = 0..4, and [0, 4^-5], each with 16 Gauss points (96
+  nodes), which also covers singular points off the real axis.
 """
 from __future__ import annotations
 
@@ -93,10 +99,14 @@ def self_rule(i: int):
     return tau, wt
 
 
-def adjacent_rule(shared_end: int):
+def adjacent_rule(shared_end: int, corner: bool = True):
     """Support nodes for a neighbouring panel whose endpoint tau = shared_end
-    (-1 or +1) touches the target's panel."""
-    u, w = graded_rule(ADJ_LEVELS, ADJ_GAUSS)
+    (-1 or +1) touches the target's panel: the graded composite rule at a
+    corner, the tabulated rule for smooth junctions otherwise."""
+    if corner:
+        u, w = graded_rule(ADJ_LEVELS, ADJ_GAUSS)
+    else:
+        u, w = near_rule_table("ADJ_U"), near_rule_table("ADJ_W")
     if shared_end < 0:
         return -1.0 + 2.0 * u, 2.0 * w
     return 1.0 - 2.0 * u, 2.0 * w

@@ -56,6 +56,19 @@ def wavenumbers(media):
     return complex(k0), complex(k1)
 
 
+def junction_is_corner(curve, A: int, B: int) -> bool:
+    """Whether the curve turns by more than 10 degrees where panel A's end
+    (tau = +1) meets panel B's start (tau = -1): the end tangents are the
+    panels' degree-15 Lagrange interpolants of (dr, dz) at tau = +1 and -1."""
+    x, _ = gauss.gauss_legendre(P)
+    Lp = gauss.lagrange_basis(x, np.array([1.0]))[0]
+    Lm = gauss.lagrange_basis(x, np.array([-1.0]))[0]
+    sa, sb = slice(A * P, (A + 1) * P), slice(B * P, (B + 1) * P)
+    ta = np.array([Lp @ curve.dr[sa], Lp @ curve.dz[sa]])
+    tb = np.array([Lm @ curve.dr[sb], Lm @ curve.dz[sb]])
+    return float(ta @ tb / (np.linalg.norm(ta) * np.linalg.norm(tb))) < np.cos(np.deg2rad(10.0))
+
+
 def panel_support(curve, target_panel: int, target_local: int, Q: int):
     """Support points on source panel Q for a target node, as
     (r, z, r', z', W, L, disp) with W the ds-weights, L[s, k] the Lagrange
@@ -77,9 +90,9 @@ def panel_support(curve, target_panel: int, target_local: int, Q: int):
         nxt = target_panel + 1 if target_panel + 1 < nP else (0 if wrap else None)
         prv = target_panel - 1 if target_panel - 1 >= 0 else (nP - 1 if wrap else None)
         if Q == nxt:
-            tau, wt = gauss.adjacent_rule(-1)
+            tau, wt = gauss.adjacent_rule(-1, junction_is_corner(curve, target_panel, Q))
         elif Q == prv:
-            tau, wt = gauss.adjacent_rule(+1)
+            tau, wt = gauss.adjacent_rule(+1, junction_is_corner(curve, Q, target_panel))
         else:
             return None
     x, _ = gauss.gauss_legendre(P)

@@ -575,11 +575,13 @@ __device__ __forceinline__ bool support_point(const BuildArgs& a, int i, int slo
   if (slot < SELF_PTS + ADJ_PTS) {
     int Q = P - 1;
     if (Q < 0) { if (!a.closed || nP <= 2) return false; Q = nP - 1; }
+    if (slot - SELF_PTS >= a.sup.adj_n[2 * Q + 1]) return false;  // beyond the rule of Q's end +1
     *pid = (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + ADJ_PTS + (slot - SELF_PTS);
     return true;
   }
   int Q = P + 1;
   if (Q >= nP) { if (!a.closed || nP <= 2) return false; Q = 0; }
+  if (slot - SELF_PTS - ADJ_PTS >= a.sup.adj_n[2 * Q + 0]) return false;  // beyond the rule of Q's end -1
   *pid = (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + (slot - SELF_PTS - ADJ_PTS);
   return true;
 }
@@ -623,14 +625,16 @@ __global__ void __launch_bounds__(384) near_kernel(BuildArgs a) {
   const double* L;
   if (which == 1) {
     Q = P; slot0 = 0; S = SELF_PTS; L = a.sup.Lself + (size_t)loc * SELF_PTS * P_NODES;
-  } else if (which == 0) {
+  } else if (which == 0) {  // previous panel: its end +1 touches the target's panel
     Q = P - 1;
     if (Q < 0) { if (!a.closed || nP <= 2) return; Q = nP - 1; }
-    slot0 = SELF_PTS; S = ADJ_PTS; L = a.sup.Ladj + (size_t)1 * ADJ_PTS * P_NODES;
-  } else {
+    slot0 = SELF_PTS; S = a.sup.adj_n[2 * Q + 1];
+    L = a.sup.Ladj + (size_t)(a.sup.adj_rule[2 * Q + 1] * 2 + 1) * ADJ_PTS * P_NODES;
+  } else {                  // next panel: its end -1
     Q = P + 1;
     if (Q >= nP) { if (!a.closed || nP <= 2) return; Q = 0; }
-    slot0 = SELF_PTS + ADJ_PTS; S = ADJ_PTS; L = a.sup.Ladj;
+    slot0 = SELF_PTS + ADJ_PTS; S = a.sup.adj_n[2 * Q + 0];
+    L = a.sup.Ladj + (size_t)(a.sup.adj_rule[2 * Q + 0] * 2 + 0) * ADJ_PTS * P_NODES;
   }
   const int Ms = gp.Ms;
   cd* R = (cd*)smem;                              // [kc][3][NFAM][Ms]

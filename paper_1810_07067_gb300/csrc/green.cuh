@@ -35,13 +35,18 @@ struct SupportTable {
   const double *r, *z, *rp, *zp, *W;  // support points, [n_panels * PTS_PER_PANEL]
   const double *dr, *dz;              // target - point displacement (own-panel points)
   const double* Lself;                // [16][SELF_PTS][16]
-  const double* Ladj;                 // [2][ADJ_PTS][16]  (0: shared end -1, 1: shared end +1)
+  const double* Ladj;                 // [2 rules][2 ends][ADJ_PTS][16]  (rule 0 smooth junction, 1 corner;
+                                      // end 0: shared end -1, 1: shared end +1)
+  const int* adj_rule;                // [n_panels][2] rule of each panel end (-1: no neighbour)
+  const int* adj_n;                   // [n_panels][2] its number of points (0: no neighbour)
 };
 
 #include "mueller_near_rules.h"
 // support points of the near-panel rules (Section 5): the target's own panel
-// takes the generalized Gaussian rule on each side of the target (the table
-// of mueller_near_rules.h), each neighbouring panel a graded composite rule
+// takes the generalized Gaussian rule on each side of the target, each
+// neighbouring panel the compressed generalized Gaussian rule for smooth
+// junctions (both tables of mueller_near_rules.h) or, at a corner, a graded
+// composite rule of 96 points; ADJ_PTS slots are reserved per panel end
 #define SELF_SIDE MUELLER_SELF_SIDE
 #define SELF_PTS (2 * SELF_SIDE)
 #define ADJ_PTS 96

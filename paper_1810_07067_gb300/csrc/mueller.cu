@@ -69,7 +69,8 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 struct Rules {
   std::vector<double> x16, w16, bary;   // panel nodes, weights, barycentric weights
   std::vector<double> self_u, self_w;   // reference self rule on [0, 1]
-  std::vector<double> adj_u, adj_w;     // reference adjacent rule on [0, 1]
+  std::vector<double> adj_u, adj_w;     // reference adjacent rule on [0, 1] at corners (graded composite)
+  std::vector<double> adjs_u, adjs_w;   // reference adjacent rule on [0, 1] at smooth junctions
 };
 
 // Reference rule on [0, 1] graded toward 0: intervals [4^-(j+1), 4^-j] and
@@ -96,6 +97,8 @@ static Rules make_rules() {
   R.self_u.assign(MUELLER_SELF_U, MUELLER_SELF_U + MUELLER_SELF_SIDE);
   R.self_w.assign(MUELLER_SELF_W, MUELLER_SELF_W + MUELLER_SELF_SIDE);
   graded_rule(5, 16, R.adj_u, R.adj_w);
+  R.adjs_u.assign(MUELLER_ADJ_U, MUELLER_ADJ_U + MUELLER_ADJ_SMOOTH);
+  R.adjs_w.assign(MUELLER_ADJ_W, MUELLER_ADJ_W + MUELLER_ADJ_SMOOTH);
   return R;
 }
 
@@ -130,6 +133,7 @@ struct Setup {
   std::vector<double> sr, sz, srp, szp, sW;                 // support points
   std::vector<double> sdr, sdz;                             // own-panel: target - point
   std::vector<double> Lself, Ladj;
+  std::vector<int> adj_rule, adj_n;    // [nP][2]: rule (0 smooth, 1 corner) and point count of each panel end
   std::vector<int> split_far, split_sup;
   std::vector<double> split_pairs;                          // [n_split][4]
   long long n_far = 0, n_sup = 0;
@@ -273,9 +277,8 @@ static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M,
 // Support points and interpolation tables (eq. eq_nyslike2).
 static void setup_support(const mueller_curve* cv, Setup& S) {
   const Rules& R = rules();
-  const int ns = (int)R.self_u.size(), na = (int)R.adj_u.size();
+  const int ns = (int)R.self_u.size();
   S.Lself.assign((size_t)P_NODES * SELF_PTS * P_NODES, 0.0);
-  S.Ladj.assign((size_t)2 * ADJ_PTS * P_NODES, 0.0);
   std::vector<double> tau_self((size_t)P_NODES * SELF_PTS), wt_self((size_t)P_NODES * SELF_PTS);
   for (int a = 0; a < P_NODES; ++a) {
     double ti = R.x16[a], Lm = ti + 1.0, Lp = 1.0 - ti;
@@ -288,12 +291,45 @@ static void setup_support(const mueller_curve* cv, Setup& S) {
     for (int s = 0; s < SELF_PTS; ++s)
       lagrange_row(R, tau_self[a * SELF_PTS + s], &S.Lself[((size_t)a * SELF_PTS + s) * P_NODES]);
   }
-  std::vector<double> tau_adj(2 * ADJ_PTS), wt_adj(2 * ADJ_PTS);
-  for (int s = 0; s < na; ++s) {
-    tau_adj[s] = -1.0 + 2.0 * R.adj_u[s]; wt_adj[s] = 2.0 * R.adj_w[s];
-    tau_adj[ADJ_PTS + s] = 1.0 - 2.0 * R.adj_u[s]; wt_adj[ADJ_PTS + s] = 2.0 * R.adj_w[s];
+  // neighbouring panels: per rule (0 smooth junction, 1 corner) and panel end
+  // (0: tau = -1, 1: tau = +1), points tau = -1 + 2u or 1 - 2u
+  std::vector<double> tau_adj(4 * ADJ_PTS, 0.0), wt_adj(4 * ADJ_PTS, 0.0);
+  S.Ladj.assign((size_t)4 * ADJ_PTS * P_NODES, 0.0);
+  for (int rule = 0; rule < 2; ++rule) {
+    const std::vector<double>& u = rule ? R.adj_u : R.adjs_u;
+    const std::vector<double>& w = rule ? R.adj_w : R.adjs_w;
+    for (int e = 0; e < 2; ++e)
+      for (size_t s = 0; s < u.size(); ++s) {
+        const size_t k = (size_t)(rule * 2 + e) * ADJ_PTS + s;
+        tau_adj[k] = e == 0 ? -1.0 + 2.0 * u[s] : 1.0 - 2.0 * u[s];
+        wt_adj[k] = 2.0 * w[s];
+        lagrange_row(R, tau_adj[k], &S.Ladj[k * P_NODES]);
+      }
   }
-  for (int s = 0; s < 2 * ADJ_PTS; ++s) lagrange_row(R, tau_adj[s], &S.Ladj[(size_t)s * P_NODES]);
+  // junction j joins panel j's end +1 and panel j+1's end -1 (the last one
+  // wraps for closed curves): a corner when the two end tangents, from the
+  // panels' degree-15 interpolants of (dr, dz), differ by more than 10 degrees
+  std::vector<double> Lm1(P_NODES), Lp1(P_NODES);
+  lagrange_row(R, -1.0, Lm1.data());
+  lagrange_row(R, 1.0, Lp1.data());
+  auto tangent = [&](int Q, const std::vector<double>& L, double* t) {
+    t[0] = t[1] = 0.0;
+    for (int k = 0; k < P_NODES; ++k) { t[0] += L[k] * cv->dr[Q * P_NODES + k]; t[1] += L[k] * cv->dz[Q * P_NODES + k]; }
+  };
+  const int wrap = S.closed && S.nP > 2;
+  S.adj_rule.assign((size_t)2 * S.nP, -1);
+  S.adj_n.assign((size_t)2 * S.nP, 0);
+  for (int j = 0; j < S.nP - 1 + wrap; ++j) {
+    const int A = j, B = (j + 1) % S.nP;
+    double ta[2], tb[2];
+    tangent(A, Lp1, ta);
+    tangent(B, Lm1, tb);
+    const double c = (ta[0] * tb[0] + ta[1] * tb[1]) / (std::hypot(ta[0], ta[1]) * std::hypot(tb[0], tb[1]));
+    const int rule = c < 0.98480775301220806 ? 1 : 0;  // cos 10 degrees
+    const int n = rule ? (int)R.adj_u.size() : (int)R.adjs_u.size();
+    S.adj_rule[2 * A + 1] = rule; S.adj_n[2 * A + 1] = n;
+    S.adj_rule[2 * B + 0] = rule; S.adj_n[2 * B + 0] = n;
+  }
   const size_t npts = (size_t)S.nP * PTS_PER_PANEL;
   S.sr.resize(npts); S.sz.resize(npts); S.srp.resize(npts); S.szp.resize(npts); S.sW.resize(npts);
   S.sdr.assign(npts, 0.0); S.sdz.assign(npts, 0.0);
@@ -307,7 +343,17 @@ static void setup_support(const mueller_curve* cv, Setup& S) {
       const double* L;
       double wt;
       if (t < P_NODES * SELF_PTS) { L = &S.Lself[(size_t)t * P_NODES]; wt = wt_self[t]; }
-      else { L = &S.Ladj[(size_t)(t - P_NODES * SELF_PTS) * P_NODES]; wt = wt_adj[t - P_NODES * SELF_PTS]; }
+      else {
+        const int e = (t - P_NODES * SELF_PTS) / ADJ_PTS, s = (t - P_NODES * SELF_PTS) % ADJ_PTS;
+        const int rule = S.adj_rule[2 * Q + e];
+        if (rule < 0 || s >= S.adj_n[2 * Q + e]) {  // no neighbour at this end, or beyond the rule's points
+          const size_t id = (size_t)Q * PTS_PER_PANEL + t;
+          S.sr[id] = S.sz[id] = S.srp[id] = S.szp[id] = S.sW[id] = 0.0;
+          continue;
+        }
+        const size_t k = (size_t)(rule * 2 + e) * ADJ_PTS + s;
+        L = &S.Ladj[k * P_NODES]; wt = wt_adj[k];
+      }
       double vr = 0, vz = 0, vdr = 0, vdz = 0;
       for (int k = 0; k < P_NODES; ++k) {
         vr += L[k] * r[k]; vz += L[k] * z[k]; vdr += L[k] * dr[k]; vdz += L[k] * dz[k];
@@ -344,10 +390,12 @@ static long long support_pid(const Setup& S, int i, int slot) {
   if (slot < SELF_PTS + ADJ_PTS) {
     int Q = P - 1;
     if (Q < 0) { if (!S.closed) return -1; Q = S.nP - 1; }
+    if (slot - SELF_PTS >= S.adj_n[2 * Q + 1]) return -1;  // beyond the rule of Q's end +1
     return (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + ADJ_PTS + (slot - SELF_PTS);
   }
   int Q = P + 1;
   if (Q >= S.nP) { if (!S.closed) return -1; Q = 0; }
+  if (slot - SELF_PTS - ADJ_PTS >= S.adj_n[2 * Q + 0]) return -1;  // beyond the rule of Q's end -1
   return (long long)Q * PTS_PER_PANEL + P_NODES * SELF_PTS + (slot - SELF_PTS - ADJ_PTS);
 }
 
@@ -613,6 +661,8 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   CK(tmp.upload(&sszp, S.szp, s)); CK(tmp.upload(&ssW, S.sW, s));
   CK(tmp.upload(&ssdr, S.sdr, s)); CK(tmp.upload(&ssdz, S.sdz, s));
   CK(tmp.upload(&sLs, S.Lself, s)); CK(tmp.upload(&sLa, S.Ladj, s));
+  int *dadj_rule, *dadj_n;
+  CK(tmp.upload(&dadj_rule, S.adj_rule, s)); CK(tmp.upload(&dadj_n, S.adj_n, s));
   CK(tmp.upload(&dcos, cos_table(S.nphi), s)); CK(tmp.upload(&ds2, s2_table(S.nphi), s));
   double *dladC = nullptr, *dladS = nullptr;
   if (S.gp.qmax >= 2) {
@@ -633,7 +683,7 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   cd* dspec;
   if (tmp.alloc(&dspec, (size_t)S.N * NEAR_SLOTS * NFAM * Ms) != cudaSuccess)
     return fail(MUELLER_ENOMEM, "support spectra scratch");
-  a.sup = SupportTable{ssr, ssz, ssrp, sszp, ssW, ssdr, ssdz, sLs, sLa};
+  a.sup = SupportTable{ssr, ssz, ssrp, sszp, ssW, ssdr, ssdz, sLs, sLa, dadj_rule, dadj_n};
   a.cosT = dcos; a.s2T = ds2; a.ladC = dladC; a.ladS = dladS; a.split_far = dsf; a.split_sup = dss; a.leg = dleg; a.n_split = n_split;
   a.spec_sup = dspec; a.A = A_dev;
   a.lneps = -std::log(S.split_eps);

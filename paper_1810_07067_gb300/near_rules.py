@@ -21,7 +21,30 @@ minimum-norm Gauss-Newton steps, until n nodes remain.  The moments are
     int_0^1 Pt_j(u) du = delta_j0,   int_0^1 log u du = -1,
     int_0^1 Pt_j(u) log u du = (-1)^(j+1) / (j (j+1))   (j >= 1).
 
-Usage: python -m paper_1810_07067_gb300.near_rules   (about a minute)
+Neighbouring panels.  A panel that shares an endpoint with the target's
+panel is integrated with a target-independent rule in u in [0, 1], the
+distance from the shared endpoint over the panel's parameter length.  Where
+the curve is smooth across the junction, the integrand's singular part sits
+at u = s* just outside the panel: s* = delta e^{i a} with delta the target's
+distance from the junction in the panel's units (at least half the first
+Gauss node's offset, 0.0026, up to 2 under dyadic grading) and a near 180
+degrees (a = 180 for a straight continuation; curvature and parametrisation
+move it slightly off the real axis).  The rule is built for the span of
+Pt_j(u) and Pt_j(u) log|u - s*|, j < 16, delta in [0.002, 2.5] (40
+log-spaced values) and a in [135, 180] degrees (4 values): the sampled
+functions (unit L2 norm on a composite rule graded toward u = 0, 17 pieces
+of 40 Gauss points) are compressed by an SVD to the singular values above
+3e-14 (50 directions), an interpolatory rule on 50 of the composite nodes
+(column-pivoted QR) is reduced by node elimination with minimum-norm
+Gauss-Newton steps (nodes kept in (0, 1), weights positive), in double
+precision: the orthonormal directions are well conditioned.  The result
+integrates every member of the family, and members between the sampled
+(delta, a), to 3e-14 of its L1 norm.  At a corner (the two panels' end
+tangents differ by more than 10 degrees) the singular point leaves the real
+axis (a down to 30 degrees for the wedges of cones); that family does not
+compress below the graded composite rule the library keeps for corners.
+
+Usage: python -m paper_1810_07067_gb300.near_rules   (about five minutes)
 """
 from __future__ import annotations
 
@@ -132,8 +155,118 @@ def _gl(n):
     return [x[s] for s in order], [w[s] for s in order]
 
 
+ADJ_DELTA = (0.002, 2.5, 40)     # log-spaced distances of the singular point
+ADJ_ANGLE = (135.0, 180.0, 4)    # its angles, degrees
+ADJ_EPS = 3e-14                  # singular values kept (unit-norm functions)
+
+
+def _composite(levels=16, npts=40):
+    """Gauss-Legendre pieces [2^-(l+1), 2^-l] and [0, 2^-levels] of [0, 1]."""
+    import numpy as np
+    xs, ws, iv = [], [], []
+    xg, wg = np.polynomial.legendre.leggauss(npts)
+    for l in range(levels + 1):
+        a = 2.0 ** -(l + 1) if l < levels else 0.0
+        b = 2.0 ** -l
+        xs.append(0.5 * (a + b) + 0.5 * (b - a) * xg)
+        ws.append(0.5 * (b - a) * wg)
+        iv.append((a, b))
+    return np.concatenate(xs), np.concatenate(ws), iv
+
+
+def _adjacent_family(u, J=16):
+    import numpy as np
+    u = np.asarray(u, float)
+    y = 2.0 * u - 1.0
+    P = np.zeros((J,) + u.shape)
+    P[0] = 1.0
+    P[1] = y
+    for j in range(1, J - 1):
+        P[j + 1] = ((2 * j + 1) * y * P[j] - j * P[j - 1]) / (j + 1)
+    rows = [P]
+    deltas = np.logspace(np.log10(ADJ_DELTA[0]), np.log10(ADJ_DELTA[1]), ADJ_DELTA[2])
+    angles = np.deg2rad(np.linspace(ADJ_ANGLE[0], ADJ_ANGLE[1], ADJ_ANGLE[2]))
+    for d in deltas:
+        for a in angles:
+            sr, si = d * np.cos(a), d * np.sin(a)
+            rows.append(P * (0.5 * np.log((u - sr) ** 2 + si ** 2)))
+    return np.concatenate(rows)
+
+
+def adjacent_smooth_rule(levels=16, npts=40):
+    """Nodes and weights (increasing nodes) of the neighbouring-panel rule for
+    smooth junctions (see the module docstring)."""
+    import numpy as np
+    import scipy.linalg
+    x0, w0, iv = _composite(levels, npts)
+    F = _adjacent_family(x0)
+    F /= np.sqrt((F ** 2 * w0).sum(1, keepdims=True))
+    U, S, _ = np.linalg.svd((F * np.sqrt(w0)[None, :]).T, full_matrices=False)
+    r = int((S > ADJ_EPS).sum())
+    Psi = U[:, :r] / np.sqrt(w0)[:, None]        # orthonormal directions at the composite nodes
+    mu = (w0[:, None] * Psi).sum(0)
+    xg, _ = np.polynomial.legendre.leggauss(npts)
+    bw = np.array([1.0 / np.prod([xg[k] - xg[l] for l in range(npts) if l != k]) for k in range(npts)])
+
+    def basis(x):  # values and derivatives: barycentric interpolation on the composite pieces
+        V = np.zeros((len(x), r))
+        D = np.zeros((len(x), r))
+        for q, xv in enumerate(x):
+            l = next(l for l, (a, b) in enumerate(iv) if a <= xv <= b)
+            a, b = iv[l]
+            t = (2.0 * xv - a - b) / (b - a)
+            vals = Psi[l * npts:(l + 1) * npts]
+            dif = t - xg
+            k = int(np.argmin(np.abs(dif)))
+            if abs(dif[k]) < 1e-15:
+                dk = np.array([(bw[j] / bw[k]) / (xg[k] - xg[j]) if j != k else 0.0 for j in range(npts)])
+                dk[k] = -dk.sum()
+                V[q], D[q] = vals[k], (dk @ vals) * 2.0 / (b - a)
+                continue
+            c = bw / dif
+            p = c @ vals / c.sum()
+            V[q] = p
+            D[q] = ((c / dif) @ (p[None, :] - vals)) / c.sum() * 2.0 / (b - a)
+        return V, D
+
+    def gauss_newton(u, w, iters=60):
+        for _ in range(iters):
+            V, D = basis(u)
+            R = V.T @ w - mu
+            if np.abs(R).max() < 1e-15:
+                return u, w
+            J = np.concatenate([D.T * w[None, :], V.T], axis=1)
+            st = np.linalg.lstsq(J, -R, rcond=None)[0]
+            du, dw = st[:len(u)], st[len(u):]
+            t = 1.0
+            while not (np.all(u + t * du > 0.0) and np.all(u + t * du < 1.0)):
+                t *= 0.5
+                if t < 1e-8:
+                    return None
+            u, w = u + t * du, w + t * dw
+        V, _ = basis(u)
+        return (u, w) if np.abs(V.T @ w - mu).max() < 1e-14 else None
+
+    _, _, piv = scipy.linalg.qr(Psi.T * np.sqrt(w0)[None, :], pivoting=True, mode="economic")
+    u = np.sort(x0[piv[:r]])
+    w = np.linalg.solve(basis(u)[0].T, mu)
+    while True:
+        V, _ = basis(u)
+        sig = np.abs(w) * (V ** 2).sum(1)
+        for k in np.argsort(sig)[:8]:
+            res = gauss_newton(np.delete(u, k), np.delete(w, k))
+            if res is not None and np.all(res[1] > 0):
+                u, w = res
+                break
+        else:
+            break
+    o = np.argsort(u)
+    return u[o], w[o]
+
+
 def write_header(path=HEADER):
     u, w = self_side_rule()
+    ua, wa = adjacent_smooth_rule()
     lines = [
         "/*",
         " * mueller_near_rules.h -- near-panel quadrature data of the Nystrom",
@@ -156,6 +289,16 @@ def write_header(path=HEADER):
     lines += [f"  {repr(float(v))}," for v in u]
     lines += ["};", "static const double MUELLER_SELF_W[MUELLER_SELF_SIDE] = {"]
     lines += [f"  {repr(float(v))}," for v in w]
+    lines += ["};",
+              "/* MUELLER_ADJ_U / MUELLER_ADJ_W: the neighbouring-panel rule on [0, 1] (u = distance",
+              " * from the shared endpoint over the panel's parameter length) for smooth junctions:",
+              " * exact to 3e-14 for Pt_j(u) and Pt_j(u) log|u - s*|, j < 16, with s* = delta e^{ia},",
+              " * delta in [0.002, 2.5], a in [135, 180] degrees (compressed generalized Gaussian rule). */",
+              f"#define MUELLER_ADJ_SMOOTH {len(ua)}",
+              "static const double MUELLER_ADJ_U[MUELLER_ADJ_SMOOTH] = {"]
+    lines += [f"  {repr(float(v))}," for v in ua]
+    lines += ["};", "static const double MUELLER_ADJ_W[MUELLER_ADJ_SMOOTH] = {"]
+    lines += [f"  {repr(float(v))}," for v in wa]
     lines += ["};", "#endif", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))

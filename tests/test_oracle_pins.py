@@ -61,6 +61,39 @@ def test_adjacent_rule(delta):
     assert abs(num - float(ex)) < 2e-15
 
 
+@pytest.mark.parametrize("delta,angle,j", [(0.0026, 180.0, 0), (0.0026, 180.0, 15), (0.02, 150.0, 7),
+                                           (0.3, 135.0, 15), (1.9, 170.0, 3), (0.0041, 140.0, 11)])
+def test_adjacent_smooth_rule(delta, angle, j):
+    """Neighbouring-panel rule for smooth junctions: P_j(2u-1) log|u - s| with
+    the singular point s = delta e^{i angle} beside the shared endpoint
+    (including values between the ones the rule was built on), against mpmath."""
+    u, w = gauss.near_rule_table("ADJ_U"), gauss.near_rule_table("ADJ_W")
+    assert (w > 0).all() and 0 < u.min() and u.max() < 1
+    sr, si = delta * math.cos(math.radians(angle)), delta * math.sin(math.radians(angle))
+    Pj = np.polynomial.legendre.Legendre.basis(j)
+    f = lambda v: Pj(2 * v - 1) * 0.5 * np.log((v - sr) ** 2 + si ** 2)
+    g = lambda v: mp.legendre(j, 2 * v - 1) * 0.5 * mp.log((v - sr) ** 2 + si ** 2)
+    ex = mp.quad(g, [0, min(1.0, 4 * delta), 1]) if 4 * delta < 1 else mp.quad(g, [0, 1])
+    l1 = mp.quad(lambda v: abs(g(v)), [0, min(1.0, 4 * delta), 1]) if 4 * delta < 1 else mp.quad(lambda v: abs(g(v)), [0, 1])
+    assert abs((w * f(u)).sum() - float(ex)) < 1e-13 * float(l1)
+
+
+def test_junction_corners():
+    """Junctions where the curve turns by more than 10 degrees take the corner
+    rule: the cylinder's two edges, the cone's rim; none on smooth curves."""
+    cyl = W.cylinder(3)
+    corners = [j for j in range(cyl.n_panels - 1) if system.junction_is_corner(cyl, j, j + 1)]
+    assert len(corners) == 2
+    for j in corners:                      # at r = 1, z = +-1
+        assert abs(cyl.r[16 * j + 15] - 1.0) < 0.05 and abs(abs(cyl.z[16 * j + 15]) - 1.0) < 0.05
+    cone = W.cone(3, 1.0, 0.7)
+    assert sum(system.junction_is_corner(cone, j, j + 1) for j in range(cone.n_panels - 1)) == 1
+    for smooth in (W.sphere(6), W.random_body(12, seed=3)):
+        assert not any(system.junction_is_corner(smooth, j, j + 1) for j in range(smooth.n_panels - 1))
+    tor = W.torus(8)
+    assert not any(system.junction_is_corner(tor, j, (j + 1) % 8) for j in range(8))
+
+
 def test_lagrange_basis_interpolates():
     x, _ = gauss.gauss_legendre(16)
     L = gauss.lagrange_basis(x, x)

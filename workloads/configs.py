@@ -124,16 +124,9 @@ def config_batch(n_random: int = 64, n_edged: int = 8) -> list:
 
 
 def config_pool(n_bodies: int = 32, seed0: int = 100) -> list:
-    """The serving pool: n_bodies smooth random bodies (seeds seed0..), sizes
-    and wavenumbers drawn as in config_batch (N ~ U[200, 1200], M ~ U{32..128},
-    k0 ~ U[1, 12], k1 = 1.5 k0, from default_rng(10000 + seed)); each body
-    is served at its own k0, so a (body, k0) key is the body."""
-    out = []
-    for s in range(seed0, seed0 + n_bodies):
-        rng = np.random.default_rng(10000 + s)
-        N = int(rng.uniform(200, 1200))
-        M = int(rng.integers(32, 129))
-        k0 = float(rng.uniform(1.0, 12.0))
-        curve = random_body(max(1, round(N / 16)), seed=s)
-        out.append(Config(f"pool{s}_N{curve.N}_M{M}", curve, Media.from_k(k0, 1.5 * k0), M, 16, []))
-    return out
+    """The serving pool: n_bodies smooth random bodies as in config_random
+    (64 panels, N = 1024, modes -128..128, 512 azimuthal samples, k0 = 10,
+    k1 = 15), seeds seed0.. for the shape coefficients; every body is served
+    at k0 = 10, so a (body, k0) key is the body."""
+    return [Config(f"pool{s}_N1024_M128", random_body(64, seed=s), Media.from_k(10.0, 15.0), 128, 512, [])
+            for s in range(seed0, seed0 + n_bodies)]
