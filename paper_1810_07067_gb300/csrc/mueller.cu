@@ -999,7 +999,7 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   const int n = c->S.n, M = c->S.M;
   const long long nvec = (long long)(2 * M + 1) * nrhs;
   const bool tcres = c->Asl != nullptr;
-  const int njt = (2 * nrhs + OZ_JT - 1) / OZ_JT;
+  const int ojt = ozaki_job_tile(nrhs), njt = ozaki_job_tiles(nrhs);
   DevBuf tmp;
   cd *bw, *y, *r, *d;
   double* norms;  // [3][nvec]: b', y, r
@@ -1008,8 +1008,8 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   int* derr = nullptr;
   if (tmp.alloc(&bw, (size_t)nvec * n) || tmp.alloc(&y, (size_t)nvec * n) || tmp.alloc(&r, (size_t)nvec * n) ||
       tmp.alloc(&d, (size_t)nvec * n) || tmp.alloc(&norms, (size_t)3 * nvec) ||
-      (tcres && (tmp.alloc(&Ysl, ozaki_vector_slices_elems(c->npad, M + 1, njt)) ||
-                 tmp.alloc(&colscale, (size_t)(M + 1) * njt * OZ_JT) || tmp.alloc(&derr, 1))))
+      (tcres && (tmp.alloc(&Ysl, ozaki_vector_slices_elems(c->npad, M + 1, njt, ojt)) ||
+                 tmp.alloc(&colscale, (size_t)(M + 1) * njt * ojt) || tmp.alloc(&derr, 1))))
     return fail(MUELLER_ENOMEM, "refinement work vectors");
   if (derr) CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
   double *bn = norms, *yn = norms + nvec, *rn = norms + 2 * nvec;
@@ -1073,7 +1073,7 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   // tensor work per residual: 36 digit products x 4 real products of
   // (npad x npad) x (npad x 32 jobs per job tile) per mode, 2 flops per MAC
   c->st.residual_tc_flops = (double)c->st.residual_launches * 144.0 * 2.0 * (double)c->npad * c->npad *
-                            OZ_JT * ((2 * nrhs + OZ_JT - 1) / OZ_JT) * (M + 1);
+                            ojt * njt * (M + 1);
   c->st.backward_err_max = worst;
   if (backward_err) std::copy(be.begin(), be.end(), backward_err);
   if (derr) {

@@ -7,12 +7,16 @@
 
 #define OZ_S 8        // digits per value (7 bits each)
 #define OZ_RT 128     // output rows per CTA
-#define OZ_JT 32      // right-hand sides per CTA
+#define OZ_JT 32      // right-hand sides per CTA (largest job tile; 16 when there are at most 16 jobs)
 #define OZ_KT 16      // k per tile
 #define OZ_CHUNK 16   // k-tiles per exact FP32 accumulation (256 values of k)
 
 size_t ozaki_matrix_slices_elems(int npad, int batch);  // bf16 elements
-size_t ozaki_vector_slices_elems(int npad, int batch, int njt);
+// job tile (right-hand-side columns of one MMA) for nrhs right-hand sides:
+// 16 when the 2 nrhs jobs (modes +m and -m) fit one tile of 16, else 32
+inline int ozaki_job_tile(int nrhs) { return 2 * nrhs <= 16 ? 16 : OZ_JT; }
+inline int ozaki_job_tiles(int nrhs) { const int jt = ozaki_job_tile(nrhs); return (2 * nrhs + jt - 1) / jt; }
+size_t ozaki_vector_slices_elems(int npad, int batch, int njt, int jt);
 
 // Slices of the complex matrices A[batch][n][n] (column-major) for rows padded
 // to npad (multiple of 128), given rowscale[batch][npad], the power-of-two
