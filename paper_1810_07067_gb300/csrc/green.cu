@@ -392,8 +392,8 @@ __device__ __forceinline__ V2 iy(double y, V2 x) { return v2(iy(y, x.a), iy(y, x
 
 // The block from the gathered coefficients c1, c2, c3 of the nine families.
 __device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
-                                                   const AsmParams& ap, double rt, double rpt, double zpt,
-                                                   cd out[4][4]);
+                                                   const AsmParams& ap, double rt, double irt, double rpt,
+                                                   double zpt, cd out[4][4]);
 
 template <class Get>
 __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double rt, double rpt, double zpt,
@@ -410,15 +410,17 @@ __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double r
     c2[f] = v2(mul_i(G3a), G2b);
     c3[f] = v2(R(2, f, a0), C(0.0));
   }
-  mueller_block_core(c1, c2, c3, m, ap, rt, rpt, zpt, out);
+  mueller_block_core(c1, c2, c3, m, ap, rt, 1.0 / rt, rpt, zpt, out);
 }
 
 // The same block from one pair's unscaled spectra S[f * stride + (mode - base)]
 // and its three quadrature weights fac (sigma = 0, 1, 2): the weights multiply
-// the sums and differences of modes m +- 1 once instead of every term.
+// the sums and differences of modes m +- 1 once instead of every term.  The
+// block is linear in the spectra, so a common factor of the block (the L2
+// row/column weight ratio) can ride in fac; irt = 1 / rt.
 __device__ __forceinline__ void mueller_block_spec(const cd* S, int stride, int base, const double fac[3], int m,
-                                                   const AsmParams& ap, double rt, double rpt, double zpt,
-                                                   cd out[4][4]) {
+                                                   const AsmParams& ap, double rt, double irt, double rpt,
+                                                   double zpt, cd out[4][4]) {
   const int ap1 = m + 1 - base, am1 = ((m >= 1) ? m - 1 : 1) - base, a0 = m - base;
   const double h0 = 0.5 * fac[0], h1 = 0.5 * fac[1];
   V2 c1[NFAM], c2[NFAM], c3[NFAM];
@@ -430,13 +432,13 @@ __device__ __forceinline__ void mueller_block_spec(const cd* S, int stride, int 
     c2[f] = v2(mul_i(h0 * dif), h1 * sum);
     c3[f] = v2(fac[2] * S[f * stride + a0], C(0.0));
   }
-  mueller_block_core(c1, c2, c3, m, ap, rt, rpt, zpt, out);
+  mueller_block_core(c1, c2, c3, m, ap, rt, irt, rpt, zpt, out);
 }
 
 __device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
-                                                   const AsmParams& ap, double rt, double rpt, double zpt,
-                                                   cd out[4][4]) {
-  const double irt = 1.0 / rt, irt2 = irt * irt;
+                                                   const AsmParams& ap, double rt, double irt, double rpt,
+                                                   double zpt, cd out[4][4]) {
+  const double irt2 = irt * irt;
   const double mr = m * irt, mr2 = m * irt2;  // i m / r_t and i m / r_t^2 act as iy(mr, .), iy(mr2, .)
   V2 Nt[2], Nth[2];
 #pragma unroll
@@ -514,18 +516,26 @@ __global__ void far_kernel(BuildArgs a) {
   cd* Qs = tq ? a.tailq + gw * (long long)tq * tw * NFAM : nullptr;
   int* Qij = tq ? a.tailij + gw * 2LL * tq : nullptr;
   int qn = 0;  // pairs in the queue (warp-uniform)
-  auto assemble = [&](const cd* S, int stride, int base, int i, int j, int m) {
-    const double rs = a.geo.r[j], w = a.geo.w[j];
-    const double fac[3] = {w * rs * a.geo.rp[j], w * rs, w * rs * a.geo.zp[j]};
+  // per-pair constants: quadrature weights times the L2 weight ratio, 1 / r_t
+  auto pair_consts = [&](int i, int j, double fac[3], double* irt) {
+    const double rs = a.geo.r[j], w = a.geo.w[j] * rs * (a.geo.sw[i] / a.geo.sw[j]);
+    fac[0] = w * a.geo.rp[j];
+    fac[1] = w;
+    fac[2] = w * a.geo.zp[j];
+    *irt = 1.0 / a.geo.r[i];
+  };
+  auto assemble = [&](const cd* S, int stride, int base, int i, int j, int m, const double fac[3], double irt) {
     cd blk[4][4];
-    mueller_block_spec(S, stride, base, fac, m, a.ap, a.geo.r[i], a.geo.rp[i], a.geo.zp[i], blk);
-    store_block(a.A, n, m, i, j, blk, a.geo.sw[i] / a.geo.sw[j]);
+    mueller_block_spec(S, stride, base, fac, m, a.ap, a.geo.r[i], irt, a.geo.rp[i], a.geo.zp[i], blk);
+    store_block(a.A, n, m, i, j, blk, 1.0);
   };
   auto flush = [&]() {
     __syncwarp();  // the queue's global writes are visible to the whole warp
     for (int it = lane; it < qn * tail; it += 32) {
       const int q = it / tail, m = full + it % tail;
-      assemble(Qs + (long long)q * tw * NFAM, tw, full - 1, Qij[2 * q], Qij[2 * q + 1], m);
+      double fac[3], irt;
+      pair_consts(Qij[2 * q], Qij[2 * q + 1], fac, &irt);
+      assemble(Qs + (long long)q * tw * NFAM, tw, full - 1, Qij[2 * q], Qij[2 * q + 1], m, fac, irt);
     }
     __syncwarp();
     qn = 0;
@@ -540,8 +550,10 @@ __global__ void far_kernel(BuildArgs a) {
     warp_pair_spectra(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, a.s2T, W, lane, g);
     // modes above mz have zero spectra at m - 1, m and m + 1: their blocks are zero
     const int mz = min(gp.M, g.mc + 1);
+    double fac[3], irt;
+    pair_consts(i, j, fac, &irt);
     for (int m = lane; m < full; m += 32) {
-      if (m <= mz) assemble(W.spec, gp.Ms, 0, i, j, m);
+      if (m <= mz) assemble(W.spec, gp.Ms, 0, i, j, m, fac, irt);
       else store_zero_block(a.A, n, m, i, j);
     }
     if (tq) {

@@ -9,12 +9,20 @@
 // their sums over 256 values of k stay below 2^24 and hence exact as well.
 // Levels s + t <= 9 are kept (36 digit products per real product; the dropped
 // part is below 2^-68 of |a||y| per term).  Tensor memory holds one FP32
-// accumulator per level and per real/imaginary part (8 x 2 x jt columns, jt
-// the job tile of 16 or 32 right-hand-side columns); every 256 values of k
-// they are drained into FP64 registers.
+// accumulator per level, [Re | Im] side by side (8 x 2 jt columns, jt the job
+// tile of 16 or 32 right-hand-side columns); every 256 values of k they are
+// drained into FP64 registers.  The complex product takes two MMAs per digit
+// pair: the B operand stacks the digits of Re y over those of Im y (2 jt
+// rows), so Re a [Re y | Im y] + Im a [-Im y | Re y] lands in [Re | Im] of the
+// accumulator; the y slices are stored as [-Im, Re, Im] per digit, and the
+// two B operands start at Re and at -Im.
 // Operand tiles are stored in global memory in the shared-memory layout of the
 // MMA (no-swizzle K-major core matrices), so each 16-wide k-tile is a single
-// bulk asynchronous copy (TMA), double-buffered behind mbarriers.
+// bulk asynchronous copy (TMA).  The residual kernel is warp-specialised: a
+// copy thread keeps a ring of k-tile stages full, an MMA thread consumes
+// them, and four drain warps empty the accumulators of a finished 256-k
+// chunk while the MMAs of the next chunk run (two accumulator sets in tensor
+// memory where they fit).
 #include <cstdio>
 #include "ozaki.cuh"
 #include "tc.cuh"
@@ -23,7 +31,7 @@
 #define OZ_ABLOCK (2 * OZ_S * OZ_ATILE)   // per (row tile, k-tile): re/im x 8 slices
 // slice tile and block of Y for a job tile of jt right-hand-side columns
 __host__ __device__ constexpr int oz_ytile(int jt) { return jt * OZ_KT; }
-__host__ __device__ constexpr int oz_yblock(int jt) { return 2 * OZ_S * jt * OZ_KT; }
+__host__ __device__ constexpr int oz_yblock(int jt) { return 3 * OZ_S * jt * OZ_KT; }  // [digit][-Im, Re, Im]
 
 size_t ozaki_matrix_slices_elems(int npad, int batch) {
   return (size_t)batch * (npad / OZ_RT) * (npad / OZ_KT) * OZ_ABLOCK;
@@ -184,11 +192,16 @@ __global__ void oz_slice_vectors_kernel(const cd* __restrict__ y, int n, int npa
   const int off = core_off(jj, kk);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
-    __align__(16) __nv_bfloat16 re[8], im[8];
+    __align__(16) __nv_bfloat16 re[8], im[8], nim[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) { re[c] = __float2bfloat16(dre[c][s]); im[c] = __float2bfloat16(dim_[c][s]); }
-    *(uint4*)(blk + (0 * OZ_S + s) * ytile + off) = *(uint4*)re;
-    *(uint4*)(blk + (1 * OZ_S + s) * ytile + off) = *(uint4*)im;
+    for (int c = 0; c < 8; ++c) {
+      re[c] = __float2bfloat16(dre[c][s]);
+      im[c] = __float2bfloat16(dim_[c][s]);
+      nim[c] = __float2bfloat16(-dim_[c][s]);
+    }
+    *(uint4*)(blk + (3 * s + 0) * ytile + off) = *(uint4*)nim;
+    *(uint4*)(blk + (3 * s + 1) * ytile + off) = *(uint4*)re;
+    *(uint4*)(blk + (3 * s + 2) * ytile + off) = *(uint4*)im;
   }
 }
 
@@ -196,134 +209,160 @@ __device__ __forceinline__ void atomic_max_pos_oz(double* addr, double v) {
   atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// CTA per (row tile, mode, job tile of JT columns); 128 threads; thread 0 issues copies and MMAs.
+// Shape of the residual kernel for a job tile of JT columns.
+template <int JT> struct OzShape {
+  static constexpr int YT = oz_ytile(JT), YB = oz_yblock(JT);
+  static constexpr uint32_t SET_COLS = 2 * OZ_S * JT;          // accumulators of one chunk: 8 levels x [Re | Im]
+  static constexpr int NACC = (2 * SET_COLS <= 512) ? 2 : 1;   // two sets (drain overlaps the next chunk) if they fit
+  static constexpr uint32_t TMEM_COLS = 512;                   // NACC x SET_COLS, allocated as a power of two
+  static constexpr int STAGE = (OZ_ABLOCK + YB) * 2;           // bytes of one k-tile (A and y digits)
+  static constexpr int NST = 2;                                // k-tile stages in shared memory
+  static constexpr int SMEM = NST * STAGE;
+  static constexpr int THREADS = 192;                          // warps 0-3 drain, 4 copies, 5 issues MMAs
+};
+static_assert(OzShape<16>::NACC * OzShape<16>::SET_COLS <= 512 && OzShape<OZ_JT>::NACC * OzShape<OZ_JT>::SET_COLS <= 512,
+              "accumulator sets exceed tensor memory");
+static_assert(OzShape<OZ_JT>::SMEM <= 227 * 1024, "stages exceed shared memory");
+
+// CTA per (row tile, mode, job tile of JT columns).  Every wait is bounded:
+// a role that gives up sets the CTA's failure flag (and *err), the others
+// stop at their next wait, and before the CTA exits the copy thread lets its
+// copies in flight land and the MMA thread waits for its MMAs.
 template <int JT>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     oz_residual_kernel(const __nv_bfloat16* __restrict__ Asl, const double* __restrict__ rowscale,
                        const __nv_bfloat16* __restrict__ Ysl, const double* __restrict__ colscale, int n, int npad,
                        int M, int nrhs, int njt, const cd* __restrict__ bw, cd* __restrict__ r,
                        double* __restrict__ rnorm, int* __restrict__ err) {
-  constexpr int YT = oz_ytile(JT), YB = oz_yblock(JT);
-  constexpr uint32_t TMEM_COLS = 2 * OZ_S * JT;   // 8 levels x re/im x JT columns
+  using S = OzShape<JT>;
+  constexpr int NST = S::NST, NACC = S::NACC;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __nv_bfloat16* bufA = (__nv_bfloat16*)smem;                         // [2][OZ_ABLOCK]
-  __nv_bfloat16* bufY = bufA + 2 * OZ_ABLOCK;                         // [2][YB]
-  __shared__ __align__(8) uint64_t full[2], empty[2], drain;
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[NACC], tempty[NACC], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
+  volatile int* fail = &s_fail;
   const int rt = blockIdx.x, m = blockIdx.y, jt = blockIdx.z;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nrt = npad / OZ_RT, nkt = npad / OZ_KT;
-  const __nv_bfloat16* Ab = Asl + ((size_t)m * nrt + rt) * nkt * OZ_ABLOCK;
-  const __nv_bfloat16* Yb = Ysl + ((size_t)m * njt + jt) * nkt * YB;
-  const uint32_t abytes = OZ_ABLOCK * 2, ybytes = YB * 2;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, TMEM_COLS);
-  if (tid == 0) {
+  const int nchunk = (nkt + OZ_CHUNK - 1) / OZ_CHUNK;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, S::TMEM_COLS);
+  if (tid == 32) {
     s_fail = 0;
-    tc::mbar_init(&full[0], 1); tc::mbar_init(&full[1], 1);
-    tc::mbar_init(&empty[0], 1); tc::mbar_init(&empty[1], 1);
-    tc::mbar_init(&drain, 1);
+#pragma unroll
+    for (int b = 0; b < NST; ++b) { tc::mbar_init(&full[b], 1); tc::mbar_init(&empty[b], 1); }
+#pragma unroll
+    for (int b = 0; b < NACC; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 4); }
+    tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  auto load = [&](int kt) {
-    int b = kt & 1;
-    tc::mbar_expect_tx(&full[b], abytes + ybytes);
-    tc::bulk_g2s(bufA + b * OZ_ABLOCK, Ab + (size_t)kt * OZ_ABLOCK, abytes, &full[b]);
-    tc::bulk_g2s(bufY + b * YB, Yb + (size_t)kt * YB, ybytes, &full[b]);
-  };
-  if (tid == 0) {
-    load(0);
-    if (nkt > 1) load(1);
-  }
-  const uint32_t id_pos = tc::idesc_bf16_f32(OZ_RT, JT, false);
-  const uint32_t id_neg = tc::idesc_bf16_f32(OZ_RT, JT, true);
   double zre[JT], zim[JT];
 #pragma unroll
   for (int j = 0; j < JT; ++j) { zre[j] = 0.0; zim[j] = 0.0; }
-  const int nchunk = (nkt + OZ_CHUNK - 1) / OZ_CHUNK;
-  for (int c = 0; c < nchunk; ++c) {
-    const int kt0 = c * OZ_CHUNK, kt1 = min(nkt, kt0 + OZ_CHUNK);
-    if (tid == 0 && !s_fail) {
-      for (int kt = kt0; kt < kt1; ++kt) {
-        const int b = kt & 1;
-        if (!tc::mbar_wait(&full[b], (kt >> 1) & 1)) { s_fail = 1; break; }
-        tc::fence_after();
-        // descriptors of slice 0 of this buffer; slice tiles follow at fixed
-        // offsets (4 KiB for A, 1 KiB for y: 256 and 64 in the 16-byte units
-        // of the descriptor's start-address field, which cannot carry)
-        const uint64_t a_re0 = tc::desc_noswizzle(tc::smem_u32(bufA + b * OZ_ABLOCK), 128, 256);
-        const uint64_t y_re0 = tc::desc_noswizzle(tc::smem_u32(bufY + b * YB), 128, 256);
-        const uint64_t a_im0 = a_re0 + (uint64_t)(OZ_S * OZ_ATILE * 2 / 16);
-        const uint64_t y_im0 = y_re0 + (uint64_t)(OZ_S * YT * 2 / 16);
-        const uint32_t first = (kt == kt0) ? 1u : 0u;
-#pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
-#pragma unroll
-          for (int t = 0; t < OZ_S - s; ++t) {
-            const int l = s + t;
-            const uint32_t acc_re = tmem + (uint32_t)((l * 2 + 0) * JT);
-            const uint32_t acc_im = tmem + (uint32_t)((l * 2 + 1) * JT);
-            const uint64_t are = a_re0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
-            const uint64_t aim = a_im0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
-            const uint64_t yre = y_re0 + (uint64_t)(t * (YT * 2 / 16));
-            const uint64_t yim = y_im0 + (uint64_t)(t * (YT * 2 / 16));
-            const uint32_t fresh = (s == 0) ? (first ^ 1u) : 1u;  // first product of this level in the chunk
-            tc::mma_bf16(acc_re, are, yre, id_pos, fresh);
-            tc::mma_bf16(acc_re, aim, yim, id_neg, 1u);
-            tc::mma_bf16(acc_im, are, yim, id_pos, fresh);
-            tc::mma_bf16(acc_im, aim, yre, id_pos, 1u);
-          }
-        }
-        tc::commit(&empty[b]);
-        // refill the buffer of the previous k-tile with k-tile kt + 1
-        if (kt >= 1 && kt + 1 < nkt) {
-          const int pb = (kt - 1) & 1;
-          if (!tc::mbar_wait(&empty[pb], ((kt - 1) >> 1) & 1)) { s_fail = 1; break; }
-          load(kt + 1);
-        }
+  int issued = 0;  // copy thread: k-tiles whose copies were issued
+  if (warp == 4) {
+    if (lane == 0) {
+      const __nv_bfloat16* Ab = Asl + ((size_t)m * nrt + rt) * nkt * OZ_ABLOCK;
+      const __nv_bfloat16* Yb = Ysl + ((size_t)m * njt + jt) * nkt * S::YB;
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int st = kt % NST;
+        if (kt >= NST && !tc::mbar_wait(&empty[st], ((kt / NST) - 1) & 1)) { *fail = 1; break; }
+        if (*fail) break;
+        unsigned char* base = smem + (size_t)st * S::STAGE;
+        tc::mbar_expect_tx(&full[st], S::STAGE);
+        tc::bulk_g2s(base, Ab + (size_t)kt * OZ_ABLOCK, OZ_ABLOCK * 2, &full[st]);
+        tc::bulk_g2s(base + OZ_ABLOCK * 2, Yb + (size_t)kt * S::YB, S::YB * 2, &full[st]);
+        issued = kt + 1;
       }
-      tc::commit(&drain);
     }
-    __syncthreads();
-    if (s_fail) break;
-    if (!tc::mbar_wait(&drain, c & 1)) { atomicExch(&s_fail, 1); }
-    __syncthreads();
-    if (s_fail) break;
-    tc::fence_after();
-    // drain: this warp's 32 rows, all levels
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int l = 0; l < OZ_S; ++l) {
-      const double sc = ldexp(1.0, -7 * (l + 2));
-      float v[JT];
-      tc::tmem_ld32(tw + (uint32_t)((l * 2 + 0) * JT), v);
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(OZ_RT, 2 * JT, false);
+      int kt = 0;
+      for (int c = 0; c < nchunk && !*fail; ++c) {
+        const int set = c % NACC;
+        if (c >= NACC && !tc::mbar_wait(&tempty[set], ((c / NACC) - 1) & 1)) { *fail = 1; break; }
+        tc::fence_after();
+        const uint32_t acc0 = tmem + (uint32_t)set * S::SET_COLS;
+        const int kt1 = min(nkt, (c + 1) * OZ_CHUNK);
+        for (; kt < kt1; ++kt) {
+          const int st = kt % NST;
+          if (!tc::mbar_wait(&full[st], (kt / NST) & 1)) { *fail = 1; break; }
+          tc::fence_after();
+          unsigned char* base = smem + (size_t)st * S::STAGE;
+          // digit s of Re a at s tiles, of Im a at OZ_S + s tiles (4 KiB each);
+          // digit t of y: [-Im, Re, Im] at 3t tiles (JT x 16 each)
+          const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(base), 128, 256);
+          const uint64_t y0 = tc::desc_noswizzle(tc::smem_u32(base + OZ_ABLOCK * 2), 128, 256);
+          const bool first = kt == c * OZ_CHUNK;
 #pragma unroll
-      for (int j = 0; j < JT; ++j) zre[j] = fma(sc, (double)v[j], zre[j]);
-      tc::tmem_ld32(tw + (uint32_t)((l * 2 + 1) * JT), v);
+          for (int s = 0; s < OZ_S; ++s) {
 #pragma unroll
-      for (int j = 0; j < JT; ++j) zim[j] = fma(sc, (double)v[j], zim[j]);
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-  }
-  if (s_fail) {
-    if (tid == 0) {
-      atomicExch(err, 1);
-      // let copies still in flight land before the CTA exits (bounded)
-      tc::mbar_wait(&full[0], 0, 1 << 20);
-      tc::mbar_wait(&full[1], 0, 1 << 20);
+            for (int t = 0; t < OZ_S - s; ++t) {
+              const uint32_t acc = acc0 + (uint32_t)((s + t) * 2 * JT);
+              const uint64_t are = a0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
+              const uint64_t aim = a0 + (uint64_t)((OZ_S + s) * (OZ_ATILE * 2 / 16));
+              const uint64_t yri = y0 + (uint64_t)((3 * t + 1) * (S::YT * 2 / 16));  // [Re | Im]
+              const uint64_t ymr = y0 + (uint64_t)((3 * t + 0) * (S::YT * 2 / 16));  // [-Im | Re]
+              tc::mma_bf16(acc, are, yri, idesc, (first && s == 0) ? 0u : 1u);
+              tc::mma_bf16(acc, aim, ymr, idesc, 1u);
+            }
+          }
+          tc::commit(&empty[st]);  // the stage is free once these MMAs have read it
+        }
+        if (*fail) break;
+        tc::commit(&tfull[set]);   // the chunk's accumulators are complete
+      }
+      tc::commit(&mdone);          // arrives once every MMA issued above has completed
+      if (!tc::mbar_wait(&mdone, 0)) *fail = 1;
     }
   } else {
+    // drain warps: warp w owns tensor-memory lanes (rows) 32w .. 32w + 31
+    for (int c = 0; c < nchunk; ++c) {
+      const int set = c % NACC;
+      if (!tc::mbar_wait(&tfull[set], (c / NACC) & 1)) { *fail = 1; break; }
+      tc::fence_after();
+      const uint32_t tw = tmem + (uint32_t)set * S::SET_COLS + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+      for (int l = 0; l < OZ_S; ++l) {
+        const double sc = ldexp(1.0, -7 * (l + 2));
+#pragma unroll
+        for (int h = 0; h < 2 * JT; h += 32) {  // 32 columns per load: [Re | Im] of JT = 16, half of it for JT = 32
+          float v[32];
+          tc::tmem_ld32(tw + (uint32_t)(l * 2 * JT + h), v);
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const int col = h + u;
+            if (col < JT) zre[col] = fma(sc, (double)v[u], zre[col]);
+            else zim[col - JT] = fma(sc, (double)v[u], zim[col - JT]);
+          }
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[set]);
+    }
+  }
+  __syncthreads();
+  if (*fail) {
+    if (tid == 0) atomicExch(err, 1);
+    if (warp == 4 && lane == 0) {
+      // let the copies still in flight land before the CTA exits (bounded):
+      // the newest copy of each stage completes the newest phase of its barrier
+      for (int st = 0; st < NST; ++st) {
+        const int last = issued - 1 - ((issued - 1 - st) % NST + NST) % NST;  // newest k-tile issued into st
+        if (last >= 0 && last < issued) tc::mbar_wait(&full[st], (last / NST) & 1, 1 << 20);
+      }
+    }
+  } else if (warp < 4) {
     const int i = rt * OZ_RT + warp * 32 + lane;
     if (i < n) {
       const double si = rowscale[(size_t)m * npad + i];
-#pragma unroll 1
-      for (int j = 0; j < JT; ++j) {
+#pragma unroll
+      for (int j = 0; j < JT; ++j) {  // unrolled: zre / zim stay in registers
         const int g = jt * JT + j;
         int q, ridx;
         bool neg;
@@ -340,17 +379,18 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 template <int JT>
 static void oz_residual_launch(const __nv_bfloat16* Asl, const double* rowscale, int n, int npad, int M,
                                const cd* bw, cd* r, int nrhs, int njt, double* rnorm, const __nv_bfloat16* Ysl,
                                const double* colscale, int* err, cudaStream_t s) {
-  const int smem = 2 * (OZ_ABLOCK + oz_yblock(JT)) * 2;
-  cudaFuncSetAttribute(oz_residual_kernel<JT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  oz_residual_kernel<JT><<<dim3(npad / OZ_RT, M + 1, njt), 128, smem, s>>>(Asl, rowscale, Ysl, colscale, n, npad,
-                                                                           M, nrhs, njt, bw, r, rnorm, err);
+  using S = OzShape<JT>;
+  cudaFuncSetAttribute(oz_residual_kernel<JT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+  oz_residual_kernel<JT><<<dim3(npad / OZ_RT, M + 1, njt), S::THREADS, S::SMEM, s>>>(
+      Asl, rowscale, Ysl, colscale, n, npad, M, nrhs, njt, bw, r, rnorm, err);
 }
 
 void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int npad, int M, const cd* bw,
