@@ -117,12 +117,14 @@ __global__ void __launch_bounds__(1024) panel_kernel(const LuMat* __restrict__ m
 // ---------------------------------------------------------------- cluster panel
 // The panel (rows k0..n-1, nbk columns) held in the shared memory of a
 // cluster of C CTAs: CTA q owns rows k0 + q R .. k0 + (q+1) R - 1 as a
-// column-major slice [nbk][R].  Per column: local argmax, candidates written
-// into every CTA's shared memory through the cluster's distributed shared
-// memory, cluster barrier; the pivot row's owner broadcasts it (and the
-// displaced row is sent to the pivot's owner), cluster barrier; then the
-// interchange and the rank-1 update of the owned rows.  Same pivot rule as
-// panel_kernel (largest |a|^2, lowest row on ties).
+// column-major slice [nbk][R].  Per column: local argmax; each CTA writes its
+// candidate (value, row index and the row itself) into every CTA's shared
+// memory through the cluster's distributed shared memory, and CTA 0, which
+// owns row c whenever C > 1 (then R > LU_NB), writes row c as well; one
+// cluster barrier; then every CTA picks the winner, the pivot's owner takes
+// row c, CTA 0 takes the pivot row, and each CTA applies the rank-1 update to
+// its rows.  Same pivot rule as panel_kernel (largest |a|^2, lowest row on
+// ties).
 #define PANEL_SMEM_MAX (200 * 1024)
 #define PANEL_THREADS 512
 
@@ -141,11 +143,16 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(const LuMa
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T* a = (T*)panel_smem;  // [nbk][R]
   using V = typename Pivot<T>::V;
-  __shared__ V cand_v[8];
-  __shared__ int cand_i[8];
-  __shared__ T s_row[LU_NB], s_rowc[LU_NB];
+  // exchange slots, double-buffered by column parity: a slot written for
+  // column jj is written again only for column jj + 2, after every CTA has
+  // passed the cluster barrier of column jj + 1 (so it has read it)
+  __shared__ V cand_v[2][8];
+  __shared__ int cand_i[2][8];
+  __shared__ T cand_row[2][8][LU_NB];   // each CTA's candidate row of the panel
+  __shared__ T top_row[2][LU_NB];       // row c (CTA 0 owns every row c of the panel)
   __shared__ V red_v[PANEL_THREADS / 32];
   __shared__ int red_i[PANEL_THREADS / 32];
+  __shared__ int s_bi;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int row0 = k0 + q * R;
   const int nr = max(0, min(R, n - row0));  // rows owned by this CTA
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(const LuMa
   }
   __syncthreads();
   for (int jj = 0; jj < nbk; ++jj) {
-    const int c = k0 + jj;
+    const int c = k0 + jj, buf = jj & 1;
     const T* aj = a + jj * R;
     V best = V(-1);
     int bi = n;
@@ -177,37 +184,46 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_cluster_kernel(const LuMa
         argmax_merge(best, bi, v2, i2);
       }
       if (lane < C) {  // this CTA's candidate into slot q of every CTA
-        cl.map_shared_rank(cand_v, lane)[q] = best;
-        cl.map_shared_rank(cand_i, lane)[q] = bi;
+        cl.map_shared_rank(cand_v[buf], lane)[q] = best;
+        cl.map_shared_rank(cand_i[buf], lane)[q] = bi;
       }
+      if (lane == 0) s_bi = bi;
+    }
+    __syncthreads();
+    // the candidate row (and, from CTA 0, row c) into every CTA
+    const int cb = s_bi;
+    if (tid < nbk * C) {
+      const int j = tid % nbk, u = tid / nbk;
+      if (cb < n) cl.map_shared_rank(cand_row[buf][q], u)[j] = a[j * R + cb - row0];
+      if (q == 0) cl.map_shared_rank(top_row[buf], u)[j] = a[j * R + c - row0];
     }
     cl.sync();
     best = V(-1);
     bi = n;
-    for (int u = 0; u < C; ++u) argmax_merge(best, bi, cand_v[u], cand_i[u]);
+    int win = -1;
+    for (int u = 0; u < C; ++u) {
+      const V v2 = cand_v[buf][u];
+      const int i2 = cand_i[buf][u];
+      if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; win = u; }
+    }
     const int p = (best > V(0)) ? bi : -1;
     if (q == 0 && tid == 0) {
       pv[c] = (p >= 0) ? p : c;
       if (p < 0 && info[0] == 0) info[0] = c + 1;
     }
-    const int qp = (p >= 0) ? (p - k0) / R : -1, qc = (c - k0) / R;
     if (p >= 0) {
-      if (q == qp && tid < nbk * C) {
-        int j = tid % nbk, u = tid / nbk;
-        cl.map_shared_rank(s_row, u)[j] = a[j * R + p - row0];
+      const T* prow = cand_row[buf][win];
+      const int qp = (p - k0) / R;
+      if (tid < nbk) {
+        if (q == qp && p != c) a[tid * R + p - row0] = top_row[buf][tid];  // row c moves to p
+        if (q == 0) a[tid * R + c - row0] = prow[tid];                       // the pivot row to c
       }
-      if (q == qc && p != c && tid < nbk) cl.map_shared_rank(s_rowc, qp)[tid] = a[tid * R + c - row0];
-    }
-    cl.sync();
-    if (p >= 0) {
-      if (q == qc && tid < nbk) a[tid * R + c - row0] = s_row[tid];
-      if (q == qp && p != c && tid < nbk) a[tid * R + p - row0] = s_rowc[tid];
       __syncthreads();
-      const T inv = cone<T>() / s_row[jj];
+      const T inv = cone<T>() / prow[jj];
       for (int r = max(0, c + 1 - row0) + tid; r < nr; r += PANEL_THREADS) {
         T l = a[jj * R + r] * inv;
         a[jj * R + r] = l;
-        for (int j = jj + 1; j < nbk; ++j) a[j * R + r] = a[j * R + r] - l * s_row[j];
+        for (int j = jj + 1; j < nbk; ++j) a[j * R + r] = a[j * R + r] - l * prow[j];
       }
     }
     __syncthreads();
@@ -505,14 +521,19 @@ __global__ void __launch_bounds__(256) strip_update_kernel(const LuMat* __restri
 #define TCU_ATILE (TCU_M * LU_NB)  // bf16 elements per piece chunk of an L tile (128 rows x 32 k)
 
 // Column tile TN of the update: 32, 64 or 128 (chosen per block by the tile
-// autotuner below).  TMEM holds 4 TN accumulator columns; the launch's shared
-// memory is sized so that the CTAs resident on one SM never ask for more than
-// the 512 TMEM columns: 3 CTAs at TN = 32, 2 at 64, 1 at 128.
+// autotuner below).  The update kernel is persistent (one CTA per SM) and
+// warp-specialised: a copy thread keeps a ring of NST operand chunks full, an
+// MMA thread consumes them into one of NACC accumulator sets in tensor memory
+// (4 TN columns each), and four epilogue warps apply a finished tile to C
+// while the MMAs of the next tile run.
 template <int TN> struct TcuShape {
   static constexpr int BTILE = TN * LU_NB;                        // bf16 elements per piece chunk of a U tile
-  static constexpr int SMEM = 6 * (TCU_ATILE + BTILE) * 2;        // one chunk of both operands, six pieces each
-  static constexpr int SMEM_LAUNCH = TN == 32 ? 64 * 1024 : TN == 64 ? 100 * 1024 : 120 * 1024;
-  static constexpr int TMEM_COLS = 4 * TN;
+  static constexpr int STAGE = 6 * (TCU_ATILE + BTILE) * 2;       // one chunk of both operands, six pieces each
+  static constexpr int NST = (3 * STAGE <= 220 * 1024) ? 3 : 2;
+  static constexpr int SMEM = NST * STAGE;
+  static constexpr uint32_t SET_COLS = 4 * TN;
+  static constexpr int NACC = (2 * SET_COLS <= 512) ? 2 : 1;
+  static constexpr uint32_t TMEM_COLS = NACC * SET_COLS <= 256 ? 256 : 512;
 };
 
 __device__ __forceinline__ int tcu_off(int r, int k) {  // 4 core matrices along k
@@ -578,133 +599,206 @@ __global__ void __launch_bounds__(256) tcu_split_kernel(const LuMat* __restrict_
   }
 }
 
+// Persistent update over the tiles of every matrix of the launch: tile t =
+// (matrix z, column tile y, row tile x), x fastest, taken by CTA t mod
+// gridDim.x; tiles outside a matrix's own trailing block are skipped by all
+// three roles alike.  Every wait is bounded: a role that gives up sets the
+// CTA's failure flag (and *err), the others stop at their next wait, and
+// before the CTA exits the copy thread lets its copies in flight land and the
+// MMA thread waits for its MMAs.
 template <int TN>
-__global__ void __launch_bounds__(128) gemm_update_tc_kernel(const LuMat* __restrict__ mats, int K0,
-                                                            int* __restrict__ err) {
+__global__ void __launch_bounds__(192, 1) gemm_update_tc_kernel(const LuMat* __restrict__ mats, int K0, int nLmax,
+                                                               int nUmax, int count, int* __restrict__ err) {
   using S = TcuShape<TN>;
-  const LuMat mat = mats[blockIdx.z];
-  const int n = mat.n;
-  const int start = K0 + LU_OB;
-  if ((int)blockIdx.x * TCU_M >= n - start || (int)blockIdx.y * TN >= n - start) return;  // before any allocation
+  constexpr int NST = S::NST, NACC = S::NACC;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __nv_bfloat16* As = (__nv_bfloat16*)smem;
-  __nv_bfloat16* Bs = As + 6 * TCU_ATILE;
-  __shared__ __align__(8) uint64_t mbar_load, mbar_mma, mbar_done;
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[NACC], tempty[NACC], mdone;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_ok;
-  cf* M = (cf*)mat.A;
-  const int i0 = start + blockIdx.x * TCU_M, j0 = start + blockIdx.y * TN;
+  __shared__ int s_fail;
+  volatile int* fail = &s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int start = K0 + LU_OB;
+  const long long per = (long long)nLmax * nUmax, total = per * count;
+  auto tile_of = [&](long long t, int& z, int& x, int& y) -> bool {
+    z = (int)(t / per);
+    const long long r = t - (long long)z * per;
+    y = (int)(r / nLmax);
+    x = (int)(r - (long long)y * nLmax);
+    const int rest = mats[z].n - start;
+    return x * TCU_M < rest && y * TN < rest;
+  };
   if (warp == 0) tc::tmem_alloc(&tmem_base, S::TMEM_COLS);
-  if (tid == 0) {
-    s_ok = 1;
-    tc::mbar_init(&mbar_load, 1);
-    tc::mbar_init(&mbar_mma, 1);
-    tc::mbar_init(&mbar_done, 1);
+  if (tid == 32) {
+    s_fail = 0;
+#pragma unroll
+    for (int b = 0; b < NST; ++b) { tc::mbar_init(&full[b], 1); tc::mbar_init(&empty[b], 1); }
+#pragma unroll
+    for (int b = 0; b < NACC; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 4); }
+    tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  // accumulator columns: [0,TN) hh Re, [TN,2TN) hh Im, [2TN,3TN) corrections Re, [3TN,4TN) corrections Im
-  if (tid == 0) {
-    const __nv_bfloat16* W = (const __nv_bfloat16*)mat.ws;
-    const __nv_bfloat16* Lsrc = W + (size_t)blockIdx.x * LU_OB_CHUNKS * 6 * TCU_ATILE;
-    const __nv_bfloat16* Usrc = W + (size_t)((n + TCU_M - 1) / TCU_M) * LU_OB_CHUNKS * 6 * TCU_ATILE +
-                                (size_t)blockIdx.y * LU_OB_CHUNKS * 6 * S::BTILE;
-    const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TN, false);
-    const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TN, true);
-    const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(As), 128, (LU_NB / 8) * 128);
-    const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(Bs), 128, (LU_NB / 8) * 128);
-    const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(S::BTILE * 2 / 16);  // 16-byte units
-    const int qa_[6] = {0, 0, 1, 0, 1, 2}, qb_[6] = {0, 1, 0, 2, 1, 0};
-    bool ok = true;
-    for (int ch = 0; ch < LU_OB_CHUNKS; ++ch) {
-      // the buffer is free: chunk 0 is the first use, later chunks waited for the previous MMAs below
-      tc::mbar_expect_tx(&mbar_load, S::SMEM);
-      tc::bulk_g2s(As, Lsrc + (size_t)ch * 6 * TCU_ATILE, 6 * TCU_ATILE * 2, &mbar_load);
-      tc::bulk_g2s(Bs, Usrc + (size_t)ch * 6 * S::BTILE, 6 * S::BTILE * 2, &mbar_load);
-      if (!tc::mbar_wait(&mbar_load, ch & 1)) {
-        ok = false;
-        tc::mbar_wait(&mbar_load, ch & 1);  // let copies still in flight land before the CTA can exit
-        break;
-      }
-      tc::fence_after();
-#pragma unroll
-      for (int ks = 0; ks < LU_NB / 16; ++ks) {
-        const uint64_t kof = (uint64_t)(ks * 256 / 16);  // two core matrices along k
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-          const uint64_t are = a0 + qa_[u] * at + kof, aim = a0 + (3 + qa_[u]) * at + kof;
-          const uint64_t bre = b0 + qb_[u] * bt + kof, bim = b0 + (3 + qb_[u]) * bt + kof;
-          const uint32_t dre = tmem + (u == 0 ? 0 : 2 * TN), dim = tmem + (u == 0 ? TN : 3 * TN);
-          const uint32_t acc = (ch == 0 && ks == 0 && u <= 1) ? 0u : 1u;  // first write of each accumulator
-          tc::mma_bf16(dre, are, bre, id_pos, acc);
-          tc::mma_bf16(dre, aim, bim, id_neg, 1u);
-          tc::mma_bf16(dim, are, bim, id_pos, acc);
-          tc::mma_bf16(dim, aim, bre, id_pos, 1u);
+  int issued = 0;  // copy thread: chunks whose copies were issued
+  if (warp == 4) {
+    if (lane == 0) {
+      int q = 0;
+      for (long long t = blockIdx.x; t < total && !*fail; t += gridDim.x) {
+        int z, x, y;
+        if (!tile_of(t, z, x, y)) continue;
+        const int n = mats[z].n;
+        const __nv_bfloat16* W = (const __nv_bfloat16*)mats[z].ws;
+        const __nv_bfloat16* Lsrc = W + (size_t)x * LU_OB_CHUNKS * 6 * TCU_ATILE;
+        const __nv_bfloat16* Usrc = W + (size_t)((n + TCU_M - 1) / TCU_M) * LU_OB_CHUNKS * 6 * TCU_ATILE +
+                                    (size_t)y * LU_OB_CHUNKS * 6 * S::BTILE;
+        for (int ch = 0; ch < LU_OB_CHUNKS; ++ch, ++q) {
+          const int st = q % NST;
+          if (q >= NST && !tc::mbar_wait(&empty[st], ((q / NST) - 1) & 1)) { *fail = 1; break; }
+          unsigned char* base = smem + (size_t)st * S::STAGE;
+          tc::mbar_expect_tx(&full[st], S::STAGE);
+          tc::bulk_g2s(base, Lsrc + (size_t)ch * 6 * TCU_ATILE, 6 * TCU_ATILE * 2, &full[st]);
+          tc::bulk_g2s(base + 6 * TCU_ATILE * 2, Usrc + (size_t)ch * 6 * S::BTILE, 6 * S::BTILE * 2, &full[st]);
+          issued = q + 1;
         }
-      }
-      if (ch + 1 < LU_OB_CHUNKS) {  // the next chunk overwrites the buffer these MMAs read
-        tc::commit(&mbar_mma);
-        if (!tc::mbar_wait(&mbar_mma, ch & 1)) { ok = false; break; }
       }
     }
-    if (!ok) s_ok = 0;
-    tc::commit(&mbar_done);  // arrives once every MMA issued above has completed
-  }
-  // while the MMAs run: fetch this thread's row of the first 32 output columns
-  const int i = i0 + warp * 32 + lane;
-  cf cv[32];
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t id_pos = tc::idesc_bf16_f32(TCU_M, TN, false);
+      const uint32_t id_neg = tc::idesc_bf16_f32(TCU_M, TN, true);
+      const uint64_t at = (uint64_t)(TCU_ATILE * 2 / 16), bt = (uint64_t)(S::BTILE * 2 / 16);  // 16-byte units
+      const int qa_[6] = {0, 0, 1, 0, 1, 2}, qb_[6] = {0, 1, 0, 2, 1, 0};
+      int q = 0, k = 0;
+      for (long long t = blockIdx.x; t < total && !*fail; t += gridDim.x) {
+        int z, x, y;
+        if (!tile_of(t, z, x, y)) continue;
+        const int set = k % NACC;
+        if (k >= NACC && !tc::mbar_wait(&tempty[set], ((k / NACC) - 1) & 1)) { *fail = 1; break; }
+        tc::fence_after();
+        // accumulator columns of the set: [0,TN) hh Re, [TN,2TN) hh Im, [2TN,3TN) corrections Re, [3TN,4TN) Im
+        const uint32_t d0 = tmem + (uint32_t)set * S::SET_COLS;
+        for (int ch = 0; ch < LU_OB_CHUNKS; ++ch, ++q) {
+          const int st = q % NST;
+          if (!tc::mbar_wait(&full[st], (q / NST) & 1)) { *fail = 1; break; }
+          tc::fence_after();
+          unsigned char* base = smem + (size_t)st * S::STAGE;
+          const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(base), 128, (LU_NB / 8) * 128);
+          const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(base + 6 * TCU_ATILE * 2), 128, (LU_NB / 8) * 128);
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    int j = j0 + c;
-    cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
-  }
-  const bool done = tc::mbar_wait(&mbar_done, 0);
-  tc::fence_after();
-  __syncthreads();
-  const bool ok = done && s_ok;
-  if (!ok && tid == 0 && err) atomicExch(err, 1);
-  if (ok) {
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+          for (int ks = 0; ks < LU_NB / 16; ++ks) {
+            const uint64_t kof = (uint64_t)(ks * 256 / 16);  // two core matrices along k
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+              const uint64_t are = a0 + qa_[u] * at + kof, aim = a0 + (3 + qa_[u]) * at + kof;
+              const uint64_t bre = b0 + qb_[u] * bt + kof, bim = b0 + (3 + qb_[u]) * bt + kof;
+              const uint32_t dre = d0 + (u == 0 ? 0 : 2 * TN), dim = d0 + (u == 0 ? TN : 3 * TN);
+              const uint32_t acc = (ch == 0 && ks == 0 && u <= 1) ? 0u : 1u;  // first write of each accumulator
+              tc::mma_bf16(dre, are, bre, id_pos, acc);
+              tc::mma_bf16(dre, aim, bim, id_neg, 1u);
+              tc::mma_bf16(dim, are, bim, id_pos, acc);
+              tc::mma_bf16(dim, aim, bre, id_pos, 1u);
+            }
+          }
+          tc::commit(&empty[st]);  // the stage is free once these MMAs have read it
+        }
+        if (*fail) break;
+        tc::commit(&tfull[set]);   // the tile's accumulators are complete
+        ++k;
+      }
+      tc::commit(&mdone);          // arrives once every MMA issued above has completed
+      if (!tc::mbar_wait(&mdone, 0)) *fail = 1;
+    }
+  } else {
+    // epilogue warps: warp w owns tensor-memory lanes (tile rows) 32w .. 32w + 31
+    int k = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+      int z, x, y;
+      if (!tile_of(t, z, x, y)) continue;
+      const int set = k % NACC;
+      const int n = mats[z].n;
+      cf* M = (cf*)mats[z].A;
+      const int i = start + x * TCU_M + warp * 32 + lane, j0 = start + y * TN;
+      cf cv[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {  // C of the first 32 columns while the MMAs run
+        const int j = j0 + c;
+        cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
+      }
+      if (!tc::mbar_wait(&tfull[set], (k / NACC) & 1)) { *fail = 1; break; }
+      tc::fence_after();
+      const uint32_t tw = tmem + (uint32_t)set * S::SET_COLS + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 32) {
-      if (c0 > 0) {
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        if (c0 > 0) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          int j = j0 + c0 + c;
-          cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
+          for (int c = 0; c < 32; ++c) {
+            const int j = j0 + c0 + c;
+            cv[c] = (i < n && j < n) ? M[(size_t)j * n + i] : CF(0.f);
+          }
+        }
+        float h[32], e[32];  // Re parts into cv first, then Im: two accumulator pairs live at a time
+        tc::tmem_ld32(tw + c0, h);
+        tc::tmem_ld32(tw + 2 * TN + c0, e);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) cv[c].x -= h[c] + e[c];
+        tc::tmem_ld32(tw + TN + c0, h);
+        tc::tmem_ld32(tw + 3 * TN + c0, e);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) cv[c].y -= h[c] + e[c];
+        if (i < n) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int j = j0 + c0 + c;
+            if (j < n) M[(size_t)j * n + i] = cv[c];
+          }
         }
       }
-      float hr[32], hi[32], cr[32], ci[32];
-      tc::tmem_ld32(tw + c0, hr);
-      tc::tmem_ld32(tw + TN + c0, hi);
-      tc::tmem_ld32(tw + 2 * TN + c0, cr);
-      tc::tmem_ld32(tw + 3 * TN + c0, ci);
-      if (i < n) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          int j = j0 + c0 + c;
-          if (j < n) M[(size_t)j * n + i] = CF(cv[c].x - (hr[c] + cr[c]), cv[c].y - (hi[c] + ci[c]));
-        }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[set]);
+      ++k;
+    }
+  }
+  __syncthreads();
+  if (*fail) {
+    if (tid == 0 && err) atomicExch(err, 1);
+    if (warp == 4 && lane == 0) {
+      // let the copies still in flight land before the CTA exits (bounded):
+      // the newest copy of each stage completes the newest phase of its barrier
+      for (int st = 0; st < NST; ++st) {
+        const int last = issued - 1 - ((issued - 1 - st) % NST + NST) % NST;  // newest chunk issued into st
+        if (last >= 0) tc::mbar_wait(&full[st], (last / NST) & 1, 1 << 20);
       }
     }
   }
   tc::fence_before();
   __syncthreads();
+  tc::fence_after();
   if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 // ---------------------------------------------------------------- driver
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  return sms;
+}
+
 // R3 of outer block K0 for the matrices 0..active-1 (those with n > K0 + LU_OB);
 // rest = nmax - K0 - LU_OB is the largest trailing size.
 template <int TN>
 static void tc_update_tn(const LuMat* d, int K0, int rest, int active, int* tc_err, cudaStream_t s) {
   const int nL = (rest + TCU_M - 1) / TCU_M, nU = (rest + TN - 1) / TN;
   tcu_split_kernel<TN><<<dim3(nL + nU, active), 256, 0, s>>>(d, K0, nL);
-  gemm_update_tc_kernel<TN><<<dim3(nL, nU, active), 128, TcuShape<TN>::SMEM_LAUNCH, s>>>(d, K0, tc_err);
+  const long long tiles = (long long)nL * nU * active;
+  const int grid = (int)std::min<long long>(tiles, sm_count());
+  gemm_update_tc_kernel<TN><<<grid, 192, TcuShape<TN>::SMEM, s>>>(d, K0, nL, nU, active, tc_err);
 }
 
 static void tc_update(int tn, const LuMat* d, int K0, int rest, int active, int* tc_err, cudaStream_t s) {
@@ -714,10 +808,9 @@ static void tc_update(int tn, const LuMat* d, int K0, int rest, int active, int*
 }
 
 static void tc_set_attributes() {
-  cudaFuncSetAttribute(gemm_update_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<32>::SMEM_LAUNCH);
-  cudaFuncSetAttribute(gemm_update_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<64>::SMEM_LAUNCH);
-  cudaFuncSetAttribute(gemm_update_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       TcuShape<128>::SMEM_LAUNCH);
+  cudaFuncSetAttribute(gemm_update_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<32>::SMEM);
+  cudaFuncSetAttribute(gemm_update_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<64>::SMEM);
+  cudaFuncSetAttribute(gemm_update_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcuShape<128>::SMEM);
 }
 
 __global__ void lu_info_zero_kernel(const LuMat* __restrict__ mats, int count) {
@@ -1048,12 +1141,16 @@ __device__ __forceinline__ cd to_cd(cd a) { return a; }
 // TF: factor type (cd, or cf for the mixed path's correction solves, which
 // then run in FP32 arithmetic on FP64 storage).  PHYS: right-hand sides and
 // solutions in physical unknowns (scaled by the sqrt weights here); otherwise
-// both are already in the weighted space.
+// both are already in the weighted space.  The SB x SB diagonal triangle of a
+// block is solved by warp 0 alone (warp-synchronous steps); the block
+// column's update of the other rows is a streaming product over all NT
+// threads, eight factor columns in flight per thread.
+template <int SGT> struct SolveShape { static constexpr int NT = SGT <= 4 ? 1024 : 256; };
+
 template <class TF, bool PHYS, int SGT>
-__global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict__ LU, const int* __restrict__ piv,
-                                                            int n, int M, const double* __restrict__ sw,
-                                                            const cd* __restrict__ rhs, cd* __restrict__ x,
-                                                            int nrhs) {
+__global__ void __launch_bounds__(SolveShape<SGT>::NT) solve_blocked_kernel(
+    const TF* __restrict__ LU, const int* __restrict__ piv, int n, int M, const double* __restrict__ sw,
+    const cd* __restrict__ rhs, cd* __restrict__ x, int nrhs) {
   __shared__ TF Ls[SB][SB + 1];
   __shared__ TF Xs[SB][SGT];
   extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation; then pv_s [n]
@@ -1064,7 +1161,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
   const int G = min(SGT, njobs_all - job0);
   const TF* L = LU + (size_t)m * n * n;
   const int* pv = piv + (size_t)m * n;
-  const int tid = threadIdx.x, T = blockDim.x;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
   cd* X[SGT];
   for (int g = 0; g < SGT; ++g) {
     int q, ri; bool neg;
@@ -1104,13 +1201,16 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
       Xs[r][g] = conv<TF>(X[g][kb + r]);
     }
     __syncthreads();
-    for (int c = 0; c < bs - 1; ++c) {
-      for (int t = tid; t < (bs - 1 - c) * G; t += T) {
-        int r = c + 1 + t % (bs - 1 - c), g = t / (bs - 1 - c);
-        Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
+    if (tid < 32) {
+      for (int c = 0; c < bs - 1; ++c) {
+        for (int t = lane; t < (bs - 1 - c) * G; t += 32) {
+          int r = c + 1 + t % (bs - 1 - c), g = t / (bs - 1 - c);
+          Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
+        }
+        __syncwarp();
       }
-      __syncthreads();
     }
+    __syncthreads();
     for (int t = tid; t < bs * G; t += T) {
       int r = t % bs, g = t / bs;
       X[g][kb + r] = to_cd(Xs[r][g]);
@@ -1119,6 +1219,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
       TF acc[SGT];
 #pragma unroll
       for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
+#pragma unroll 8
       for (int c = 0; c < bs; ++c) {
         TF l = L[(size_t)(kb + c) * n + r];
 #pragma unroll
@@ -1143,15 +1244,18 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
       Xs[r][g] = conv<TF>(X[g][kb + r]);
     }
     __syncthreads();
-    for (int c = bs - 1; c >= 0; --c) {
-      if (tid < G) Xs[c][tid] = Xs[c][tid] / Ls[c][c];
-      __syncthreads();
-      for (int t = tid; t < c * G; t += T) {
-        int r = t % c, g = t / c;
-        Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
+    if (tid < 32) {
+      for (int c = bs - 1; c >= 0; --c) {
+        if (lane < G) Xs[c][lane] = Xs[c][lane] / Ls[c][c];
+        __syncwarp();
+        for (int t = lane; t < c * G; t += 32) {
+          int r = t % c, g = t / c;
+          Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
+        }
+        __syncwarp();
       }
-      __syncthreads();
     }
+    __syncthreads();
     for (int t = tid; t < bs * G; t += T) {
       int r = t % bs, g = t / bs;
       X[g][kb + r] = to_cd(Xs[r][g]);
@@ -1160,6 +1264,7 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
       TF acc[SGT];
 #pragma unroll
       for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
+#pragma unroll 8
       for (int c = 0; c < bs; ++c) {
         TF u = L[(size_t)(kb + c) * n + r];
 #pragma unroll
@@ -1186,13 +1291,14 @@ __global__ void __launch_bounds__(256) solve_blocked_kernel(const TF* __restrict
 // it fewer times), else 8 when that leaves four, else 4 (more CTAs hide the
 // latency of the per-block triangle steps; measured on the cylinder's 65
 // modes x 32 vectors: 4 vectors 53 ms, 8 vectors 63 ms, 2 vectors 75 ms for
-// the three correction solves with residuals).
+// the three correction solves with residuals, with 256 threads per CTA).
 template <class TF, bool PHYS, int W>
 static void launch_solve_w(const TF* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
                            int smem, cudaStream_t s) {
   const int groups = (2 * nrhs + W - 1) / W;
   cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  solve_blocked_kernel<TF, PHYS, W><<<dim3(M + 1, groups), 256, smem, s>>>(LU, piv, n, M, sw, rhs, x, nrhs);
+  solve_blocked_kernel<TF, PHYS, W><<<dim3(M + 1, groups), SolveShape<W>::NT, smem, s>>>(LU, piv, n, M, sw, rhs, x,
+                                                                                          nrhs);
 }
 
 template <class TF, bool PHYS>
