@@ -85,9 +85,17 @@ HD cf operator*(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y *
 HD cf operator*(float s, cf a) { return cf{s * a.x, s * a.y}; }
 HD cf& operator+=(cf& a, cf b) { a.x += b.x; a.y += b.y; return a; }
 HD double norm2(cf a) { return (double)a.x * a.x + (double)a.y * a.y; }
+// Smith's scaled division in FP32: the complex64 kernels divide once per
+// column or step in every thread, and FP64 arithmetic is a small share of
+// this part's issue rate.
 HD cf operator/(cf a, cf b) {
-  cd q = cd{a.x, a.y} / cd{b.x, b.y};
-  return cf{(float)q.x, (float)q.y};
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    const float r = b.y / b.x, den = b.x + b.y * r;
+    return cf{(a.x + a.y * r) / den, (a.y - a.x * r) / den};
+  } else {
+    const float r = b.x / b.y, den = b.x * r + b.y;
+    return cf{(a.x * r + a.y) / den, (a.y * r - a.x) / den};
+  }
 }
 HD cf fma(cf a, cf b, cf c) {
   return cf{fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y))};

@@ -280,6 +280,201 @@ static bool launch_panel_cluster(const LuMat* mats, int rows, int k0, int batch,
   return true;
 }
 
+// ---------------------------------------------------------------- register panel
+// Complex64 panel with the rows in registers: CTA q of a cluster of C owns
+// rows k0 + q R .. k0 + (q+1) R - 1 (R = PREG_THREADS x PREG_RPT), thread t
+// rows t + PREG_THREADS s (s < PREG_RPT), all LU_NB columns of each (the
+// column loop is unrolled, so every register index is static).  Per column:
+// local argmax (warp shuffles, then across the CTA's warps); the candidate
+// row is staged in shared memory by its owner (and row c by its owner in CTA
+// 0, which holds the panel's first R > LU_NB rows); every CTA's candidate
+// (value, index, row) and row c reach every CTA through distributed shared
+// memory (slots double-buffered by column parity); one cluster barrier; then
+// each thread applies the interchange and the rank-1 update to its own rows.
+// Same pivot rule and arithmetic as panel_cluster_kernel.
+#define PREG_THREADS 256
+#define PREG_RPT 2
+#define PREG_R (PREG_THREADS * PREG_RPT)
+
+struct PregShared {
+  float cand_v[2][8];
+  int cand_i[2][8];
+  cf cand_row[2][8][LU_NB];  // each CTA's candidate row
+  cf top_row[2][LU_NB];      // row c
+  cf loc_row[LU_NB], loc_top[LU_NB];
+  float red_v[PREG_THREADS / 32];
+  int red_i[PREG_THREADS / 32];
+};
+struct PregCtx {
+  int k0, n, nbk, C, q, tid, lane, wid;
+  int* pv;
+  int* info;
+};
+
+// Column jj of the panel.  The column loop is not unrolled (a fully unrolled
+// panel overflows the instruction cache); every register access uses a
+// compile-time column index, the column jj itself being picked out by a
+// select over the 32 columns and the rank-1 update predicated on j > jj.
+__device__ __forceinline__ void preg_column(int jj, const cg::cluster_group& cl, PregShared& sh, const PregCtx& x,
+                                            cf (&a)[PREG_RPT][LU_NB], const int (&grow)[PREG_RPT]) {
+  const int c = x.k0 + jj, buf = jj & 1, n = x.n;
+  cf colv[PREG_RPT];
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s) {
+    colv[s] = a[s][0];
+#pragma unroll
+    for (int j = 1; j < LU_NB; ++j)
+      if (j == jj) colv[s] = a[s][j];
+  }
+  float best = -1.f;
+  int bi = n;
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s)
+    if (grow[s] >= c && grow[s] < n) argmax_merge(best, bi, Pivot<cf>::measure(colv[s]), grow[s]);
+  for (int o = 16; o > 0; o >>= 1) {
+    float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    argmax_merge(best, bi, v2, i2);
+  }
+  if (x.lane == 0) { sh.red_v[x.wid] = best; sh.red_i[x.wid] = bi; }
+  __syncthreads();
+  best = -1.f;
+  bi = n;
+#pragma unroll
+  for (int w = 0; w < PREG_THREADS / 32; ++w) argmax_merge(best, bi, sh.red_v[w], sh.red_i[w]);
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s) {
+    if (grow[s] == bi) {
+#pragma unroll
+      for (int j = 0; j < LU_NB; ++j) sh.loc_row[j] = a[s][j];
+    }
+    if (x.q == 0 && grow[s] == c) {
+#pragma unroll
+      for (int j = 0; j < LU_NB; ++j) sh.loc_top[j] = a[s][j];
+    }
+  }
+  __syncthreads();
+  if (x.tid < 32 * x.C) {
+    const int j = x.tid & 31, u = x.tid >> 5;
+    if (j < x.nbk) {
+      if (bi < n) cl.map_shared_rank(&sh.cand_row[buf][x.q][0], u)[j] = sh.loc_row[j];
+      if (x.q == 0) cl.map_shared_rank(&sh.top_row[buf][0], u)[j] = sh.loc_top[j];
+    }
+    if (j == 0) {
+      cl.map_shared_rank(&sh.cand_v[buf][0], u)[x.q] = best;
+      cl.map_shared_rank(&sh.cand_i[buf][0], u)[x.q] = bi;
+    }
+  }
+  cl.sync();
+  float bv = -1.f;
+  int p = n, win = 0;
+  for (int u = 0; u < x.C; ++u) {
+    const float v2 = sh.cand_v[buf][u];
+    const int i2 = sh.cand_i[buf][u];
+    if (v2 > bv || (v2 == bv && i2 < p)) { bv = v2; p = i2; win = u; }
+  }
+  const bool ok = bv > 0.f;
+  if (x.q == 0 && x.tid == 0) {
+    x.pv[c] = ok ? p : c;
+    if (!ok && x.info[0] == 0) x.info[0] = c + 1;
+  }
+  if (!ok) return;
+  const cf* prow = sh.cand_row[buf][win];
+  const cf* trow = sh.top_row[buf];
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s) {
+    if (grow[s] == c) {  // row c takes the pivot row
+#pragma unroll
+      for (int j = 0; j < LU_NB; ++j) a[s][j] = prow[j];
+    } else if (grow[s] == p) {  // the pivot's row takes row c
+#pragma unroll
+      for (int j = 0; j < LU_NB; ++j) a[s][j] = trow[j];
+      colv[s] = trow[jj];
+    }
+  }
+  const cf inv = cone<cf>() / prow[jj];
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s) {
+    if (grow[s] > c && grow[s] < n) {
+      const cf l = colv[s] * inv;
+#pragma unroll
+      for (int j = 0; j < LU_NB; ++j) {
+        if (j > jj) a[s][j] = a[s][j] - l * prow[j];
+        else if (j == jj) a[s][j] = l;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PREG_THREADS, 1) panel_reg_kernel(const LuMat* __restrict__ mats, int k0) {
+  cg::cluster_group cl = cg::this_cluster();
+  const LuMat mat = mats[blockIdx.y];  // the whole cluster works on one matrix
+  const int n = mat.n;
+  if (k0 >= n) return;                 // every CTA of the cluster, before any cluster barrier
+  __shared__ PregShared sh;
+  PregCtx x;
+  x.k0 = k0;
+  x.n = n;
+  x.nbk = min(LU_NB, n - k0);
+  x.C = (int)cl.num_blocks();
+  x.q = (int)cl.block_rank();
+  x.tid = threadIdx.x;
+  x.lane = threadIdx.x & 31;
+  x.wid = threadIdx.x >> 5;
+  x.pv = mat.piv;
+  x.info = mat.info;
+  cf* M = (cf*)mat.A;
+  const int row0 = k0 + x.q * PREG_R;
+  int grow[PREG_RPT];
+  cf a[PREG_RPT][LU_NB];
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s) {
+    grow[s] = row0 + x.tid + PREG_THREADS * s;
+#pragma unroll
+    for (int j = 0; j < LU_NB; ++j)
+      a[s][j] = (grow[s] < n && j < x.nbk) ? M[(size_t)(k0 + j) * n + grow[s]] : CF(0.f);
+  }
+#pragma unroll 1
+  for (int jj = 0; jj < x.nbk; ++jj) preg_column(jj, cl, sh, x, a, grow);
+#pragma unroll
+  for (int s = 0; s < PREG_RPT; ++s)
+    if (grow[s] < n) {
+#pragma unroll
+      for (int j = 0; j < LU_NB; ++j)
+        if (j < x.nbk) M[(size_t)(k0 + j) * n + grow[s]] = a[s][j];
+    }
+  cl.sync();  // no CTA leaves while a peer could still address its shared memory
+}
+
+// Cluster of C = ceil(rows / PREG_R) <= 8 CTAs; false when the panel is taller
+// or no such cluster can be resident.
+static bool launch_panel_reg(const LuMat* mats, int rows, int k0, int batch, cudaStream_t s) {
+  const int C = (rows + PREG_R - 1) / PREG_R;
+  if (C < 1 || C > 8) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, batch);
+  cfg.blockDim = dim3(PREG_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, panel_reg_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaLaunchKernelEx(&cfg, panel_reg_kernel, mats, k0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- swaps
 // The nbk interchanges of a block column compose to a permutation of at most
 // 2 nbk rows: the block's own rows (slots 0..nbk-1) and the distinct targets
@@ -569,18 +764,30 @@ __global__ void __launch_bounds__(256) tcu_split_kernel(const LuMat* __restrict_
   if (rest <= 0) return;
   const cf* M = (const cf*)mat.A;
   __nv_bfloat16* W = (__nv_bfloat16*)mat.ws;
-  __nv_bfloat16 pr[3], pi[3];
+  // thread item: one row (of L) or column (of U) and 8 consecutive k, written
+  // as one 16-byte core-matrix row per piece
+  auto put = [&](__nv_bfloat16* d, int stride, const cf* v) {
+    __align__(16) __nv_bfloat16 pc[6][8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      __nv_bfloat16 pr[3], pi[3];
+      split3(v[c].x, pr); split3(v[c].y, pi);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) { pc[q][c] = pr[q]; pc[3 + q][c] = pi[q]; }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) *(uint4*)(d + (size_t)q * stride) = *(const uint4*)pc[q];
+  };
   if ((int)blockIdx.x < nL) {
     if ((int)blockIdx.x * TCU_M >= rest) return;
     const int r0 = start + blockIdx.x * TCU_M;
     __nv_bfloat16* dst = W + (size_t)blockIdx.x * LU_OB_CHUNKS * 6 * TCU_ATILE;
-    for (int t = threadIdx.x; t < TCU_M * LU_OB; t += 256) {
-      const int r = t % TCU_M, kb = t / TCU_M, ch = kb / LU_NB, k = kb % LU_NB;
-      const cf v = (r0 + r < n) ? M[(size_t)(K0 + kb) * n + r0 + r] : CF(0.f);
-      split3(v.x, pr); split3(v.y, pi);
-      __nv_bfloat16* d = dst + (size_t)ch * 6 * TCU_ATILE + tcu_off(r, k);
+    for (int t = threadIdx.x; t < TCU_M * (LU_OB / 8); t += 256) {
+      const int r = t % TCU_M, kb0 = (t / TCU_M) * 8, ch = kb0 / LU_NB, k0 = kb0 % LU_NB;
+      cf v[8];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) { d[q * TCU_ATILE] = pr[q]; d[(3 + q) * TCU_ATILE] = pi[q]; }
+      for (int c = 0; c < 8; ++c) v[c] = (r0 + r < n) ? M[(size_t)(K0 + kb0 + c) * n + r0 + r] : CF(0.f);
+      put(dst + (size_t)ch * 6 * TCU_ATILE + tcu_off(r, k0), TCU_ATILE, v);
     }
   } else {
     const int y = blockIdx.x - nL;
@@ -588,13 +795,12 @@ __global__ void __launch_bounds__(256) tcu_split_kernel(const LuMat* __restrict_
     const int c0 = start + y * TN;
     __nv_bfloat16* dst = W + (size_t)((n + TCU_M - 1) / TCU_M) * LU_OB_CHUNKS * 6 * TCU_ATILE +
                          (size_t)y * LU_OB_CHUNKS * 6 * S::BTILE;
-    for (int t = threadIdx.x; t < TN * LU_OB; t += 256) {
-      const int kb = t % LU_OB, j = t / LU_OB, ch = kb / LU_NB, k = kb % LU_NB;
-      const cf v = (c0 + j < n) ? M[(size_t)(c0 + j) * n + K0 + kb] : CF(0.f);
-      split3(v.x, pr); split3(v.y, pi);
-      __nv_bfloat16* d = dst + (size_t)ch * 6 * S::BTILE + tcu_off(j, k);
+    for (int t = threadIdx.x; t < TN * (LU_OB / 8); t += 256) {
+      const int kb0 = (t % (LU_OB / 8)) * 8, j = t / (LU_OB / 8), ch = kb0 / LU_NB, k0 = kb0 % LU_NB;
+      cf v[8];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) { d[q * S::BTILE] = pr[q]; d[(3 + q) * S::BTILE] = pi[q]; }
+      for (int c = 0; c < 8; ++c) v[c] = (c0 + j < n) ? M[(size_t)(c0 + j) * n + K0 + kb0 + c] : CF(0.f);
+      put(dst + (size_t)ch * 6 * S::BTILE + tcu_off(j, k0), S::BTILE, v);
     }
   }
 }
@@ -985,7 +1191,9 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
   auto panel_step = [&](int k0, int K0, int mode) -> int {
     while (active > 0 && it[active - 1].n <= k0) --active;
     const int nbk = std::min(LU_NB, nmax - k0);
-    if (!launch_panel_cluster<T>(d, nmax - k0, k0, active, ls)) panel_kernel<T><<<active, 1024, 0, ls>>>(d, k0);
+    bool done = false;
+    if constexpr (c64) done = launch_panel_reg(d, nmax - k0, k0, active, ls);
+    if (!done && !launch_panel_cluster<T>(d, nmax - k0, k0, active, ls)) panel_kernel<T><<<active, 1024, 0, ls>>>(d, k0);
     ++launches;
     const int hi = mode == 1 ? std::min(K0 + LU_OB, nmax) : nmax;
     if (hi - nbk > 0) {
@@ -1141,19 +1349,125 @@ __device__ __forceinline__ cd to_cd(cd a) { return a; }
 // TF: factor type (cd, or cf for the mixed path's correction solves, which
 // then run in FP32 arithmetic on FP64 storage).  PHYS: right-hand sides and
 // solutions in physical unknowns (scaled by the sqrt weights here); otherwise
-// both are already in the weighted space.  The SB x SB diagonal triangle of a
-// block is solved by warp 0 alone (warp-synchronous steps); the block
-// column's update of the other rows is a streaming product over all NT
-// threads, eight factor columns in flight per thread.
-template <int SGT> struct SolveShape { static constexpr int NT = SGT <= 4 ? 1024 : 256; };
+// both are already in the weighted space.
+//
+// Schedule of one pass (forward shown; the backward pass mirrors it): with
+// block i solved (its x in Xs[i & 1]), threads 0..63 update the rows of block
+// i+1 with block i's factor column, then warp 0 solves block i+1's diagonal
+// triangle in registers (rows lane and lane + 32, broadcast by shuffles),
+// while the other threads load the diagonal block i+2 into shared memory and
+// update every row beyond block i+1 (a streaming product, eight factor
+// columns in flight per thread): the triangle is off the critical path.
+template <int SGT> struct SolveShape { static constexpr int NT = SGT <= 4 ? 512 : 256; };
+
+template <class T> __device__ __forceinline__ T shfl_c(T v, int src) {
+  T r;
+  r.x = __shfl_sync(0xffffffffu, v.x, src);
+  r.y = __shfl_sync(0xffffffffu, v.y, src);
+  return r;
+}
+
+// Warp 0: the diagonal triangle of the block at rows kb.. (bs rows) for all
+// G jobs, JC at a time (2 under the 64-register cap of 1024-thread CTAs);
+// unit lower (FWD) or upper with its diagonal.  The solution goes to Xo
+// (shared, for the block's column product) and to X.
+template <class TF, int SGT, bool FWD, int JC = (SolveShape<SGT>::NT >= 1024 ? 2 : 4)>
+__device__ __forceinline__ void warp_triangle(const TF (*Lb)[SB + 1], TF (*Xo)[SGT], cd* const* X, int kb, int bs,
+                                              int G, int lane) {
+  for (int g0 = 0; g0 < G; g0 += JC) {
+    TF xv[2][JC];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int r = lane + 32 * s;
+#pragma unroll
+      for (int gg = 0; gg < JC; ++gg)
+        xv[s][gg] = (r < bs && g0 + gg < G) ? conv<TF>(X[g0 + gg][kb + r]) : czero<TF>();
+    }
+    if (FWD) {
+      for (int c = 0; c < bs - 1; ++c) {
+        const int owner = c & 31;
+        TF xc[JC];
+#pragma unroll
+        for (int gg = 0; gg < JC; ++gg) xc[gg] = shfl_c(c < 32 ? xv[0][gg] : xv[1][gg], owner);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int r = lane + 32 * s;
+          if (r > c && r < bs) {
+            const TF l = Lb[r][c];
+#pragma unroll
+            for (int gg = 0; gg < JC; ++gg) xv[s][gg] = xv[s][gg] - l * xc[gg];
+          }
+        }
+      }
+    } else {
+      for (int c = bs - 1; c >= 0; --c) {
+        const int owner = c & 31, slot = c >> 5;
+        const TF d = Lb[c][c];
+        TF xc[JC];
+#pragma unroll
+        for (int gg = 0; gg < JC; ++gg) xc[gg] = shfl_c(slot ? xv[1][gg] : xv[0][gg], owner) / d;
+        if (lane == owner) {
+#pragma unroll
+          for (int gg = 0; gg < JC; ++gg) {
+            if (slot) xv[1][gg] = xc[gg];
+            else xv[0][gg] = xc[gg];
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int r = lane + 32 * s;
+          if (r < c) {
+            const TF u = Lb[r][c];
+#pragma unroll
+            for (int gg = 0; gg < JC; ++gg) xv[s][gg] = xv[s][gg] - u * xc[gg];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int r = lane + 32 * s;
+#pragma unroll
+      for (int gg = 0; gg < JC; ++gg)
+        if (r < bs && g0 + gg < G) {
+          Xo[r][g0 + gg] = xv[s][gg];
+          X[g0 + gg][kb + r] = to_cd(xv[s][gg]);
+        }
+    }
+  }
+}
+
+// x_r -= sum_c F[r, kb + c] x_c over the bs columns of one block (x_c in Xb).
+template <class TF, int SGT>
+__device__ __forceinline__ void block_row_update(const TF* __restrict__ F, int n, int r, int kb, int bs,
+                                                 const TF (*Xb)[SGT], cd* const* X, int G) {
+  TF acc[SGT];
+#pragma unroll
+  for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
+#pragma unroll 8
+  for (int c = 0; c < bs; ++c) {
+    const TF l = F[(size_t)(kb + c) * n + r];
+#pragma unroll
+    for (int g = 0; g < SGT; ++g) acc[g] = fma(l, Xb[c][g], acc[g]);
+  }
+#pragma unroll
+  for (int g = 0; g < SGT; ++g)
+    if (g < G) X[g][r] = X[g][r] - to_cd(acc[g]);
+}
+
+template <class TF, int SGT>
+__host__ __device__ constexpr size_t solve_smem_fixed() {
+  return 2 * (size_t)SB * (SB + 1) * sizeof(TF) + 2 * (size_t)SB * SGT * sizeof(TF);
+}
 
 template <class TF, bool PHYS, int SGT>
 __global__ void __launch_bounds__(SolveShape<SGT>::NT) solve_blocked_kernel(
     const TF* __restrict__ LU, const int* __restrict__ piv, int n, int M, const double* __restrict__ sw,
     const cd* __restrict__ rhs, cd* __restrict__ x, int nrhs) {
-  __shared__ TF Ls[SB][SB + 1];
-  __shared__ TF Xs[SB][SGT];
-  extern __shared__ int perm[];  // [n]: row interchanges composed into one permutation; then pv_s [n]
+  extern __shared__ __align__(16) unsigned char sraw[];
+  TF (*Ls)[SB][SB + 1] = (TF (*)[SB][SB + 1])sraw;                                   // [2] diagonal blocks
+  TF (*Xs)[SB][SGT] = (TF (*)[SB][SGT])(sraw + 2 * (size_t)SB * (SB + 1) * sizeof(TF));  // [2] block solutions
+  int* perm = (int*)(sraw + solve_smem_fixed<TF, SGT>());  // [n] composed interchanges, then pv_s [n]
   const int m = blockIdx.x;
   const int job0 = blockIdx.y * SGT;
   const int njobs_all = (m == 0) ? nrhs : 2 * nrhs;
@@ -1188,91 +1502,55 @@ __global__ void __launch_bounds__(SolveShape<SGT>::NT) solve_blocked_kernel(
     double sg = (neg && ((src & 3) == 0 || (src & 3) == 3)) ? -1.0 : 1.0;
     X[g][r] = ((PHYS ? sw[src >> 2] : 1.0) * sg) * rhs[((size_t)q * nrhs + ri) * n + src];
   }
-  __syncthreads();
+  const int nblk = (n + SB - 1) / SB;
+  auto load_diag = [&](int bi, int t0, int step) {
+    const int kb = bi * SB, bs = min(SB, n - kb);
+    TF (*D)[SB + 1] = Ls[bi & 1];
+    for (int t = t0; t < bs * bs; t += step) {
+      const int r = t % bs, c = t / bs;
+      D[r][c] = L[(size_t)(kb + c) * n + kb + r];
+    }
+  };
   // forward: L unit lower
-  for (int kb = 0; kb < n; kb += SB) {
-    const int bs = min(SB, n - kb);
-    for (int t = tid; t < bs * bs; t += T) {
-      int r = t % bs, c = t / bs;
-      Ls[r][c] = L[(size_t)(kb + c) * n + kb + r];
-    }
-    for (int t = tid; t < bs * G; t += T) {
-      int r = t % bs, g = t / bs;
-      Xs[r][g] = conv<TF>(X[g][kb + r]);
-    }
-    __syncthreads();
-    if (tid < 32) {
-      for (int c = 0; c < bs - 1; ++c) {
-        for (int t = lane; t < (bs - 1 - c) * G; t += 32) {
-          int r = c + 1 + t % (bs - 1 - c), g = t / (bs - 1 - c);
-          Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
-        }
-        __syncwarp();
+  load_diag(0, tid, T);
+  if (nblk > 1) load_diag(1, tid, T);
+  __syncthreads();
+  if (tid < 32) warp_triangle<TF, SGT, true>(Ls[0], Xs[0], X, 0, min(SB, n), G, lane);
+  __syncthreads();
+  for (int i = 0; i < nblk; ++i) {
+    const int kb = i * SB, bs = min(SB, n - kb), b = i & 1;
+    const int kn = kb + SB, bsn = min(SB, n - kn);
+    if (tid < 64) {
+      if (bsn > 0) {
+        if (tid < bsn) block_row_update<TF, SGT>(L, n, kn + tid, kb, bs, Xs[b], X, G);
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+        if (tid < 32) warp_triangle<TF, SGT, true>(Ls[b ^ 1], Xs[b ^ 1], X, kn, bsn, G, lane);
       }
-    }
-    __syncthreads();
-    for (int t = tid; t < bs * G; t += T) {
-      int r = t % bs, g = t / bs;
-      X[g][kb + r] = to_cd(Xs[r][g]);
-    }
-    for (int r = kb + bs + tid; r < n; r += T) {
-      TF acc[SGT];
-#pragma unroll
-      for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
-#pragma unroll 8
-      for (int c = 0; c < bs; ++c) {
-        TF l = L[(size_t)(kb + c) * n + r];
-#pragma unroll
-        for (int g = 0; g < SGT; ++g) acc[g] = fma(l, Xs[c][g], acc[g]);
-      }
-#pragma unroll
-      for (int g = 0; g < SGT; ++g)
-        if (g < G) X[g][r] = X[g][r] - to_cd(acc[g]);
+    } else {
+      if (i + 2 < nblk) load_diag(i + 2, tid - 64, T - 64);
+      for (int r = kn + SB + (tid - 64); r < n; r += T - 64) block_row_update<TF, SGT>(L, n, r, kb, bs, Xs[b], X, G);
     }
     __syncthreads();
   }
   // backward: U upper, non-unit diagonal
-  const int nblk = (n + SB - 1) / SB;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int kb = bi * SB, bs = min(SB, n - kb);
-    for (int t = tid; t < bs * bs; t += T) {
-      int r = t % bs, c = t / bs;
-      Ls[r][c] = L[(size_t)(kb + c) * n + kb + r];
-    }
-    for (int t = tid; t < bs * G; t += T) {
-      int r = t % bs, g = t / bs;
-      Xs[r][g] = conv<TF>(X[g][kb + r]);
-    }
-    __syncthreads();
-    if (tid < 32) {
-      for (int c = bs - 1; c >= 0; --c) {
-        if (lane < G) Xs[c][lane] = Xs[c][lane] / Ls[c][c];
-        __syncwarp();
-        for (int t = lane; t < c * G; t += 32) {
-          int r = t % c, g = t / c;
-          Xs[r][g] = Xs[r][g] - Ls[r][c] * Xs[c][g];
-        }
-        __syncwarp();
+  const int last = nblk - 1;
+  load_diag(last, tid, T);
+  if (last >= 1) load_diag(last - 1, tid, T);
+  __syncthreads();
+  if (tid < 32) warp_triangle<TF, SGT, false>(Ls[last & 1], Xs[last & 1], X, last * SB, n - last * SB, G, lane);
+  __syncthreads();
+  for (int i = last; i >= 0; --i) {
+    const int kb = i * SB, bs = min(SB, n - kb), b = i & 1;
+    const int kp = kb - SB;  // the block above (full size)
+    if (tid < 64) {
+      if (i >= 1) {
+        block_row_update<TF, SGT>(L, n, kp + tid, kb, bs, Xs[b], X, G);
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+        if (tid < 32) warp_triangle<TF, SGT, false>(Ls[b ^ 1], Xs[b ^ 1], X, kp, SB, G, lane);
       }
-    }
-    __syncthreads();
-    for (int t = tid; t < bs * G; t += T) {
-      int r = t % bs, g = t / bs;
-      X[g][kb + r] = to_cd(Xs[r][g]);
-    }
-    for (int r = tid; r < kb; r += T) {
-      TF acc[SGT];
-#pragma unroll
-      for (int g = 0; g < SGT; ++g) acc[g] = czero<TF>();
-#pragma unroll 8
-      for (int c = 0; c < bs; ++c) {
-        TF u = L[(size_t)(kb + c) * n + r];
-#pragma unroll
-        for (int g = 0; g < SGT; ++g) acc[g] = fma(u, Xs[c][g], acc[g]);
-      }
-#pragma unroll
-      for (int g = 0; g < SGT; ++g)
-        if (g < G) X[g][r] = X[g][r] - to_cd(acc[g]);
+    } else {
+      if (i - 2 >= 0) load_diag(i - 2, tid - 64, T - 64);
+      for (int r = tid - 64; r < kp; r += T - 64) block_row_update<TF, SGT>(L, n, r, kb, bs, Xs[b], X, G);
     }
     __syncthreads();
   }
@@ -1294,8 +1572,9 @@ __global__ void __launch_bounds__(SolveShape<SGT>::NT) solve_blocked_kernel(
 // the three correction solves with residuals, with 256 threads per CTA).
 template <class TF, bool PHYS, int W>
 static void launch_solve_w(const TF* LU, const int* piv, int n, int M, const double* sw, const cd* rhs, cd* x, int nrhs,
-                           int smem, cudaStream_t s) {
+                           int smem_perm, cudaStream_t s) {
   const int groups = (2 * nrhs + W - 1) / W;
+  const int smem = (int)solve_smem_fixed<TF, W>() + smem_perm;
   cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   solve_blocked_kernel<TF, PHYS, W><<<dim3(M + 1, groups), SolveShape<W>::NT, smem, s>>>(LU, piv, n, M, sw, rhs, x,
                                                                                           nrhs);

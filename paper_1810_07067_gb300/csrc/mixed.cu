@@ -23,6 +23,11 @@ __device__ __forceinline__ double pow2_above_twice(double mx) {
   return ldexp(1.0, e + 1);  // mx / scale < 1/2
 }
 
+// The element loop keeps off the FP64 pipe (a small share of the SM on this
+// part): the largest |Re a|, |Im a| is taken on the IEEE bit patterns (for
+// non-negative doubles their order as unsigned integers is the numeric
+// order), and the row sums of |a| run in FP32 per thread (the stopping test's
+// norm needs no more), joined in FP64 across the block.
 __global__ void __launch_bounds__(256) row_pass_kernel(const cd* __restrict__ A, int n, int npad, cf* __restrict__ A32,
                                                        double* __restrict__ normA, double* __restrict__ rowscale) {
   const int b = blockIdx.y;
@@ -30,28 +35,33 @@ __global__ void __launch_bounds__(256) row_pass_kernel(const cd* __restrict__ A,
   const int i = blockIdx.x * 32 + lane;
   const cd* Mx = A + (size_t)b * n * n;
   cf* My = A32 ? A32 + (size_t)b * n * n : nullptr;  // null: norms only
-  // |a| in FP32 (a norm for the stopping test needs no more), summed in FP64
-  double s = 0.0, mx = 0.0;
+  float s = 0.f;
+  unsigned long long mxb = 0ull;  // bits of the largest |Re a|, |Im a|
   if (i < n) {
 #pragma unroll 4
     for (int j = slice; j < n; j += 8) {
       const cd v = Mx[(size_t)j * n + i];
-      if (My) My[(size_t)j * n + i] = to_cf(v);
-      const float fx = fabsf((float)v.x), fy = fabsf((float)v.y);
+      const cf w = to_cf(v);
+      if (My) My[(size_t)j * n + i] = w;
+      const float fx = fabsf(w.x), fy = fabsf(w.y);
       const float hi = fmaxf(fx, fy), lo = fminf(fx, fy);
       const float q = (hi > 0.f) ? lo / hi : 0.f;
-      s += (double)(hi * sqrtf(1.f + q * q));
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      s += hi * sqrtf(1.f + q * q);
+      const unsigned long long bx = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long by = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull;
+      mxb = max(mxb, max(bx, by));
     }
   }
-  __shared__ double part[8][32], pmax[8][32];
-  part[slice][lane] = s;
-  pmax[slice][lane] = mx;
+  __shared__ double part[8][32];
+  __shared__ unsigned long long pmax[8][32];
+  part[slice][lane] = (double)s;
+  pmax[slice][lane] = mxb;
   __syncthreads();
   if (slice == 0) {
-    double t = 0.0, m2 = 0.0;
-    for (int q = 0; q < 8; ++q) { t += part[q][lane]; m2 = fmax(m2, pmax[q][lane]); }
-    if (rowscale && i < npad) rowscale[(size_t)b * npad + i] = pow2_above_twice(m2);
+    double t = 0.0;
+    unsigned long long m2 = 0ull;
+    for (int q = 0; q < 8; ++q) { t += part[q][lane]; m2 = max(m2, pmax[q][lane]); }
+    if (rowscale && i < npad) rowscale[(size_t)b * npad + i] = pow2_above_twice(__longlong_as_double((long long)m2));
     for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
     if (lane == 0) atomic_max_pos(normA + b, t);
   }
