@@ -1,4 +1,5 @@
 // Incident data and far fields (Section 6).
+#include "smem.cuh"
 #include "fields.cuh"
 
 // One CTA per (node, wave): samples of the tangential traces on the node's
@@ -109,7 +110,7 @@ __global__ void rhs_samples_kernel(FieldGeom g, int M, cd sE, cd sH, const cd* _
 void launch_rhs_samples(const FieldGeom& g, int M, cd sE, cd sH, const cd* EH, int nrhs, int n_theta, cd* rhs,
                         cudaStream_t s) {
   int smem = n_theta * 5 * (int)sizeof(cd);
-  cudaFuncSetAttribute(rhs_samples_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(rhs_samples_kernel);
   rhs_samples_kernel<<<dim3(g.N, nrhs), 256, smem, s>>>(g, M, sE, sH, EH, nrhs, n_theta, rhs);
 }
 
@@ -117,7 +118,7 @@ void launch_rhs_planewave(const FieldGeom& g, int M, cd k0, double omega, cd mu0
                           const double* dirs_dev, const double* pols_dev, int nrhs, int n_theta, cd* rhs,
                           cudaStream_t s) {
   int smem = n_theta * 5 * (int)sizeof(cd);
-  cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(rhs_kernel);
   rhs_kernel<<<dim3(g.N, nrhs), 256, smem, s>>>(g, M, k0, omega, mu0, sE, sH, dirs_dev, pols_dev, nrhs, n_theta,
                                                  rhs);
 }
@@ -424,12 +425,12 @@ __global__ void ffgrid_synth_kernel(int M, int n_polar, int n_azim, const cd* __
 void launch_far_field_grid(const FieldGeom& g, int M, cd k0, double omega, cd eps0, const cd* x, int nrhs,
                            int n_polar, int n_azim, int n_alpha, cd* coef, cd* F, cd* E, cudaStream_t s) {
   const int smem1 = 2 * n_alpha * (int)sizeof(cd);
-  cudaFuncSetAttribute(ffgrid_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
+  smem_optin(ffgrid_coef_kernel);
   ffgrid_coef_kernel<<<dim3(n_polar, g.N), 256, smem1, s>>>(g, M, k0, n_polar, n_alpha, coef);
   ffgrid_mode_kernel<<<dim3(n_polar, 2 * M + 1, nrhs), 128, 0, s>>>(g, M, k0, omega, eps0, n_polar, coef, x, nrhs,
                                                                     F);
   const int smem3 = (3 * (2 * M + 1) + n_azim) * (int)sizeof(cd);
-  cudaFuncSetAttribute(ffgrid_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
+  smem_optin(ffgrid_synth_kernel);
   ffgrid_synth_kernel<<<dim3(n_polar, nrhs), 256, smem3, s>>>(M, n_polar, n_azim, F, nrhs, E);
 }
 

@@ -24,7 +24,9 @@
 // above the requested accuracy (zeta^{nphi-M-1} > eps, zeta = chi - sqrt(chi^2-1)).
 #include <cuda_runtime.h>
 #include <cstdio>
+#include "smem.cuh"
 #include "green.cuh"
+#include "digits.cuh"
 
 __constant__ SeriesTables c_tab;
 
@@ -118,7 +120,7 @@ __global__ void legendre_kernel(const double* __restrict__ pairs, long long n, i
 void launch_legendre(const double* pairs, long long n, int Mq, int Ms, double* leg, cudaStream_t s) {
   if (n <= 0) return;
   const int tpb = 128, nr = legendre_table_entries(Mq);
-  cudaFuncSetAttribute(legendre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, nr * 8);
+  smem_optin(legendre_kernel);
   legendre_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, nr * 8, s>>>(pairs, n, Mq, Ms, leg, nr);
 }
 
@@ -189,16 +191,16 @@ __device__ PairGrid pair_grid(const GreenParams& gp, double rt, double dr0, doub
   return PairGrid{8 * q, mc, ladC + offc, ladS + offs};
 }
 
-__device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
+// The weighted samples W.smp[f][j] = w_j F_f(phi_j), j = 0..nl/2 (w = 1/2 at
+// both ends), of one pair on its grid g: the first half of warp_pair_spectra.
+__device__ void warp_pair_samples(const GreenParams& gp, double rt, double dr0, double zd,
                                   long long sid, const double* __restrict__ leg, long long n_split,
-                                  const double* __restrict__ cosT, const double* __restrict__ s2T,
-                                  const WarpSmem& W, int lane, const PairGrid& g) {
-  const int Ms = gp.Ms, Mq = gp.Mq, mask = gp.nphi - 1;
+                                  const double* __restrict__ cosT, const WarpSmem& W, int lane,
+                                  const PairGrid& g) {
+  const int Mq = gp.Mq, mask = gp.nphi - 1;
   const int nl = g.nl;  // local grid size; sample j sits at entry j of its tables
-  const double* __restrict__ cosL = g.cosL;
   const double* __restrict__ s2L = g.s2L;
-  const int T = nl, tstride = 1;
-  const int Me = g.mc + 1;  // modes 0..mc computed, the rest zero
+  const int tstride = 1;
   const int H = nl / 2 + 1, Q = nl / 4;  // samples on [0, pi]; fold point
   const double rs = rt - dr0;
   const double d2 = dr0 * dr0 + zd * zd;
@@ -293,6 +295,23 @@ __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, 
     for (int f = 0; f < NFAM; ++f) W.smp[f * H + j] = wj * F[f];
   }
   __syncwarp();
+}
+
+__device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
+                                  long long sid, const double* __restrict__ leg, long long n_split,
+                                  const double* __restrict__ cosT, const double* __restrict__ s2T,
+                                  const WarpSmem& W, int lane, const PairGrid& g) {
+  const int Ms = gp.Ms, Mq = gp.Mq;
+  const int nl = g.nl;  // local grid size; sample j sits at entry j of its tables
+  const double* __restrict__ cosL = g.cosL;
+  const int T = nl, tstride = 1;
+  const int Me = g.mc + 1;  // modes 0..mc computed, the rest zero
+  const int H = nl / 2 + 1, Q = nl / 4;  // samples on [0, pi]; fold point
+  const double d2 = dr0 * dr0 + zd * zd;
+  const double alpha = dr0 - d2 / (2.0 * rt);
+  const bool split = sid >= 0;
+  const cd g0 = gp.gamma0;
+  warp_pair_samples(gp, rt, dr0, zd, sid, leg, n_split, cosT, W, lane, g);
   // fold: smp[j] <- w_j F_j + w_{n/2-j} F_{n/2-j} (even m), smp[n/2-j] <- difference (odd m)
   for (int t = lane; t < NFAM * Q; t += 32) {
     int f = t / Q, j = t % Q;
@@ -621,6 +640,135 @@ __global__ void support_kernel(BuildArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Support spectra with the transform on the tensor cores.  The support pairs
+// are sampled on the full grid (they are near pairs: their spectra keep all
+// modes), and the cosine transform spec_m = (1/n) sum_j w_j F_j cos(2 pi m j / n)
+// becomes one real product for a chunk of pairs: rows = (pair, family,
+// Re/Im), k = j (n/2 + 1 samples), columns = modes; FP64-accurate through
+// exact digit slicing (oz_real_gemm_kernel).  The sampling kernel writes each
+// row's digits and scale; the product writes Y[m][row]; the last kernel forms
+// the complex spectra and adds the exact u^{-3/2} part of split pairs.
+#define SUP_ROWS (2 * NFAM)  // rows per pair
+
+__device__ __forceinline__ void support_geometry(const BuildArgs& a, int i, int slot, long long pid, double* rt,
+                                                 double* dr0, double* zd) {
+  *rt = a.geo.r[i];
+  if (slot < SELF_PTS) { *dr0 = a.sup.dr[pid]; *zd = a.sup.dz[pid]; }
+  else { *dr0 = *rt - a.sup.r[pid]; *zd = a.geo.z[i] - a.sup.z[pid]; }
+}
+
+// warp per support pair of the chunk: list[q0 + q], q < count
+__global__ void support_sample_kernel(BuildArgs a, const int* __restrict__ list, int q0, int count,
+                                      __nv_bfloat16* __restrict__ Asl, double* __restrict__ Ascale, int nkt) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const GreenParams& gp = a.gp;
+  WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
+  const int H = gp.H;
+  for (int q = blockIdx.x * wpb + wib; q < count; q += gridDim.x * wpb) {
+    const int p = list[q0 + q];
+    const int i = p / NEAR_SLOTS, slot = p % NEAR_SLOTS;
+    long long pid;
+    support_point(a, i, slot, &pid);
+    double rt, dr0, zd;
+    support_geometry(a, i, slot, pid, &rt, &dr0, &zd);
+    const long long sid = a.split_sup[p];
+    warp_pair_samples(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, W, lane, full_grid(gp, a.cosT, a.s2T));
+    __syncwarp();
+    // row scales: powers of two above twice each row's largest magnitude
+    double mx[SUP_ROWS];
+#pragma unroll
+    for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0.0;
+    for (int j = lane; j < H; j += 32)
+#pragma unroll
+      for (int f = 0; f < NFAM; ++f) {
+        const cd v = W.smp[f * H + j];
+        mx[2 * f] = fmax(mx[2 * f], fabs(v.x));
+        mx[2 * f + 1] = fmax(mx[2 * f + 1], fabs(v.y));
+      }
+    double inv[SUP_ROWS];
+#pragma unroll
+    for (int rr = 0; rr < SUP_ROWS; ++rr) {
+      double m = mx[rr];
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const double sc = pow2_scale(m);
+      inv[rr] = 72057594037927936.0 / sc;  // 2^56 / scale
+      if (lane == 0) Ascale[(size_t)q * SUP_ROWS + rr] = sc;
+    }
+    // digits: lane item = (row, group of 8 consecutive k), one 16-byte store per digit
+    const int kg_n = nkt * 2;
+    for (int it = lane; it < SUP_ROWS * kg_n; it += 32) {
+      const int rr = it / kg_n, kg = it % kg_n, f = rr >> 1, im = rr & 1;
+      double iv = inv[0];
+#pragma unroll
+      for (int u = 1; u < SUP_ROWS; ++u)
+        if (u == rr) iv = inv[u];
+      int dg[8][OZ_S];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = kg * 8 + c;
+        double v = 0.0;
+        if (k < H) { const cd z = W.smp[f * H + k]; v = im ? z.y : z.x; }
+        digits28(__double2ll_rn(v * iv), dg[c]);
+      }
+      const long long row = (long long)q * SUP_ROWS + rr;
+      const long long rt_ = row >> 7;
+      const int r = (int)(row & 127), kt = kg >> 1, kk = (kg & 1) * 8;
+      __nv_bfloat16* blk = Asl + ((size_t)rt_ * nkt + kt) * (OZ_S * 2048);
+      const int off = core_off(r, kk);
+#pragma unroll
+      for (int d = 0; d < OZ_S; ++d) {
+        __align__(16) __nv_bfloat16 e8[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) e8[c] = __float2bfloat16((float)dg[c][d]);
+        *(uint4*)(blk + d * 2048 + off) = *(uint4*)e8;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// thread per (pair q, family f, mode m): spec = (1/n)(Y_re + i Y_im) + the
+// exact u^{-3/2} part of a split pair (its coefficient beta_f and S^_m)
+__global__ void support_post_kernel(BuildArgs a, const int* __restrict__ list, int q0, int count,
+                                    const double* __restrict__ Y, int ldy) {
+  const GreenParams& gp = a.gp;
+  const int Ms = gp.Ms;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)count * NFAM * Ms) return;
+  const int m = (int)(t % Ms);
+  const int f = (int)((t / Ms) % NFAM);
+  const int q = (int)(t / ((long long)Ms * NFAM));
+  const int p = list[q0 + q];
+  const long long row = (long long)q * SUP_ROWS + 2 * f;
+  const double invn = 1.0 / gp.nphi;
+  cd v = C(invn * Y[(size_t)m * ldy + row], invn * Y[(size_t)m * ldy + row + 1]);
+  const long long sid = a.split_sup[p];
+  if (sid >= 0 && f >= 2) {
+    const int i = p / NEAR_SLOTS, slot = p % NEAR_SLOTS;
+    long long pid;
+    support_point(a, i, slot, &pid);
+    double rt, dr0, zd;
+    support_geometry(a, i, slot, pid, &rt, &dr0, &zd);
+    const double d2 = dr0 * dr0 + zd * zd;
+    const double alpha = dr0 - d2 / (2.0 * rt);
+    const cd g0 = gp.gamma0;
+    cd beta;
+    switch (f) {
+      case 2: case 4: beta = C(-alpha); break;
+      case 3: case 5: beta = C(-zd); break;
+      case 6: beta = (-2.0 * alpha * alpha) * g0; break;
+      case 7: beta = (-2.0 * alpha * zd) * g0; break;
+      default: beta = (-2.0 * zd * zd) * g0; break;
+    }
+    const double* Shat = a.leg + (long long)(gp.Mq + 1) * a.n_split;
+    const double Sm = Shat[(long long)m * a.n_split + sid] / 12.566370614359172;  // / 4 pi
+    v = fma(Sm, beta, v);
+  }
+  a.spec_sup[(size_t)p * NFAM * Ms + (size_t)f * Ms + m] = v;
+}
+
+// ---------------------------------------------------------------------------
 // Near panels: R_k(sigma, f, m) = sum_s W_s L_k(tau_s) sigma_s F_f(s, m)
 // (eqs. eq_nyslike, eq_nyslike2 with sum_j U_jk P_j = L_k), then the blocks of
 // the panel's columns k.  One CTA per (target, near panel, chunk of kc columns).
@@ -767,15 +915,29 @@ size_t far_tail_scratch(const BuildArgs& a, size_t* ij_elems) {
 void launch_far_assembly(const BuildArgs& a, cudaStream_t s) {
   int wpb = warps_per_block(a.gp);
   int smem = wpb * green_smem_bytes(a.gp);
-  cudaFuncSetAttribute(far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(far_kernel);
   far_kernel<<<grid_for((long long)a.N * a.N, wpb), wpb * 32, smem, s>>>(a);
 }
 
 void launch_support_spectra(const BuildArgs& a, cudaStream_t s) {
   int wpb = warps_per_block(a.gp);
   int smem = wpb * green_smem_bytes(a.gp);
-  cudaFuncSetAttribute(support_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(support_kernel);
   support_kernel<<<grid_for((long long)a.N * NEAR_SLOTS, wpb), wpb * 32, smem, s>>>(a);
+}
+
+void launch_support_samples(const BuildArgs& a, const int* list, int q0, int count, __nv_bfloat16* Asl,
+                            double* Ascale, int nkt, cudaStream_t s) {
+  int wpb = warps_per_block(a.gp);
+  int smem = wpb * green_smem_bytes(a.gp);
+  smem_optin(support_sample_kernel);
+  support_sample_kernel<<<grid_for(count, wpb), wpb * 32, smem, s>>>(a, list, q0, count, Asl, Ascale, nkt);
+}
+
+void launch_support_post(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy,
+                         cudaStream_t s) {
+  const long long items = (long long)count * NFAM * a.gp.Ms;
+  support_post_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a, list, q0, count, Y, ldy);
 }
 
 // Threads per CTA: the fewest rounds (at most 384 threads) over the larger
@@ -786,7 +948,7 @@ void launch_near_assembly(const BuildArgs& a, cudaStream_t s) {
   const int items = std::max(NFAM * a.gp.Ms, a.kc * (a.gp.M + 1));
   const int rounds = (items + 383) / 384;
   const int threads = std::min(384, ((items + rounds - 1) / rounds + 31) / 32 * 32);
-  cudaFuncSetAttribute(near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(near_kernel);
   near_kernel<<<a.N * 3 * (P_NODES / a.kc), threads, smem, s>>>(a);
 }
 
@@ -796,7 +958,7 @@ void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* 
   if (npairs <= 0) return;
   int wpb = warps_per_block(gp);
   int smem = wpb * green_smem_bytes(gp);
-  cudaFuncSetAttribute(pair_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(pair_spectra_kernel);
   pair_spectra_kernel<<<grid_for(npairs, wpb), wpb * 32, smem, s>>>(gp, pairs, sidx, leg, n_split, npairs, cosT,
                                                                       s2T, out);
 }
@@ -921,7 +1083,7 @@ extern "C" int mueller_modal_kernels_noalloc(const double* pairs_dev, long long 
   unsigned blocks = (unsigned)((npairs + 127) / 128);
   noalloc_prep_kernel<<<blocks, 128, 0, s>>>(pairs_dev, npairs, n_phi, M, -log(eps), disp, sid);
   const int nr = legendre_table_entries(Mq);
-  cudaFuncSetAttribute(noalloc_legendre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, nr * 8);
+  smem_optin(noalloc_legendre_kernel);
   noalloc_legendre_kernel<<<blocks, 128, nr * 8, s>>>(disp, sid, npairs, Mq, Ms, leg, nr);
   launch_pair_spectra(gp, disp, sid, leg, npairs, npairs, cosT, s2T, (cd*)out_dev, s);
   cudaError_t e = cudaGetLastError();

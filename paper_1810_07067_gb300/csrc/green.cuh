@@ -1,5 +1,6 @@
 // Modal Green's function evaluation and per-mode assembly (Sections 3-5).
 #pragma once
+#include <cuda_bf16.h>
 #include "cplx.cuh"
 #include "special.cuh"
 
@@ -96,6 +97,14 @@ int far_tail_pairs(const GreenParams& gp);
 size_t far_tail_scratch(const BuildArgs& a, size_t* ij_elems);
 void launch_far_assembly(const BuildArgs& a, cudaStream_t s);
 void launch_support_spectra(const BuildArgs& a, cudaStream_t s);
+// support spectra with the transform on the tensor cores, for the support
+// pairs list[q0 .. q0 + count) (p = target * NEAR_SLOTS + slot): samples ->
+// row digits (rows = 18 per pair, a multiple of 128 padded) -> (ozaki_real_gemm) ->
+// spectra into BuildArgs::spec_sup
+void launch_support_samples(const BuildArgs& a, const int* list, int q0, int count, __nv_bfloat16* Asl,
+                            double* Ascale, int nkt, cudaStream_t s);
+void launch_support_post(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy,
+                         cudaStream_t s);
 void launch_near_assembly(const BuildArgs& a, cudaStream_t s);
 void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* split_id, const double* leg,
                          long long n_split, long long npairs, const double* cosT, const double* s2T,

@@ -14,7 +14,13 @@
 #include <vector>
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
+#include "smem.cuh"
 #include "lu.cuh"
+
+std::mutex& lu_capture_mutex() {
+  static std::mutex m;
+  return m;
+}
 #include "tc.cuh"
 
 namespace cg = cooperative_groups;
@@ -1158,6 +1164,10 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
     if (tile == 0) autotune_tiles(nmax, count, s);
   }
   cudaStream_t ls = s, cs = nullptr;
+  // while this thread captures, no other thread of the library frees device
+  // memory (a free synchronizes the device, which would end the capture)
+  std::unique_lock<std::mutex> capture_lock(lu_capture_mutex(), std::defer_lock);
+  if (graph) capture_lock.lock();
   if (graph) {
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1165,6 +1175,7 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
       if (cs) cudaStreamDestroy(cs);
       cs = nullptr;
       graph = false;
+      capture_lock.unlock();
     } else {
       ls = cs;
     }
@@ -1275,6 +1286,7 @@ static cudaError_t lu_factor_impl(const LuMat* items, int count, cudaStream_t s,
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     e = cudaStreamEndCapture(cs, &g);
+    capture_lock.unlock();
     if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(x, s);
     if (x) cudaGraphExecDestroy(x);
@@ -1455,6 +1467,51 @@ __device__ __forceinline__ void block_row_update(const TF* __restrict__ F, int n
     if (g < G) X[g][r] = X[g][r] - to_cd(acc[g]);
 }
 
+// The same for rows r and r + 1 (r even, both below the matrix's end): one
+// 16-byte load per factor column feeds both rows (more bytes in flight per
+// thread on this bandwidth-bound product).
+template <int SGT>
+__device__ __forceinline__ void block_row_update2(const cf* __restrict__ F, int n, int r, int kb, int bs,
+                                                  const cf (*Xb)[SGT], cd* const* X, int G) {
+  cf acc0[SGT], acc1[SGT];
+#pragma unroll
+  for (int g = 0; g < SGT; ++g) { acc0[g] = czero<cf>(); acc1[g] = czero<cf>(); }
+#pragma unroll 8
+  for (int c = 0; c < bs; ++c) {
+    const float4 v = __ldg((const float4*)(F + (size_t)(kb + c) * n + r));
+    const cf l0 = CF(v.x, v.y), l1 = CF(v.z, v.w);
+#pragma unroll
+    for (int g = 0; g < SGT; ++g) {
+      const cf xc = Xb[c][g];
+      acc0[g] = fma(l0, xc, acc0[g]);
+      acc1[g] = fma(l1, xc, acc1[g]);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < SGT; ++g)
+    if (g < G) {
+      X[g][r] = X[g][r] - to_cd(acc0[g]);
+      X[g][r + 1] = X[g][r + 1] - to_cd(acc1[g]);
+    }
+}
+
+// Rows [r0, r1) of the block's column product by the threads t0.. of a
+// stride: pairs of rows with 16-byte loads for complex64 factors (n even).
+template <class TF, int SGT>
+__device__ __forceinline__ void rows_update(const TF* __restrict__ F, int n, int r0, int r1, int kb, int bs,
+                                           const TF (*Xb)[SGT], cd* const* X, int G, int t0, int stride) {
+  if constexpr (std::is_same<TF, cf>::value) {
+    if ((n & 1) == 0 && (r0 & 1) == 0) {
+      for (int r = r0 + 2 * t0; r < r1; r += 2 * stride) {
+        if (r + 1 < r1) block_row_update2<SGT>(F, n, r, kb, bs, Xb, X, G);
+        else block_row_update<TF, SGT>(F, n, r, kb, bs, Xb, X, G);
+      }
+      return;
+    }
+  }
+  for (int r = r0 + t0; r < r1; r += stride) block_row_update<TF, SGT>(F, n, r, kb, bs, Xb, X, G);
+}
+
 template <class TF, int SGT>
 __host__ __device__ constexpr size_t solve_smem_fixed() {
   return 2 * (size_t)SB * (SB + 1) * sizeof(TF) + 2 * (size_t)SB * SGT * sizeof(TF);
@@ -1528,7 +1585,7 @@ __global__ void __launch_bounds__(SolveShape<SGT>::NT) solve_blocked_kernel(
       }
     } else {
       if (i + 2 < nblk) load_diag(i + 2, tid - 64, T - 64);
-      for (int r = kn + SB + (tid - 64); r < n; r += T - 64) block_row_update<TF, SGT>(L, n, r, kb, bs, Xs[b], X, G);
+      rows_update<TF, SGT>(L, n, kn + SB, n, kb, bs, Xs[b], X, G, tid - 64, T - 64);
     }
     __syncthreads();
   }
@@ -1550,7 +1607,7 @@ __global__ void __launch_bounds__(SolveShape<SGT>::NT) solve_blocked_kernel(
       }
     } else {
       if (i - 2 >= 0) load_diag(i - 2, tid - 64, T - 64);
-      for (int r = tid - 64; r < kp; r += T - 64) block_row_update<TF, SGT>(L, n, r, kb, bs, Xs[b], X, G);
+      rows_update<TF, SGT>(L, n, 0, kp, kb, bs, Xs[b], X, G, tid - 64, T - 64);
     }
     __syncthreads();
   }
@@ -1575,7 +1632,7 @@ static void launch_solve_w(const TF* LU, const int* piv, int n, int M, const dou
                            int smem_perm, cudaStream_t s) {
   const int groups = (2 * nrhs + W - 1) / W;
   const int smem = (int)solve_smem_fixed<TF, W>() + smem_perm;
-  cudaFuncSetAttribute(solve_blocked_kernel<TF, PHYS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_optin(solve_blocked_kernel<TF, PHYS, W>);
   solve_blocked_kernel<TF, PHYS, W><<<dim3(M + 1, groups), SolveShape<W>::NT, smem, s>>>(LU, piv, n, M, sw, rhs, x,
                                                                                           nrhs);
 }

@@ -63,3 +63,9 @@ void lu_solve_modes(const cd* LU, const int* piv, int n, int M, const double* sw
 // -M..M (layout [2M+1][nrhs][n], -m by reflection).
 void lu_correction_solve_c64(const cf* LU, const int* piv, int n, int M, const cd* r, cd* d, int nrhs,
                              cudaStream_t s);
+
+// Held by a thread while it captures the LU's launches into a CUDA graph;
+// code that frees device memory (and so synchronizes the device) takes it
+// first, so that it never ends another thread's capture.
+#include <mutex>
+std::mutex& lu_capture_mutex();

@@ -482,6 +482,7 @@ size_t cached = 0, cap = (size_t)32 << 30;
 inline size_t rounded(size_t b) { return (b + kRound - 1) / kRound * kRound; }
 
 void trim() {
+  std::lock_guard<std::mutex> capture(lu_capture_mutex());
   std::lock_guard<std::mutex> lk(mu);
   int cur = 0;
   cudaGetDevice(&cur);
@@ -525,6 +526,7 @@ cudaError_t alloc(void** p, size_t bytes) {
 
 void release(void* p, size_t bytes) {
   if (!p) return;
+  std::lock_guard<std::mutex> capture(lu_capture_mutex());
   if (bytes >= kMinBlock) {
     const size_t req = rounded(bytes);
     int dev = 0;
@@ -625,10 +627,14 @@ static bool fault_injected(const char* what) {
   const char* v = std::getenv("MUELLER_FAULT_INJECT");
   return v && std::strstr(v, what) != nullptr;
 }
-static void inject_status(int* dev_word, const char* what) {
+// Device-to-host reads of status words and small results go through the
+// caller's stream (never the legacy default stream, which would join another
+// host thread's stream capture).
+static void inject_status(int* dev_word, const char* what, cudaStream_t s) {
   if (dev_word && fault_injected(what)) {
     const int one = 1;
-    cudaMemcpy(dev_word, &one, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(dev_word, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
   }
 }
 
@@ -641,6 +647,83 @@ struct Timer {
   void mark() { cudaEventRecord(e[n++], s); }
   double ms(int a, int b) { float v = 0; cudaEventElapsedTime(&v, e[a], e[b]); return v; }
 };
+
+// Support pairs per chunk of the tensor-core support transform (its digit and
+// product scratch: 18 rows x (16 nkt x 16 + 8 Ms) bytes per pair).
+#define SUP_TC_CHUNK 8192
+
+static size_t support_tc_scratch_bytes(int N, int nphi, int M) {
+  const int H = nphi / 2 + 1, nkt = (H + 15) / 16, Ms = M + 2;
+  const int rows_pad = (SUP_TC_CHUNK * 2 * NFAM + 127) / 128 * 128;
+  return ozaki_real_a_elems(rows_pad, nkt) * 2 + (size_t)rows_pad * 8 + (size_t)Ms * rows_pad * 8 +
+         ozaki_real_b_elems(Ms, nkt) * 2 + (size_t)N * NEAR_SLOTS * 4 + 64;
+}
+
+// Support spectra: on the tensor cores (sampling, digit rows, one real product
+// per chunk of pairs, spectra) when the half grid fits one exact product
+// (n_phi / 2 + 1 <= OZR_KMAX samples), else the warp-per-pair kernel.
+static int support_spectra(const Setup& S, BuildArgs& a, DevBuf& tmp, int** err_out, cudaStream_t s) {
+  const int H = S.gp.H, Ms = S.gp.Ms;
+  if (H > OZR_KMAX) {
+    launch_support_spectra(a, s);
+    return MUELLER_OK;
+  }
+  std::vector<int> list;
+  list.reserve((size_t)S.N * (SELF_PTS + 2 * 32));
+  for (int i = 0; i < S.N; ++i) {
+    const int P = i / P_NODES;
+    for (int slot = 0; slot < NEAR_SLOTS; ++slot) {
+      if (support_pid(S, i, slot) < 0) continue;
+      // the device skips the wrap-around neighbour of a closed curve of one or two panels
+      if (slot >= SELF_PTS && S.closed && S.nP <= 2 &&
+          ((slot < SELF_PTS + ADJ_PTS && P == 0) || (slot >= SELF_PTS + ADJ_PTS && P == S.nP - 1)))
+        continue;
+      list.push_back(i * NEAR_SLOTS + slot);
+    }
+  }
+  if (list.empty()) return MUELLER_OK;
+  const int nkt = (H + 15) / 16;
+  const int rows_pad = (SUP_TC_CHUNK * 2 * NFAM + 127) / 128 * 128;
+  int* dlist = nullptr;
+  __nv_bfloat16 *Asl = nullptr, *Bsl = nullptr;
+  double *Ascale = nullptr, *Y = nullptr;
+  int* err = nullptr;
+  if (tmp.upload(&dlist, list, s) != cudaSuccess || tmp.alloc(&Asl, ozaki_real_a_elems(rows_pad, nkt)) != cudaSuccess ||
+      tmp.alloc(&Ascale, (size_t)rows_pad) != cudaSuccess || tmp.alloc(&Y, (size_t)Ms * rows_pad) != cudaSuccess ||
+      tmp.alloc(&Bsl, ozaki_real_b_elems(Ms, nkt)) != cudaSuccess || tmp.alloc(&err, 1) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "support transform scratch");
+  // B: cos(2 pi m j / n_phi), j = 0..n_phi/2 (the samples' weights are in the rows), digits of b / 2
+  {
+    std::vector<double> b((size_t)H * Ms);
+    const double two_pi = 6.283185307179586;
+    for (int j = 0; j < H; ++j)
+      for (int m = 0; m < Ms; ++m) {
+        const long long t = ((long long)m * j) % S.nphi;  // the angle reduced exactly
+        b[(size_t)j * Ms + m] = std::cos(two_pi * (double)t / (double)S.nphi);
+      }
+    std::vector<__nv_bfloat16> hb(ozaki_real_b_elems(Ms, nkt));
+    ozaki_real_b_host(b.data(), H, Ms, 2.0, nkt, hb.data());
+    CK(cudaMemcpyAsync(Bsl, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // hb is a host temporary
+  }
+  CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  const int total = (int)list.size();
+  for (int q0 = 0; q0 < total; q0 += SUP_TC_CHUNK) {
+    const int cnt = std::min(SUP_TC_CHUNK, total - q0);
+    const int rows = cnt * 2 * NFAM, rp = (rows + 127) / 128 * 128;
+    if (rp > rows) {  // the last row tile's padding rows: zero digits and scales
+      const int t = rows / 128;
+      CK(cudaMemsetAsync(Asl + (size_t)t * nkt * (OZ_S * OZ_RT * OZ_KT), 0,
+                         (size_t)nkt * OZ_S * OZ_RT * OZ_KT * sizeof(__nv_bfloat16), s));
+      CK(cudaMemsetAsync(Ascale + rows, 0, (size_t)(rp - rows) * sizeof(double), s));
+    }
+    launch_support_samples(a, dlist, q0, cnt, Asl, Ascale, nkt, s);
+    ozaki_real_gemm(Asl, Ascale, rp, Bsl, 2.0, nkt, Y, rp, Ms, err, s);
+    launch_support_post(a, dlist, q0, cnt, Y, rp, s);
+  }
+  *err_out = err;
+  return MUELLER_OK;
+}
 
 // Assemble modes 0..M into A_dev (column-major per mode, L2-weighted).
 static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st, DevBuf& keep,
@@ -704,12 +787,22 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   T.mark();
   launch_far_assembly(a, s);
   T.mark();
-  launch_support_spectra(a, s);
+  int* sup_err = nullptr;
+  {
+    const int rc = support_spectra(S, a, tmp, &sup_err, s);
+    if (rc != MUELLER_OK) return rc;
+  }
   T.mark();
   launch_near_assembly(a, s);
   T.mark();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  if (sup_err) {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, sup_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core support transform timed out");
+  }
   if (st) {
     st->ms_legendre = T.ms(0, 1); st->ms_far = T.ms(1, 2); st->ms_support = T.ms(2, 3); st->ms_near = T.ms(3, 4);
     st->n_phi_used = S.nphi; st->n_split_pairs = n_split; st->n_far_pairs = S.n_far; st->n_support_pairs = S.n_sup;
@@ -840,7 +933,7 @@ static int build_assemble(mueller_ctx* c, cudaStream_t s) {
   return MUELLER_OK;
 }
 
-static int build_finish(mueller_ctx* c, const LuTiming& lt, double ms_lu, int wave_bodies) {
+static int build_finish(mueller_ctx* c, const LuTiming& lt, double ms_lu, int wave_bodies, cudaStream_t s) {
   const int M = c->S.M;
   c->st.ms_lu = ms_lu;
   c->st.ms_build += ms_lu;
@@ -852,10 +945,11 @@ static int build_finish(mueller_ctx* c, const LuTiming& lt, double ms_lu, int wa
   c->st.lu_wave_bodies = wave_bodies;
   c->st.lu_launches = lt.launches;
   std::vector<int> info(M + 1);
-  CK(cudaMemcpy(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(info.data(), c->info, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost, s));
   int tce = 0;
-  inject_status(c->tc_err, "lu_timeout");
-  CK(cudaMemcpy(&tce, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  inject_status(c->tc_err, "lu_timeout", s);
+  CK(cudaMemcpyAsync(&tce, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   if (tce) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core LU update timed out");
   c->st.singular_mode = -1; c->st.singular_column = -1;
   c->st.kappa_max_mode = -1;
@@ -913,7 +1007,7 @@ extern "C" int mueller_build(const mueller_curve* curve, const mueller_media* me
   cudaEventElapsedTime(&b, e1, e2);
   cudaEventDestroy(e1); cudaEventDestroy(e2);
   if (err != cudaSuccess) { delete c; return fail(MUELLER_ECUDA, cudaGetErrorString(err)); }
-  rc = build_finish(c, lt, b, 1);
+  rc = build_finish(c, lt, b, 1, s);
   if (rc) { delete c; return rc; }
   *out = c;
   if (c->st.singular_mode >= 0) return fail(MUELLER_ESINGULAR, "exact zero pivot");
@@ -966,10 +1060,11 @@ extern "C" int mueller_build_many(int count, const mueller_curve* curves, const 
   if (err == cudaSuccess) err = err2;
   if (err != cudaSuccess) return drop(fail(MUELLER_ECUDA, cudaGetErrorString(err)));
   int tce = 0;
-  CK(cudaMemcpy(&tce, cs[0]->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&tce, cs[0]->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   for (int i = 0; i < count; ++i) {
-    if (tce) cudaMemcpy(cs[i]->tc_err, cs[0]->tc_err, sizeof(int), cudaMemcpyDeviceToDevice);
-    int rc = build_finish(cs[i], lt, b, count);
+    if (tce) cudaMemcpyAsync(cs[i]->tc_err, cs[0]->tc_err, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    int rc = build_finish(cs[i], lt, b, count, s);
     if (rc) return drop(rc);
   }
   bool singular = false;
@@ -1078,8 +1173,9 @@ static int solve_mixed(mueller_ctx* c, const cd* rhs, int nrhs, cd* x, double* b
   if (backward_err) std::copy(be.begin(), be.end(), backward_err);
   if (derr) {
     int h = 0;
-    inject_status(derr, "residual_timeout");
-    cudaMemcpy(&h, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    inject_status(derr, "residual_timeout", s);
+    cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
     if (h) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core residual timed out");
   }
   if (!done) return fail(MUELLER_ENOCONV, "refinement stopped at refine_max_iter");
@@ -1368,7 +1464,7 @@ extern "C" size_t mueller_build_bytes(int N, int M, int precision, size_t* resid
   const size_t A32 = precision != 0 ? modes * n * n * sizeof(cf) : 0;
   const size_t sl = precision == 1 ? ozaki_matrix_slices_elems((int)npad, (int)modes) * 2 + modes * npad * 8 : 0;
   const size_t small = modes * n * 4 + modes * 16 + (size_t)N * 64;
-  const size_t scratch = (size_t)N * NEAR_SLOTS * NFAM * (size_t)(M + 2) * sizeof(cd);
+  const size_t scratch = (size_t)N * NEAR_SLOTS * NFAM * (size_t)(M + 2) * sizeof(cd) + support_tc_scratch_bytes(N, 512, M);
   if (resident) *resident = (precision == 1 ? 0 : A) + A32 + sl + small;
   return A + A32 + sl + small + scratch;
 }

@@ -25,6 +25,7 @@
 // memory where they fit).
 #include <cstdio>
 #include "ozaki.cuh"
+#include "digits.cuh"
 #include "tc.cuh"
 
 #define OZ_ATILE (OZ_RT * OZ_KT)          // bf16 elements per slice tile of A
@@ -39,10 +40,6 @@ size_t ozaki_matrix_slices_elems(int npad, int batch) {
 size_t ozaki_vector_slices_elems(int npad, int batch, int njt, int jt) {
   return (size_t)batch * njt * (npad / OZ_KT) * oz_yblock(jt);
 }
-
-// offset of element (row r, k) inside a slice tile with R rows and 16 columns
-// (core matrices of 8 x 8, row-group major; two core matrices along k)
-__device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
 __device__ __forceinline__ void digits(double v, float* d) {
   // v in (-1/2, 1/2): the fixed-point integer F = round(v 2^56) (|F| < 2^55),
@@ -59,38 +56,7 @@ __device__ __forceinline__ void digits(double v, float* d) {
   d[0] = (float)F;
 }
 
-__device__ __forceinline__ double pow2_scale(double mx) {
-  if (!(mx > 0.0)) return 1.0;
-  int e;
-  frexp(mx, &e);               // mx = f 2^e, f in [1/2, 1)
-  return ldexp(1.0, e + 1);    // |a| / scale < 1/2
-}
-
 // thread per (row i, group of 8 consecutive k): 16 digit rows of 16 bytes.
-// The 16 values are held as fixed-point integers F = round(v 2^56) and
-// written in balanced base 128 from the least significant digit up, as in
-// digits(), on two 28-bit halves in 32-bit integer arithmetic:
-// d = ((F + 64) mod 128) - 64, F <- (F - d) / 128; the low half's carry joins
-// the high half, and the top digit ends in [-64, 64].  v = sum_s d_s 2^{-7(s+1)}
-// up to the rounding of F.
-__device__ __forceinline__ void digits28(long long F, int* d) {
-  int lo = (int)(F & 0xFFFFFFFll), hi = (int)(F >> 28);
-#pragma unroll
-  for (int s = OZ_S - 1; s >= OZ_S / 2; --s) {
-    const int dd = ((lo + 64) & 127) - 64;
-    d[s] = dd;
-    lo = (lo - dd) >> 7;
-  }
-  hi += lo;  // carry of the low half (0 or 1)
-#pragma unroll
-  for (int s = OZ_S / 2 - 1; s >= 1; --s) {
-    const int dd = ((hi + 64) & 127) - 64;
-    d[s] = dd;
-    hi = (hi - dd) >> 7;
-  }
-  d[0] = hi;
-}
-
 __global__ void __launch_bounds__(128) oz_slice_matrix_kernel(const cd* __restrict__ A, int n, int npad,
                                                               const double* __restrict__ rowscale,
                                                               __nv_bfloat16* __restrict__ Asl) {
@@ -404,4 +370,170 @@ void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int
   cudaMemsetAsync(rnorm, 0, sizeof(double) * (2 * M + 1) * nrhs, s);
   if (jt == 16) oz_residual_launch<16>(Asl, rowscale, n, npad, M, bw, r, nrhs, njt, rnorm, Ysl, colscale, err, s);
   else oz_residual_launch<OZ_JT>(Asl, rowscale, n, npad, M, bw, r, nrhs, njt, rnorm, Ysl, colscale, err, s);
+}
+
+// ---------------------------------------------------------------------------
+// Real product Y = A B with A given by the digits of its rows (row scales
+// Ascale, a power of two each) and B by the digits of its columns (one scale
+// bscale): Y[c * ldy + r] for the first ncols columns.  Operand blocks per
+// (row tile, k-tile) and (column tile, k-tile) hold the 8 digits of a 128 x 16
+// (48 x 16) tile in the MMA's layout.  K is at most OZR_KMAX, so that every
+// level's sum stays an exact FP32 integer (8 digit pairs x 272 x 64^2 < 2^24)
+// and one drain at the end suffices; the levels are joined exactly in 64-bit
+// integers (levels 0-3 and 4-7 apart) and converted to FP64 twice per entry.
+// CTA per (column tile, row tile); warps 0-3 drain, 4 copies, 5 issues MMAs.
+#define OZR_NT 48
+#define OZR_BBLOCK (OZ_S * OZR_NT * OZ_KT)       // bf16 elements per (column tile, k-tile)
+#define OZR_ABLOCK (OZ_S * OZ_ATILE)             // per (row tile, k-tile)
+#define OZR_STAGE ((OZR_ABLOCK + OZR_BBLOCK) * 2)
+#define OZR_NST 4
+
+__global__ void __launch_bounds__(192, 1)
+    oz_real_gemm_kernel(const __nv_bfloat16* __restrict__ Asl, const double* __restrict__ Ascale,
+                        const __nv_bfloat16* __restrict__ Bsl, double bscale, int nkt, double* __restrict__ Y,
+                        int ldy, int ncols, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[OZR_NST], empty[OZR_NST], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  volatile int* fail = &s_fail;
+  const int nt = blockIdx.x, rt = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 32) {
+    s_fail = 0;
+#pragma unroll
+    for (int b = 0; b < OZR_NST; ++b) { tc::mbar_init(&full[b], 1); tc::mbar_init(&empty[b], 1); }
+    tc::mbar_init(&done, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  int issued = 0;
+  if (warp == 4) {
+    if (lane == 0) {
+      const __nv_bfloat16* Ab = Asl + (size_t)rt * nkt * OZR_ABLOCK;
+      const __nv_bfloat16* Bb = Bsl + (size_t)nt * nkt * OZR_BBLOCK;
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int st = kt % OZR_NST;
+        if (kt >= OZR_NST && !tc::mbar_wait(&empty[st], ((kt / OZR_NST) - 1) & 1)) { *fail = 1; break; }
+        if (*fail) break;
+        unsigned char* base = smem + (size_t)st * OZR_STAGE;
+        tc::mbar_expect_tx(&full[st], OZR_STAGE);
+        tc::bulk_g2s(base, Ab + (size_t)kt * OZR_ABLOCK, OZR_ABLOCK * 2, &full[st]);
+        tc::bulk_g2s(base + OZR_ABLOCK * 2, Bb + (size_t)kt * OZR_BBLOCK, OZR_BBLOCK * 2, &full[st]);
+        issued = kt + 1;
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(OZ_RT, OZR_NT, false);
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int st = kt % OZR_NST;
+        if (!tc::mbar_wait(&full[st], (kt / OZR_NST) & 1)) { *fail = 1; break; }
+        tc::fence_after();
+        unsigned char* base = smem + (size_t)st * OZR_STAGE;
+        const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(base), 128, 256);
+        const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(base + OZR_ABLOCK * 2), 128, 256);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) {
+#pragma unroll
+          for (int t = 0; t < OZ_S - s; ++t) {
+            const uint32_t acc = tmem + (uint32_t)((s + t) * OZR_NT);
+            const uint64_t ad = a0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
+            const uint64_t bd = b0 + (uint64_t)(t * (OZR_NT * OZ_KT * 2 / 16));
+            tc::mma_bf16(acc, ad, bd, idesc, (kt == 0 && s == 0) ? 0u : 1u);  // (0, t) opens level t
+          }
+        }
+        tc::commit(&empty[st]);
+      }
+      tc::commit(&done);  // arrives once every MMA issued above has completed
+      if (!tc::mbar_wait(&done, 0)) *fail = 1;
+    }
+  }
+  if (warp < 4) {
+    // drain: this warp's 32 rows, 16 columns at a time, levels joined in integers
+    if (!tc::mbar_wait(&done, 0)) *fail = 1;
+    tc::fence_after();
+    const int r = rt * OZ_RT + warp * 32 + lane;
+    const double sc = Ascale[r] * bscale;
+    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < OZR_NT; c0 += 16) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) { hi[c] = 0; lo[c] = 0; }
+      if (!*fail) {
+#pragma unroll
+        for (int l = 0; l < OZ_S; ++l) {
+          float v[16];
+          tc::tmem_ld16(tw + (uint32_t)(l * OZR_NT + c0), v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const long long iv = (long long)__float2int_rn(v[c]);  // an exact integer below 2^24
+            if (l < 4) hi[c] = hi[c] * 128 + iv;
+            else lo[c] = lo[c] * 128 + iv;
+          }
+        }
+      }
+      // hi = sum_{l<4} acc_l 2^{7(3-l)}, lo = sum_{l>=4} acc_l 2^{7(7-l)};
+      // level l carries 2^{-7(l+2)}: value = hi 2^-35 + lo 2^-63
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = nt * OZR_NT + c0 + c;
+        if (col < ncols)
+          Y[(size_t)col * ldy + r] = sc * fma((double)hi[c], 2.9103830456733704e-11, (double)lo[c] * 1.0842021724855044e-19);
+      }
+    }
+  }
+  __syncthreads();
+  if (*fail) {
+    if (tid == 0 && err) atomicExch(err, 1);
+    if (warp == 4 && lane == 0) {
+      for (int st = 0; st < OZR_NST; ++st) {
+        const int last = issued - 1 - ((issued - 1 - st) % OZR_NST + OZR_NST) % OZR_NST;
+        if (last >= 0) tc::mbar_wait(&full[st], (last / OZR_NST) & 1, 1 << 20);
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+size_t ozaki_real_a_elems(int rows_pad, int nkt) { return (size_t)(rows_pad / OZ_RT) * nkt * OZR_ABLOCK; }
+size_t ozaki_real_b_elems(int ncols, int nkt) { return (size_t)((ncols + OZR_NT - 1) / OZR_NT) * nkt * OZR_BBLOCK; }
+
+void ozaki_real_gemm(const __nv_bfloat16* Asl, const double* Ascale, int rows_pad, const __nv_bfloat16* Bsl,
+                     double bscale, int nkt, double* Y, int ldy, int ncols, int* err, cudaStream_t s) {
+  const int smem = OZR_NST * OZR_STAGE;
+  cudaFuncSetAttribute(oz_real_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const dim3 grid((ncols + OZR_NT - 1) / OZR_NT, rows_pad / OZ_RT);
+  oz_real_gemm_kernel<<<grid, 192, smem, s>>>(Asl, Ascale, Bsl, bscale, nkt, Y, ldy, ncols, err);
+}
+
+// Digits of the columns of B[k][c] = b(k, c) / bscale for the real product
+// (host): balanced base-128 digits of round(v 2^56), the same digits as on
+// the device, in the operand layout of oz_real_gemm_kernel.
+void ozaki_real_b_host(const double* b, int K, int ncols, double bscale, int nkt, __nv_bfloat16* out) {
+  const int ntile = (ncols + OZR_NT - 1) / OZR_NT;
+  for (size_t e = 0; e < (size_t)ntile * nkt * OZR_BBLOCK; ++e) out[e] = __float2bfloat16(0.f);
+  for (int c = 0; c < ncols; ++c)
+    for (int k = 0; k < K; ++k) {
+      long long F = llrint(b[(size_t)k * ncols + c] / bscale * 72057594037927936.0);  // 2^56
+      int d[OZ_S];
+      for (int q = OZ_S - 1; q >= 1; --q) {
+        const long long dd = ((F + 64) & 127) - 64;
+        d[q] = (int)dd;
+        F = (F - dd) >> 7;
+      }
+      d[0] = (int)F;
+      const int t = c / OZR_NT, cc = c % OZR_NT, kt = k / OZ_KT, kk = k % OZ_KT;
+      const int off = ((cc >> 3) * 2 + (kk >> 3)) * 64 + (cc & 7) * 8 + (kk & 7);
+      for (int q = 0; q < OZ_S; ++q)
+        out[((size_t)t * nkt + kt) * OZR_BBLOCK + (size_t)q * OZR_NT * OZ_KT + off] = __float2bfloat16((float)d[q]);
+    }
 }

@@ -30,3 +30,15 @@ void ozaki_slice_matrix(const cd* A, int n, int npad, int batch, __nv_bfloat16* 
 void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int npad, int M, const cd* bw,
                     const cd* y, cd* r, int nrhs, double* rnorm, __nv_bfloat16* Ysl, double* colscale, int* err,
                     cudaStream_t s);
+
+// Real product Y[c * ldy + r] = sum_k A[r][k] B[k][c], c < ncols, on BF16
+// tensor cores with FP64 accuracy (the digit slicing above): A as the 8
+// digits of its rows (rows_pad a multiple of 128, row scales Ascale), B as
+// the digits of b / bscale built on the host by ozaki_real_b_host; K =
+// 16 nkt <= 272.  err is set on a timed-out device wait.
+#define OZR_KMAX 272
+size_t ozaki_real_a_elems(int rows_pad, int nkt);   // bf16 elements of the A digits
+size_t ozaki_real_b_elems(int ncols, int nkt);      // bf16 elements of the B digits
+void ozaki_real_b_host(const double* b, int K, int ncols, double bscale, int nkt, __nv_bfloat16* out);
+void ozaki_real_gemm(const __nv_bfloat16* Asl, const double* Ascale, int rows_pad, const __nv_bfloat16* Bsl,
+                     double bscale, int nkt, double* Y, int ldy, int ncols, int* err, cudaStream_t s);
