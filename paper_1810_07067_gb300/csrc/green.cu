@@ -192,11 +192,13 @@ __device__ PairGrid pair_grid(const GreenParams& gp, double rt, double dr0, doub
 }
 
 // The weighted samples W.smp[f][j] = w_j F_f(phi_j), j = 0..nl/2 (w = 1/2 at
-// both ends), of one pair on its grid g: the first half of warp_pair_spectra.
-__device__ void warp_pair_samples(const GreenParams& gp, double rt, double dr0, double zd,
-                                  long long sid, const double* __restrict__ leg, long long n_split,
-                                  const double* __restrict__ cosT, const WarpSmem& W, int lane,
-                                  const PairGrid& g) {
+// both ends), of one pair on its grid g: the first half of warp_pair_spectra,
+// by the threads t = 0..NT-1 of a group whose barrier is sync().
+template <int NT, class Sync>
+__device__ __forceinline__ void group_pair_samples(const GreenParams& gp, double rt, double dr0, double zd,
+                                                   long long sid, const double* __restrict__ leg, long long n_split,
+                                                   const double* __restrict__ cosT, const WarpSmem& W, int t,
+                                                   const PairGrid& g, const Sync& sync) {
   const int Mq = gp.Mq, mask = gp.nphi - 1;
   const int nl = g.nl;  // local grid size; sample j sits at entry j of its tables
   const double* __restrict__ s2L = g.s2L;
@@ -208,11 +210,11 @@ __device__ void warp_pair_samples(const GreenParams& gp, double rt, double dr0, 
   const bool split = sid >= 0;
   const double TWO_PI = 6.283185307179586;
   if (split) {  // dec == 1
-    for (int nn = lane; nn <= Mq; nn += 32) W.phs[nn] = leg[(long long)nn * n_split + sid];
-    __syncwarp();
+    for (int nn = t; nn <= Mq; nn += NT) W.phs[nn] = leg[(long long)nn * n_split + sid];
+    sync();
     // q_j = (P^_0 + 2 sum_n P^_n cos(n phi_j)) / 2pi, folded: even n give E, odd n give O,
     // q_j = E + O and q_{n/2 - j} = E - O
-    for (int j = lane; j <= Q; j += 32) {
+    for (int j = t; j <= Q; j += NT) {
       double e = 0.0, o = 0.0;
       for (int nn = 1; nn <= Mq; nn += 2) o = fma(W.phs[nn], cosT[(nn * j) & mask], o);
       for (int nn = 2; nn <= Mq; nn += 2) e = fma(W.phs[nn], cosT[(nn * j) & mask], e);
@@ -221,11 +223,11 @@ __device__ void warp_pair_samples(const GreenParams& gp, double rt, double dr0, 
       W.q[j] = (e + o) / TWO_PI;
       W.q[H - 1 - j] = (e - o) / TWO_PI;
     }
-    __syncwarp();
+    sync();
   }
   const cd g0 = gp.gamma0;
   const double kmin = fmin(cabs(gp.kp0.k), cabs(gp.kp1.k));
-  for (int j = lane; j < H; j += 32) {
+  for (int j = t; j < H; j += NT) {
     double s2 = s2L[j * tstride];
     double u = d2 + 4.0 * rt * rs * s2;
     double su = sqrt(u);
@@ -294,7 +296,14 @@ __device__ void warp_pair_samples(const GreenParams& gp, double rt, double dr0, 
 #pragma unroll
     for (int f = 0; f < NFAM; ++f) W.smp[f * H + j] = wj * F[f];
   }
-  __syncwarp();
+  sync();
+}
+
+__device__ void warp_pair_samples(const GreenParams& gp, double rt, double dr0, double zd,
+                                  long long sid, const double* __restrict__ leg, long long n_split,
+                                  const double* __restrict__ cosT, const WarpSmem& W, int lane,
+                                  const PairGrid& g) {
+  group_pair_samples<32>(gp, rt, dr0, zd, sid, leg, n_split, cosT, W, lane, g, [] { __syncwarp(); });
 }
 
 __device__ void warp_pair_spectra(const GreenParams& gp, double rt, double dr0, double zd,
@@ -657,15 +666,28 @@ __device__ __forceinline__ void support_geometry(const BuildArgs& a, int i, int 
   else { *dr0 = *rt - a.sup.r[pid]; *zd = a.geo.z[i] - a.sup.z[pid]; }
 }
 
-// warp per support pair of the chunk: list[q0 + q], q < count
-__global__ void support_sample_kernel(BuildArgs a, const int* __restrict__ list, int q0, int count,
-                                      __nv_bfloat16* __restrict__ Asl, double* __restrict__ Ascale, int nkt) {
+// CTA of SUP_NT threads per support pair of the chunk: list[q0 + q], q < count.
+// Shared: the samples [NFAM][H], q [H], the Legendre coefficients [Mq + 1].
+#define SUP_NT 128
+
+__host__ __device__ inline int support_sample_smem(int H, int Mq) {
+  return NFAM * H * 16 + H * 8 + (Mq + 1) * 8 + (SUP_NT / 32) * SUP_ROWS * 8 + SUP_ROWS * 8;
+}
+
+__global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, const int* __restrict__ list, int q0,
+                                                                   int count, __nv_bfloat16* __restrict__ Asl,
+                                                                   double* __restrict__ Ascale, int nkt) {
   extern __shared__ __align__(16) char smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const GreenParams& gp = a.gp;
-  WarpSmem W = warp_smem(gp, smem + (size_t)wib * green_smem_bytes(gp));
-  const int H = gp.H;
-  for (int q = blockIdx.x * wpb + wib; q < count; q += gridDim.x * wpb) {
+  const int H = gp.H, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  WarpSmem W;
+  W.smp = (cd*)smem;
+  W.spec = nullptr;
+  W.q = (double*)(W.smp + NFAM * H);
+  W.phs = W.q + H;
+  double* red = W.phs + gp.Mq + 1;         // [SUP_NT / 32][SUP_ROWS]
+  double* inv_s = red + (SUP_NT / 32) * SUP_ROWS;  // [SUP_ROWS]
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {
     const int p = list[q0 + q];
     const int i = p / NEAR_SLOTS, slot = p % NEAR_SLOTS;
     long long pid;
@@ -673,36 +695,40 @@ __global__ void support_sample_kernel(BuildArgs a, const int* __restrict__ list,
     double rt, dr0, zd;
     support_geometry(a, i, slot, pid, &rt, &dr0, &zd);
     const long long sid = a.split_sup[p];
-    warp_pair_samples(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, W, lane, full_grid(gp, a.cosT, a.s2T));
-    __syncwarp();
+    group_pair_samples<SUP_NT>(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, W, t,
+                               full_grid(gp, a.cosT, a.s2T), [] { __syncthreads(); });
+    __syncthreads();
     // row scales: powers of two above twice each row's largest magnitude
     double mx[SUP_ROWS];
 #pragma unroll
     for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0.0;
-    for (int j = lane; j < H; j += 32)
+    for (int j = t; j < H; j += SUP_NT)
 #pragma unroll
       for (int f = 0; f < NFAM; ++f) {
         const cd v = W.smp[f * H + j];
         mx[2 * f] = fmax(mx[2 * f], fabs(v.x));
         mx[2 * f + 1] = fmax(mx[2 * f + 1], fabs(v.y));
       }
-    double inv[SUP_ROWS];
 #pragma unroll
     for (int rr = 0; rr < SUP_ROWS; ++rr) {
       double m = mx[rr];
       for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      const double sc = pow2_scale(m);
-      inv[rr] = 72057594037927936.0 / sc;  // 2^56 / scale
-      if (lane == 0) Ascale[(size_t)q * SUP_ROWS + rr] = sc;
+      if (lane == 0) red[wid * SUP_ROWS + rr] = m;
     }
-    // digits: lane item = (row, group of 8 consecutive k), one 16-byte store per digit
+    __syncthreads();
+    if (t < SUP_ROWS) {
+      double m = 0.0;
+      for (int w = 0; w < SUP_NT / 32; ++w) m = fmax(m, red[w * SUP_ROWS + t]);
+      const double sc = pow2_scale(m);
+      inv_s[t] = 72057594037927936.0 / sc;  // 2^56 / scale
+      Ascale[(size_t)q * SUP_ROWS + t] = sc;
+    }
+    __syncthreads();
+    // digits: thread item = (row, group of 8 consecutive k), one 16-byte store per digit
     const int kg_n = nkt * 2;
-    for (int it = lane; it < SUP_ROWS * kg_n; it += 32) {
+    for (int it = t; it < SUP_ROWS * kg_n; it += SUP_NT) {
       const int rr = it / kg_n, kg = it % kg_n, f = rr >> 1, im = rr & 1;
-      double iv = inv[0];
-#pragma unroll
-      for (int u = 1; u < SUP_ROWS; ++u)
-        if (u == rr) iv = inv[u];
+      const double iv = inv_s[rr];
       int dg[8][OZ_S];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -724,7 +750,7 @@ __global__ void support_sample_kernel(BuildArgs a, const int* __restrict__ list,
         *(uint4*)(blk + d * 2048 + off) = *(uint4*)e8;
       }
     }
-    __syncwarp();
+    __syncthreads();  // the shared samples are rewritten by the next pair
   }
 }
 
@@ -928,10 +954,13 @@ void launch_support_spectra(const BuildArgs& a, cudaStream_t s) {
 
 void launch_support_samples(const BuildArgs& a, const int* list, int q0, int count, __nv_bfloat16* Asl,
                             double* Ascale, int nkt, cudaStream_t s) {
-  int wpb = warps_per_block(a.gp);
-  int smem = wpb * green_smem_bytes(a.gp);
+  const int smem = support_sample_smem(a.gp.H, a.gp.Mq);
   smem_optin(support_sample_kernel);
-  support_sample_kernel<<<grid_for(count, wpb), wpb * 32, smem, s>>>(a, list, q0, count, Asl, Ascale, nkt);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(count, 3 * sms * 8);
+  support_sample_kernel<<<grid, SUP_NT, smem, s>>>(a, list, q0, count, Asl, Ascale, nkt);
 }
 
 void launch_support_post(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy,
