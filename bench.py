@@ -296,8 +296,11 @@ def _kernel_rooflines(st, M, N, fp64_peak, hbm_peak):
       far_kernel      9 FFT-class transforms 9 * 2.5 n log2 n, sampling
                       (n/2 + 1) * 140 flops (both wavenumbers), assembly
                       256 flops per mode, n = n_phi;
-      support_kernel  the same without assembly, plus 6 convolution
-                      transforms 6 * 2.5 n log2 n for split pairs;
+      support_stage   the same without assembly, plus 6 convolution
+                      transforms 6 * 2.5 n log2 n for split pairs (the
+                      stage samples on the FP64 pipe and runs the transform
+                      as digit products on the tensor cores: the count is
+                      the paper's method over the stage's time);
       near_kernel     the rule contraction, 4 flops per (support point,
                       column, family x weight, mode), and 16 x 3 blocks of
                       256 flops per mode for every target;
@@ -312,7 +315,7 @@ def _kernel_rooflines(st, M, N, fp64_peak, hbm_peak):
     out["far_kernel"] = (st["ms_far"], far, "alu")
     n_split = st["n_split_pairs"]
     sup = st["n_support_pairs"] * (9 * fft + samp) + 6 * fft * min(n_split, st["n_support_pairs"])
-    out["support_kernel"] = (st["ms_support"], sup, "alu")
+    out["support_stage"] = (st["ms_support"], sup, "alu")
     near = st["n_support_pairs"] * 16 * 27 * 4 * (M + 2) + N * 48 * (M + 1) * 256
     out["near_kernel"] = (st["ms_near"], near, "alu")
     out["legendre_kernel"] = (st["ms_legendre"], n_split * 10 * (nphi // 2), "alu")
