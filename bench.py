@@ -312,7 +312,10 @@ def _kernel_rooflines(st, M, N, fp64_peak, hbm_peak):
     samp = (nphi // 2 + 1) * 140
     out = {}
     far = st["n_far_pairs"] * (9 * fft + samp + 256 * (M + 1))
-    out["far_kernel"] = (st["ms_far"], far, "alu")
+    # the far pairs: one fused kernel, or (tensor-core transform) sampling,
+    # digit products and assembly kernels, timed apart
+    far_split = st.get("ms_far_assemble", 0) > 0
+    out["far_stage" if far_split else "far_kernel"] = (st["ms_far"], far, "alu")
     n_split = st["n_split_pairs"]
     sup = st["n_support_pairs"] * (9 * fft + samp) + 6 * fft * min(n_split, st["n_support_pairs"])
     out["support_stage"] = (st["ms_support"], sup, "alu")
@@ -326,6 +329,18 @@ def _kernel_rooflines(st, M, N, fp64_peak, hbm_peak):
         ach = work / (ms * 1e-3) / 1e12
         res[k] = {"ms": ms, "bound": bound, "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": ach / fp64_peak, "algorithmic_flops": work}
+    if far_split:
+        # far_assemble_kernel: the matrix entries of every far pair's blocks, modes 0..M, 256 bytes each
+        fb = st["n_far_pairs"] * (M + 1) * 256.0
+        ach = fb / (st["ms_far_assemble"] * 1e-3) / 1e9
+        res["far_assemble_kernel"] = {"ms": st["ms_far_assemble"], "bound": "hbm", "achieved": ach,
+                                      "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                                      "algorithmic_bytes": fb,
+                                      "note": "FP64-bound in practice: the 4 x 4 block of every mode"}
+        res["far_sample_kernel"] = {"ms": st["ms_far_sample"], "bound": "alu",
+                                    "note": "far-pair samples on their ladder grids and their digit rows"}
+        res["oz_real_gemm_kernel (far)"] = {"ms": st["ms_far_product"], "bound": "tensor",
+                                            "note": "the far pairs' transforms as digit products"}
     if st.get("ms_lu_gemm", 0) > 0 and st.get("lu_gemm_bytes", 0) > 0:
         ach = st["lu_gemm_bytes"] / (st["ms_lu_gemm"] * 1e-3) / 1e9
         res["gemm_update_tc_kernel"] = {"ms": st["ms_lu_gemm"], "bound": "hbm", "achieved": ach,
@@ -662,7 +677,8 @@ def run_single(args, cfg):
         launches = st["launches"] + st["solve_launches"] + 1  # + rhs_kernel
         hbm = _measured_peaks().get("hbm_gbs", 6790.3)
         kr = _kernel_rooflines(st, M, cfg.N, fp64_peak, hbm)
-        top = max(kr, key=lambda k: kr[k]["ms"])
+        # the dominant kernel: the longest single kernel with an algorithmic count (stages excluded)
+        top = max((k for k in kr if not k.endswith("_stage") and "frac" in kr[k]), key=lambda k: kr[k]["ms"])
         roof = dict(kr[top], kernel=top)
         roof["peak_source"] = ("measured live: DFMA register loop (mueller_fp64_peak)" if roof["bound"] == "alu"
                                else "MEASURED_PEAKS.json hbm_gbs")

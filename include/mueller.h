@@ -133,6 +133,10 @@ typedef struct {
   double kappa_max;          /* ... the largest over modes 0..M ...                   */
   int kappa_max_mode;        /* ... and its mode (-1 before any estimate)             */
   double ms_cond;            /* device time of that estimate                          */
+  double ms_far_sample;      /* far pairs on the tensor-core path (0 otherwise): device time of the sampling */
+  double ms_far_product;     /* ... of the digit products (the transform) ...                                */
+  double ms_far_assemble;    /* ... and of the block assembly (all within ms_far)                            */
+  double far_blocks;         /* 4 x 4 blocks the far-pair assembly formed (pairs x modes up to m_c + 1)       */
 } mueller_stats;
 
 typedef struct mueller_ctx mueller_ctx;

@@ -56,7 +56,8 @@ class Stats(ct.Structure):
                 ("lu_graph", ct.c_int), ("lu_tile_steps", ct.c_int * 3), ("lu_wave_bodies", ct.c_int),
                 ("lu_launches", ct.c_int), ("lu_gemm_bytes", ct.c_double), ("spilled", ct.c_int),
                 ("host_bytes", ct.c_size_t), ("kappa_mode0", ct.c_double), ("kappa_max", ct.c_double),
-                ("kappa_max_mode", ct.c_int), ("ms_cond", ct.c_double)]
+                ("kappa_max_mode", ct.c_int), ("ms_cond", ct.c_double), ("ms_far_sample", ct.c_double),
+                ("ms_far_product", ct.c_double), ("ms_far_assemble", ct.c_double), ("far_blocks", ct.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -674,19 +674,85 @@ __host__ __device__ inline int support_sample_smem(int H, int Mq) {
   return NFAM * H * 16 + H * 8 + (Mq + 1) * 8 + (SUP_NT / 32) * SUP_ROWS * 8 + SUP_ROWS * 8;
 }
 
-__global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, const int* __restrict__ list, int q0,
-                                                                   int count, __nv_bfloat16* __restrict__ Asl,
-                                                                   double* __restrict__ Ascale, int nkt) {
-  extern __shared__ __align__(16) char smem[];
-  const GreenParams& gp = a.gp;
-  const int H = gp.H, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+// Row scales and digits of one pair's samples W.smp[f][j], j < H, as rows
+// q * 18 + (2 f + Re/Im) of the digit operand (k-tiles of 16, nkt of them):
+// by the SUP_NT threads of the CTA.
+__device__ __forceinline__ void pair_rows_to_digits(const WarpSmem& W, int H, int q, int nkt,
+                                                    __nv_bfloat16* __restrict__ Asl, double* __restrict__ Ascale,
+                                                    double* red, double* inv_s) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  double mx[SUP_ROWS];
+#pragma unroll
+  for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0.0;
+  for (int j = t; j < H; j += SUP_NT)
+#pragma unroll
+    for (int f = 0; f < NFAM; ++f) {
+      const cd v = W.smp[f * H + j];
+      mx[2 * f] = fmax(mx[2 * f], fabs(v.x));
+      mx[2 * f + 1] = fmax(mx[2 * f + 1], fabs(v.y));
+    }
+#pragma unroll
+  for (int rr = 0; rr < SUP_ROWS; ++rr) {
+    double m = mx[rr];
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[wid * SUP_ROWS + rr] = m;
+  }
+  __syncthreads();
+  if (t < SUP_ROWS) {  // row scales: powers of two above twice each row's largest magnitude
+    double m = 0.0;
+    for (int w = 0; w < SUP_NT / 32; ++w) m = fmax(m, red[w * SUP_ROWS + t]);
+    const double sc = pow2_scale(m);
+    inv_s[t] = 72057594037927936.0 / sc;  // 2^56 / scale
+    Ascale[(size_t)q * SUP_ROWS + t] = sc;
+  }
+  __syncthreads();
+  // digits: thread item = (row, group of 8 consecutive k), one 16-byte store per digit
+  const int kg_n = nkt * 2;
+  for (int it = t; it < SUP_ROWS * kg_n; it += SUP_NT) {
+    const int rr = it / kg_n, kg = it % kg_n, f = rr >> 1, im = rr & 1;
+    const double iv = inv_s[rr];
+    int dg[8][OZ_S];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int k = kg * 8 + c;
+      double v = 0.0;
+      if (k < H) { const cd z = W.smp[f * H + k]; v = im ? z.y : z.x; }
+      digits28(__double2ll_rn(v * iv), dg[c]);
+    }
+    const long long row = (long long)q * SUP_ROWS + rr;
+    const long long rt_ = row >> 7;
+    const int r = (int)(row & 127), kt = kg >> 1, kk = (kg & 1) * 8;
+    __nv_bfloat16* blk = Asl + ((size_t)rt_ * nkt + kt) * (OZ_S * 2048);
+    const int off = core_off(r, kk);
+#pragma unroll
+    for (int d = 0; d < OZ_S; ++d) {
+      __align__(16) __nv_bfloat16 e8[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) e8[c] = __float2bfloat16((float)dg[c][d]);
+      *(uint4*)(blk + d * 2048 + off) = *(uint4*)e8;
+    }
+  }
+  __syncthreads();  // the shared samples are rewritten by the next pair
+}
+
+__device__ __forceinline__ WarpSmem sample_smem(char* smem, int H, int Mq, double** red, double** inv_s) {
   WarpSmem W;
   W.smp = (cd*)smem;
   W.spec = nullptr;
   W.q = (double*)(W.smp + NFAM * H);
   W.phs = W.q + H;
-  double* red = W.phs + gp.Mq + 1;         // [SUP_NT / 32][SUP_ROWS]
-  double* inv_s = red + (SUP_NT / 32) * SUP_ROWS;  // [SUP_ROWS]
+  *red = W.phs + Mq + 1;                // [SUP_NT / 32][SUP_ROWS]
+  *inv_s = *red + (SUP_NT / 32) * SUP_ROWS;  // [SUP_ROWS]
+  return W;
+}
+
+__global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, const int* __restrict__ list, int q0,
+                                                                   int count, __nv_bfloat16* __restrict__ Asl,
+                                                                   double* __restrict__ Ascale, int nkt) {
+  extern __shared__ __align__(16) char smem[];
+  const GreenParams& gp = a.gp;
+  double *red, *inv_s;
+  const WarpSmem W = sample_smem(smem, gp.H, gp.Mq, &red, &inv_s);
   for (int q = blockIdx.x; q < count; q += gridDim.x) {
     const int p = list[q0 + q];
     const int i = p / NEAR_SLOTS, slot = p % NEAR_SLOTS;
@@ -695,17 +761,49 @@ __global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, 
     double rt, dr0, zd;
     support_geometry(a, i, slot, pid, &rt, &dr0, &zd);
     const long long sid = a.split_sup[p];
-    group_pair_samples<SUP_NT>(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, W, t,
+    group_pair_samples<SUP_NT>(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, W, threadIdx.x,
                                full_grid(gp, a.cosT, a.s2T), [] { __syncthreads(); });
     __syncthreads();
-    // row scales: powers of two above twice each row's largest magnitude
+    pair_rows_to_digits(W, gp.H, q, nkt, Asl, Ascale, red, inv_s);
+  }
+}
+
+// Far pairs of one grid-size bin (list[q0 + q], q < count, p = i N + j), on
+// their ladder grid of nl points: the same rows as the support pairs, one
+// warp per pair (far pairs have few samples: no CTA barriers).
+__host__ __device__ inline int far_sample_smem_per_warp(int H, int Mq) {
+  return NFAM * H * 16 + H * 8 + (Mq + 1) * 8 + SUP_ROWS * 8;
+}
+
+__global__ void __launch_bounds__(128, 3) far_sample_kernel(BuildArgs a, const int* __restrict__ list, int q0, int count,
+                                                         __nv_bfloat16* __restrict__ Asl,
+                                                         double* __restrict__ Ascale, int nkt, int nl) {
+  extern __shared__ __align__(16) char smem[];
+  const GreenParams& gp = a.gp;
+  const int H = nl / 2 + 1;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  char* base = smem + (size_t)wib * far_sample_smem_per_warp(H, gp.Mq);
+  WarpSmem W;
+  W.smp = (cd*)base;
+  W.spec = nullptr;
+  W.q = (double*)(W.smp + NFAM * H);
+  W.phs = W.q + H;
+  double* inv_s = W.phs + gp.Mq + 1;
+  for (int q = blockIdx.x * wpb + wib; q < count; q += gridDim.x * wpb) {
+    const int p = list[q0 + q];
+    const int i = p / a.N, j = p % a.N;
+    const long long sid = a.split_far[p];
+    const double rt = a.geo.r[i], dr0 = rt - a.geo.r[j], zd0 = a.geo.z[i] - a.geo.z[j];
+    const PairGrid g = pair_grid(gp, rt, dr0, zd0, sid >= 0, a.lneps, a.cosT, a.s2T, a.ladC, a.ladS);
+    warp_pair_samples(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, W, lane, g);
+    __syncwarp();
     double mx[SUP_ROWS];
 #pragma unroll
     for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0.0;
-    for (int j = t; j < H; j += SUP_NT)
+    for (int jj = lane; jj < H; jj += 32)
 #pragma unroll
       for (int f = 0; f < NFAM; ++f) {
-        const cd v = W.smp[f * H + j];
+        const cd v = W.smp[f * H + jj];
         mx[2 * f] = fmax(mx[2 * f], fabs(v.x));
         mx[2 * f + 1] = fmax(mx[2 * f + 1], fabs(v.y));
       }
@@ -713,20 +811,15 @@ __global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, 
     for (int rr = 0; rr < SUP_ROWS; ++rr) {
       double m = mx[rr];
       for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) red[wid * SUP_ROWS + rr] = m;
+      if (lane == rr) {
+        const double sc = pow2_scale(m);
+        inv_s[rr] = 72057594037927936.0 / sc;  // 2^56 / scale
+        Ascale[(size_t)q * SUP_ROWS + rr] = sc;
+      }
     }
-    __syncthreads();
-    if (t < SUP_ROWS) {
-      double m = 0.0;
-      for (int w = 0; w < SUP_NT / 32; ++w) m = fmax(m, red[w * SUP_ROWS + t]);
-      const double sc = pow2_scale(m);
-      inv_s[t] = 72057594037927936.0 / sc;  // 2^56 / scale
-      Ascale[(size_t)q * SUP_ROWS + t] = sc;
-    }
-    __syncthreads();
-    // digits: thread item = (row, group of 8 consecutive k), one 16-byte store per digit
+    __syncwarp();
     const int kg_n = nkt * 2;
-    for (int it = t; it < SUP_ROWS * kg_n; it += SUP_NT) {
+    for (int it = lane; it < SUP_ROWS * kg_n; it += 32) {
       const int rr = it / kg_n, kg = it % kg_n, f = rr >> 1, im = rr & 1;
       const double iv = inv_s[rr];
       int dg[8][OZ_S];
@@ -750,8 +843,126 @@ __global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, 
         *(uint4*)(blk + d * 2048 + off) = *(uint4*)e8;
       }
     }
-    __syncthreads();  // the shared samples are rewritten by the next pair
+    __syncwarp();
   }
+}
+
+// Grid-size bin of every far pair (g.nl / 8; 0xFFFF for near pairs) and the
+// bins' counts.
+__global__ void far_bin_kernel(BuildArgs a, unsigned short* __restrict__ bin_of, int* __restrict__ counts) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)a.N * a.N) return;
+  const int i = (int)(p / a.N), j = (int)(p % a.N);
+  if (near_panels(i / P_NODES, j / P_NODES, a.n_panels, a.closed)) { bin_of[p] = 0xFFFF; return; }
+  const GreenParams& gp = a.gp;
+  const double rt = a.geo.r[i], dr0 = rt - a.geo.r[j], zd0 = a.geo.z[i] - a.geo.z[j];
+  const PairGrid g = pair_grid(gp, rt, dr0, zd0, a.split_far[p] >= 0, a.lneps, a.cosT, a.s2T, a.ladC, a.ladS);
+  const int b = g.nl / 8;
+  bin_of[p] = (unsigned short)b;
+  atomicAdd(&counts[b], 1);
+}
+
+__global__ void far_scatter_kernel(long long total, const unsigned short* __restrict__ bin_of, int* __restrict__ cursor,
+                                   int* __restrict__ list) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  const int b = bin_of[p];
+  if (b != 0xFFFF) list[atomicAdd(&cursor[b], 1)] = (int)p;
+}
+
+// The blocks of far pairs from their spectra Y[m][row] (the products of one
+// bin's chunk), exactly as far_kernel assembles them from its transform:
+// modes above the pair's m_c zero, the split pairs' u^{-3/2} part added.
+__global__ void __launch_bounds__(128, 3) far_assemble_kernel(BuildArgs a, const int* __restrict__ list, int q0, int count,
+                                    const double* __restrict__ Y, int ldy, int ncols, int nl) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const GreenParams& gp = a.gp;
+  const int Ms = gp.Ms;
+  cd* spec = (cd*)smem + (size_t)wib * NFAM * Ms;
+  const int n = 4 * a.N;
+  const int tq = a.tq;
+  const int full = tq ? (gp.M + 1) / 32 * 32 : gp.M + 1;
+  const int tail = gp.M + 1 - full, tw = tail + 2;
+  const long long gw = (long long)blockIdx.x * wpb + wib;
+  cd* Qs = tq ? a.tailq + gw * (long long)tq * tw * NFAM : nullptr;
+  int* Qij = tq ? a.tailij + gw * 2LL * tq : nullptr;
+  int qn = 0;
+  const double invn = 1.0 / nl;
+  const double* Shat = a.leg + (long long)(gp.Mq + 1) * a.n_split;
+  auto pair_consts = [&](int i, int j, double fac[3], double* irt) {
+    const double rs = a.geo.r[j], w = a.geo.w[j] * rs * (a.geo.sw[i] / a.geo.sw[j]);
+    fac[0] = w * a.geo.rp[j];
+    fac[1] = w;
+    fac[2] = w * a.geo.zp[j];
+    *irt = 1.0 / a.geo.r[i];
+  };
+  auto assemble = [&](const cd* S, int stride, int base, int i, int j, int m, const double fac[3], double irt) {
+    cd blk[4][4];
+    mueller_block_spec(S, stride, base, fac, m, a.ap, a.geo.r[i], irt, a.geo.rp[i], a.geo.zp[i], blk);
+    store_block(a.A, n, m, i, j, blk, 1.0);
+  };
+  auto flush = [&]() {
+    __syncwarp();
+    for (int it = lane; it < qn * tail; it += 32) {
+      const int qq = it / tail, m = full + it % tail;
+      double fac[3], irt;
+      pair_consts(Qij[2 * qq], Qij[2 * qq + 1], fac, &irt);
+      assemble(Qs + (long long)qq * tw * NFAM, tw, full - 1, Qij[2 * qq], Qij[2 * qq + 1], m, fac, irt);
+    }
+    __syncwarp();
+    qn = 0;
+  };
+  for (long long q = gw; q < count; q += (long long)gridDim.x * wpb) {
+    const int p = list[q0 + q];
+    const int i = p / a.N, j = p % a.N;
+    const long long sid = a.split_far[p];
+    const double rt = a.geo.r[i], dr0 = rt - a.geo.r[j], zd0 = a.geo.z[i] - a.geo.z[j];
+    const PairGrid g = pair_grid(gp, rt, dr0, zd0, sid >= 0, a.lneps, a.cosT, a.s2T, a.ladC, a.ladS);
+    const int Me = min(g.mc + 1, ncols);
+    const double d2 = dr0 * dr0 + zd0 * zd0, alpha = dr0 - d2 / (2.0 * rt);
+    const long long row0 = q * SUP_ROWS;
+    for (int t = lane; t < NFAM * Ms; t += 32) {
+      const int f = t / Ms, m = t % Ms;
+      cd v = C(0.0);
+      if (m < Me) {
+        const size_t at = (size_t)m * ldy + row0 + 2 * f;
+        v = C(invn * Y[at], invn * Y[at + 1]);
+        if (sid >= 0 && f >= 2) {
+          cd beta;
+          switch (f) {
+            case 2: case 4: beta = C(-alpha); break;
+            case 3: case 5: beta = C(-zd0); break;
+            case 6: beta = (-2.0 * alpha * alpha) * gp.gamma0; break;
+            case 7: beta = (-2.0 * alpha * zd0) * gp.gamma0; break;
+            default: beta = (-2.0 * zd0 * zd0) * gp.gamma0; break;
+          }
+          v = fma(Shat[(long long)m * a.n_split + sid] / 12.566370614359172, beta, v);
+        }
+      }
+      spec[f * Ms + m] = v;
+    }
+    __syncwarp();
+    const int mz = min(gp.M, g.mc + 1);
+    double fac[3], irt;
+    pair_consts(i, j, fac, &irt);
+    for (int m = lane; m < full; m += 32) {
+      if (m <= mz) assemble(spec, Ms, 0, i, j, m, fac, irt);
+      else store_zero_block(a.A, n, m, i, j);
+    }
+    if (tq) {
+      if (mz >= full) {
+        cd* dst = Qs + (long long)qn * tw * NFAM;
+        for (int t = lane; t < NFAM * tw; t += 32) dst[t] = spec[(t / tw) * Ms + full - 1 + t % tw];
+        if (lane == 0) { Qij[2 * qn] = i; Qij[2 * qn + 1] = j; }
+        if (++qn == tq) flush();
+      } else {
+        for (int m = full + lane; m <= gp.M; m += 32) store_zero_block(a.A, n, m, i, j);
+      }
+    }
+    __syncwarp();
+  }
+  if (tq && qn > 0) flush();
 }
 
 // thread per (pair q, family f, mode m): spec = (1/n)(Y_re + i Y_im) + the
@@ -929,10 +1140,20 @@ int far_tail_pairs(const GreenParams& gp) {
   return (full >= 32 && tail > 0 && tail <= 16) ? 32 / tail : 0;
 }
 
+// Warps per CTA of far_assemble_kernel: its shared memory is only the
+// spectra, NFAM (M+2) complex values per warp.
+static int assemble_warps_per_block(const GreenParams& gp) {
+  int w = (72 * 1024) / (NFAM * gp.Ms * 16);  // up to three CTAs per SM (registers)
+  if (w > 4) w = 4;
+  if (w < 1) w = 1;
+  return w;
+}
+
 size_t far_tail_scratch(const BuildArgs& a, size_t* ij_elems) {
   const int tq = far_tail_pairs(a.gp);
-  const int wpb = warps_per_block(a.gp);
-  const long long warps = (long long)grid_for((long long)a.N * a.N, wpb) * wpb;
+  const int wpb = warps_per_block(a.gp), wpa = assemble_warps_per_block(a.gp);
+  const long long total = (long long)a.N * a.N;
+  const long long warps = std::max((long long)grid_for(total, wpb) * wpb, (long long)grid_for(total, wpa) * wpa);
   const int tail = a.gp.M + 1 - (a.gp.M + 1) / 32 * 32;
   *ij_elems = tq ? (size_t)warps * 2 * tq : 0;
   return tq ? (size_t)warps * tq * (tail + 2) * NFAM : 0;
@@ -961,6 +1182,34 @@ void launch_support_samples(const BuildArgs& a, const int* list, int q0, int cou
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::min(count, 3 * sms * 8);
   support_sample_kernel<<<grid, SUP_NT, smem, s>>>(a, list, q0, count, Asl, Ascale, nkt);
+}
+
+void launch_far_bins(const BuildArgs& a, unsigned short* bin_of, int* counts, cudaStream_t s) {
+  const long long total = (long long)a.N * a.N;
+  far_bin_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a, bin_of, counts);
+}
+
+void launch_far_scatter(long long total, const unsigned short* bin_of, int* cursor, int* list, cudaStream_t s) {
+  far_scatter_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, bin_of, cursor, list);
+}
+
+void launch_far_samples(const BuildArgs& a, const int* list, int q0, int count, __nv_bfloat16* Asl, double* Ascale,
+                        int nkt, int nl, cudaStream_t s) {
+  const int per = far_sample_smem_per_warp(nl / 2 + 1, a.gp.Mq);
+  int wpb = (72 * 1024) / per;  // up to three 4-warp CTAs per SM (registers)
+  if (wpb > 4) wpb = 4;
+  if (wpb < 1) wpb = 1;
+  smem_optin(far_sample_kernel);
+  far_sample_kernel<<<grid_for(count, wpb), wpb * 32, wpb * per, s>>>(a, list, q0, count, Asl, Ascale, nkt, nl);
+}
+
+// Launch shape: assemble_warps_per_block (the tail-queue scratch covers it).
+void launch_far_assemble(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy, int ncols,
+                         int nl, cudaStream_t s) {
+  const int wpb = assemble_warps_per_block(a.gp);
+  const int smem = wpb * NFAM * a.gp.Ms * 16;
+  smem_optin(far_assemble_kernel);
+  far_assemble_kernel<<<grid_for(count, wpb), wpb * 32, smem, s>>>(a, list, q0, count, Y, ldy, ncols, nl);
 }
 
 void launch_support_post(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy,

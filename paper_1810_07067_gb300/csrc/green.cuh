@@ -105,6 +105,16 @@ void launch_support_samples(const BuildArgs& a, const int* list, int q0, int cou
                             double* Ascale, int nkt, cudaStream_t s);
 void launch_support_post(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy,
                          cudaStream_t s);
+// far pairs with the transform on the tensor cores: bins by grid size
+// (g.nl / 8), a bin-sorted pair list, then per bin and chunk the samples'
+// digit rows, ozaki_real_gemm with the bin's cos(2 pi m j / nl), and the
+// blocks (the same modes, zeros and tail queue as far_kernel)
+void launch_far_bins(const BuildArgs& a, unsigned short* bin_of, int* counts, cudaStream_t s);
+void launch_far_scatter(long long total, const unsigned short* bin_of, int* cursor, int* list, cudaStream_t s);
+void launch_far_samples(const BuildArgs& a, const int* list, int q0, int count, __nv_bfloat16* Asl, double* Ascale,
+                        int nkt, int nl, cudaStream_t s);
+void launch_far_assemble(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy, int ncols,
+                         int nl, cudaStream_t s);
 void launch_near_assembly(const BuildArgs& a, cudaStream_t s);
 void launch_pair_spectra(const GreenParams& gp, const double* pairs, const int* split_id, const double* leg,
                          long long n_split, long long npairs, const double* cosT, const double* s2T,

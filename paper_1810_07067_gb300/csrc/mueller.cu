@@ -648,6 +648,154 @@ struct Timer {
   double ms(int a, int b) { float v = 0; cudaEventElapsedTime(&v, e[a], e[b]); return v; }
 };
 
+// Far pairs per chunk of one grid-size bin: digit rows of at most about
+// 1.5 GB (18 rows x 16 nkt x 16 bytes per pair), 1024 to 65536 pairs.
+static int far_tc_chunk(int nkt) {
+  const long long per = 18LL * nkt * 256;
+  return (int)std::max<long long>(1024, std::min<long long>(65536, 1500000000LL / per));
+}
+
+static size_t far_tc_scratch_bytes(int N, int nphi, int M) {
+  const int Ms = M + 2;
+  size_t a = 0, y = 0, b = 0, sc = 0;
+  for (int nb = 2; nb <= nphi / 8; ++nb) {
+    const int nl = 8 * nb, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
+    const int rp = (far_tc_chunk(nkt) * 2 * NFAM + 127) / 128 * 128;
+    a = std::max(a, ozaki_real_a_elems(rp, nkt) * 2);
+    y = std::max(y, (size_t)rp * ncols * 8);
+    sc = std::max(sc, (size_t)rp * 8);
+    b += ozaki_real_b_elems(ncols, nkt) * 2;
+  }
+  return a + y + sc + b + (size_t)N * N * 6 + 4096;
+}
+
+// Far pairs with the transform on the tensor cores (when the largest grid's
+// half, n_phi / 2 + 1 samples, fits one exact product), else far_kernel:
+// the pairs are binned by their grid (g.nl / 8) on the device, and per bin
+// and chunk sampled into digit rows, multiplied by the digits of
+// cos(2 pi m j / nl) (modes < min(M + 2, nl / 2 + 1)) and assembled.
+struct FarTiming {
+  std::vector<cudaEvent_t> ev[3];  // sampling, products, assembly: (start, stop) pairs
+  double blocks = 0;
+  void mark(int k, cudaStream_t s) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev[k].push_back(e);
+  }
+  // after the stream has synchronised
+  void finish(mueller_stats* st) {
+    double ms[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      for (size_t q = 0; q + 1 < ev[k].size(); q += 2) {
+        float v = 0.f;
+        cudaEventElapsedTime(&v, ev[k][q], ev[k][q + 1]);
+        ms[k] += v;
+      }
+      for (auto e : ev[k]) cudaEventDestroy(e);
+      ev[k].clear();
+    }
+    if (st) {
+      st->ms_far_sample = ms[0]; st->ms_far_product = ms[1]; st->ms_far_assemble = ms[2];
+      st->far_blocks = blocks;
+    }
+  }
+  ~FarTiming() { finish(nullptr); }
+};
+
+static int far_assembly(const Setup& S, BuildArgs& a, DevBuf& keep_err, int** err_out, FarTiming& ft,
+                        cudaStream_t s) {
+  const int Ms = S.gp.Ms;
+  if (S.gp.H > OZR_KMAX) {
+    launch_far_assembly(a, s);
+    return MUELLER_OK;
+  }
+  DevBuf tmp;  // freed (after a device synchronisation) when this returns
+  const long long total = (long long)S.N * S.N;
+  const int nbins = S.nphi / 8 + 1;
+  unsigned short* bin_of = nullptr;
+  int *counts = nullptr, *cursor = nullptr, *list = nullptr, *err = nullptr;
+  if (tmp.alloc(&bin_of, (size_t)total) != cudaSuccess || tmp.alloc(&counts, (size_t)nbins) != cudaSuccess ||
+      tmp.alloc(&cursor, (size_t)nbins) != cudaSuccess || keep_err.alloc(&err, 1) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "far-pair bins");
+  CK(cudaMemsetAsync(counts, 0, sizeof(int) * nbins, s));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  launch_far_bins(a, bin_of, counts, s);
+  std::vector<int> cnt(nbins), off(nbins + 1, 0);
+  CK(cudaMemcpyAsync(cnt.data(), counts, sizeof(int) * nbins, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int b = 0; b < nbins; ++b) off[b + 1] = off[b] + cnt[b];
+  *err_out = err;
+  if (off[nbins] == 0) return MUELLER_OK;
+  if (tmp.alloc(&list, (size_t)off[nbins]) != cudaSuccess) return fail(MUELLER_ENOMEM, "far-pair list");
+  CK(cudaMemcpyAsync(cursor, off.data(), sizeof(int) * nbins, cudaMemcpyHostToDevice, s));
+  launch_far_scatter(total, bin_of, cursor, list, s);
+  // scratch for the largest chunk, and the B digits of every bin in use
+  size_t amax = 0, ymax = 0, smax = 0, btot = 0;
+  std::vector<size_t> boff(nbins, 0);
+  for (int b = 2; b < nbins; ++b) {
+    if (!cnt[b]) continue;
+    const int nl = 8 * b, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
+    const int cp = std::min(cnt[b], far_tc_chunk(nkt));
+    const int rp = (cp * 2 * NFAM + 127) / 128 * 128;
+    amax = std::max(amax, ozaki_real_a_elems(rp, nkt));
+    ymax = std::max(ymax, (size_t)rp * ncols);
+    smax = std::max(smax, (size_t)rp);
+    boff[b] = btot;
+    btot += ozaki_real_b_elems(ncols, nkt);
+  }
+  if (cnt[0] || cnt[1]) return fail(MUELLER_EINVAL, "far-pair grid below 16 points");
+  __nv_bfloat16 *Asl = nullptr, *Bsl = nullptr;
+  double *Ascale = nullptr, *Y = nullptr;
+  if (tmp.alloc(&Asl, amax) != cudaSuccess || tmp.alloc(&Ascale, smax) != cudaSuccess ||
+      tmp.alloc(&Y, ymax) != cudaSuccess || tmp.alloc(&Bsl, btot) != cudaSuccess)
+    return fail(MUELLER_ENOMEM, "far-pair transform scratch");
+  {
+    std::vector<__nv_bfloat16> hb(btot);
+    const double two_pi = 6.283185307179586;
+    for (int b = 2; b < nbins; ++b) {
+      if (!cnt[b]) continue;
+      const int nl = 8 * b, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
+      std::vector<double> cosv((size_t)H * ncols);
+      for (int j = 0; j < H; ++j)
+        for (int m = 0; m < ncols; ++m) {
+          const long long t = ((long long)m * j) % nl;  // the angle reduced exactly
+          cosv[(size_t)j * ncols + m] = std::cos(two_pi * (double)t / (double)nl);
+        }
+      ozaki_real_b_host(cosv.data(), H, ncols, 2.0, nkt, hb.data() + boff[b]);
+    }
+    CK(cudaMemcpyAsync(Bsl, hb.data(), btot * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // hb is a host temporary
+  }
+  for (int b = 2; b < nbins; ++b) {
+    if (!cnt[b]) continue;
+    const int nl = 8 * b, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
+    const int chunk = far_tc_chunk(nkt);
+    for (int q0 = 0; q0 < cnt[b]; q0 += chunk) {
+      const int c = std::min(chunk, cnt[b] - q0);
+      const int rows = c * 2 * NFAM, rp = (rows + 127) / 128 * 128;
+      if (rp > rows) {  // the last row tile's padding rows: zero digits and scales
+        const int t = rows / 128;
+        CK(cudaMemsetAsync(Asl + (size_t)t * nkt * (OZ_S * OZ_RT * OZ_KT), 0,
+                           (size_t)nkt * OZ_S * OZ_RT * OZ_KT * sizeof(__nv_bfloat16), s));
+        CK(cudaMemsetAsync(Ascale + rows, 0, (size_t)(rp - rows) * sizeof(double), s));
+      }
+      ft.mark(0, s);
+      launch_far_samples(a, list, off[b] + q0, c, Asl, Ascale, nkt, nl, s);
+      ft.mark(0, s);
+      ft.mark(1, s);
+      ozaki_real_gemm(Asl, Ascale, rp, Bsl + boff[b], 2.0, nkt, Y, rp, ncols, err, s);
+      ft.mark(1, s);
+      ft.mark(2, s);
+      launch_far_assemble(a, list, off[b] + q0, c, Y, rp, ncols, nl, s);
+      ft.mark(2, s);
+      // blocks formed: every pair of the bin assembles modes 0..min(M, m_c + 1), m_c < nl / 2
+      ft.blocks += (double)c * std::min(S.M + 1, ncols + 1);
+    }
+  }
+  return MUELLER_OK;
+}
+
 // Support pairs per chunk of the tensor-core support transform (its digit and
 // product scratch: 18 rows x (16 nkt x 16 + 8 Ms) bytes per pair).
 #define SUP_TC_CHUNK 8192
@@ -785,7 +933,12 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   T.mark();
   launch_legendre(dpairs, n_split, Mq, Ms, dleg, s);
   T.mark();
-  launch_far_assembly(a, s);
+  int* far_err = nullptr;
+  FarTiming ft;
+  {
+    const int rc = far_assembly(S, a, tmp, &far_err, ft, s);
+    if (rc != MUELLER_OK) return rc;
+  }
   T.mark();
   int* sup_err = nullptr;
   {
@@ -797,12 +950,14 @@ static int assemble_core(Setup& S, cd* A_dev, cudaStream_t s, mueller_stats* st,
   T.mark();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
-  if (sup_err) {
+  for (int* e : {sup_err, far_err}) {
+    if (!e) continue;
     int herr = 0;
-    CK(cudaMemcpyAsync(&herr, sup_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&herr, e, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (herr) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core support transform timed out");
+    if (herr) return fail(MUELLER_ETIMEOUT, "a device-side wait of the tensor-core kernel transform timed out");
   }
+  if (st) ft.finish(st);
   if (st) {
     st->ms_legendre = T.ms(0, 1); st->ms_far = T.ms(1, 2); st->ms_support = T.ms(2, 3); st->ms_near = T.ms(3, 4);
     st->n_phi_used = S.nphi; st->n_split_pairs = n_split; st->n_far_pairs = S.n_far; st->n_support_pairs = S.n_sup;
@@ -1464,7 +1619,8 @@ extern "C" size_t mueller_build_bytes(int N, int M, int precision, size_t* resid
   const size_t A32 = precision != 0 ? modes * n * n * sizeof(cf) : 0;
   const size_t sl = precision == 1 ? ozaki_matrix_slices_elems((int)npad, (int)modes) * 2 + modes * npad * 8 : 0;
   const size_t small = modes * n * 4 + modes * 16 + (size_t)N * 64;
-  const size_t scratch = (size_t)N * NEAR_SLOTS * NFAM * (size_t)(M + 2) * sizeof(cd) + support_tc_scratch_bytes(N, 512, M);
+  const size_t scratch = (size_t)N * NEAR_SLOTS * NFAM * (size_t)(M + 2) * sizeof(cd) +
+                        std::max(support_tc_scratch_bytes(N, 512, M), far_tc_scratch_bytes(N, 512, M));
   if (resident) *resident = (precision == 1 ? 0 : A) + A32 + sl + small;
   return A + A32 + sl + small + scratch;
 }

@@ -23,6 +23,7 @@
 // them, and four drain warps empty the accumulators of a finished 256-k
 // chunk while the MMAs of the next chunk run (two accumulator sets in tensor
 // memory where they fit).
+#include <algorithm>
 #include <cstdio>
 #include "ozaki.cuh"
 #include "digits.cuh"
@@ -377,34 +378,39 @@ void ozaki_residual(const __nv_bfloat16* Asl, const double* rowscale, int n, int
 // Ascale, a power of two each) and B by the digits of its columns (one scale
 // bscale): Y[c * ldy + r] for the first ncols columns.  Operand blocks per
 // (row tile, k-tile) and (column tile, k-tile) hold the 8 digits of a 128 x 16
-// (48 x 16) tile in the MMA's layout.  K is at most OZR_KMAX, so that every
+// (32 x 16) tile in the MMA's layout.  K is at most OZR_KMAX, so that every
 // level's sum stays an exact FP32 integer (8 digit pairs x 272 x 64^2 < 2^24)
-// and one drain at the end suffices; the levels are joined exactly in 64-bit
+// and one drain per tile suffices; the levels are joined exactly in 64-bit
 // integers (levels 0-3 and 4-7 apart) and converted to FP64 twice per entry.
-// CTA per (column tile, row tile); warps 0-3 drain, 4 copies, 5 issues MMAs.
-#define OZR_NT 48
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... (column tile fastest,
+// so the CTAs of one row tile share its A in L2); warps 0-3 drain, 4 copies
+// through a ring of k-tile stages, 5 issues MMAs into one of two accumulator
+// sets (8 levels x 32 columns each), so a tile's drain overlaps the next
+// tile's products.
+#define OZR_NT 32
 #define OZR_BBLOCK (OZ_S * OZR_NT * OZ_KT)       // bf16 elements per (column tile, k-tile)
 #define OZR_ABLOCK (OZ_S * OZ_ATILE)             // per (row tile, k-tile)
 #define OZR_STAGE ((OZR_ABLOCK + OZR_BBLOCK) * 2)
 #define OZR_NST 4
+#define OZR_SET (OZ_S * OZR_NT)                  // tensor-memory columns of one accumulator set
 
 __global__ void __launch_bounds__(192, 1)
     oz_real_gemm_kernel(const __nv_bfloat16* __restrict__ Asl, const double* __restrict__ Ascale,
-                        const __nv_bfloat16* __restrict__ Bsl, double bscale, int nkt, double* __restrict__ Y,
-                        int ldy, int ncols, int* __restrict__ err) {
+                        const __nv_bfloat16* __restrict__ Bsl, double bscale, int nkt, int ntc, long long ntiles,
+                        double* __restrict__ Y, int ldy, int ncols, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[OZR_NST], empty[OZR_NST], done;
+  __shared__ __align__(8) uint64_t full[OZR_NST], empty[OZR_NST], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   volatile int* fail = &s_fail;
-  const int nt = blockIdx.x, rt = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 32) {
     s_fail = 0;
 #pragma unroll
     for (int b = 0; b < OZR_NST; ++b) { tc::mbar_init(&full[b], 1); tc::mbar_init(&empty[b], 1); }
-    tc::mbar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 4); }
+    tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
   }
   tc::fence_before();
@@ -414,58 +420,74 @@ __global__ void __launch_bounds__(192, 1)
   int issued = 0;
   if (warp == 4) {
     if (lane == 0) {
-      const __nv_bfloat16* Ab = Asl + (size_t)rt * nkt * OZR_ABLOCK;
-      const __nv_bfloat16* Bb = Bsl + (size_t)nt * nkt * OZR_BBLOCK;
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int st = kt % OZR_NST;
-        if (kt >= OZR_NST && !tc::mbar_wait(&empty[st], ((kt / OZR_NST) - 1) & 1)) { *fail = 1; break; }
-        if (*fail) break;
-        unsigned char* base = smem + (size_t)st * OZR_STAGE;
-        tc::mbar_expect_tx(&full[st], OZR_STAGE);
-        tc::bulk_g2s(base, Ab + (size_t)kt * OZR_ABLOCK, OZR_ABLOCK * 2, &full[st]);
-        tc::bulk_g2s(base + OZR_ABLOCK * 2, Bb + (size_t)kt * OZR_BBLOCK, OZR_BBLOCK * 2, &full[st]);
-        issued = kt + 1;
+      int q = 0;
+      for (long long t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x) {
+        const int nt = (int)(t % ntc);
+        const long long rt = t / ntc;
+        const __nv_bfloat16* Ab = Asl + (size_t)rt * nkt * OZR_ABLOCK;
+        const __nv_bfloat16* Bb = Bsl + (size_t)nt * nkt * OZR_BBLOCK;
+        for (int kt = 0; kt < nkt; ++kt, ++q) {
+          const int st = q % OZR_NST;
+          if (q >= OZR_NST && !tc::mbar_wait(&empty[st], ((q / OZR_NST) - 1) & 1)) { *fail = 1; break; }
+          unsigned char* base = smem + (size_t)st * OZR_STAGE;
+          tc::mbar_expect_tx(&full[st], OZR_STAGE);
+          tc::bulk_g2s(base, Ab + (size_t)kt * OZR_ABLOCK, OZR_ABLOCK * 2, &full[st]);
+          tc::bulk_g2s(base + OZR_ABLOCK * 2, Bb + (size_t)kt * OZR_BBLOCK, OZR_BBLOCK * 2, &full[st]);
+          issued = q + 1;
+        }
       }
     }
   } else if (warp == 5) {
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(OZ_RT, OZR_NT, false);
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int st = kt % OZR_NST;
-        if (!tc::mbar_wait(&full[st], (kt / OZR_NST) & 1)) { *fail = 1; break; }
+      int q = 0, k = 0;
+      for (long long t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x, ++k) {
+        const int set = k & 1;
+        if (k >= 2 && !tc::mbar_wait(&tempty[set], ((k >> 1) - 1) & 1)) { *fail = 1; break; }
         tc::fence_after();
-        unsigned char* base = smem + (size_t)st * OZR_STAGE;
-        const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(base), 128, 256);
-        const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(base + OZR_ABLOCK * 2), 128, 256);
+        const uint32_t acc0 = tmem + (uint32_t)(set * OZR_SET);
+        for (int kt = 0; kt < nkt; ++kt, ++q) {
+          const int st = q % OZR_NST;
+          if (!tc::mbar_wait(&full[st], (q / OZR_NST) & 1)) { *fail = 1; break; }
+          tc::fence_after();
+          unsigned char* base = smem + (size_t)st * OZR_STAGE;
+          const uint64_t a0 = tc::desc_noswizzle(tc::smem_u32(base), 128, 256);
+          const uint64_t b0 = tc::desc_noswizzle(tc::smem_u32(base + OZR_ABLOCK * 2), 128, 256);
 #pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
+          for (int s = 0; s < OZ_S; ++s) {
 #pragma unroll
-          for (int t = 0; t < OZ_S - s; ++t) {
-            const uint32_t acc = tmem + (uint32_t)((s + t) * OZR_NT);
-            const uint64_t ad = a0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
-            const uint64_t bd = b0 + (uint64_t)(t * (OZR_NT * OZ_KT * 2 / 16));
-            tc::mma_bf16(acc, ad, bd, idesc, (kt == 0 && s == 0) ? 0u : 1u);  // (0, t) opens level t
+            for (int u = 0; u < OZ_S - s; ++u) {
+              const uint32_t acc = acc0 + (uint32_t)((s + u) * OZR_NT);
+              const uint64_t ad = a0 + (uint64_t)(s * (OZ_ATILE * 2 / 16));
+              const uint64_t bd = b0 + (uint64_t)(u * (OZR_NT * OZ_KT * 2 / 16));
+              tc::mma_bf16(acc, ad, bd, idesc, (kt == 0 && s == 0) ? 0u : 1u);  // (0, u) opens level u
+            }
           }
+          tc::commit(&empty[st]);
         }
-        tc::commit(&empty[st]);
+        if (*fail) break;
+        tc::commit(&tfull[set]);
       }
-      tc::commit(&done);  // arrives once every MMA issued above has completed
-      if (!tc::mbar_wait(&done, 0)) *fail = 1;
+      tc::commit(&mdone);  // arrives once every MMA issued above has completed
+      if (!tc::mbar_wait(&mdone, 0)) *fail = 1;
     }
-  }
-  if (warp < 4) {
+  } else {
     // drain: this warp's 32 rows, 16 columns at a time, levels joined in integers
-    if (!tc::mbar_wait(&done, 0)) *fail = 1;
-    tc::fence_after();
-    const int r = rt * OZ_RT + warp * 32 + lane;
-    const double sc = Ascale[r] * bscale;
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int c0 = 0; c0 < OZR_NT; c0 += 16) {
-      long long hi[16], lo[16];
+    int k = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int set = k & 1;
+      if (!tc::mbar_wait(&tfull[set], (k >> 1) & 1)) { *fail = 1; break; }
+      tc::fence_after();
+      const int nt = (int)(t % ntc);
+      const long long rt = t / ntc;
+      const long long r = rt * OZ_RT + warp * 32 + lane;
+      const double sc = Ascale[r] * bscale;
+      const uint32_t tw = tmem + (uint32_t)(set * OZR_SET) + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) { hi[c] = 0; lo[c] = 0; }
-      if (!*fail) {
+      for (int c0 = 0; c0 < OZR_NT; c0 += 16) {
+        long long hi[16], lo[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) { hi[c] = 0; lo[c] = 0; }
 #pragma unroll
         for (int l = 0; l < OZ_S; ++l) {
           float v[16];
@@ -477,15 +499,18 @@ __global__ void __launch_bounds__(192, 1)
             else lo[c] = lo[c] * 128 + iv;
           }
         }
-      }
-      // hi = sum_{l<4} acc_l 2^{7(3-l)}, lo = sum_{l>=4} acc_l 2^{7(7-l)};
-      // level l carries 2^{-7(l+2)}: value = hi 2^-35 + lo 2^-63
+        // hi = sum_{l<4} acc_l 2^{7(3-l)}, lo = sum_{l>=4} acc_l 2^{7(7-l)};
+        // level l carries 2^{-7(l+2)}: value = hi 2^-35 + lo 2^-63
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int col = nt * OZR_NT + c0 + c;
-        if (col < ncols)
-          Y[(size_t)col * ldy + r] = sc * fma((double)hi[c], 2.9103830456733704e-11, (double)lo[c] * 1.0842021724855044e-19);
+        for (int c = 0; c < 16; ++c) {
+          const int col = nt * OZR_NT + c0 + c;
+          if (col < ncols)
+            Y[(size_t)col * ldy + r] = sc * fma((double)hi[c], 2.9103830456733704e-11, (double)lo[c] * 1.0842021724855044e-19);
+        }
       }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[set]);
     }
   }
   __syncthreads();
@@ -511,8 +536,13 @@ void ozaki_real_gemm(const __nv_bfloat16* Asl, const double* Ascale, int rows_pa
                      double bscale, int nkt, double* Y, int ldy, int ncols, int* err, cudaStream_t s) {
   const int smem = OZR_NST * OZR_STAGE;
   cudaFuncSetAttribute(oz_real_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  const dim3 grid((ncols + OZR_NT - 1) / OZR_NT, rows_pad / OZ_RT);
-  oz_real_gemm_kernel<<<grid, 192, smem, s>>>(Asl, Ascale, Bsl, bscale, nkt, Y, ldy, ncols, err);
+  const int ntc = (ncols + OZR_NT - 1) / OZR_NT;
+  const long long ntiles = (long long)ntc * (rows_pad / OZ_RT);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<long long>(ntiles, sms);
+  oz_real_gemm_kernel<<<grid, 192, smem, s>>>(Asl, Ascale, Bsl, bscale, nkt, ntc, ntiles, Y, ldy, ncols, err);
 }
 
 // Digits of the columns of B[k][c] = b(k, c) / bscale for the real product
