@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "mueller.h"
@@ -619,6 +620,51 @@ static void ensure_tables() {
   done[dev] = 1;
 }
 
+// Digits of the cosine matrix b(j, m) = cos(2 pi m j / nl), j = 0..nl/2,
+// m < ncols (divided by 2), in the operand layout of the real product: the
+// transform over phi of the sampled rows (far-pair bins and support pairs).
+// They depend on (nl, ncols) alone, so they are built on the host once per
+// device and key and kept until exit (about 21 MB for every grid of the
+// ladder up to 512 points at M = 128); the entry is published only after its
+// upload has completed, so builds on other streams may use it at once.
+static int cos_digits(int nl, int ncols, cudaStream_t s, const __nv_bfloat16** out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, __nv_bfloat16*> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(dev, nl, ncols);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return MUELLER_OK;
+  }
+  const int H = nl / 2 + 1, nkt = (H + 15) / 16;
+  std::vector<double> cosv((size_t)H * ncols);
+  const double two_pi = 6.283185307179586;
+  for (int j = 0; j < H; ++j)
+    for (int m = 0; m < ncols; ++m) {
+      const long long t = ((long long)m * j) % nl;  // the angle reduced exactly
+      cosv[(size_t)j * ncols + m] = std::cos(two_pi * (double)t / (double)nl);
+    }
+  std::vector<__nv_bfloat16> hb(ozaki_real_b_elems(ncols, nkt));
+  ozaki_real_b_host(cosv.data(), H, ncols, 2.0, nkt, hb.data());
+  __nv_bfloat16* d = nullptr;
+  if (cudaMalloc(&d, hb.size() * sizeof(__nv_bfloat16)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MUELLER_ENOMEM, "cosine digit table");
+  }
+  cudaError_t e = cudaMemcpyAsync(d, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // hb is a host temporary
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return fail(MUELLER_ECUDA, std::string("cosine digit table: ") + cudaGetErrorString(e));
+  }
+  cache.emplace(key, d);
+  *out = d;
+  return MUELLER_OK;
+}
+
 // Host-side fault injection for tests (nothing faults on the device): when
 // the environment variable MUELLER_FAULT_INJECT names a status word
 // ("lu_timeout", "residual_timeout"), the host writes 1 into that device word
@@ -730,9 +776,9 @@ static int far_assembly(const Setup& S, BuildArgs& a, DevBuf& keep_err, int** er
   if (tmp.alloc(&list, (size_t)off[nbins]) != cudaSuccess) return fail(MUELLER_ENOMEM, "far-pair list");
   CK(cudaMemcpyAsync(cursor, off.data(), sizeof(int) * nbins, cudaMemcpyHostToDevice, s));
   launch_far_scatter(total, bin_of, cursor, list, s);
-  // scratch for the largest chunk, and the B digits of every bin in use
-  size_t amax = 0, ymax = 0, smax = 0, btot = 0;
-  std::vector<size_t> boff(nbins, 0);
+  // scratch for the largest chunk; the B digits of every bin in use
+  size_t amax = 0, ymax = 0, smax = 0;
+  std::vector<const __nv_bfloat16*> Bsl(nbins, nullptr);
   for (int b = 2; b < nbins; ++b) {
     if (!cnt[b]) continue;
     const int nl = 8 * b, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
@@ -741,32 +787,15 @@ static int far_assembly(const Setup& S, BuildArgs& a, DevBuf& keep_err, int** er
     amax = std::max(amax, ozaki_real_a_elems(rp, nkt));
     ymax = std::max(ymax, (size_t)rp * ncols);
     smax = std::max(smax, (size_t)rp);
-    boff[b] = btot;
-    btot += ozaki_real_b_elems(ncols, nkt);
+    const int rc = cos_digits(nl, ncols, s, &Bsl[b]);
+    if (rc != MUELLER_OK) return rc;
   }
   if (cnt[0] || cnt[1]) return fail(MUELLER_EINVAL, "far-pair grid below 16 points");
-  __nv_bfloat16 *Asl = nullptr, *Bsl = nullptr;
+  __nv_bfloat16* Asl = nullptr;
   double *Ascale = nullptr, *Y = nullptr;
   if (tmp.alloc(&Asl, amax) != cudaSuccess || tmp.alloc(&Ascale, smax) != cudaSuccess ||
-      tmp.alloc(&Y, ymax) != cudaSuccess || tmp.alloc(&Bsl, btot) != cudaSuccess)
+      tmp.alloc(&Y, ymax) != cudaSuccess)
     return fail(MUELLER_ENOMEM, "far-pair transform scratch");
-  {
-    std::vector<__nv_bfloat16> hb(btot);
-    const double two_pi = 6.283185307179586;
-    for (int b = 2; b < nbins; ++b) {
-      if (!cnt[b]) continue;
-      const int nl = 8 * b, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
-      std::vector<double> cosv((size_t)H * ncols);
-      for (int j = 0; j < H; ++j)
-        for (int m = 0; m < ncols; ++m) {
-          const long long t = ((long long)m * j) % nl;  // the angle reduced exactly
-          cosv[(size_t)j * ncols + m] = std::cos(two_pi * (double)t / (double)nl);
-        }
-      ozaki_real_b_host(cosv.data(), H, ncols, 2.0, nkt, hb.data() + boff[b]);
-    }
-    CK(cudaMemcpyAsync(Bsl, hb.data(), btot * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));  // hb is a host temporary
-  }
   for (int b = 2; b < nbins; ++b) {
     if (!cnt[b]) continue;
     const int nl = 8 * b, H = nl / 2 + 1, nkt = (H + 15) / 16, ncols = std::min(Ms, nl / 2 + 1);
@@ -784,7 +813,7 @@ static int far_assembly(const Setup& S, BuildArgs& a, DevBuf& keep_err, int** er
       launch_far_samples(a, list, off[b] + q0, c, Asl, Ascale, nkt, nl, s);
       ft.mark(0, s);
       ft.mark(1, s);
-      ozaki_real_gemm(Asl, Ascale, rp, Bsl + boff[b], 2.0, nkt, Y, rp, ncols, err, s);
+      ozaki_real_gemm(Asl, Ascale, rp, Bsl[b], 2.0, nkt, Y, rp, ncols, err, s);
       ft.mark(1, s);
       ft.mark(2, s);
       launch_far_assemble(a, list, off[b] + q0, c, Y, rp, ncols, nl, s);
@@ -833,26 +862,18 @@ static int support_spectra(const Setup& S, BuildArgs& a, DevBuf& tmp, int** err_
   const int nkt = (H + 15) / 16;
   const int rows_pad = (SUP_TC_CHUNK * 2 * NFAM + 127) / 128 * 128;
   int* dlist = nullptr;
-  __nv_bfloat16 *Asl = nullptr, *Bsl = nullptr;
+  __nv_bfloat16* Asl = nullptr;
   double *Ascale = nullptr, *Y = nullptr;
   int* err = nullptr;
   if (tmp.upload(&dlist, list, s) != cudaSuccess || tmp.alloc(&Asl, ozaki_real_a_elems(rows_pad, nkt)) != cudaSuccess ||
       tmp.alloc(&Ascale, (size_t)rows_pad) != cudaSuccess || tmp.alloc(&Y, (size_t)Ms * rows_pad) != cudaSuccess ||
-      tmp.alloc(&Bsl, ozaki_real_b_elems(Ms, nkt)) != cudaSuccess || tmp.alloc(&err, 1) != cudaSuccess)
+      tmp.alloc(&err, 1) != cudaSuccess)
     return fail(MUELLER_ENOMEM, "support transform scratch");
   // B: cos(2 pi m j / n_phi), j = 0..n_phi/2 (the samples' weights are in the rows), digits of b / 2
+  const __nv_bfloat16* Bsl = nullptr;
   {
-    std::vector<double> b((size_t)H * Ms);
-    const double two_pi = 6.283185307179586;
-    for (int j = 0; j < H; ++j)
-      for (int m = 0; m < Ms; ++m) {
-        const long long t = ((long long)m * j) % S.nphi;  // the angle reduced exactly
-        b[(size_t)j * Ms + m] = std::cos(two_pi * (double)t / (double)S.nphi);
-      }
-    std::vector<__nv_bfloat16> hb(ozaki_real_b_elems(Ms, nkt));
-    ozaki_real_b_host(b.data(), H, Ms, 2.0, nkt, hb.data());
-    CK(cudaMemcpyAsync(Bsl, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));  // hb is a host temporary
+    const int rc = cos_digits(S.nphi, Ms, s, &Bsl);
+    if (rc != MUELLER_OK) return rc;
   }
   CK(cudaMemsetAsync(err, 0, sizeof(int), s));
   const int total = (int)list.size();
