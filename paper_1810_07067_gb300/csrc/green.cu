@@ -418,8 +418,13 @@ __device__ __forceinline__ V2 operator-(V2 x) { return v2(-x.a, -x.b); }
 __device__ __forceinline__ cd iy(double y, cd a) { return cd{-y * a.y, y * a.x}; }
 __device__ __forceinline__ V2 iy(double y, V2 x) { return v2(iy(y, x.a), iy(y, x.b)); }
 
-// The block from the gathered coefficients c1, c2, c3 of the nine families.
-__device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
+// The block from the gathered coefficients c1, c2 (of J^1 and J^2) and c3
+// (of J^1 alone) of the nine families.  SIMPLE: k0^2 and k1^2 real, the
+// coupling coefficients cEM and cHJ purely imaginary and the K factors
+// aEJ = 1, aHM = -1 (real wavenumbers and eps0 = mu0 = 1, as AsmParams::simple
+// records): the same block without the products by zero parts.
+template <bool SIMPLE = false>
+__device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const cd* c3, int m,
                                                    const AsmParams& ap, double rt, double irt, double rpt,
                                                    double zpt, cd out[4][4]);
 
@@ -427,7 +432,8 @@ template <class Get>
 __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double rt, double rpt, double zpt,
                               cd out[4][4]) {
   int a0 = m, ap1 = m + 1, am1 = (m >= 1) ? m - 1 : 1;
-  V2 c1[NFAM], c2[NFAM], c3[NFAM];
+  V2 c1[NFAM], c2[NFAM];
+  cd c3[NFAM];
 #pragma unroll
   for (int f = 0; f < NFAM; ++f) {
     cd A0p = R(0, f, ap1), A0m = R(0, f, am1);
@@ -436,7 +442,7 @@ __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double r
     cd G2b = 0.5 * (A1p + A1m), G3b = 0.5 * (A1m - A1p);
     c1[f] = v2(G2a, -mul_i(G3b));
     c2[f] = v2(mul_i(G3a), G2b);
-    c3[f] = v2(R(2, f, a0), C(0.0));
+    c3[f] = R(2, f, a0);
   }
   mueller_block_core(c1, c2, c3, m, ap, rt, 1.0 / rt, rpt, zpt, out);
 }
@@ -446,24 +452,36 @@ __device__ void mueller_block(const Get& R, int m, const AsmParams& ap, double r
 // the sums and differences of modes m +- 1 once instead of every term.  The
 // block is linear in the spectra, so a common factor of the block (the L2
 // row/column weight ratio) can ride in fac; irt = 1 / rt.
+template <bool SIMPLE = false>
 __device__ __forceinline__ void mueller_block_spec(const cd* S, int stride, int base, const double fac[3], int m,
                                                    const AsmParams& ap, double rt, double irt, double rpt,
                                                    double zpt, cd out[4][4]) {
   const int ap1 = m + 1 - base, am1 = ((m >= 1) ? m - 1 : 1) - base, a0 = m - base;
   const double h0 = 0.5 * fac[0], h1 = 0.5 * fac[1];
-  V2 c1[NFAM], c2[NFAM], c3[NFAM];
+  V2 c1[NFAM], c2[NFAM];
+  cd c3[NFAM];
 #pragma unroll
   for (int f = 0; f < NFAM; ++f) {
     const cd sp = S[f * stride + ap1], sm = S[f * stride + am1];
     const cd sum = sp + sm, dif = sm - sp;
     c1[f] = v2(h0 * sum, -mul_i(h1 * dif));
     c2[f] = v2(mul_i(h0 * dif), h1 * sum);
-    c3[f] = v2(fac[2] * S[f * stride + a0], C(0.0));
+    c3[f] = fac[2] * S[f * stride + a0];
   }
-  mueller_block_core(c1, c2, c3, m, ap, rt, irt, rpt, zpt, out);
+  mueller_block_core<SIMPLE>(c1, c2, c3, m, ap, rt, irt, rpt, zpt, out);
 }
 
-__device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const V2* c3, int m,
+// k x for k = k0^2 or k1^2: a real scalar when SIMPLE
+template <bool SIMPLE>
+__device__ __forceinline__ V2 ksq_mul(cd k, V2 x) { return SIMPLE ? k.x * x : k * x; }
+template <bool SIMPLE>
+__device__ __forceinline__ cd ksq_mul(cd k, cd x) { return SIMPLE ? k.x * x : k * x; }
+// c x for a coupling coefficient c: i Im(c) when SIMPLE
+template <bool SIMPLE>
+__device__ __forceinline__ V2 coup_mul(cd c, V2 x) { return SIMPLE ? iy(c.y, x) : c * x; }
+
+template <bool SIMPLE>
+__device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, const cd* c3, int m,
                                                    const AsmParams& ap, double rt, double irt, double rpt,
                                                    double zpt, cd out[4][4]) {
   const double irt2 = irt * irt;
@@ -472,26 +490,40 @@ __device__ __forceinline__ void mueller_block_core(const V2* c1, const V2* c2, c
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
     int g = kk, dr = 2 + 2 * kk, dz = 3 + 2 * kk;
-    Nt[kk] = c1[dz] - c3[dr];
+    Nt[kk] = v2(c1[dz].a - c3[dr], c1[dz].b);
     V2 t1 = c2[g] + rt * c2[dr] - iy((double)m, c1[g]);
-    V2 t2 = iy(mr, c3[g]) - c2[dz];
+    V2 t2 = v2(iy(mr, c3[g]) - c2[dz].a, -c2[dz].b);
     Nth[kk] = -((zpt * irt) * t1 + rpt * t2);
   }
   V2 c1D = c1[0] - c1[1], c2D = c2[0] - c2[1];
   V2 c1rD = c1[2] - c1[4], c2rD = c2[2] - c2[4];
-  V2 c1zD = c1[3] - c1[5], c2zD = c2[3] - c2[5], c3zD = c3[3] - c3[5];
-  V2 Kt = ap.k0sq * c2[0] - ap.k1sq * c2[1] + iy(mr2, c1D) + iy(mr, c1rD) - (double(m) * m * irt2) * c2D +
-          iy(mr, c3zD);
-  V2 dPr = (-irt2) * c1D + irt * c1rD + c1[6] - iy(mr2, c2D) + iy(mr, c2rD) + c3[7];
-  V2 dPz = irt * c1zD + c1[7] + iy(mr, c2zD) + c3[8];
-  V2 Kth = -(rpt * (ap.k0sq * c1[0] - ap.k1sq * c1[1] + dPr) +
-             zpt * (ap.k0sq * c3[0] - ap.k1sq * c3[1] + dPz));
-  V2 EM_t = ap.cEM0 * Nt[0] + ap.cEM1 * Nt[1], EM_th = ap.cEM0 * Nth[0] + ap.cEM1 * Nth[1];
-  V2 HJ_t = ap.cHJ0 * Nt[0] + ap.cHJ1 * Nt[1], HJ_th = ap.cHJ0 * Nth[0] + ap.cHJ1 * Nth[1];
-  out[0][0] = ap.aEJ * Kt.a;  out[0][1] = ap.aEJ * Kt.b;  out[0][2] = EM_t.a;  out[0][3] = EM_t.b;
-  out[1][0] = ap.aEJ * Kth.a; out[1][1] = ap.aEJ * Kth.b; out[1][2] = EM_th.a; out[1][3] = EM_th.b;
-  out[2][0] = HJ_t.a;  out[2][1] = HJ_t.b;  out[2][2] = ap.aHM * Kt.a;  out[2][3] = ap.aHM * Kt.b;
-  out[3][0] = HJ_th.a; out[3][1] = HJ_th.b; out[3][2] = ap.aHM * Kth.a; out[3][3] = ap.aHM * Kth.b;
+  V2 c1zD = c1[3] - c1[5], c2zD = c2[3] - c2[5];
+  const cd c3zD = c3[3] - c3[5];
+  V2 Kt = ksq_mul<SIMPLE>(ap.k0sq, c2[0]) - ksq_mul<SIMPLE>(ap.k1sq, c2[1]) + iy(mr2, c1D) + iy(mr, c1rD) -
+          (double(m) * m * irt2) * c2D;
+  Kt.a = Kt.a + iy(mr, c3zD);
+  V2 dPr = (-irt2) * c1D + irt * c1rD + c1[6] - iy(mr2, c2D) + iy(mr, c2rD);
+  dPr.a = dPr.a + c3[7];
+  V2 dPz = irt * c1zD + c1[7] + iy(mr, c2zD);
+  dPz.a = dPz.a + c3[8];
+  const V2 Kr = ksq_mul<SIMPLE>(ap.k0sq, c1[0]) - ksq_mul<SIMPLE>(ap.k1sq, c1[1]) + dPr;
+  const V2 Kz = v2(ksq_mul<SIMPLE>(ap.k0sq, c3[0]) - ksq_mul<SIMPLE>(ap.k1sq, c3[1]) + dPz.a, dPz.b);
+  V2 Kth = -(rpt * Kr + zpt * Kz);
+  V2 EM_t = coup_mul<SIMPLE>(ap.cEM0, Nt[0]) + coup_mul<SIMPLE>(ap.cEM1, Nt[1]);
+  V2 EM_th = coup_mul<SIMPLE>(ap.cEM0, Nth[0]) + coup_mul<SIMPLE>(ap.cEM1, Nth[1]);
+  V2 HJ_t = coup_mul<SIMPLE>(ap.cHJ0, Nt[0]) + coup_mul<SIMPLE>(ap.cHJ1, Nt[1]);
+  V2 HJ_th = coup_mul<SIMPLE>(ap.cHJ0, Nth[0]) + coup_mul<SIMPLE>(ap.cHJ1, Nth[1]);
+  if (SIMPLE) {  // aEJ = 1, aHM = -1
+    out[0][0] = Kt.a;   out[0][1] = Kt.b;   out[0][2] = EM_t.a;  out[0][3] = EM_t.b;
+    out[1][0] = Kth.a;  out[1][1] = Kth.b;  out[1][2] = EM_th.a; out[1][3] = EM_th.b;
+    out[2][0] = HJ_t.a;  out[2][1] = HJ_t.b;  out[2][2] = -Kt.a;  out[2][3] = -Kt.b;
+    out[3][0] = HJ_th.a; out[3][1] = HJ_th.b; out[3][2] = -Kth.a; out[3][3] = -Kth.b;
+  } else {
+    out[0][0] = ap.aEJ * Kt.a;  out[0][1] = ap.aEJ * Kt.b;  out[0][2] = EM_t.a;  out[0][3] = EM_t.b;
+    out[1][0] = ap.aEJ * Kth.a; out[1][1] = ap.aEJ * Kth.b; out[1][2] = EM_th.a; out[1][3] = EM_th.b;
+    out[2][0] = HJ_t.a;  out[2][1] = HJ_t.b;  out[2][2] = ap.aHM * Kt.a;  out[2][3] = ap.aHM * Kt.b;
+    out[3][0] = HJ_th.a; out[3][1] = HJ_th.b; out[3][2] = ap.aHM * Kth.a; out[3][3] = ap.aHM * Kth.b;
+  }
 }
 
 __device__ __forceinline__ void store_block(cd* __restrict__ A, int n, int m, int i, int j, cd blk[4][4],
@@ -679,45 +711,50 @@ __host__ __device__ inline int support_sample_smem(int H, int Mq) {
 // by the SUP_NT threads of the CTA.
 __device__ __forceinline__ void pair_rows_to_digits(const WarpSmem& W, int H, int q, int nkt,
                                                     __nv_bfloat16* __restrict__ Asl, double* __restrict__ Ascale,
-                                                    double* red, double* inv_s) {
+                                                    double* red, double* shift) {
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  double mx[SUP_ROWS];
+  // row maxima of |v| on the bits of the samples (integer pipe)
+  unsigned long long mx[SUP_ROWS];
 #pragma unroll
-  for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0.0;
+  for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0ull;
   for (int j = t; j < H; j += SUP_NT)
 #pragma unroll
     for (int f = 0; f < NFAM; ++f) {
       const cd v = W.smp[f * H + j];
-      mx[2 * f] = fmax(mx[2 * f], fabs(v.x));
-      mx[2 * f + 1] = fmax(mx[2 * f + 1], fabs(v.y));
+      const unsigned long long bx = abs_bits(v.x), by = abs_bits(v.y);
+      mx[2 * f] = bx > mx[2 * f] ? bx : mx[2 * f];
+      mx[2 * f + 1] = by > mx[2 * f + 1] ? by : mx[2 * f + 1];
     }
 #pragma unroll
   for (int rr = 0; rr < SUP_ROWS; ++rr) {
-    double m = mx[rr];
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) red[wid * SUP_ROWS + rr] = m;
+    unsigned long long m = mx[rr];
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y > m ? y : m;
+    }
+    if (lane == 0) red[wid * SUP_ROWS + rr] = __longlong_as_double((long long)m);
   }
   __syncthreads();
-  if (t < SUP_ROWS) {  // row scales: powers of two above twice each row's largest magnitude
+  if (t < SUP_ROWS) {  // row scales: powers of two 2^E above twice each row's largest magnitude
     double m = 0.0;
     for (int w = 0; w < SUP_NT / 32; ++w) m = fmax(m, red[w * SUP_ROWS + t]);
-    const double sc = pow2_scale(m);
-    inv_s[t] = 72057594037927936.0 / sc;  // 2^56 / scale
-    Ascale[(size_t)q * SUP_ROWS + t] = sc;
+    const int E = pow2_scale_exp(m);
+    shift[t] = (double)(56 - E);  // digits of round(v 2^(56 - E))
+    Ascale[(size_t)q * SUP_ROWS + t] = ldexp(1.0, E);
   }
   __syncthreads();
   // digits: thread item = (row, group of 8 consecutive k), one 16-byte store per digit
   const int kg_n = nkt * 2;
   for (int it = t; it < SUP_ROWS * kg_n; it += SUP_NT) {
     const int rr = it / kg_n, kg = it % kg_n, f = rr >> 1, im = rr & 1;
-    const double iv = inv_s[rr];
+    const int S = (int)shift[rr];
     int dg[8][OZ_S];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int k = kg * 8 + c;
       double v = 0.0;
       if (k < H) { const cd z = W.smp[f * H + k]; v = im ? z.y : z.x; }
-      digits28(__double2ll_rn(v * iv), dg[c]);
+      digits28(fixed_rn(v, S), dg[c]);
     }
     const long long row = (long long)q * SUP_ROWS + rr;
     const long long rt_ = row >> 7;
@@ -735,14 +772,14 @@ __device__ __forceinline__ void pair_rows_to_digits(const WarpSmem& W, int H, in
   __syncthreads();  // the shared samples are rewritten by the next pair
 }
 
-__device__ __forceinline__ WarpSmem sample_smem(char* smem, int H, int Mq, double** red, double** inv_s) {
+__device__ __forceinline__ WarpSmem sample_smem(char* smem, int H, int Mq, double** red, double** shift) {
   WarpSmem W;
   W.smp = (cd*)smem;
   W.spec = nullptr;
   W.q = (double*)(W.smp + NFAM * H);
   W.phs = W.q + H;
   *red = W.phs + Mq + 1;                // [SUP_NT / 32][SUP_ROWS]
-  *inv_s = *red + (SUP_NT / 32) * SUP_ROWS;  // [SUP_ROWS]
+  *shift = *red + (SUP_NT / 32) * SUP_ROWS;  // [SUP_ROWS]
   return W;
 }
 
@@ -751,8 +788,8 @@ __global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, 
                                                                    double* __restrict__ Ascale, int nkt) {
   extern __shared__ __align__(16) char smem[];
   const GreenParams& gp = a.gp;
-  double *red, *inv_s;
-  const WarpSmem W = sample_smem(smem, gp.H, gp.Mq, &red, &inv_s);
+  double *red, *shift;
+  const WarpSmem W = sample_smem(smem, gp.H, gp.Mq, &red, &shift);
   for (int q = blockIdx.x; q < count; q += gridDim.x) {
     const int p = list[q0 + q];
     const int i = p / NEAR_SLOTS, slot = p % NEAR_SLOTS;
@@ -764,7 +801,7 @@ __global__ void __launch_bounds__(SUP_NT, 3) support_sample_kernel(BuildArgs a, 
     group_pair_samples<SUP_NT>(gp, rt, dr0, zd, sid, a.leg, a.n_split, a.cosT, W, threadIdx.x,
                                full_grid(gp, a.cosT, a.s2T), [] { __syncthreads(); });
     __syncthreads();
-    pair_rows_to_digits(W, gp.H, q, nkt, Asl, Ascale, red, inv_s);
+    pair_rows_to_digits(W, gp.H, q, nkt, Asl, Ascale, red, shift);
   }
 }
 
@@ -788,7 +825,7 @@ __global__ void __launch_bounds__(128, 3) far_sample_kernel(BuildArgs a, const i
   W.spec = nullptr;
   W.q = (double*)(W.smp + NFAM * H);
   W.phs = W.q + H;
-  double* inv_s = W.phs + gp.Mq + 1;
+  double* shift = W.phs + gp.Mq + 1;
   for (int q = blockIdx.x * wpb + wib; q < count; q += gridDim.x * wpb) {
     const int p = list[q0 + q];
     const int i = p / a.N, j = p % a.N;
@@ -797,38 +834,43 @@ __global__ void __launch_bounds__(128, 3) far_sample_kernel(BuildArgs a, const i
     const PairGrid g = pair_grid(gp, rt, dr0, zd0, sid >= 0, a.lneps, a.cosT, a.s2T, a.ladC, a.ladS);
     warp_pair_samples(gp, rt, dr0, zd0, sid, a.leg, a.n_split, a.cosT, W, lane, g);
     __syncwarp();
-    double mx[SUP_ROWS];
+    // row maxima of |v| on the bits of the samples (integer pipe)
+    unsigned long long mx[SUP_ROWS];
 #pragma unroll
-    for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0.0;
+    for (int rr = 0; rr < SUP_ROWS; ++rr) mx[rr] = 0ull;
     for (int jj = lane; jj < H; jj += 32)
 #pragma unroll
       for (int f = 0; f < NFAM; ++f) {
         const cd v = W.smp[f * H + jj];
-        mx[2 * f] = fmax(mx[2 * f], fabs(v.x));
-        mx[2 * f + 1] = fmax(mx[2 * f + 1], fabs(v.y));
+        const unsigned long long bx = abs_bits(v.x), by = abs_bits(v.y);
+        mx[2 * f] = bx > mx[2 * f] ? bx : mx[2 * f];
+        mx[2 * f + 1] = by > mx[2 * f + 1] ? by : mx[2 * f + 1];
       }
 #pragma unroll
     for (int rr = 0; rr < SUP_ROWS; ++rr) {
-      double m = mx[rr];
-      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == rr) {
-        const double sc = pow2_scale(m);
-        inv_s[rr] = 72057594037927936.0 / sc;  // 2^56 / scale
-        Ascale[(size_t)q * SUP_ROWS + rr] = sc;
+      unsigned long long m = mx[rr];
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+      }
+      if (lane == rr) {  // row scale 2^E above twice the row's largest magnitude
+        const int E = pow2_scale_exp(__longlong_as_double((long long)m));
+        shift[rr] = (double)(56 - E);  // digits of round(v 2^(56 - E))
+        Ascale[(size_t)q * SUP_ROWS + rr] = ldexp(1.0, E);
       }
     }
     __syncwarp();
     const int kg_n = nkt * 2;
     for (int it = lane; it < SUP_ROWS * kg_n; it += 32) {
       const int rr = it / kg_n, kg = it % kg_n, f = rr >> 1, im = rr & 1;
-      const double iv = inv_s[rr];
+      const int S = (int)shift[rr];
       int dg[8][OZ_S];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int k = kg * 8 + c;
         double v = 0.0;
         if (k < H) { const cd z = W.smp[f * H + k]; v = im ? z.y : z.x; }
-        digits28(__double2ll_rn(v * iv), dg[c]);
+        digits28(fixed_rn(v, S), dg[c]);
       }
       const long long row = (long long)q * SUP_ROWS + rr;
       const long long rt_ = row >> 7;
@@ -873,6 +915,7 @@ __global__ void far_scatter_kernel(long long total, const unsigned short* __rest
 // The blocks of far pairs from their spectra Y[m][row] (the products of one
 // bin's chunk), exactly as far_kernel assembles them from its transform:
 // modes above the pair's m_c zero, the split pairs' u^{-3/2} part added.
+template <bool SIMPLE>
 __global__ void __launch_bounds__(128, 3) far_assemble_kernel(BuildArgs a, const int* __restrict__ list, int q0, int count,
                                     const double* __restrict__ Y, int ldy, int ncols, int nl) {
   extern __shared__ __align__(16) char smem[];
@@ -899,7 +942,7 @@ __global__ void __launch_bounds__(128, 3) far_assemble_kernel(BuildArgs a, const
   };
   auto assemble = [&](const cd* S, int stride, int base, int i, int j, int m, const double fac[3], double irt) {
     cd blk[4][4];
-    mueller_block_spec(S, stride, base, fac, m, a.ap, a.geo.r[i], irt, a.geo.rp[i], a.geo.zp[i], blk);
+    mueller_block_spec<SIMPLE>(S, stride, base, fac, m, a.ap, a.geo.r[i], irt, a.geo.rp[i], a.geo.zp[i], blk);
     store_block(a.A, n, m, i, j, blk, 1.0);
   };
   auto flush = [&]() {
@@ -922,12 +965,14 @@ __global__ void __launch_bounds__(128, 3) far_assemble_kernel(BuildArgs a, const
     const int Me = min(g.mc + 1, ncols);
     const double d2 = dr0 * dr0 + zd0 * zd0, alpha = dr0 - d2 / (2.0 * rt);
     const long long row0 = q * SUP_ROWS;
+    // lanes take consecutive families of one mode: a mode's 18 values of the
+    // pair are contiguous in Y (16-byte loads of one 144-byte run)
     for (int t = lane; t < NFAM * Ms; t += 32) {
-      const int f = t / Ms, m = t % Ms;
+      const int m = t / NFAM, f = t - m * NFAM;
       cd v = C(0.0);
       if (m < Me) {
-        const size_t at = (size_t)m * ldy + row0 + 2 * f;
-        v = C(invn * Y[at], invn * Y[at + 1]);
+        const double2 y = *(const double2*)(Y + (size_t)m * ldy + row0 + 2 * f);  // even offset: 16-byte aligned
+        v = C(invn * y.x, invn * y.y);
         if (sid >= 0 && f >= 2) {
           cd beta;
           switch (f) {
@@ -1208,8 +1253,13 @@ void launch_far_assemble(const BuildArgs& a, const int* list, int q0, int count,
                          int nl, cudaStream_t s) {
   const int wpb = assemble_warps_per_block(a.gp);
   const int smem = wpb * NFAM * a.gp.Ms * 16;
-  smem_optin(far_assemble_kernel);
-  far_assemble_kernel<<<grid_for(count, wpb), wpb * 32, smem, s>>>(a, list, q0, count, Y, ldy, ncols, nl);
+  if (a.ap.simple) {
+    smem_optin(far_assemble_kernel<true>);
+    far_assemble_kernel<true><<<grid_for(count, wpb), wpb * 32, smem, s>>>(a, list, q0, count, Y, ldy, ncols, nl);
+  } else {
+    smem_optin(far_assemble_kernel<false>);
+    far_assemble_kernel<false><<<grid_for(count, wpb), wpb * 32, smem, s>>>(a, list, q0, count, Y, ldy, ncols, nl);
+  }
 }
 
 void launch_support_post(const BuildArgs& a, const int* list, int q0, int count, const double* Y, int ldy,

@@ -26,6 +26,7 @@ struct AsmParams {
   cd cEM0, cEM1;        // E rows, M columns: cEM0 N0 + cEM1 N1
   cd cHJ0, cHJ1;        // H rows, J columns
   cd dEM, dHJ;          // identity terms
+  int simple;           // 1: k0^2, k1^2 real, cEM and cHJ purely imaginary, aEJ = 1, aHM = -1
 };
 
 struct NodeGeom {

@@ -272,6 +272,9 @@ static int setup_inputs(const mueller_curve* cv, const mueller_media* md, int M,
     ap.dEM = -0.5 * (iw * (S.mu0 + S.mu1)); ap.dHJ = -0.5 * (iw * (S.eps0 + S.eps1));
     S.sE = iw * S.mu0; S.sH = iw * S.eps0;
   }
+  // the far-pair assembly drops the products by zero parts when these hold exactly
+  ap.simple = ap.k0sq.y == 0.0 && ap.k1sq.y == 0.0 && ap.cEM0.x == 0.0 && ap.cEM1.x == 0.0 && ap.cHJ0.x == 0.0 &&
+              ap.cHJ1.x == 0.0 && ap.aEJ.x == 1.0 && ap.aEJ.y == 0.0 && ap.aHM.x == -1.0 && ap.aHM.y == 0.0;
   return MUELLER_OK;
 }
 
