@@ -75,7 +75,7 @@ __host__ __device__ __forceinline__ long long fixed_rn(double v, int S) {
 // d = ((F + 64) mod 128) - 64, F <- (F - d) / 128; the low half's carry joins
 // the high half, and the top digit ends in [-64, 64].  v = sum_s d_s 2^{-7(s+1)}
 // up to the rounding of F.
-__device__ __forceinline__ void digits28(long long F, int* d) {
+__host__ __device__ __forceinline__ void digits28(long long F, int* d) {
   int lo = (int)(F & 0xFFFFFFFll), hi = (int)(F >> 28);
 #pragma unroll
   for (int s = OZ_S - 1; s >= OZ_S / 2; --s) {

@@ -3,7 +3,9 @@
 // to even -- the C library's llrint of the exact product ldexp(v, S) in the
 // default rounding mode -- for every |v 2^S| < 2^55, including exact ties,
 // subnormal samples and rows whose scale is subnormal; abs_bits must order
-// finite values as fabs does.  Exit status 0 when every case agrees.
+// finite values as fabs does; digits28 must split each fixed-point value
+// into 8 balanced base-128 digits that sum back to it.  Exit status 0 when
+// every case agrees.
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -51,6 +53,28 @@ int main() {
     const double a = ldexp(U(gen), (int)(gen() % 400) - 200), b = ldexp(U(gen), (int)(gen() % 400) - 200);
     if ((fabs(a) < fabs(b)) != (abs_bits(a) < abs_bits(b))) ++order_bad;
   }
-  printf("%lld rounding cases, %lld mismatches; %lld ordering mismatches\n", n, bad, order_bad);
-  return (bad || order_bad) ? 1 : 0;
+  // digits28: balanced base-128 digits of F = round(v 2^56), |v| < 1/2, that
+  // sum back to F exactly, each exact in BF16 (|d| <= 64, the top one too)
+  long long digit_bad = 0;
+  auto check_digits = [&](long long F) {
+    int d[OZ_S];
+    digits28(F, d);
+    long long back = 0;
+    bool in_range = true;
+    for (int s = 0; s < OZ_S; ++s) {
+      back = back * 128 + d[s];
+      in_range = in_range && d[s] >= -64 && d[s] <= 64;
+    }
+    if (back != F || !in_range) {
+      if (digit_bad < 5) printf("digits28(%lld) does not sum back or leaves [-64, 64]\n", F);
+      ++digit_bad;
+    }
+  };
+  for (int it = 0; it < 2000000; ++it) check_digits(fixed_rn(U(gen) * 0.5, 56));
+  const long long edge = (1ll << 55) - 1;
+  for (long long F : {0ll, 1ll, -1ll, 63ll, 64ll, 65ll, -64ll, -65ll, edge, -edge, edge - 64, -(edge - 64)})
+    check_digits(F);
+  printf("%lld rounding cases, %lld mismatches; %lld ordering mismatches; %lld digit mismatches\n", n, bad,
+         order_bad, digit_bad);
+  return (bad || order_bad || digit_bad) ? 1 : 0;
 }
