@@ -148,9 +148,14 @@ typedef struct mueller_ctx mueller_ctx;
  * D_r = diag(-1, 1, 1, -1) and D_c = diag(1, -1, -1, 1) per node, and
  * mueller_solve uses the factors of A_m for both.  Rows and unknowns are
  * L2-weighted internally (Section 6 remark); the API stays in physical
- * unknowns.  Host inputs are copied; the context owns all device memory.
- * Work runs on `stream`; the call returns after the factorization has
- * finished (stage times are measured with CUDA events). */
+ * unknowns.  Host inputs are copied; the context owns all device memory of
+ * the body.  Besides it the library keeps, per device and until exit, the
+ * BF16 digits of the cosine matrices of the transform over phi, one per grid
+ * size and mode count in use (about 21 MB for every grid up to n_phi = 512 at
+ * M = 128), built on the host by the first build that needs them (which then
+ * waits once for their upload on `stream`).  Work runs on `stream`; the call
+ * returns after the factorization has finished (stage times are measured
+ * with CUDA events). */
 int mueller_build(const mueller_curve* curve, const mueller_media* media, int M,
                   const mueller_options* opts, void* stream, mueller_ctx** out);
 
