@@ -41,8 +41,8 @@ void upload_series_tables(const SeriesTables& t) { cudaMemcpyToSymbol(c_tab, &t,
 // rinv[k] = 1 / (2k + 1) for k < nr (shared memory): the recurrences divide by
 // odd integers at every step, and FP64 division costs several dependent
 // operations, so the quotients are multiplications by the table's entries.
-__device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms,
-                             double* __restrict__ leg, const double* rinv, int nr) {
+__host__ __device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms,
+                                      double* __restrict__ leg, const double* rinv, int nr) {
   auto inv_odd = [&](int k) { return k < nr ? rinv[k] : 1.0 / (2.0 * k + 1.0); };  // 1 / (2k + 1)
   double rs = rt - dr;
   double d2 = dr * dr + dz * dz, B = 2.0 * rt * rs;

@@ -88,8 +88,8 @@ HD int green_smem_bytes(const GreenParams& gp) {
 
 // Laplace-type coefficients of one split pair p (target r_t, displacement dr, dz)
 // into leg (stride n, rows 0..Mq P^_m, rows Mq+1.. S^_m).
-__device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms, double* leg,
-                             const double* rinv, int nr);
+__host__ __device__ void legendre_one(double rt, double dr, double dz, long long p, long long n, int Mq, int Ms,
+                                      double* leg, const double* rinv, int nr);
 
 // host-side launchers (green.cu)
 void launch_legendre(const double* pairs, long long n_split, int Mq, int Ms, double* leg, cudaStream_t s);
