@@ -7,7 +7,12 @@
 //   F6, F7, F8 = d2/dr_t2, d2/dr_t dz_t, d2/dz_t2 of (g^{k0} - g^{k1})_m
 //                                                       (Section 4.3, differences)
 // are computed for m = 0..M+1 from nphi azimuthal samples of the integrand
-// and a cosine transform (the integrands are even in phi).
+// and a cosine transform (the integrands are even in phi).  Where the half
+// grid fits one exact digit product (nphi/2 + 1 <= 272 samples) the transform
+// runs on the tensor cores: support pairs in chunks (support_sample_kernel,
+// oz_real_gemm_kernel, support_post_kernel), far pairs binned by their own
+// grid (far_sample_kernel, oz_real_gemm_kernel, far_assemble_kernel);
+// otherwise each pair's warp sums it directly (far_kernel, support_kernel).
 //
 // Kernel splitting (Section 4): with u = rho^2 and G = exp(ik sqrt u)/(4pi sqrt u),
 // every family is written as  a(phi) u^{-1/2} + beta u^{-3/2} + c(phi)  with
